@@ -1,0 +1,205 @@
+/*
+ * rbm.h - C ABI of the GB300 (sm_103a) Random Batch Method library.
+ *
+ * The library advances an interacting particle system (Jin, Li & Liu,
+ * arXiv:1812.10575, Sec. 1, eq. "interactingps")
+ *
+ *     dX^i = -grad V(X^i) dt + 1/(N-1) sum_{j != i} K(X^i - X^j) dt + sigma dB^i
+ *
+ * by RBM-1 (Sec. 2.1, Algorithm "randomdiv": each step a fresh random division
+ * of the N particles into batches of size p, the interaction replaced by
+ * 1/(p-1) times the in-batch sum, one Euler-Maruyama step) or by the direct
+ * O(N^2) forward-Euler step the paper compares it with (Sec. 4.1).  All work
+ * runs in the library's own CUDA kernels on the caller's stream.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Positions: row-major N x ld array of the run's dtype in device memory, with
+ *   ld = d for d = 1, 2 and ld = 4 for d = 3 (the fourth lane is padding; the
+ *   library preserves its bits).  The base address must be 16-byte aligned.
+ *   The caller owns it and keeps it alive until rbm_free.
+ * Stream: every call enqueues work on the stream given to rbm_init (a
+ *   cudaStream_t passed as void*, NULL = the legacy default stream) and
+ *   returns without waiting, except rbm_sync, rbm_step_host and the calls
+ *   documented as synchronous.
+ * Randomness: counter-based Philox4x32-10 keyed by the 64-bit seed.  Counter
+ *   (id, m mod 2^32, replica, stream*256 + call): stream 0 gives the
+ *   permutation key of particle id at step m, (w1 << 32) | w0; stream 1,
+ *   call t, gives Box-Muller pair t of particle id's Brownian increment.  The
+ *   increment depends on (id, m) only, so RBM and direct steps from the same
+ *   state share it (the synchronous coupling of Sec. 3, eq. "coupling").
+ *   Uniforms take the top 53 bits (FP64 runs) or 24 bits (FP32 runs) of each
+ *   64-bit word w: u = ((w >> (64-b)) + 1) * 2^-b, in (0, 1].
+ * Random division: particle ids sorted ascending by (key, id); batch q is
+ *   sorted positions [q p, min(q p + p, N)).  The last batch has N mod p
+ *   members when p does not divide N; a singleton batch feels no interaction.
+ * K(0) := 0 for every kernel (coincident particles exert no force).
+ * Errors: parameter errors return synchronously (RBM_ERR_INVALID, nothing is
+ *   enqueued).  Device-side conditions (a non-finite position, a bounded wait
+ *   that ran out) are latched in a device status word and returned by
+ *   rbm_sync (and by the next rbm_step_host).  After any error other than
+ *   RBM_ERR_INVALID the context accepts only rbm_get_step, rbm_sync and
+ *   rbm_free.
+ * Threads: a context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef RBM_H
+#define RBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rbm_ctx rbm_ctx; /* opaque; owned by the library */
+
+typedef enum {
+    RBM_OK = 0,
+    RBM_ERR_INVALID = -1,     /* bad parameter or pointer; nothing enqueued   */
+    RBM_ERR_CUDA = -2,        /* a CUDA runtime call failed                   */
+    RBM_ERR_NOMEM = -3,       /* device or pinned allocation failed           */
+    RBM_ERR_TIMEOUT = -4,     /* a bounded device-side wait ran out           */
+    RBM_ERR_NONFINITE = -5,   /* a step produced a NaN or infinite position   */
+    RBM_ERR_STATE = -6,       /* context unusable after an earlier error      */
+    RBM_ERR_UNSUPPORTED = -7  /* valid request this build does not implement  */
+} rbm_status;
+
+typedef enum { RBM_F32 = 0, RBM_F64 = 1 } rbm_dtype;
+
+/* Confining potential V (Sec. 1). */
+typedef enum {
+    RBM_V_ZERO = 0,      /* V = 0                                 */
+    RBM_V_QUADRATIC = 1  /* V = v_coef |x|^2 / 2, -grad V = -v_coef x */
+} rbm_potential;
+
+/* Interaction kernel K, x = X^i - X^j (the paper's examples, Secs. 4-5). */
+typedef enum {
+    RBM_K_INV1D = 0,        /* 1/x, d = 1 only (Dyson Brownian motion, Sec. 4.2) */
+    RBM_K_COULOMB = 1,      /* x/|x|^3 (Thomson problem, Sec. 5.1)              */
+    RBM_K_BOUNDED_CONF = 2, /* -x if |x| < k_param else 0 (opinions, Sec. 5.2)  */
+    RBM_K_GAUSS_AGG = 3,    /* -x exp(-|x|^2/2)                                  */
+    RBM_K_REG_ATTRACT = 4,  /* -x / (|x|^2 + k_param)                            */
+    RBM_K_SMOOTH_TEST = 5,  /* x / (1 + |x|^2) (test example, Sec. 4.1)          */
+    RBM_K_LINEAR = 6        /* -k_param x                                        */
+} rbm_kernel;
+
+typedef enum {
+    RBM_METHOD_RBM = 0,    /* RBM-1 step (Algorithm "randomdiv")            */
+    RBM_METHOD_DIRECT = 1  /* direct O(N^2) forward-Euler step (Sec. 4.1)   */
+} rbm_method;
+
+/* Time scheme of the RBM step. */
+typedef enum {
+    RBM_SCHEME_EULER = 0, /* explicit Euler-Maruyama of eq. "firstalgorithm" */
+    RBM_SCHEME_SPLIT = 1  /* splitting, Sec. 2.3 item 5: the p = 2 pair flow of
+                             K solved exactly (K = 1/x: |delta|^2 += 4 dt;
+                             K = x/|x|^3: |delta|^3 += 6 dt, Secs. 4.2, 5.1),
+                             then Euler-Maruyama for -grad V and the noise.
+                             Requires p = 2 and K = INV1D or COULOMB.      */
+} rbm_scheme;
+
+#define RBM_FLAG_RENORM_SPHERE 1u /* X^i <- X^i/|X^i| after each step (Sec. 5.1) */
+
+typedef struct {
+    int64_t n;        /* particles N >= 2                                    */
+    int32_t d;        /* dimension 1..3                                      */
+    int32_t p;        /* batch size, 2 <= p <= min(N, 4096)                  */
+    double dt;        /* time step tau > 0                                   */
+    double sigma;     /* noise amplitude >= 0                                */
+    uint64_t seed;    /* Philox key                                          */
+    int32_t dtype;    /* rbm_dtype                                           */
+    int32_t v;        /* rbm_potential                                       */
+    double v_coef;    /* V coefficient                                       */
+    int32_t k;        /* rbm_kernel                                          */
+    double k_param;   /* kernel parameter (radius, epsilon or coefficient)   */
+    uint32_t flags;   /* RBM_FLAG_*                                          */
+    int32_t scheme;   /* rbm_scheme                                          */
+    uint32_t replica; /* replica index r used in the Philox counter          */
+} rbm_params;
+
+/* Optional launch and scratch tuning (zero = library default). */
+typedef struct {
+    int32_t bucket_bits;  /* log2 of the number of permutation buckets       */
+    int32_t slot_cap;     /* slots per bucket before spilling to the overflow list */
+    int32_t sort_cap;     /* largest bucket sorted in shared memory (power of 2) */
+    int32_t block;        /* threads per block of the fused step kernel      */
+    int32_t direct_block; /* threads per block of the direct kernel          */
+    int32_t graph_steps;  /* steps captured per CUDA graph by rbm_run        */
+} rbm_tuning;
+
+/* Create a context for one particle system whose positions live at x_dev
+ * (layout above).  Allocates all scratch on the device (permutation buckets,
+ * the permutation, a second position buffer, the status word).  *out is set
+ * on success.  Synchronous with respect to the host (allocations). */
+rbm_status rbm_init(const rbm_params *prm, void *x_dev, void *cuda_stream, rbm_ctx **out);
+
+/* One RBM-1 step m -> m+1 (Algorithm "randomdiv", eq. "firstalgorithm"),
+ * in place: keys, random division, in-batch forces, -grad V, noise, update. */
+rbm_status rbm_step(rbm_ctx *ctx);
+
+/* One direct forward-Euler step m -> m+1 (the O(N^2) reference method of
+ * Sec. 4.1, eq. "interactingps"), same noise as rbm_step at step m. */
+rbm_status rbm_direct_step(rbm_ctx *ctx);
+
+/* `steps` steps of `method`, launched as CUDA graphs of graph_steps steps
+ * (captured on first use, replayed afterwards) plus eager remainder steps. */
+rbm_status rbm_run(rbm_ctx *ctx, int64_t steps, int32_t method);
+
+/* End to end from host memory: copy N x ld positions from x_host (pinned for
+ * speed, pageable accepted) to the context's device positions, take one step
+ * of `method`, copy them back to x_host and wait.  Returns latched errors. */
+rbm_status rbm_step_host(rbm_ctx *ctx, void *x_host, int32_t method);
+
+rbm_status rbm_get_step(const rbm_ctx *ctx, int64_t *m);
+rbm_status rbm_set_step(rbm_ctx *ctx, int64_t m);
+
+/* Set launch/scratch tuning; reallocates scratch.  Synchronous. */
+rbm_status rbm_set_tuning(rbm_ctx *ctx, const rbm_tuning *tuning);
+rbm_status rbm_get_tuning(const rbm_ctx *ctx, rbm_tuning *tuning);
+
+/* Wait for the stream and return the latched device status. */
+rbm_status rbm_sync(rbm_ctx *ctx);
+
+/* Release the context and its scratch (waits for the stream first). */
+rbm_status rbm_free(rbm_ctx *ctx);
+
+/* Human-readable name of a status code (static storage). */
+const char *rbm_status_string(int32_t status);
+
+/* Text of the last CUDA runtime failure seen by the calling thread (the call
+ * and the runtime's message), or "" if none.  Thread-local, static storage. */
+const char *rbm_last_error(void);
+
+/* ---- diagnostics (same conventions; used by the tests) ------------------ */
+
+/* The random division of the current step m as the sorted id list: writes N
+ * uint32 ids to perm_dev (device, caller-owned).  Does not advance m. */
+rbm_status rbm_permutation(rbm_ctx *ctx, uint32_t *perm_dev);
+
+/* Interaction force only, F^K_i (no -grad V, no noise, no update) of the
+ * current step m into f_dev (N x ld, run dtype): the in-batch sum scaled by
+ * 1/(|C|-1) for RBM_METHOD_RBM, the full sum scaled by 1/(N-1) for
+ * RBM_METHOD_DIRECT.  Does not advance m. */
+rbm_status rbm_forces(rbm_ctx *ctx, int32_t method, void *f_dev);
+
+/* Mean-field force at nq query points q_dev (nq x ld, run dtype):
+ * F(q) = 1/(N-1) sum_j K(q - X^j) over all particles, into f_dev. */
+rbm_status rbm_direct_forces_at(rbm_ctx *ctx, const void *q_dev, int64_t nq, void *f_dev);
+
+/* One step of `method` (m -> m+1) with a CUDA event recorded on the
+ * context's stream before and after each kernel it launches; waits for the
+ * step and writes each kernel's duration in milliseconds to kernel_ms (up to
+ * `capacity` entries), their number to *nkernels and, when `names` is given,
+ * their ';'-separated names (NUL-terminated, truncated to names_len).
+ * Synchronous.  Used by the benchmark to time kernels on their own stream. */
+rbm_status rbm_step_profiled(rbm_ctx *ctx, int32_t method, float *kernel_ms, int32_t capacity, int32_t *nkernels,
+                             char *names, int32_t names_len);
+
+/* Number of kernel launches one step of `method` enqueues (for accounting). */
+rbm_status rbm_launches_per_step(const rbm_ctx *ctx, int32_t method, int32_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBM_H */

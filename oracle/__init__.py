@@ -103,11 +103,13 @@ def lib() -> ctypes.CDLL:
             L.orc_split_pair_solve.argtypes = [P, dp, dp, dp, dp]
             L.orc_direct_step.argtypes = [P, dp, ctypes.c_int64]
             L.orc_direct_forces_at.argtypes = [P, dp, dp, ctypes.c_int64, dp]
+            L.orc_direct_step_sampled.argtypes = [P, dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                                  ctypes.c_int64, dp]
             L.orc_num_threads.restype = ctypes.c_int
             for f in (L.orc_philox4x32_10, L.orc_perm_keys, L.orc_permutation, L.orc_normals,
                       L.orc_kernel_pair, L.orc_direct_interaction, L.orc_rbm_interaction,
                       L.orc_euler_update, L.orc_rbm_step, L.orc_rbm_split_step, L.orc_split_pair_solve, L.orc_direct_step,
-                      L.orc_direct_forces_at):
+                      L.orc_direct_forces_at, L.orc_direct_step_sampled):
                 f.restype = None
             _lib = L
     return _lib
@@ -243,6 +245,17 @@ def run(prm: OrcParams, X, m0: int, steps: int, method: str = "rbm") -> np.ndarr
     Y = _x(X, prm).copy()
     for s in range(steps):
         Y = step(prm, Y, m0 + s)
+    return Y
+
+
+def direct_step_sampled(prm: OrcParams, X, m: int, idx) -> np.ndarray:
+    """New positions of particles ``idx`` after one direct step from ``X``."""
+    X = _x(X, prm)
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+    Y = np.zeros((len(idx), prm.d))
+    lib().orc_direct_step_sampled(ctypes.byref(prm), _ptr(X, ctypes.c_double), int(m),
+                                  idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(idx),
+                                  _ptr(Y, ctypes.c_double))
     return Y
 
 

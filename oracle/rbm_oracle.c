@@ -279,23 +279,30 @@ void orc_rbm_interaction(const orc_params *prm, const double *X, const uint32_t 
 /*   X'^i = X^i + dt (FK_i - grad V(X^i)) + sigma sqrt(dt) z_i               */
 /*   RENORM: X'^i <- X'^i / |X'^i|                                           */
 /* ------------------------------------------------------------------------ */
-void orc_euler_update(const orc_params *prm, double *X, const double *FK, int64_t m)
+static void orc_euler_update_one(const orc_params *prm, uint32_t id, const double *x, const double *fk, int64_t m,
+                                 double *y)
 {
     int d = prm->d;
     double sq = prm->sigma * sqrt(prm->dt);
+    double z[4] = {0.0, 0.0, 0.0, 0.0}, fv[3];
+    orc_normals_one(prm, id, m, z);
+    orc_confining(prm, x, fv);
+    for (int k = 0; k < d; ++k) y[k] = x[k] + prm->dt * (fk[k] + fv[k]) + sq * z[k];
+    if (prm->renorm) {
+        double nrm = 0.0;
+        for (int k = 0; k < d; ++k) nrm += y[k] * y[k];
+        nrm = sqrt(nrm);
+        for (int k = 0; k < d; ++k) y[k] /= nrm;
+    }
+}
+
+void orc_euler_update(const orc_params *prm, double *X, const double *FK, int64_t m)
+{
+    int d = prm->d;
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < prm->n; ++i) {
-        double z[4] = {0.0, 0.0, 0.0, 0.0}, fv[3];
-        orc_normals_one(prm, (uint32_t)i, m, z);
-        orc_confining(prm, X + i * d, fv);
         double y[3];
-        for (int k = 0; k < d; ++k) y[k] = X[i * d + k] + prm->dt * (FK[i * d + k] + fv[k]) + sq * z[k];
-        if (prm->renorm) {
-            double nrm = 0.0;
-            for (int k = 0; k < d; ++k) nrm += y[k] * y[k];
-            nrm = sqrt(nrm);
-            for (int k = 0; k < d; ++k) y[k] /= nrm;
-        }
+        orc_euler_update_one(prm, (uint32_t)i, X + i * d, FK + i * d, m, y);
         for (int k = 0; k < d; ++k) X[i * d + k] = y[k];
     }
 }
@@ -379,6 +386,22 @@ void orc_direct_step(const orc_params *prm, double *X, int64_t m)
     orc_direct_interaction(prm, X, FK);
     orc_euler_update(prm, X, FK, m);
     free(FK);
+}
+
+/* The direct step of the listed particles only: Y[a] = new position of
+ * particle idx[a] after one direct step from X (same arithmetic as
+ * orc_direct_step, restricted to a sample so large N stays affordable). */
+void orc_direct_step_sampled(const orc_params *prm, const double *X, int64_t m, const int64_t *idx, int64_t nidx,
+                             double *Y)
+{
+    int d = prm->d;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t a = 0; a < nidx; ++a) {
+        double fk[3];
+        int64_t i = idx[a];
+        orc_direct_interaction_one(prm, X, i, fk);
+        orc_euler_update_one(prm, (uint32_t)i, X + i * d, fk, m, Y + a * d);
+    }
 }
 
 /* Mean-field force at query points: F(q) = 1/(N-1) sum_j K(q - X^j) over all

@@ -56,6 +56,8 @@ void orc_split_pair_solve(const orc_params *prm, const double *xi, const double 
 void orc_rbm_split_step(const orc_params *prm, double *X, int64_t m);
 void orc_rbm_step(const orc_params *prm, double *X, int64_t m);
 void orc_direct_step(const orc_params *prm, double *X, int64_t m);
+void orc_direct_step_sampled(const orc_params *prm, const double *X, int64_t m, const int64_t *idx, int64_t nidx,
+                             double *Y);
 void orc_direct_forces_at(const orc_params *prm, const double *X, const double *Q, int64_t nq, double *F);
 int orc_num_threads(void);
 

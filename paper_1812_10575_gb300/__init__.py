@@ -1,0 +1,115 @@
+"""GB300-native Random Batch Method (RBM-1) hot path (arXiv:1812.10575).
+
+The compute lives in ``librbm.so`` (hand-written sm_103a CUDA behind the C ABI
+of ``include/rbm.h``); this package is its thin Python binding plus a small
+convenience wrapper, :class:`System`.  PyTorch supplies device memory and
+streams only.
+
+    import torch, paper_1812_10575_gb300 as rbm
+    x = torch.randn(4096, 4, device="cuda")            # N x ld, d = 3
+    sysm = rbm.System(x, d=3, p=2, dt=1e-3, k="coulomb", renorm=True)
+    sysm.run(100)                                        # 100 RBM-1 steps
+    sysm.sync()
+"""
+from __future__ import annotations
+
+from ._lib import (  # noqa: F401
+    EXPORTS, KERNELS, METHODS, POTENTIALS, SCHEMES, RbmError, RbmParams, RbmTuning, library_path, load,
+    make_params, rbm_direct_forces_at, rbm_direct_step, rbm_forces, rbm_free, rbm_get_step, rbm_get_tuning,
+    rbm_init, rbm_last_error, rbm_launches_per_step, rbm_permutation, rbm_run, rbm_set_step, rbm_set_tuning,
+    rbm_status_string, rbm_step, rbm_step_host, rbm_step_profiled, rbm_sync,
+)
+
+
+def leading_dim(d: int) -> int:
+    """Row length of the position array: d for d = 1, 2 and 4 for d = 3."""
+    return 4 if d == 3 else d
+
+
+class System:
+    """One particle system bound to a caller-owned CUDA tensor ``x`` of shape
+    ``(N, leading_dim(d))``.  Methods map one-to-one onto the C entry points."""
+
+    def __init__(self, x, d, p=2, dt=1e-3, sigma=0.0, seed=0, v="zero", v_coef=1.0, k="linear",
+                 k_param=0.0, renorm=False, scheme="euler", replica=0, stream=None):
+        import torch
+
+        if x.dtype not in (torch.float32, torch.float64):
+            raise ValueError("positions must be float32 or float64")
+        if x.dim() != 2 or x.shape[1] != leading_dim(d):
+            raise ValueError(f"positions must have shape (N, {leading_dim(d)})")
+        self.x = x
+        self.d = d
+        self.params = make_params(x.shape[0], d, p=p, dt=dt, sigma=sigma, seed=seed,
+                                  dtype="f32" if x.dtype == torch.float32 else "f64", v=v, v_coef=v_coef,
+                                  k=k, k_param=k_param, renorm=renorm, scheme=scheme, replica=replica)
+        self.ctx = rbm_init(self.params, x, stream)
+
+    def step(self):
+        rbm_step(self.ctx)
+
+    def direct_step(self):
+        rbm_direct_step(self.ctx)
+
+    def run(self, steps, method="rbm"):
+        rbm_run(self.ctx, steps, method)
+
+    def step_host(self, x_host, method="rbm"):
+        rbm_step_host(self.ctx, x_host, method)
+
+    @property
+    def m(self):
+        return rbm_get_step(self.ctx)
+
+    @m.setter
+    def m(self, value):
+        rbm_set_step(self.ctx, value)
+
+    def sync(self):
+        rbm_sync(self.ctx)
+
+    def permutation(self):
+        import torch
+
+        perm = torch.empty(self.x.shape[0], dtype=torch.int32, device=self.x.device)
+        rbm_permutation(self.ctx, perm)
+        return perm
+
+    def forces(self, method="rbm"):
+        import torch
+
+        f = torch.zeros_like(self.x)
+        rbm_forces(self.ctx, method, f)
+        return f
+
+    def direct_forces_at(self, q):
+        import torch
+
+        f = torch.zeros_like(q)
+        rbm_direct_forces_at(self.ctx, q, f)
+        return f
+
+    def set_tuning(self, **kw):
+        t = RbmTuning(**kw)
+        rbm_set_tuning(self.ctx, t)
+
+    def tuning(self):
+        t = rbm_get_tuning(self.ctx)
+        return {f: getattr(t, f) for f, _ in RbmTuning._fields_}
+
+    def step_profiled(self, method="rbm"):
+        return rbm_step_profiled(self.ctx, method)
+
+    def launches_per_step(self, method="rbm"):
+        return rbm_launches_per_step(self.ctx, method)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            rbm_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,259 @@
+"""ctypes binding of ``include/rbm.h``: argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method; all work runs in the CUDA kernels of ``librbm.so``.
+Positions are caller-owned CUDA tensors of shape ``(N, ld)`` (``ld = d`` for
+d = 1, 2 and 4 for d = 3) in float32 or float64; PyTorch provides the device
+memory and the stream only.
+
+If ``librbm.so`` is missing or cannot be loaded the binding raises: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+RBM_OK = 0
+RBM_ERR_INVALID = -1
+RBM_ERR_CUDA = -2
+RBM_ERR_NOMEM = -3
+RBM_ERR_TIMEOUT = -4
+RBM_ERR_NONFINITE = -5
+RBM_ERR_STATE = -6
+RBM_ERR_UNSUPPORTED = -7
+
+RBM_F32, RBM_F64 = 0, 1
+RBM_V_ZERO, RBM_V_QUADRATIC = 0, 1
+KERNELS = {"inv1d": 0, "coulomb": 1, "bounded_conf": 2, "gauss_agg": 3, "reg_attract": 4, "smooth_test": 5,
+           "linear": 6}
+POTENTIALS = {"zero": 0, "quadratic": 1}
+RBM_METHOD_RBM, RBM_METHOD_DIRECT = 0, 1
+METHODS = {"rbm": 0, "direct": 1}
+RBM_SCHEME_EULER, RBM_SCHEME_SPLIT = 0, 1
+SCHEMES = {"euler": 0, "split": 1}
+RBM_FLAG_RENORM_SPHERE = 1
+
+# Every symbol include/rbm.h declares.
+EXPORTS = (
+    "rbm_init", "rbm_step", "rbm_direct_step", "rbm_run", "rbm_step_host", "rbm_get_step", "rbm_set_step",
+    "rbm_set_tuning", "rbm_get_tuning", "rbm_sync", "rbm_free", "rbm_status_string", "rbm_last_error",
+    "rbm_permutation", "rbm_forces", "rbm_direct_forces_at", "rbm_step_profiled", "rbm_launches_per_step",
+)
+
+
+class RbmParams(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64),
+        ("d", ctypes.c_int32),
+        ("p", ctypes.c_int32),
+        ("dt", ctypes.c_double),
+        ("sigma", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("dtype", ctypes.c_int32),
+        ("v", ctypes.c_int32),
+        ("v_coef", ctypes.c_double),
+        ("k", ctypes.c_int32),
+        ("k_param", ctypes.c_double),
+        ("flags", ctypes.c_uint32),
+        ("scheme", ctypes.c_int32),
+        ("replica", ctypes.c_uint32),
+    ]
+
+
+class RbmTuning(ctypes.Structure):
+    _fields_ = [
+        ("bucket_bits", ctypes.c_int32),
+        ("slot_cap", ctypes.c_int32),
+        ("sort_cap", ctypes.c_int32),
+        ("block", ctypes.c_int32),
+        ("direct_block", ctypes.c_int32),
+        ("graph_steps", ctypes.c_int32),
+    ]
+
+
+class RbmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = f"{where}: {rbm_status_string(status)} ({status})"
+        detail = rbm_last_error() if status == RBM_ERR_CUDA else ""
+        super().__init__(msg + (f" [{detail}]" if detail else ""))
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load ``librbm.so`` (building it first if it is stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if path is None:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"librbm.so not found at {path}")
+    L = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    i32, i64 = ctypes.c_int32, ctypes.c_int64
+    P = ctypes.POINTER(RbmParams)
+    TP = ctypes.POINTER(RbmTuning)
+    sig = {
+        "rbm_init": [P, vp, vp, ctypes.POINTER(vp)],
+        "rbm_step": [vp],
+        "rbm_direct_step": [vp],
+        "rbm_run": [vp, i64, i32],
+        "rbm_step_host": [vp, vp, i32],
+        "rbm_get_step": [vp, ctypes.POINTER(i64)],
+        "rbm_set_step": [vp, i64],
+        "rbm_set_tuning": [vp, TP],
+        "rbm_get_tuning": [vp, TP],
+        "rbm_sync": [vp],
+        "rbm_free": [vp],
+        "rbm_permutation": [vp, vp],
+        "rbm_forces": [vp, i32, vp],
+        "rbm_direct_forces_at": [vp, vp, i64, vp],
+        "rbm_launches_per_step": [vp, i32, ctypes.POINTER(i32)],
+        "rbm_step_profiled": [vp, i32, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(i32), ctypes.c_char_p,
+                              i32],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int32
+    L.rbm_status_string.argtypes = [i32]
+    L.rbm_status_string.restype = ctypes.c_char_p
+    L.rbm_last_error.argtypes = []
+    L.rbm_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _check(status: int, where: str) -> None:
+    if status != RBM_OK:
+        raise RbmError(status, where)
+
+
+def rbm_status_string(status: int) -> str:
+    return load().rbm_status_string(int(status)).decode()
+
+
+def rbm_last_error() -> str:
+    return load().rbm_last_error().decode()
+
+
+def make_params(n, d, p=2, dt=1e-3, sigma=0.0, seed=0, dtype="f32", v="zero", v_coef=1.0, k="linear",
+                k_param=0.0, renorm=False, scheme="euler", replica=0) -> RbmParams:
+    return RbmParams(
+        n=int(n), d=int(d), p=int(p), dt=float(dt), sigma=float(sigma), seed=int(seed),
+        dtype=RBM_F32 if dtype in ("f32", "float32") else RBM_F64,
+        v=POTENTIALS[v] if isinstance(v, str) else int(v), v_coef=float(v_coef),
+        k=KERNELS[k] if isinstance(k, str) else int(k), k_param=float(k_param),
+        flags=RBM_FLAG_RENORM_SPHERE if renorm else 0,
+        scheme=SCHEMES[scheme] if isinstance(scheme, str) else int(scheme), replica=int(replica),
+    )
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+
+        return int(torch.cuda.current_stream().cuda_stream)
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def _dev_ptr(t) -> int:
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return int(t.data_ptr())
+
+
+def rbm_init(params: RbmParams, x, stream=None) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(load().rbm_init(ctypes.byref(params), ctypes.c_void_p(_dev_ptr(x)),
+                           ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(ctx)), "rbm_init")
+    return ctx
+
+
+def rbm_step(ctx) -> None:
+    _check(load().rbm_step(ctx), "rbm_step")
+
+
+def rbm_direct_step(ctx) -> None:
+    _check(load().rbm_direct_step(ctx), "rbm_direct_step")
+
+
+def rbm_run(ctx, steps: int, method="rbm") -> None:
+    _check(load().rbm_run(ctx, int(steps), METHODS.get(method, method)), "rbm_run")
+
+
+def rbm_step_host(ctx, x_host, method="rbm") -> None:
+    """``x_host``: a CPU tensor (pinned for speed) of the positions' shape."""
+    if x_host.is_cuda or not x_host.is_contiguous():
+        raise ValueError("expected a contiguous host tensor")
+    _check(load().rbm_step_host(ctx, ctypes.c_void_p(int(x_host.data_ptr())), METHODS.get(method, method)),
+           "rbm_step_host")
+
+
+def rbm_get_step(ctx) -> int:
+    m = ctypes.c_int64()
+    _check(load().rbm_get_step(ctx, ctypes.byref(m)), "rbm_get_step")
+    return m.value
+
+
+def rbm_set_step(ctx, m: int) -> None:
+    _check(load().rbm_set_step(ctx, int(m)), "rbm_set_step")
+
+
+def rbm_set_tuning(ctx, tuning: RbmTuning) -> None:
+    _check(load().rbm_set_tuning(ctx, ctypes.byref(tuning)), "rbm_set_tuning")
+
+
+def rbm_get_tuning(ctx) -> RbmTuning:
+    t = RbmTuning()
+    _check(load().rbm_get_tuning(ctx, ctypes.byref(t)), "rbm_get_tuning")
+    return t
+
+
+def rbm_sync(ctx) -> None:
+    _check(load().rbm_sync(ctx), "rbm_sync")
+
+
+def rbm_free(ctx) -> None:
+    _check(load().rbm_free(ctx), "rbm_free")
+
+
+def rbm_permutation(ctx, perm) -> None:
+    """``perm``: int32 CUDA tensor of N entries (holds uint32 ids)."""
+    _check(load().rbm_permutation(ctx, ctypes.c_void_p(_dev_ptr(perm))), "rbm_permutation")
+
+
+def rbm_forces(ctx, method, f) -> None:
+    _check(load().rbm_forces(ctx, METHODS.get(method, method), ctypes.c_void_p(_dev_ptr(f))), "rbm_forces")
+
+
+def rbm_direct_forces_at(ctx, q, f) -> None:
+    _check(load().rbm_direct_forces_at(ctx, ctypes.c_void_p(_dev_ptr(q)), int(q.shape[0]),
+                                       ctypes.c_void_p(_dev_ptr(f))), "rbm_direct_forces_at")
+
+
+def rbm_step_profiled(ctx, method="rbm"):
+    """One step with per-kernel CUDA-event timing: returns [(name, ms), ...]."""
+    ms = (ctypes.c_float * 16)()
+    nk = ctypes.c_int32()
+    names = ctypes.create_string_buffer(512)
+    _check(load().rbm_step_profiled(ctx, METHODS.get(method, method), ms, 16, ctypes.byref(nk), names, 512),
+           "rbm_step_profiled")
+    return list(zip(names.value.decode().split(";"), [ms[i] for i in range(nk.value)]))
+
+
+def rbm_launches_per_step(ctx, method="rbm") -> int:
+    n = ctypes.c_int32()
+    _check(load().rbm_launches_per_step(ctx, METHODS.get(method, method), ctypes.byref(n)),
+           "rbm_launches_per_step")
+    return n.value

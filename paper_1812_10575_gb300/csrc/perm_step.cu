@@ -1,0 +1,582 @@
+// RBM-1 step on the GPU: random division by a bucketed sort of 64-bit Philox
+// keys with an id tie-break, and the in-batch interaction + -grad V +
+// Brownian increment + Euler-Maruyama update fused into the sort kernel.
+//
+// Algorithm "randomdiv" (Sec. 2.1 of arXiv:1812.10575) per step m:
+//   1. key_i = Philox(i, m, r, 0); the random division is the id list sorted
+//      by (key, id); batch q = sorted positions [q p, min(q p + p, N)).
+//   2. every batch C_q moves by eq. "firstalgorithm":
+//      X^i += dt (1/(|C_q|-1) sum_{j in C_q, j != i} K(X^i - X^j) - grad V(X^i))
+//             + sigma sqrt(dt) z_i.
+// The sort runs in two passes over buckets of the top `bucket_bits` key bits:
+//   k_bucket_scatter  - one Philox per particle, an atomic slot in its bucket
+//                       (overflowing members go to a spill list);
+//   k_bucket_sort_step - one block per bucket: regenerate the keys, bitonic
+//                       sort of (key, id) in shared memory, write the bucket's
+//                       stretch of the permutation, and step every batch that
+//                       lies wholly inside the bucket (p <= 32: one group of p
+//                       lanes per batch, positions exchanged by warp shuffles).
+// Batches that straddle a bucket boundary are stepped afterwards by the last
+// block to finish (few buckets) or by k_straddle_fixup (many buckets).  They
+// read only positions no other batch writes, so every update uses the
+// positions of step m as the explicit scheme requires.
+#include <cstdio>
+
+#include "rbm_device.cuh"
+#include "rbm_internal.h"
+
+namespace rbm {
+
+namespace {
+
+constexpr int kModePerm = 0;
+constexpr int kModeStep = 1;
+constexpr int kModeForces = 2;
+
+__device__ __forceinline__ uint32_t bucket_of(uint64_t key, int bits) {
+  return bits ? static_cast<uint32_t>(key >> (64 - bits)) : 0u;
+}
+
+struct PermArgs {
+  uint32_t* cnt;
+  uint32_t* start;
+  uint32_t* slots;
+  uint32_t* ovf_cnt;
+  uint32_t* ovf;
+  uint32_t* done;
+  uint32_t* perm;
+  uint32_t n;
+  int bits;
+  uint32_t nbuckets;
+  uint32_t slot_cap;
+  uint32_t sort_cap;
+  int separate_scan;
+  uint2 seed;
+  uint32_t replica;
+  const int64_t* m_ptr;
+  int64_t m_off;
+};
+
+__device__ __forceinline__ uint32_t perm_step_index(const PermArgs& a) {
+  const int64_t m = (a.m_ptr ? *a.m_ptr : 0) + a.m_off;
+  return static_cast<uint32_t>(static_cast<uint64_t>(m));
+}
+
+PermArgs make_perm_args(const PermScratch& ps, uint32_t n, uint2 seed, uint32_t replica, const int64_t* m_ptr,
+                        int64_t m_off) {
+  PermArgs a;
+  a.cnt = ps.cnt; a.start = ps.start; a.slots = ps.slots; a.ovf_cnt = ps.ovf_cnt; a.ovf = ps.ovf;
+  a.done = ps.done; a.perm = ps.perm; a.n = n; a.bits = ps.bucket_bits; a.nbuckets = ps.nbuckets;
+  a.slot_cap = ps.slot_cap; a.sort_cap = ps.sort_cap; a.separate_scan = ps.separate_scan ? 1 : 0;
+  a.seed = seed; a.replica = replica; a.m_ptr = m_ptr; a.m_off = m_off;
+  return a;
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1: bucket every particle by the top bits of its key.
+// ---------------------------------------------------------------------------
+__global__ void k_bucket_scatter(PermArgs a) {
+  const uint32_t m32 = perm_step_index(a);
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const uint64_t key = perm_key(i, m32, a.replica, a.seed);
+    const uint32_t b = bucket_of(key, a.bits);
+    const uint32_t pos = atomicAdd(&a.cnt[b], 1u);
+    if (pos < a.slot_cap) {
+      a.slots[static_cast<size_t>(b) * a.slot_cap + pos] = i;
+    } else {
+      const uint32_t o = atomicAdd(a.ovf_cnt, 1u);  // o < n: the list holds every particle
+      a.ovf[o] = i;
+    }
+  }
+}
+
+// Exclusive scan of the bucket counts by one block (many-bucket case).
+__global__ void k_bucket_scan(PermArgs a) {
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_carry;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (uint32_t base = 0; base < a.nbuckets; base += blockDim.x) {
+    const uint32_t b = base + threadIdx.x;
+    const uint32_t v = (b < a.nbuckets) ? a.cnt[b] : 0u;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = (lane < nwarps) ? s_warp[lane] : 0u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += t;
+      }
+      if (lane < nwarps) s_warp[lane] = w;  // inclusive warp totals
+    }
+    __syncthreads();
+    const uint32_t warp_excl = (warp > 0) ? s_warp[warp - 1] : 0u;
+    if (b < a.nbuckets) a.start[b] = s_carry + warp_excl + incl - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) s_carry += warp_excl + incl;
+    __syncthreads();
+  }
+}
+
+// Sum of v over the block, returned to every thread.
+__device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* s_red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) s_red[warp] = v;
+  __syncthreads();
+  uint32_t t = 0;
+  for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += s_red[w];
+  return t;
+}
+
+__device__ __forceinline__ bool key_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
+  return ka < kb || (ka == kb && ia < ib);
+}
+
+// Bitonic sort of (skey, sid)[0, p2) ascending; p2 a power of two.
+__device__ void bitonic_sort(uint64_t* skey, uint32_t* sid, uint32_t p2) {
+  for (uint32_t k = 2; k <= p2; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t t = threadIdx.x; t < (p2 >> 1); t += blockDim.x) {
+        const uint32_t i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+        const uint32_t l = i + j;
+        const bool up = (i & k) == 0;
+        const uint64_t ki = skey[i], kl = skey[l];
+        const uint32_t ii = sid[i], il = sid[l];
+        const bool gt = key_less(kl, il, ki, ii);
+        if (gt == up) {
+          skey[i] = kl; skey[l] = ki;
+          sid[i] = il; sid[l] = ii;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One batch per group of p consecutive lanes (p <= 32).  All 32 lanes of the
+// warp call this together (the shuffles use the full mask); lanes outside a
+// valid batch member pass valid = false and store nothing.
+//   bs    - members of this batch (p, or N mod p for the last batch)
+//   lg    - this lane's index inside its group
+// ---------------------------------------------------------------------------
+template <typename T, int D, int MODE>
+__device__ __forceinline__ void batch_group(const StepParams<T>& a, uint32_t m32, uint32_t id, bool valid, int lg,
+                                            int bs) {
+  const int p = a.p;
+  const int lane = threadIdx.x & 31;
+  const int base = lane - lg;
+  Row<T, D> r;
+  if (valid) {
+    r = load_row<T, D>(a.x, id);
+  } else {
+#pragma unroll
+    for (int k = 0; k < D; ++k) r.x[k] = T(0);
+    r.pad = T(0);
+  }
+  T fk[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) fk[k] = T(0);
+
+  if (MODE == kModeStep && a.scheme == RBM_SCHEME_SPLIT) {
+    // Exact pair flow of K (p = 2), then the Euler-Maruyama step of V and noise.
+    const int src = base + (lg ^ 1);
+    T xj[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) xj[k] = __shfl_sync(0xffffffffu, r.x[k], src);
+    if (!valid) return;
+    T y0[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) y0[k] = r.x[k];
+    if (bs == 2) {
+      T delta[D], mid[D];
+      T len2 = T(0);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        delta[k] = r.x[k] - xj[k];
+        mid[k] = T(0.5) * (r.x[k] + xj[k]);
+        len2 += delta[k] * delta[k];
+      }
+      T dd[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) dd[k] = fsub_rn(r.x[k], xj[k]);
+      if (sqnorm_rn<T, D>(dd) != T(0)) {
+        const T len = sqrt(len2);
+        const T newlen = (a.kf == RBM_K_INV1D) ? sqrt(len2 + T(4) * a.dt) : cbrt(len2 * len + T(6) * a.dt);
+#pragma unroll
+        for (int k = 0; k < D; ++k) y0[k] = mid[k] + T(0.5) * newlen * (delta[k] / len);
+      }
+    }
+    T y[D];
+    euler_update<T, D>(a, id, m32, y0, fk, y);
+#pragma unroll
+    for (int k = 0; k < D; ++k) r.x[k] = y[k];
+    store_row<T, D>(a.x, id, r);
+    return;
+  }
+
+  for (int j = 1; j < p; ++j) {
+    int sg = lg + j;
+    if (sg >= p) sg -= p;
+    T xj[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) xj[k] = __shfl_sync(0xffffffffu, r.x[k], base + sg);
+    if (valid && sg < bs) add_pair_force_rt<T, D>(a.kf, a.kparam, a.radius_sq, r.x, xj, fk);
+  }
+  if (!valid) return;
+  const T inv = (bs > 1) ? T(1) / static_cast<T>(bs - 1) : T(0);
+#pragma unroll
+  for (int k = 0; k < D; ++k) fk[k] = (bs > 1) ? fk[k] * inv : T(0);
+  if (MODE == kModeForces) {
+    Row<T, D> f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) f.x[k] = fk[k];
+    f.pad = T(0);
+    store_row<T, D>(a.fout, id, f);
+    return;
+  }
+  T y[D];
+  euler_update<T, D>(a, id, m32, r.x, fk, y);
+#pragma unroll
+  for (int k = 0; k < D; ++k) r.x[k] = y[k];
+  store_row<T, D>(a.x, id, r);
+}
+
+// Steps the batches whose first sorted position is q0 + k (k < count), ids
+// read from `ids` at offset (batch start - ids_base).  Warp-uniform loop.
+template <typename T, int D, int MODE>
+__device__ void step_batches(const StepParams<T>& a, uint32_t m32, const uint32_t* ids, uint32_t ids_base,
+                             uint32_t q0, uint32_t count) {
+  const int p = a.p;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gpw = 32 / p;                       // batch groups per warp
+  const int nwarps = blockDim.x >> 5;
+  const uint32_t per_round = static_cast<uint32_t>(gpw * nwarps);
+  const int g = lane / p, lg = lane - g * p;
+  for (uint32_t r0 = 0; r0 < count; r0 += per_round) {
+    const uint32_t kb = r0 + static_cast<uint32_t>(warp * gpw + g);
+    bool valid = (g < gpw) && (kb < count);
+    uint32_t id = 0;
+    int bs = p;
+    if (valid) {
+      const uint32_t q = q0 + kb;
+      const uint32_t lo = q * static_cast<uint32_t>(p);
+      const uint32_t hi = min(lo + static_cast<uint32_t>(p), a.n);
+      bs = static_cast<int>(hi - lo);
+      valid = lg < bs;
+      if (valid) id = ids[lo + lg - ids_base];
+    }
+    batch_group<T, D, MODE>(a, m32, id, valid, lg, bs);
+  }
+}
+
+// Steps the batches that straddle bucket boundaries b in [b_begin, b_end)
+// (each batch once: from the first boundary strictly inside it).
+template <typename T, int D, int MODE>
+__device__ void step_straddling(const StepParams<T>& a, uint32_t m32, const PermArgs& pa, uint32_t b_begin,
+                                uint32_t b_end, uint32_t b_stride_groups, uint32_t group_offset) {
+  const int p = a.p;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gpw = 32 / p;
+  const int nwarps = blockDim.x >> 5;
+  const int g = lane / p, lg = lane - g * p;
+  const uint32_t per_round = static_cast<uint32_t>(gpw * nwarps);
+  for (uint32_t r0 = b_begin; r0 < b_end; r0 += per_round * b_stride_groups) {
+    const uint32_t b = r0 + (group_offset + static_cast<uint32_t>(warp * gpw + g)) ;
+    bool valid = (g < gpw) && (b < b_end) && (b > 0);
+    uint32_t id = 0;
+    int bs = p;
+    if (valid) {
+      const uint32_t s = pa.start[b];
+      const uint32_t up = static_cast<uint32_t>(p);
+      valid = (s % up != 0) && (s < a.n);
+      if (valid) {
+        const uint32_t q = s / up;
+        valid = pa.start[b - 1] <= q * up;      // first boundary inside batch q
+        if (valid) {
+          const uint32_t lo = q * up, hi = min(lo + up, a.n);
+          bs = static_cast<int>(hi - lo);
+          valid = lg < bs;
+          if (valid) id = pa.perm[lo + lg];
+        }
+      }
+    }
+    batch_group<T, D, MODE>(a, m32, id, valid, lg, bs);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 2: one block per bucket.
+// ---------------------------------------------------------------------------
+template <typename T, int D, int MODE>
+__global__ void __launch_bounds__(256) k_bucket_sort_step(PermArgs pa, StepParams<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* skey = reinterpret_cast<uint64_t*>(smem_raw);
+  uint32_t* sid = reinterpret_cast<uint32_t*>(skey + pa.sort_cap);
+  __shared__ uint32_t s_red[32];
+  __shared__ uint32_t s_fill;
+  __shared__ int s_last;
+
+  const uint32_t b = blockIdx.x;
+  const uint32_t m32 = perm_step_index(pa);
+
+  uint32_t start;
+  if (pa.separate_scan) {
+    start = pa.start[b];
+  } else {
+    uint32_t part = 0;
+    for (uint32_t t = threadIdx.x; t < b; t += blockDim.x) part += pa.cnt[t];
+    start = block_sum(part, s_red);
+    if (threadIdx.x == 0) pa.start[b] = start;
+  }
+  const uint32_t nb = pa.cnt[b];
+  const uint32_t nslot = min(nb, pa.slot_cap);
+  const uint32_t* ids;
+
+  if (nb <= pa.sort_cap) {
+    for (uint32_t t = threadIdx.x; t < nslot; t += blockDim.x) {
+      const uint32_t id = pa.slots[static_cast<size_t>(b) * pa.slot_cap + t];
+      sid[t] = id;
+      skey[t] = perm_key(id, m32, pa.replica, pa.seed);
+    }
+    if (nb > nslot) {  // members that spilled to the overflow list
+      if (threadIdx.x == 0) s_fill = nslot;
+      __syncthreads();
+      const uint32_t novf = *pa.ovf_cnt;
+      for (uint32_t t = threadIdx.x; t < novf; t += blockDim.x) {
+        const uint32_t id = pa.ovf[t];
+        const uint64_t key = perm_key(id, m32, pa.replica, pa.seed);
+        if (bucket_of(key, pa.bits) == b) {
+          const uint32_t pos = atomicAdd(&s_fill, 1u);
+          sid[pos] = id;
+          skey[pos] = key;
+        }
+      }
+    }
+    uint32_t p2 = 1;
+    while (p2 < nb) p2 <<= 1;
+    for (uint32_t t = nb + threadIdx.x; t < p2; t += blockDim.x) {
+      skey[t] = ~0ull;
+      sid[t] = ~0u;
+    }
+    __syncthreads();
+    bitonic_sort(skey, sid, p2);
+    for (uint32_t t = threadIdx.x; t < nb; t += blockDim.x) pa.perm[start + t] = sid[t];
+    ids = sid;
+  } else {
+    // Rare: a bucket larger than the shared-memory sort.  Rank every member by
+    // counting the members before it in (key, id) order.
+    const uint32_t novf = (nb > nslot) ? *pa.ovf_cnt : 0u;
+    const uint32_t total = nslot + novf;
+    for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
+      const uint32_t ide = (e < nslot) ? pa.slots[static_cast<size_t>(b) * pa.slot_cap + e] : pa.ovf[e - nslot];
+      const uint64_t ke = perm_key(ide, m32, pa.replica, pa.seed);
+      if (e >= nslot && bucket_of(ke, pa.bits) != b) continue;
+      uint32_t rank = 0;
+      for (uint32_t f = 0; f < total; ++f) {
+        const uint32_t idf = (f < nslot) ? pa.slots[static_cast<size_t>(b) * pa.slot_cap + f] : pa.ovf[f - nslot];
+        const uint64_t kf = perm_key(idf, m32, pa.replica, pa.seed);
+        if (f >= nslot && bucket_of(kf, pa.bits) != b) continue;
+        rank += key_less(kf, idf, ke, ide) ? 1u : 0u;
+      }
+      pa.perm[start + rank] = ide;
+    }
+    __syncthreads();
+    ids = pa.perm + start;
+  }
+  __syncthreads();
+
+  if (MODE != kModePerm) {
+    const uint32_t up = static_cast<uint32_t>(a.p);
+    const uint32_t end = start + nb;
+    const uint32_t q0 = (start + up - 1) / up;
+    const uint32_t q_end = (end == a.n) ? (a.n + up - 1) / up : end / up;
+    const uint32_t count = (q_end > q0) ? q_end - q0 : 0u;
+    step_batches<T, D, MODE>(a, m32, ids, start, q0, count);
+  }
+
+  if (pa.separate_scan) {
+    __syncthreads();
+    if (threadIdx.x == 0) pa.cnt[b] = 0;  // ready for the next step
+    return;
+  }
+
+  // Last block to finish: straddling batches and the counter reset.
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(pa.done, 1u) == gridDim.x - 1) ? 1 : 0;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (MODE != kModePerm) step_straddling<T, D, MODE>(a, m32, pa, 0, pa.nbuckets, 1, 0);
+  __syncthreads();
+  for (uint32_t t = threadIdx.x; t < pa.nbuckets; t += blockDim.x) pa.cnt[t] = 0;
+  if (threadIdx.x == 0) {
+    *pa.ovf_cnt = 0;
+    *pa.done = 0;
+  }
+}
+
+// Many-bucket case: straddling batches over a grid, then the spill counter reset.
+template <typename T, int D, int MODE>
+__global__ void __launch_bounds__(256) k_straddle_fixup(PermArgs pa, StepParams<T> a) {
+  const uint32_t m32 = perm_step_index(pa);
+  const int gpw = 32 / a.p;
+  const uint32_t per_block = static_cast<uint32_t>(gpw * (blockDim.x >> 5));
+  if (MODE != kModePerm)
+    step_straddling<T, D, MODE>(a, m32, pa, 0, pa.nbuckets, gridDim.x, blockIdx.x * per_block);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *pa.ovf_cnt = 0;
+}
+
+// Batches larger than a warp (p > 32): one block per batch, all members'
+// new positions staged in xout before any is written back.
+template <typename T, int D, int MODE>
+__global__ void __launch_bounds__(256) k_batch_generic(PermArgs pa, StepParams<T> a) {
+  const uint32_t m32 = step_index(a);
+  const uint32_t up = static_cast<uint32_t>(a.p);
+  const uint32_t lo = blockIdx.x * up;
+  const uint32_t hi = min(lo + up, a.n);
+  const uint32_t bs = hi - lo;
+  const T inv = (bs > 1) ? T(1) / static_cast<T>(bs - 1) : T(0);
+  for (uint32_t e = threadIdx.x; e < bs; e += blockDim.x) {
+    const uint32_t id = pa.perm[lo + e];
+    Row<T, D> r = load_row<T, D>(a.x, id);
+    T fk[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) fk[k] = T(0);
+    for (uint32_t f = 0; f < bs; ++f) {
+      if (f == e) continue;
+      const Row<T, D> o = load_row<T, D>(a.x, pa.perm[lo + f]);
+      add_pair_force_rt<T, D>(a.kf, a.kparam, a.radius_sq, r.x, o.x, fk);
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) fk[k] = (bs > 1) ? fk[k] * inv : T(0);
+    if (MODE == kModeForces) {
+      Row<T, D> f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) f.x[k] = fk[k];
+      f.pad = T(0);
+      store_row<T, D>(a.fout, id, f);
+    } else {
+      T y[D];
+      euler_update<T, D>(a, id, m32, r.x, fk, y);
+#pragma unroll
+      for (int k = 0; k < D; ++k) r.x[k] = y[k];
+      store_row<T, D>(a.xout, lo + e, r);
+    }
+  }
+  if (MODE != kModeStep) return;
+  __syncthreads();
+  for (uint32_t e = threadIdx.x; e < bs; e += blockDim.x)
+    store_row<T, D>(a.x, pa.perm[lo + e], load_row<T, D>(a.xout, lo + e));
+}
+
+__global__ void k_set_i64(int64_t* dst, int64_t v) { *dst = v; }
+__global__ void k_add_i64(int64_t* dst, int64_t v) { *dst += v; }
+
+template <typename T, int D>
+void launch_tail_d(const PermScratch& ps, int mode, const StepParams<T>& a, const LaunchCfg& cfg, cudaStream_t st) {
+  const PermArgs pa = make_perm_args(ps, a.n, a.seed, a.replica, a.m_ptr, a.m_off);
+  const size_t smem = static_cast<size_t>(ps.sort_cap) * (sizeof(uint64_t) + sizeof(uint32_t));
+  const bool small_p = a.p <= 32;
+  const int block = 256;
+  if (ps.separate_scan) {
+    k_bucket_scan<<<1, 1024, 0, st>>>(pa);
+    mark_launch(cfg, st, "k_bucket_scan");
+  }
+  const int kmode = small_p ? mode : kModePerm;
+  auto launch_sort = [&](auto kern) { kern<<<ps.nbuckets, block, smem, st>>>(pa, a); };
+  if (kmode == kModeStep) launch_sort(k_bucket_sort_step<T, D, kModeStep>);
+  else if (kmode == kModeForces) launch_sort(k_bucket_sort_step<T, D, kModeForces>);
+  else launch_sort(k_bucket_sort_step<T, D, kModePerm>);
+  mark_launch(cfg, st, "k_bucket_sort_step");
+  if (ps.separate_scan) {
+    const int gpw = small_p ? 32 / a.p : 1;
+    const uint32_t per_block = static_cast<uint32_t>(gpw * (block / 32));
+    const uint32_t grid = max(1u, (ps.nbuckets + per_block - 1) / per_block);
+    if (kmode == kModeStep) k_straddle_fixup<T, D, kModeStep><<<grid, block, 0, st>>>(pa, a);
+    else if (kmode == kModeForces) k_straddle_fixup<T, D, kModeForces><<<grid, block, 0, st>>>(pa, a);
+    else k_straddle_fixup<T, D, kModePerm><<<1, 32, 0, st>>>(pa, a);
+    mark_launch(cfg, st, "k_straddle_fixup");
+  }
+  if (!small_p && mode != kModePerm) {
+    const uint32_t nbatch = (a.n + a.p - 1) / a.p;
+    if (mode == kModeStep) k_batch_generic<T, D, kModeStep><<<nbatch, block, 0, st>>>(pa, a);
+    else k_batch_generic<T, D, kModeForces><<<nbatch, block, 0, st>>>(pa, a);
+    mark_launch(cfg, st, "k_batch_generic");
+  }
+}
+
+}  // namespace
+
+void launch_bucket_scatter(const PermScratch& ps, uint32_t n, uint2 seed, uint32_t replica, const int64_t* m_ptr,
+                           int64_t m_off, const LaunchCfg& cfg, cudaStream_t st) {
+  const PermArgs pa = make_perm_args(ps, n, seed, replica, m_ptr, m_off);
+  const int block = 256;
+  const uint32_t want = (n + block - 1) / block;
+  const uint32_t grid = max(1u, min(want, static_cast<uint32_t>(cfg.num_sms * 8)));
+  k_bucket_scatter<<<grid, block, 0, st>>>(pa);
+  mark_launch(cfg, st, "k_bucket_scatter");
+}
+
+template <typename T>
+void launch_rbm_tail(const PermScratch& ps, int d, int mode, const void* params, const LaunchCfg& cfg,
+                     cudaStream_t st) {
+  const StepParams<T>& a = *static_cast<const StepParams<T>*>(params);
+  if (d == 1) launch_tail_d<T, 1>(ps, mode, a, cfg, st);
+  else if (d == 2) launch_tail_d<T, 2>(ps, mode, a, cfg, st);
+  else launch_tail_d<T, 3>(ps, mode, a, cfg, st);
+}
+
+template void launch_rbm_tail<float>(const PermScratch&, int, int, const void*, const LaunchCfg&, cudaStream_t);
+template void launch_rbm_tail<double>(const PermScratch&, int, int, const void*, const LaunchCfg&, cudaStream_t);
+
+int rbm_tail_launches(const PermScratch& ps, int p) {
+  int n = 1;                      // sort (+ fused step)
+  if (ps.separate_scan) n += 2;   // scan, straddle fix-up
+  if (p > 32) n += 1;             // generic batch kernel
+  return n;
+}
+
+namespace {
+template <typename T, int D>
+cudaError_t allow_sort_smem_d(int bytes) {
+  cudaError_t e = cudaFuncSetAttribute(k_bucket_sort_step<T, D, kModePerm>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_bucket_sort_step<T, D, kModeStep>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_bucket_sort_step<T, D, kModeForces>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             bytes);
+  return e;
+}
+}  // namespace
+
+cudaError_t prepare_rbm_kernels() {
+  // The largest shared-memory sort (4096 keys + ids) plus static shared data.
+  const int bytes = 4096 * static_cast<int>(sizeof(uint64_t) + sizeof(uint32_t)) + 1024;
+  cudaError_t e = allow_sort_smem_d<float, 1>(bytes);
+  if (e == cudaSuccess) e = allow_sort_smem_d<float, 2>(bytes);
+  if (e == cudaSuccess) e = allow_sort_smem_d<float, 3>(bytes);
+  if (e == cudaSuccess) e = allow_sort_smem_d<double, 1>(bytes);
+  if (e == cudaSuccess) e = allow_sort_smem_d<double, 2>(bytes);
+  if (e == cudaSuccess) e = allow_sort_smem_d<double, 3>(bytes);
+  return e;
+}
+
+void launch_set_i64(int64_t* dst, int64_t value, cudaStream_t st) { k_set_i64<<<1, 1, 0, st>>>(dst, value); }
+void launch_add_i64(int64_t* dst, int64_t value, cudaStream_t st) { k_add_i64<<<1, 1, 0, st>>>(dst, value); }
+
+}  // namespace rbm

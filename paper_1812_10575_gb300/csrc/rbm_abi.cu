@@ -1,0 +1,525 @@
+// C ABI of the library (include/rbm.h): context life cycle, parameter
+// checks, scratch sizing, step dispatch and CUDA-graph replay.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "rbm_device.cuh"
+#include "rbm_internal.h"
+
+using namespace rbm;
+
+struct rbm_ctx {
+  rbm_params prm{};
+  int ld = 1;
+  size_t elem = 4;
+  size_t row_bytes = 4;
+  void* x = nullptr;            // caller's positions
+  cudaStream_t stream = nullptr;
+  int64_t m = 0;                // host copy of the step counter
+  int64_t m_dev_value = -1;     // value last written to m_dev by the host side
+  int32_t* status = nullptr;    // device
+  int64_t* m_dev = nullptr;     // device step counter read by graph replays
+  void* xtmp = nullptr;         // second position buffer (direct step, generic batches)
+  PermScratch ps;
+  LaunchCfg cfg;
+  rbm_tuning tuning{};
+  int32_t latched = RBM_OK;     // host copy of a device error
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int64_t graph_len[2] = {0, 0};
+};
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+void set_error(const char* what, cudaError_t e) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define RBM_CUDA(call)                         \
+  do {                                         \
+    cudaError_t e_ = (call);                   \
+    if (e_ != cudaSuccess) {                   \
+      set_error(#call, e_);                    \
+      return RBM_ERR_CUDA;                     \
+    }                                          \
+  } while (0)
+
+bool valid_kernel(int32_t k) { return k >= RBM_K_INV1D && k <= RBM_K_LINEAR; }
+
+rbm_status check_params(const rbm_params* p) {
+  if (!p) return RBM_ERR_INVALID;
+  if (p->n < 2 || p->n > (int64_t(1) << 31)) return RBM_ERR_INVALID;
+  if (p->d < 1 || p->d > 3) return RBM_ERR_INVALID;
+  if (p->p < 2 || p->p > p->n || p->p > 4096) return RBM_ERR_INVALID;
+  if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return RBM_ERR_INVALID;
+  if (!(p->sigma >= 0.0) || !std::isfinite(p->sigma)) return RBM_ERR_INVALID;
+  if (p->dtype != RBM_F32 && p->dtype != RBM_F64) return RBM_ERR_INVALID;
+  if (p->v != RBM_V_ZERO && p->v != RBM_V_QUADRATIC) return RBM_ERR_INVALID;
+  if (!valid_kernel(p->k)) return RBM_ERR_INVALID;
+  if (p->k == RBM_K_INV1D && p->d != 1) return RBM_ERR_INVALID;
+  if (!std::isfinite(p->v_coef) || !std::isfinite(p->k_param)) return RBM_ERR_INVALID;
+  if (p->flags & ~RBM_FLAG_RENORM_SPHERE) return RBM_ERR_INVALID;
+  if (p->scheme != RBM_SCHEME_EULER && p->scheme != RBM_SCHEME_SPLIT) return RBM_ERR_INVALID;
+  if (p->scheme == RBM_SCHEME_SPLIT && (p->p != 2 || (p->k != RBM_K_INV1D && p->k != RBM_K_COULOMB)))
+    return RBM_ERR_INVALID;
+  return RBM_OK;
+}
+
+void free_scratch(rbm_ctx* c) {
+  PermScratch& s = c->ps;
+  cudaFree(s.cnt); cudaFree(s.start); cudaFree(s.slots); cudaFree(s.ovf_cnt); cudaFree(s.ovf);
+  cudaFree(s.done); cudaFree(s.perm);
+  s = PermScratch{};
+  cudaFree(c->xtmp);
+  c->xtmp = nullptr;
+}
+
+void drop_graphs(rbm_ctx* c) {
+  for (int i = 0; i < 2; ++i) {
+    if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
+    c->graph[i] = nullptr;
+    c->graph_len[i] = 0;
+  }
+}
+
+uint32_t next_pow2(uint32_t v) {
+  uint32_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// Bucket geometry: about 512 members per bucket by default; slots hold the
+// mean plus eight standard deviations plus 64, the shared-memory sort twice
+// that (power of two, at most 4096); members beyond either bound take the
+// spill list and the counting fallback, so any bucket size stays correct.
+rbm_status alloc_scratch(rbm_ctx* c) {
+  const uint32_t n = static_cast<uint32_t>(c->prm.n);
+  PermScratch& s = c->ps;
+  int bits = c->tuning.bucket_bits;
+  if (bits <= 0) {
+    bits = 0;
+    while (bits < 22 && (static_cast<uint64_t>(n) >> bits) > 512) ++bits;
+  }
+  if (bits > 24) bits = 24;
+  s.bucket_bits = bits;
+  s.nbuckets = 1u << bits;
+  const double mean = static_cast<double>(n) / s.nbuckets;
+  uint32_t cap = c->tuning.slot_cap > 0 ? static_cast<uint32_t>(c->tuning.slot_cap)
+                                        : static_cast<uint32_t>(mean + 8.0 * std::sqrt(mean) + 64.0);
+  if (cap > n) cap = n;
+  s.slot_cap = cap;
+  uint32_t sc = c->tuning.sort_cap > 0 ? next_pow2(static_cast<uint32_t>(c->tuning.sort_cap))
+                                       : next_pow2(2 * cap);
+  if (sc > 4096) sc = 4096;
+  if (sc < 2) sc = 2;
+  s.sort_cap = sc;
+  s.separate_scan = s.nbuckets > 1024;
+  RBM_CUDA(cudaMalloc(&s.cnt, sizeof(uint32_t) * s.nbuckets));
+  RBM_CUDA(cudaMalloc(&s.start, sizeof(uint32_t) * s.nbuckets));
+  RBM_CUDA(cudaMalloc(&s.slots, sizeof(uint32_t) * static_cast<size_t>(s.nbuckets) * s.slot_cap));
+  RBM_CUDA(cudaMalloc(&s.ovf_cnt, sizeof(uint32_t)));
+  RBM_CUDA(cudaMalloc(&s.ovf, sizeof(uint32_t) * n));
+  RBM_CUDA(cudaMalloc(&s.done, sizeof(uint32_t)));
+  RBM_CUDA(cudaMalloc(&s.perm, sizeof(uint32_t) * n));
+  RBM_CUDA(cudaMalloc(&c->xtmp, c->row_bytes * n));
+  RBM_CUDA(cudaMemset(s.cnt, 0, sizeof(uint32_t) * s.nbuckets));
+  RBM_CUDA(cudaMemset(s.ovf_cnt, 0, sizeof(uint32_t)));
+  RBM_CUDA(cudaMemset(s.done, 0, sizeof(uint32_t)));
+  c->cfg.block = c->tuning.block > 0 ? c->tuning.block : 256;
+  c->cfg.direct_block = c->tuning.direct_block > 0 ? c->tuning.direct_block : 256;
+  return RBM_OK;
+}
+
+template <typename T>
+StepParams<T> step_params(const rbm_ctx* c, const int64_t* m_ptr, int64_t m_off) {
+  StepParams<T> a{};
+  const rbm_params& p = c->prm;
+  a.x = static_cast<T*>(c->x);
+  a.xout = static_cast<T*>(c->xtmp);
+  a.fout = nullptr;
+  a.status = c->status;
+  a.n = static_cast<uint32_t>(p.n);
+  a.p = p.p;
+  a.kf = p.k;
+  a.vkind = p.v;
+  a.renorm = (p.flags & RBM_FLAG_RENORM_SPHERE) ? 1 : 0;
+  a.scheme = p.scheme;
+  a.dt = static_cast<T>(p.dt);
+  a.sq = static_cast<T>(p.sigma * std::sqrt(p.dt));
+  a.vcoef = static_cast<T>(p.v_coef);
+  a.kparam = static_cast<T>(p.k_param);
+  a.radius_sq = static_cast<T>(p.k_param * p.k_param);
+  a.seed = make_uint2(static_cast<uint32_t>(p.seed), static_cast<uint32_t>(p.seed >> 32));
+  a.replica = p.replica;
+  a.m_ptr = m_ptr;
+  a.m_off = m_off;
+  return a;
+}
+
+uint2 seed_of(const rbm_ctx* c) {
+  return make_uint2(static_cast<uint32_t>(c->prm.seed), static_cast<uint32_t>(c->prm.seed >> 32));
+}
+
+// Enqueue one RBM step (mode 1), the permutation only (0) or the forces (2).
+rbm_status enqueue_rbm(rbm_ctx* c, int mode, const int64_t* m_ptr, int64_t m_off, void* fout, cudaStream_t st) {
+  launch_bucket_scatter(c->ps, static_cast<uint32_t>(c->prm.n), seed_of(c), c->prm.replica, m_ptr, m_off, c->cfg,
+                        st);
+  if (c->prm.dtype == RBM_F32) {
+    StepParams<float> a = step_params<float>(c, m_ptr, m_off);
+    a.fout = static_cast<float*>(fout);
+    launch_rbm_tail<float>(c->ps, c->prm.d, mode, &a, c->cfg, st);
+  } else {
+    StepParams<double> a = step_params<double>(c, m_ptr, m_off);
+    a.fout = static_cast<double*>(fout);
+    launch_rbm_tail<double>(c->ps, c->prm.d, mode, &a, c->cfg, st);
+  }
+  RBM_CUDA(cudaGetLastError());
+  return RBM_OK;
+}
+
+// Enqueue one direct step (mode 0), forces (1) or forces at queries (2).
+rbm_status enqueue_direct(rbm_ctx* c, int mode, const int64_t* m_ptr, int64_t m_off, const void* q, uint32_t nq,
+                          void* fout, cudaStream_t st) {
+  if (c->prm.dtype == RBM_F32) {
+    StepParams<float> a = step_params<float>(c, m_ptr, m_off);
+    a.fout = static_cast<float*>(fout);
+    launch_direct<float>(c->prm.d, mode, &a, static_cast<const float*>(q), nq, c->cfg, st);
+  } else {
+    StepParams<double> a = step_params<double>(c, m_ptr, m_off);
+    a.fout = static_cast<double*>(fout);
+    launch_direct<double>(c->prm.d, mode, &a, static_cast<const double*>(q), nq, c->cfg, st);
+  }
+  RBM_CUDA(cudaGetLastError());
+  if (mode == 0)
+    RBM_CUDA(cudaMemcpyAsync(c->x, c->xtmp, c->row_bytes * static_cast<size_t>(c->prm.n),
+                             cudaMemcpyDeviceToDevice, st));
+  return RBM_OK;
+}
+
+rbm_status enqueue_step(rbm_ctx* c, int32_t method, const int64_t* m_ptr, int64_t m_off, cudaStream_t st) {
+  if (method == RBM_METHOD_RBM) return enqueue_rbm(c, 1, m_ptr, m_off, nullptr, st);
+  return enqueue_direct(c, 0, m_ptr, m_off, nullptr, 0, nullptr, st);
+}
+
+rbm_status usable(const rbm_ctx* c) {
+  if (!c) return RBM_ERR_INVALID;
+  if (c->latched != RBM_OK) return RBM_ERR_STATE;
+  return RBM_OK;
+}
+
+rbm_status capture_graph(rbm_ctx* c, int32_t method, int64_t len) {
+  if (!c->cap_stream) RBM_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  RBM_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  rbm_status st = RBM_OK;
+  for (int64_t s = 0; s < len && st == RBM_OK; ++s) st = enqueue_step(c, method, c->m_dev, s, c->cap_stream);
+  if (st == RBM_OK) launch_add_i64(c->m_dev, len, c->cap_stream);
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  if (st != RBM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) {
+    set_error("cudaStreamEndCapture", e);
+    return RBM_ERR_CUDA;
+  }
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    set_error("cudaGraphInstantiate", e);
+    return RBM_ERR_CUDA;
+  }
+  c->graph[method] = ex;
+  c->graph_len[method] = len;
+  return RBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rbm_last_error(void) { return g_last_error; }
+
+const char* rbm_status_string(int32_t status) {
+  switch (status) {
+    case RBM_OK: return "ok";
+    case RBM_ERR_INVALID: return "invalid argument";
+    case RBM_ERR_CUDA: return "CUDA runtime error";
+    case RBM_ERR_NOMEM: return "out of memory";
+    case RBM_ERR_TIMEOUT: return "device wait timed out";
+    case RBM_ERR_NONFINITE: return "non-finite position";
+    case RBM_ERR_STATE: return "context unusable after an earlier error";
+    case RBM_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+rbm_status rbm_init(const rbm_params* prm, void* x_dev, void* cuda_stream, rbm_ctx** out) {
+  if (!out) return RBM_ERR_INVALID;
+  *out = nullptr;
+  rbm_status st = check_params(prm);
+  if (st != RBM_OK) return st;
+  if (!x_dev || (reinterpret_cast<uintptr_t>(x_dev) & 15u)) return RBM_ERR_INVALID;
+  rbm_ctx* c = new (std::nothrow) rbm_ctx();
+  if (!c) return RBM_ERR_NOMEM;
+  c->prm = *prm;
+  c->ld = (prm->d == 3) ? 4 : prm->d;
+  c->elem = (prm->dtype == RBM_F32) ? 4 : 8;
+  c->row_bytes = c->elem * c->ld;
+  c->x = x_dev;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+    c->cfg.num_sms = sms;
+  {
+    const cudaError_t e = prepare_rbm_kernels();
+    if (e != cudaSuccess) {
+      set_error("prepare_rbm_kernels", e);
+      delete c;
+      return RBM_ERR_CUDA;
+    }
+  }
+  if (cudaMalloc(&c->status, sizeof(int32_t)) != cudaSuccess || cudaMalloc(&c->m_dev, sizeof(int64_t)) != cudaSuccess) {
+    cudaFree(c->status);
+    delete c;
+    return RBM_ERR_NOMEM;
+  }
+  cudaMemset(c->status, 0, sizeof(int32_t));
+  cudaMemset(c->m_dev, 0, sizeof(int64_t));
+  c->tuning.graph_steps = 100;
+  st = alloc_scratch(c);
+  if (st != RBM_OK) {
+    free_scratch(c);
+    cudaFree(c->status);
+    cudaFree(c->m_dev);
+    delete c;
+    return st == RBM_ERR_CUDA ? RBM_ERR_NOMEM : st;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    free_scratch(c);
+    cudaFree(c->status);
+    cudaFree(c->m_dev);
+    delete c;
+    return RBM_ERR_CUDA;
+  }
+  *out = c;
+  return RBM_OK;
+}
+
+rbm_status rbm_step(rbm_ctx* ctx) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  st = enqueue_step(ctx, RBM_METHOD_RBM, nullptr, ctx->m, ctx->stream);
+  if (st == RBM_OK) ctx->m += 1;
+  return st;
+}
+
+rbm_status rbm_direct_step(rbm_ctx* ctx) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  st = enqueue_step(ctx, RBM_METHOD_DIRECT, nullptr, ctx->m, ctx->stream);
+  if (st == RBM_OK) ctx->m += 1;
+  return st;
+}
+
+rbm_status rbm_run(rbm_ctx* ctx, int64_t steps, int32_t method) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (steps < 0 || (method != RBM_METHOD_RBM && method != RBM_METHOD_DIRECT)) return RBM_ERR_INVALID;
+  const int64_t len = ctx->tuning.graph_steps > 0 ? ctx->tuning.graph_steps : 100;
+  while (steps >= len) {
+    if (!ctx->graph[method] || ctx->graph_len[method] != len) {
+      if (ctx->graph[method]) cudaGraphExecDestroy(ctx->graph[method]);
+      ctx->graph[method] = nullptr;
+      st = capture_graph(ctx, method, len);
+      if (st != RBM_OK) return st;
+    }
+    if (ctx->m_dev_value != ctx->m) launch_set_i64(ctx->m_dev, ctx->m, ctx->stream);
+    RBM_CUDA(cudaGraphLaunch(ctx->graph[method], ctx->stream));
+    ctx->m += len;
+    ctx->m_dev_value = ctx->m;
+    steps -= len;
+  }
+  for (; steps > 0; --steps) {
+    st = enqueue_step(ctx, method, nullptr, ctx->m, ctx->stream);
+    if (st != RBM_OK) return st;
+    ctx->m += 1;
+  }
+  return RBM_OK;
+}
+
+rbm_status rbm_sync(rbm_ctx* ctx) {
+  if (!ctx) return RBM_ERR_INVALID;
+  RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+  int32_t s = 0;
+  RBM_CUDA(cudaMemcpy(&s, ctx->status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (s != 0 && ctx->latched == RBM_OK) ctx->latched = s;
+  return static_cast<rbm_status>(ctx->latched);
+}
+
+rbm_status rbm_step_host(rbm_ctx* ctx, void* x_host, int32_t method) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (!x_host || (method != RBM_METHOD_RBM && method != RBM_METHOD_DIRECT)) return RBM_ERR_INVALID;
+  const size_t bytes = ctx->row_bytes * static_cast<size_t>(ctx->prm.n);
+  RBM_CUDA(cudaMemcpyAsync(ctx->x, x_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  st = enqueue_step(ctx, method, nullptr, ctx->m, ctx->stream);
+  if (st != RBM_OK) return st;
+  ctx->m += 1;
+  RBM_CUDA(cudaMemcpyAsync(x_host, ctx->x, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  return rbm_sync(ctx);
+}
+
+rbm_status rbm_get_step(const rbm_ctx* ctx, int64_t* m) {
+  if (!ctx || !m) return RBM_ERR_INVALID;
+  *m = ctx->m;
+  return RBM_OK;
+}
+
+rbm_status rbm_set_step(rbm_ctx* ctx, int64_t m) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (m < 0) return RBM_ERR_INVALID;
+  ctx->m = m;
+  return RBM_OK;
+}
+
+rbm_status rbm_set_tuning(rbm_ctx* ctx, const rbm_tuning* tuning) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (!tuning) return RBM_ERR_INVALID;
+  if (tuning->bucket_bits < 0 || tuning->bucket_bits > 24 || tuning->slot_cap < 0 || tuning->sort_cap < 0 ||
+      tuning->sort_cap > 4096 || tuning->graph_steps < 0)
+    return RBM_ERR_INVALID;
+  if ((tuning->block != 0 && tuning->block != 256) ||
+      (tuning->direct_block != 0 && (tuning->direct_block < 32 || tuning->direct_block > 1024 ||
+                                     tuning->direct_block % 32 != 0)))
+    return RBM_ERR_INVALID;
+  RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+  drop_graphs(ctx);
+  free_scratch(ctx);
+  ctx->tuning = *tuning;
+  if (ctx->tuning.graph_steps == 0) ctx->tuning.graph_steps = 100;
+  st = alloc_scratch(ctx);
+  if (st != RBM_OK) {
+    ctx->latched = st;
+    return st;
+  }
+  RBM_CUDA(cudaDeviceSynchronize());
+  return RBM_OK;
+}
+
+rbm_status rbm_get_tuning(const rbm_ctx* ctx, rbm_tuning* tuning) {
+  if (!ctx || !tuning) return RBM_ERR_INVALID;
+  *tuning = ctx->tuning;
+  tuning->bucket_bits = ctx->ps.bucket_bits;
+  tuning->slot_cap = static_cast<int32_t>(ctx->ps.slot_cap);
+  tuning->sort_cap = static_cast<int32_t>(ctx->ps.sort_cap);
+  tuning->block = ctx->cfg.block;
+  tuning->direct_block = ctx->cfg.direct_block;
+  return RBM_OK;
+}
+
+rbm_status rbm_free(rbm_ctx* ctx) {
+  if (!ctx) return RBM_ERR_INVALID;
+  cudaStreamSynchronize(ctx->stream);
+  drop_graphs(ctx);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  free_scratch(ctx);
+  cudaFree(ctx->status);
+  cudaFree(ctx->m_dev);
+  delete ctx;
+  return RBM_OK;
+}
+
+rbm_status rbm_permutation(rbm_ctx* ctx, uint32_t* perm_dev) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (!perm_dev) return RBM_ERR_INVALID;
+  st = enqueue_rbm(ctx, 0, nullptr, ctx->m, nullptr, ctx->stream);
+  if (st != RBM_OK) return st;
+  RBM_CUDA(cudaMemcpyAsync(perm_dev, ctx->ps.perm, sizeof(uint32_t) * static_cast<size_t>(ctx->prm.n),
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+  return RBM_OK;
+}
+
+rbm_status rbm_forces(rbm_ctx* ctx, int32_t method, void* f_dev) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (!f_dev || (reinterpret_cast<uintptr_t>(f_dev) & 15u)) return RBM_ERR_INVALID;
+  if (method == RBM_METHOD_RBM) return enqueue_rbm(ctx, 2, nullptr, ctx->m, f_dev, ctx->stream);
+  if (method == RBM_METHOD_DIRECT) return enqueue_direct(ctx, 1, nullptr, ctx->m, nullptr, 0, f_dev, ctx->stream);
+  return RBM_ERR_INVALID;
+}
+
+rbm_status rbm_direct_forces_at(rbm_ctx* ctx, const void* q_dev, int64_t nq, void* f_dev) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (nq < 0 || nq > (int64_t(1) << 31)) return RBM_ERR_INVALID;
+  if (nq == 0) return RBM_OK;
+  if (!q_dev || !f_dev || (reinterpret_cast<uintptr_t>(q_dev) & 15u) || (reinterpret_cast<uintptr_t>(f_dev) & 15u))
+    return RBM_ERR_INVALID;
+  return enqueue_direct(ctx, 2, nullptr, ctx->m, q_dev, static_cast<uint32_t>(nq), f_dev, ctx->stream);
+}
+
+rbm_status rbm_step_profiled(rbm_ctx* ctx, int32_t method, float* kernel_ms, int32_t capacity, int32_t* nkernels,
+                             char* names, int32_t names_len) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (!kernel_ms || !nkernels || capacity < 1 || (method != RBM_METHOD_RBM && method != RBM_METHOD_DIRECT))
+    return RBM_ERR_INVALID;
+  constexpr int kMax = 16;
+  cudaEvent_t ev[kMax + 1];
+  const char* nm[kMax + 1] = {};
+  for (int i = 0; i <= kMax; ++i) RBM_CUDA(cudaEventCreate(&ev[i]));
+  int nev = 0;
+  LaunchCfg saved = ctx->cfg;
+  ctx->cfg.events = ev;
+  ctx->cfg.nevents = &nev;
+  ctx->cfg.max_events = kMax + 1;
+  ctx->cfg.names = nm;
+  mark_launch(ctx->cfg, ctx->stream, "start");
+  st = enqueue_step(ctx, method, nullptr, ctx->m, ctx->stream);
+  ctx->cfg = saved;
+  if (st == RBM_OK) {
+    ctx->m += 1;
+    cudaError_t e = cudaEventSynchronize(ev[nev - 1]);
+    const int nk = nev - 1;
+    *nkernels = nk;
+    std::string joined;
+    for (int i = 0; i < nk && i < capacity && e == cudaSuccess; ++i) {
+      e = cudaEventElapsedTime(&kernel_ms[i], ev[i], ev[i + 1]);
+      if (i) joined += ";";
+      joined += nm[i + 1] ? nm[i + 1] : "?";
+    }
+    if (names && names_len > 0) {
+      std::strncpy(names, joined.c_str(), static_cast<size_t>(names_len) - 1);
+      names[names_len - 1] = 0;
+    }
+    if (e != cudaSuccess) {
+      set_error("cudaEventElapsedTime", e);
+      st = RBM_ERR_CUDA;
+    }
+  }
+  for (int i = 0; i <= kMax; ++i) cudaEventDestroy(ev[i]);
+  if (st == RBM_OK) st = rbm_sync(ctx);
+  return st;
+}
+
+rbm_status rbm_launches_per_step(const rbm_ctx* ctx, int32_t method, int32_t* launches) {
+  if (!ctx || !launches) return RBM_ERR_INVALID;
+  if (method == RBM_METHOD_RBM) *launches = 1 + rbm_tail_launches(ctx->ps, ctx->prm.p);
+  else if (method == RBM_METHOD_DIRECT) *launches = 1;
+  else return RBM_ERR_INVALID;
+  return RBM_OK;
+}
+
+}  // extern "C"

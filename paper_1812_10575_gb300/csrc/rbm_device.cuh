@@ -1,0 +1,294 @@
+// Device-side building blocks of the RBM-1 hot path: the counter-based RNG,
+// Box-Muller Brownian increments, the interaction kernels K, -grad V, the
+// Euler-Maruyama update and row loads/stores of the N x ld position array.
+//
+// Everything here is written from the paper (arXiv:1812.10575) and from
+// Salmon et al., "Parallel random numbers: as easy as 1, 2, 3" (SC'11) for
+// Philox; no code is shared with the CPU oracle.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/rbm.h"
+
+namespace rbm {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10.  A round maps counter (c0,c1,c2,c3), key (k0,k1) to
+// (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)); the key
+// advances by the Weyl increments (W0, W1) between rounds.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k.x += kPhiloxW0;
+      k.y += kPhiloxW1;
+    }
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+constexpr uint32_t kStreamPerm = 0;
+constexpr uint32_t kStreamNoise = 1;
+
+// Permutation key of particle `id` at step m (counter word 1 = m mod 2^32).
+__device__ __forceinline__ uint64_t perm_key(uint32_t id, uint32_t m32, uint32_t replica, uint2 seed) {
+  const uint4 w = philox4x32_10(make_uint4(id, m32, replica, kStreamPerm * 256u), seed);
+  return (static_cast<uint64_t>(w.y) << 32) | w.x;
+}
+
+// ---------------------------------------------------------------------------
+// Box-Muller pair t of particle `id` at step m: u1, u2 from the 64-bit words
+// w1 = a1:a0 and w2 = a3:a2 of draw (id, m, r, 256 + t); u = ((w >> (64-b))
+// + 1) 2^-b in (0, 1] with b = 24 (FP32) or 53 (FP64);
+// z0 = sqrt(-2 ln u1) cos(2 pi u2), z1 = sqrt(-2 ln u1) sin(2 pi u2).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void normal_pair(uint4 a, float& z0, float& z1) {
+  const float u1 = static_cast<float>((a.y >> 8) + 1u) * 0x1p-24f;
+  const float u2 = static_cast<float>((a.w >> 8) + 1u) * 0x1p-24f;
+  const float rad = sqrtf(-2.0f * logf(u1));
+  float s, c;
+  sincospif(2.0f * u2, &s, &c);
+  z0 = rad * c;
+  z1 = rad * s;
+}
+
+__device__ __forceinline__ void normal_pair(uint4 a, double& z0, double& z1) {
+  const uint64_t w1 = (static_cast<uint64_t>(a.y) << 32) | a.x;
+  const uint64_t w2 = (static_cast<uint64_t>(a.w) << 32) | a.z;
+  const double u1 = static_cast<double>((w1 >> 11) + 1u) * 0x1p-53;
+  const double u2 = static_cast<double>((w2 >> 11) + 1u) * 0x1p-53;
+  const double rad = sqrt(-2.0 * log(u1));
+  double s, c;
+  sincospi(2.0 * u2, &s, &c);
+  z0 = rad * c;
+  z1 = rad * s;
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void brownian(uint32_t id, uint32_t m32, uint32_t replica, uint2 seed, T (&z)[D]) {
+#pragma unroll
+  for (int t = 0; 2 * t < D; ++t) {
+    const uint4 a = philox4x32_10(make_uint4(id, m32, replica, kStreamNoise * 256u + t), seed);
+    T z0, z1;
+    normal_pair(a, z0, z1);
+    z[2 * t] = z0;
+    if (2 * t + 1 < D) z[2 * t + 1] = z1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Positions: row i of the N x ld array, ld = D (D = 1, 2) or 4 (D = 3).
+// ---------------------------------------------------------------------------
+template <int D> struct Ld { static constexpr int value = (D == 3) ? 4 : D; };
+
+template <typename T, int D>
+struct Row {
+  T x[D];
+  T pad;  // lane 4 of a d = 3 row, preserved bit for bit
+};
+
+template <typename T, int D>
+__device__ __forceinline__ Row<T, D> load_row(const T* __restrict__ X, uint64_t i) {
+  Row<T, D> r;
+  r.pad = T(0);
+  if constexpr (D == 3 && sizeof(T) == 4) {
+    const float4 v = reinterpret_cast<const float4*>(X)[i];
+    r.x[0] = v.x; r.x[1] = v.y; r.x[2] = v.z; r.pad = v.w;
+  } else if constexpr (D == 3) {
+    const double2 a = reinterpret_cast<const double2*>(X)[2 * i];
+    const double2 b = reinterpret_cast<const double2*>(X)[2 * i + 1];
+    r.x[0] = a.x; r.x[1] = a.y; r.x[2] = b.x; r.pad = b.y;
+  } else if constexpr (D == 2 && sizeof(T) == 4) {
+    const float2 v = reinterpret_cast<const float2*>(X)[i];
+    r.x[0] = v.x; r.x[1] = v.y;
+  } else if constexpr (D == 2) {
+    const double2 v = reinterpret_cast<const double2*>(X)[i];
+    r.x[0] = v.x; r.x[1] = v.y;
+  } else {
+    r.x[0] = X[i];
+  }
+  return r;
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void store_row(T* __restrict__ X, uint64_t i, const Row<T, D>& r) {
+  if constexpr (D == 3 && sizeof(T) == 4) {
+    reinterpret_cast<float4*>(X)[i] = make_float4(r.x[0], r.x[1], r.x[2], r.pad);
+  } else if constexpr (D == 3) {
+    reinterpret_cast<double2*>(X)[2 * i] = make_double2(r.x[0], r.x[1]);
+    reinterpret_cast<double2*>(X)[2 * i + 1] = make_double2(r.x[2], r.pad);
+  } else if constexpr (D == 2 && sizeof(T) == 4) {
+    reinterpret_cast<float2*>(X)[i] = make_float2(r.x[0], r.x[1]);
+  } else if constexpr (D == 2) {
+    reinterpret_cast<double2*>(X)[i] = make_double2(r.x[0], r.x[1]);
+  } else {
+    X[i] = r.x[0];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Interaction kernels.  Every family is K(x) = s(|x|^2) x; the squared norm
+// that decides coincidence (K(0) := 0) and the bounded-confidence cut-off is
+// computed as fma(x2,x2, fma(x1,x1, x0*x0)) with round-to-nearest intrinsics
+// so the decision is reproducible in the run's precision.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float fmul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double fmul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float ffma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double ffma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fsub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double fsub_rn(double a, double b) { return __dsub_rn(a, b); }
+
+template <typename T, int D>
+__device__ __forceinline__ T sqnorm_rn(const T (&x)[D]) {
+  T r2 = fmul_rn(x[0], x[0]);
+#pragma unroll
+  for (int k = 1; k < D; ++k) r2 = ffma_rn(x[k], x[k], r2);
+  return r2;
+}
+
+// s(|x|^2) with K(x) = s x, for a non-zero squared norm r2.
+template <int KF>
+__device__ __forceinline__ float kernel_scale(float r2, float kparam, float radius_sq) {
+  if constexpr (KF == RBM_K_INV1D) {
+    return __fdividef(1.0f, r2);                 // 1/x = x / x^2
+  } else if constexpr (KF == RBM_K_COULOMB) {
+    const float ri = rsqrtf(r2);
+    return ri * ri * ri;                         // x/|x|^3
+  } else if constexpr (KF == RBM_K_BOUNDED_CONF) {
+    return (r2 < radius_sq) ? -1.0f : 0.0f;      // -x 1{|x| < R}
+  } else if constexpr (KF == RBM_K_GAUSS_AGG) {
+    return -__expf(-0.5f * r2);                  // -x exp(-|x|^2/2)
+  } else if constexpr (KF == RBM_K_REG_ATTRACT) {
+    return -__fdividef(1.0f, r2 + kparam);       // -x/(|x|^2 + eps)
+  } else if constexpr (KF == RBM_K_SMOOTH_TEST) {
+    return __fdividef(1.0f, 1.0f + r2);          // x/(1+|x|^2)
+  } else {
+    return -kparam;                              // -c x
+  }
+}
+
+template <int KF>
+__device__ __forceinline__ double kernel_scale(double r2, double kparam, double radius_sq) {
+  if constexpr (KF == RBM_K_INV1D) {
+    return 1.0 / r2;
+  } else if constexpr (KF == RBM_K_COULOMB) {
+    return 1.0 / (r2 * sqrt(r2));
+  } else if constexpr (KF == RBM_K_BOUNDED_CONF) {
+    return (r2 < radius_sq) ? -1.0 : 0.0;
+  } else if constexpr (KF == RBM_K_GAUSS_AGG) {
+    return -exp(-0.5 * r2);
+  } else if constexpr (KF == RBM_K_REG_ATTRACT) {
+    return -1.0 / (r2 + kparam);
+  } else if constexpr (KF == RBM_K_SMOOTH_TEST) {
+    return 1.0 / (1.0 + r2);
+  } else {
+    return -kparam;
+  }
+}
+
+// Runtime-dispatched form for the RBM paths (a few evaluations per particle).
+template <typename T>
+__device__ __forceinline__ T kernel_scale_rt(int kf, T r2, T kparam, T radius_sq) {
+  switch (kf) {
+    case RBM_K_INV1D: return kernel_scale<RBM_K_INV1D>(r2, kparam, radius_sq);
+    case RBM_K_COULOMB: return kernel_scale<RBM_K_COULOMB>(r2, kparam, radius_sq);
+    case RBM_K_BOUNDED_CONF: return kernel_scale<RBM_K_BOUNDED_CONF>(r2, kparam, radius_sq);
+    case RBM_K_GAUSS_AGG: return kernel_scale<RBM_K_GAUSS_AGG>(r2, kparam, radius_sq);
+    case RBM_K_REG_ATTRACT: return kernel_scale<RBM_K_REG_ATTRACT>(r2, kparam, radius_sq);
+    case RBM_K_SMOOTH_TEST: return kernel_scale<RBM_K_SMOOTH_TEST>(r2, kparam, radius_sq);
+    default: return kernel_scale<RBM_K_LINEAR>(r2, kparam, radius_sq);
+  }
+}
+
+// acc += K(xi - xj), runtime kernel family.
+template <typename T, int D>
+__device__ __forceinline__ void add_pair_force_rt(int kf, T kparam, T radius_sq, const T (&xi)[D], const T (&xj)[D],
+                                                  T (&acc)[D]) {
+  T x[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) x[k] = fsub_rn(xi[k], xj[k]);
+  const T r2 = sqnorm_rn<T, D>(x);
+  const T s = (r2 == T(0)) ? T(0) : kernel_scale_rt<T>(kf, r2, kparam, radius_sq);
+#pragma unroll
+  for (int k = 0; k < D; ++k) acc[k] += s * x[k];
+}
+
+// ---------------------------------------------------------------------------
+// Parameters of one step as the kernels see them.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct StepParams {
+  T* x;               // positions, N x ld (in place for RBM)
+  T* xout;            // direct step output / generic-batch staging, N x ld
+  T* fout;            // diagnostic force output, N x ld (or null)
+  int32_t* status;    // latched device status
+  uint32_t n;
+  int32_t p;
+  int32_t kf;         // rbm_kernel
+  int32_t vkind;      // rbm_potential
+  int32_t renorm;
+  int32_t scheme;     // rbm_scheme
+  T dt, sq;           // tau, sigma sqrt(tau)
+  T vcoef, kparam, radius_sq;
+  uint2 seed;
+  uint32_t replica;
+  const int64_t* m_ptr;  // step counter in device memory (graph replay) or null
+  int64_t m_off;         // added to *m_ptr (or the step itself when m_ptr is null)
+};
+
+template <typename T>
+__device__ __forceinline__ uint32_t step_index(const StepParams<T>& a) {
+  const int64_t m = (a.m_ptr ? *a.m_ptr : 0) + a.m_off;
+  return static_cast<uint32_t>(static_cast<uint64_t>(m));
+}
+
+__device__ __forceinline__ void latch_status(int32_t* status, int32_t code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+template <typename T> __device__ __forceinline__ bool finite_val(T v) { return isfinite(v); }
+
+// y = x + dt (fk - grad V(x)) + sigma sqrt(dt) z, then the optional projection
+// onto the unit sphere; latches RBM_ERR_NONFINITE on a non-finite result.
+template <typename T, int D>
+__device__ __forceinline__ void euler_update(const StepParams<T>& a, uint32_t id, uint32_t m32, const T (&x)[D],
+                                             const T (&fk)[D], T (&y)[D]) {
+  T z[D];
+  if (a.sq != T(0)) {
+    brownian<T, D>(id, m32, a.replica, a.seed, z);
+  } else {
+#pragma unroll
+    for (int k = 0; k < D; ++k) z[k] = T(0);
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const T fv = (a.vkind == RBM_V_QUADRATIC) ? -a.vcoef * x[k] : T(0);
+    y[k] = x[k] + a.dt * (fk[k] + fv) + a.sq * z[k];
+  }
+  if (a.renorm) {
+    T nrm = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) nrm += y[k] * y[k];
+    nrm = sqrt(nrm);
+#pragma unroll
+    for (int k = 0; k < D; ++k) y[k] = y[k] / nrm;
+  }
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < D; ++k) ok = ok && finite_val(y[k]);
+  if (!ok) latch_status(a.status, RBM_ERR_NONFINITE);
+}
+
+}  // namespace rbm

@@ -1,0 +1,65 @@
+// Internal declarations shared by the library's translation units: scratch
+// layout of a context and the host-side launchers of each kernel.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/rbm.h"
+
+namespace rbm {
+
+// Permutation scratch (one particle system or one replica set).
+struct PermScratch {
+  uint32_t* cnt = nullptr;      // [nbuckets] members per bucket (zero between steps)
+  uint32_t* start = nullptr;    // [nbuckets] first sorted position of each bucket
+  uint32_t* slots = nullptr;    // [nbuckets * slot_cap] member ids, bucket-major
+  uint32_t* ovf_cnt = nullptr;  // [1] members that did not fit their bucket's slots
+  uint32_t* ovf = nullptr;      // [n] those members' ids
+  uint32_t* done = nullptr;     // [1] finished-block ticket (last block runs the fix-up)
+  uint32_t* perm = nullptr;     // [n] the random permutation of this step
+  int bucket_bits = 0;
+  uint32_t nbuckets = 1;
+  uint32_t slot_cap = 0;
+  uint32_t sort_cap = 0;
+  bool separate_scan = false;   // large bucket counts: scan and fix-up kernels of their own
+};
+
+struct LaunchCfg {
+  int block = 256;
+  int direct_block = 256;
+  int num_sms = 152;
+  // Profiling: when `events` is set, every launcher records events[(*nevents)++]
+  // on its stream after each kernel and appends the kernel's name to `names`.
+  cudaEvent_t* events = nullptr;
+  int* nevents = nullptr;
+  int max_events = 0;
+  const char** names = nullptr;
+};
+
+// Record a profiling event after a launch (no-op unless profiling).
+inline void mark_launch(const LaunchCfg& cfg, cudaStream_t st, const char* name) {
+  if (!cfg.events || !cfg.nevents || *cfg.nevents >= cfg.max_events) return;
+  if (cfg.names) cfg.names[*cfg.nevents] = name;
+  cudaEventRecord(cfg.events[*cfg.nevents], st);
+  ++*cfg.nevents;
+}
+
+// RBM step pieces (perm_step.cu).  `mode`: 0 = write the permutation only,
+// 1 = step, 2 = interaction forces only.
+void launch_bucket_scatter(const PermScratch& ps, uint32_t n, uint2 seed, uint32_t replica, const int64_t* m_ptr,
+                           int64_t m_off, const LaunchCfg& cfg, cudaStream_t st);
+template <typename T>
+void launch_rbm_tail(const PermScratch& ps, int d, int mode, const void* params, const LaunchCfg& cfg, cudaStream_t st);
+cudaError_t prepare_rbm_kernels();  // per-device kernel attributes, called by rbm_init
+void launch_set_i64(int64_t* dst, int64_t value, cudaStream_t st);
+void launch_add_i64(int64_t* dst, int64_t value, cudaStream_t st);
+int rbm_tail_launches(const PermScratch& ps, int p);
+
+// Direct O(N^2) pieces (direct.cu).  `mode`: 0 = step (into xout), 1 =
+// forces at the particles (into fout), 2 = forces at query points.
+template <typename T>
+void launch_direct(int d, int mode, const void* params, const T* q, uint32_t nq, const LaunchCfg& cfg,
+                   cudaStream_t st);
+
+}  // namespace rbm
