@@ -196,6 +196,26 @@ rbm_status rbm_direct_forces_at(rbm_ctx *ctx, const void *q_dev, int64_t nq, voi
 rbm_status rbm_step_profiled(rbm_ctx *ctx, int32_t method, float *kernel_ms, int32_t capacity, int32_t *nkernels,
                              char *names, int32_t names_len);
 
+/* ---- without allocation ------------------------------------------------ */
+
+/* The random division of step m (the same ids, in the same order, as
+ * rbm_permutation gives for a context with this n, seed and replica at step
+ * m) written to perm_dev (n uint32, device, caller-owned), computed without
+ * allocating memory.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory - an application whose
+ * memory manager owns all of it, or a loop that must not block on or fail in
+ * cudaMalloc.  It needs no context; its scratch is a fixed array of about
+ * 650 KB in device memory that each GPU loading the library holds until exit.
+ *   n: 2 .. 65536; larger n returns RBM_ERR_INVALID (rbm_last_error says why).
+ *   cuda_stream: the work is enqueued there (cudaStream_t as void*); the call
+ *   returns without waiting.
+ * The first call on a device looks up the array's address (with that device
+ * current); make it before any stream capture on that device.  All calls on a
+ * device share the array: each clears what must start at zero, so calls in
+ * sequence are fine, but calls whose work overlaps on the GPU race on it. */
+rbm_status rbm_permutation_noalloc(int64_t n, uint64_t seed, uint32_t replica, int64_t m, uint32_t *perm_dev,
+                                   void *cuda_stream);
+
 /* Number of kernel launches one step of `method` enqueues (for accounting). */
 rbm_status rbm_launches_per_step(const rbm_ctx *ctx, int32_t method, int32_t *launches);
 

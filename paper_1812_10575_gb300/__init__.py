@@ -16,7 +16,7 @@ from __future__ import annotations
 from ._lib import (  # noqa: F401
     EXPORTS, KERNELS, METHODS, POTENTIALS, SCHEMES, RbmError, RbmParams, RbmTuning, library_path, load,
     make_params, rbm_direct_forces_at, rbm_direct_step, rbm_forces, rbm_free, rbm_get_step, rbm_get_tuning,
-    rbm_init, rbm_last_error, rbm_launches_per_step, rbm_permutation, rbm_run, rbm_set_step, rbm_set_tuning,
+    rbm_init, rbm_last_error, rbm_launches_per_step, rbm_permutation, rbm_permutation_noalloc, rbm_run, rbm_set_step, rbm_set_tuning,
     rbm_status_string, rbm_step, rbm_step_host, rbm_step_profiled, rbm_sync,
 )
 

@@ -41,6 +41,7 @@ EXPORTS = (
     "rbm_init", "rbm_step", "rbm_direct_step", "rbm_run", "rbm_step_host", "rbm_get_step", "rbm_set_step",
     "rbm_set_tuning", "rbm_get_tuning", "rbm_sync", "rbm_free", "rbm_status_string", "rbm_last_error",
     "rbm_permutation", "rbm_forces", "rbm_direct_forces_at", "rbm_step_profiled", "rbm_launches_per_step",
+    "rbm_permutation_noalloc",
 )
 
 
@@ -115,6 +116,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "rbm_forces": [vp, i32, vp],
         "rbm_direct_forces_at": [vp, vp, i64, vp],
         "rbm_launches_per_step": [vp, i32, ctypes.POINTER(i32)],
+        "rbm_permutation_noalloc": [i64, ctypes.c_uint64, ctypes.c_uint32, i64, vp, vp],
         "rbm_step_profiled": [vp, i32, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(i32), ctypes.c_char_p,
                               i32],
     }
@@ -250,6 +252,16 @@ def rbm_step_profiled(ctx, method="rbm"):
     _check(load().rbm_step_profiled(ctx, METHODS.get(method, method), ms, 16, ctypes.byref(nk), names, 512),
            "rbm_step_profiled")
     return list(zip(names.value.decode().split(";"), [ms[i] for i in range(nk.value)]))
+
+
+def rbm_permutation_noalloc(n: int, seed: int, replica: int, m: int, perm, stream=None) -> None:
+    """Random division of step ``m`` into ``perm`` (int32 CUDA tensor of n
+    entries) with no device allocation (n <= 65536); see include/rbm.h."""
+    if perm.numel() < n:
+        raise ValueError("perm holds fewer than n entries")
+    _check(load().rbm_permutation_noalloc(int(n), int(seed), int(replica), int(m),
+                                          ctypes.c_void_p(_dev_ptr(perm)), ctypes.c_void_p(_stream_handle(stream))),
+           "rbm_permutation_noalloc")
 
 
 def rbm_launches_per_step(ctx, method="rbm") -> int:

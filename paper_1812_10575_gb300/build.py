@@ -25,6 +25,7 @@ UNITS = [
     ("perm_step.cu", []),
     ("direct.cu", ["-DRBM_DIRECT_F32"]),
     ("direct.cu", ["-DRBM_DIRECT_F64"]),
+    ("noalloc.cu", []),
 ]
 
 

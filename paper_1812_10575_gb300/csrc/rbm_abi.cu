@@ -242,6 +242,8 @@ rbm_status capture_graph(rbm_ctx* c, int32_t method, int64_t len) {
 
 }  // namespace
 
+void rbm::set_last_error_text(const char* text) { snprintf(g_last_error, sizeof(g_last_error), "%s", text); }
+
 extern "C" {
 
 const char* rbm_last_error(void) { return g_last_error; }

@@ -51,6 +51,7 @@ void launch_bucket_scatter(const PermScratch& ps, uint32_t n, uint2 seed, uint32
                            int64_t m_off, const LaunchCfg& cfg, cudaStream_t st);
 template <typename T>
 void launch_rbm_tail(const PermScratch& ps, int d, int mode, const void* params, const LaunchCfg& cfg, cudaStream_t st);
+void set_last_error_text(const char* text);  // text returned by rbm_last_error()
 cudaError_t prepare_rbm_kernels();  // per-device kernel attributes, called by rbm_init
 void launch_set_i64(int64_t* dst, int64_t value, cudaStream_t st);
 void launch_add_i64(int64_t* dst, int64_t value, cudaStream_t st);
