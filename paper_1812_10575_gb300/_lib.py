@@ -72,6 +72,9 @@ class RbmTuning(ctypes.Structure):
         ("block", ctypes.c_int32),
         ("direct_block", ctypes.c_int32),
         ("graph_steps", ctypes.c_int32),
+        ("path", ctypes.c_int32),
+        ("wait_limit_us", ctypes.c_int32),
+        ("test_skip_arrival", ctypes.c_int32),
     ]
 
 

@@ -26,6 +26,7 @@ UNITS = [
     ("direct.cu", ["-DRBM_DIRECT_F32"]),
     ("direct.cu", ["-DRBM_DIRECT_F64"]),
     ("noalloc.cu", []),
+    ("coop_step.cu", []),
 ]
 
 

@@ -22,16 +22,13 @@
 // positions of step m as the explicit scheme requires.
 #include <cstdio>
 
+#include "rbm_batch.cuh"
 #include "rbm_device.cuh"
 #include "rbm_internal.h"
 
 namespace rbm {
 
 namespace {
-
-constexpr int kModePerm = 0;
-constexpr int kModeStep = 1;
-constexpr int kModeForces = 2;
 
 __device__ __forceinline__ uint32_t bucket_of(uint64_t key, int bits) {
   return bits ? static_cast<uint32_t>(key >> (64 - bits)) : 0u;
@@ -162,123 +159,6 @@ __device__ void bitonic_sort(uint64_t* skey, uint32_t* sid, uint32_t p2) {
       }
       __syncthreads();
     }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// One batch per group of p consecutive lanes (p <= 32).  All 32 lanes of the
-// warp call this together (the shuffles use the full mask); lanes outside a
-// valid batch member pass valid = false and store nothing.
-//   bs    - members of this batch (p, or N mod p for the last batch)
-//   lg    - this lane's index inside its group
-// ---------------------------------------------------------------------------
-template <typename T, int D, int MODE>
-__device__ __forceinline__ void batch_group(const StepParams<T>& a, uint32_t m32, uint32_t id, bool valid, int lg,
-                                            int bs) {
-  const int p = a.p;
-  const int lane = threadIdx.x & 31;
-  const int base = lane - lg;
-  Row<T, D> r;
-  if (valid) {
-    r = load_row<T, D>(a.x, id);
-  } else {
-#pragma unroll
-    for (int k = 0; k < D; ++k) r.x[k] = T(0);
-    r.pad = T(0);
-  }
-  T fk[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) fk[k] = T(0);
-
-  if (MODE == kModeStep && a.scheme == RBM_SCHEME_SPLIT) {
-    // Exact pair flow of K (p = 2), then the Euler-Maruyama step of V and noise.
-    const int src = base + (lg ^ 1);
-    T xj[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) xj[k] = __shfl_sync(0xffffffffu, r.x[k], src);
-    if (!valid) return;
-    T y0[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) y0[k] = r.x[k];
-    if (bs == 2) {
-      T delta[D], mid[D];
-      T len2 = T(0);
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        delta[k] = r.x[k] - xj[k];
-        mid[k] = T(0.5) * (r.x[k] + xj[k]);
-        len2 += delta[k] * delta[k];
-      }
-      T dd[D];
-#pragma unroll
-      for (int k = 0; k < D; ++k) dd[k] = fsub_rn(r.x[k], xj[k]);
-      if (sqnorm_rn<T, D>(dd) != T(0)) {
-        const T len = sqrt(len2);
-        const T newlen = (a.kf == RBM_K_INV1D) ? sqrt(len2 + T(4) * a.dt) : cbrt(len2 * len + T(6) * a.dt);
-#pragma unroll
-        for (int k = 0; k < D; ++k) y0[k] = mid[k] + T(0.5) * newlen * (delta[k] / len);
-      }
-    }
-    T y[D];
-    euler_update<T, D>(a, id, m32, y0, fk, y);
-#pragma unroll
-    for (int k = 0; k < D; ++k) r.x[k] = y[k];
-    store_row<T, D>(a.x, id, r);
-    return;
-  }
-
-  for (int j = 1; j < p; ++j) {
-    int sg = lg + j;
-    if (sg >= p) sg -= p;
-    T xj[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) xj[k] = __shfl_sync(0xffffffffu, r.x[k], base + sg);
-    if (valid && sg < bs) add_pair_force_rt<T, D>(a.kf, a.kparam, a.radius_sq, r.x, xj, fk);
-  }
-  if (!valid) return;
-  const T inv = (bs > 1) ? T(1) / static_cast<T>(bs - 1) : T(0);
-#pragma unroll
-  for (int k = 0; k < D; ++k) fk[k] = (bs > 1) ? fk[k] * inv : T(0);
-  if (MODE == kModeForces) {
-    Row<T, D> f;
-#pragma unroll
-    for (int k = 0; k < D; ++k) f.x[k] = fk[k];
-    f.pad = T(0);
-    store_row<T, D>(a.fout, id, f);
-    return;
-  }
-  T y[D];
-  euler_update<T, D>(a, id, m32, r.x, fk, y);
-#pragma unroll
-  for (int k = 0; k < D; ++k) r.x[k] = y[k];
-  store_row<T, D>(a.x, id, r);
-}
-
-// Steps the batches whose first sorted position is q0 + k (k < count), ids
-// read from `ids` at offset (batch start - ids_base).  Warp-uniform loop.
-template <typename T, int D, int MODE>
-__device__ void step_batches(const StepParams<T>& a, uint32_t m32, const uint32_t* ids, uint32_t ids_base,
-                             uint32_t q0, uint32_t count) {
-  const int p = a.p;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int gpw = 32 / p;                       // batch groups per warp
-  const int nwarps = blockDim.x >> 5;
-  const uint32_t per_round = static_cast<uint32_t>(gpw * nwarps);
-  const int g = lane / p, lg = lane - g * p;
-  for (uint32_t r0 = 0; r0 < count; r0 += per_round) {
-    const uint32_t kb = r0 + static_cast<uint32_t>(warp * gpw + g);
-    bool valid = (g < gpw) && (kb < count);
-    uint32_t id = 0;
-    int bs = p;
-    if (valid) {
-      const uint32_t q = q0 + kb;
-      const uint32_t lo = q * static_cast<uint32_t>(p);
-      const uint32_t hi = min(lo + static_cast<uint32_t>(p), a.n);
-      bs = static_cast<int>(hi - lo);
-      valid = lg < bs;
-      if (valid) id = ids[lo + lg - ids_base];
-    }
-    batch_group<T, D, MODE>(a, m32, id, valid, lg, bs);
   }
 }
 

@@ -24,6 +24,9 @@ struct rbm_ctx {
   int64_t* m_dev = nullptr;     // device step counter read by graph replays
   void* xtmp = nullptr;         // second position buffer (direct step, generic batches)
   PermScratch ps;
+  CoopScratch cs;
+  bool use_coop = false;
+  int coop_blocks_per_sm = 0;
   LaunchCfg cfg;
   rbm_tuning tuning{};
   int32_t latched = RBM_OK;     // host copy of a device error
@@ -75,6 +78,8 @@ void free_scratch(rbm_ctx* c) {
   cudaFree(s.cnt); cudaFree(s.start); cudaFree(s.slots); cudaFree(s.ovf_cnt); cudaFree(s.ovf);
   cudaFree(s.done); cudaFree(s.perm);
   s = PermScratch{};
+  cudaFree(c->cs.hist); cudaFree(c->cs.tmp); cudaFree(c->cs.bar);
+  c->cs = CoopScratch{};
   cudaFree(c->xtmp);
   c->xtmp = nullptr;
 }
@@ -132,6 +137,26 @@ rbm_status alloc_scratch(rbm_ctx* c) {
   RBM_CUDA(cudaMemset(s.done, 0, sizeof(uint32_t)));
   c->cfg.block = c->tuning.block > 0 ? c->tuning.block : 256;
   c->cfg.direct_block = c->tuning.direct_block > 0 ? c->tuning.direct_block : 256;
+
+  // Cooperative single-kernel path: one block per SM, B = k * grid buckets of
+  // at most ~2048 members on average, B <= 1024; batches of at most a warp.
+  const uint32_t grid = static_cast<uint32_t>(c->cfg.num_sms);
+  const uint32_t k = static_cast<uint32_t>((static_cast<uint64_t>(n) + static_cast<uint64_t>(grid) *
+                                            coop_bucket_target() - 1) / (static_cast<uint64_t>(grid) *
+                                                                         coop_bucket_target()));
+  const bool coop_fits = c->coop_blocks_per_sm >= 1 && c->prm.p <= 32 && k >= 1 && k * grid <= coop_max_buckets();
+  c->use_coop = (c->tuning.path == 2 || c->tuning.path == 0) && coop_fits;
+  if (c->use_coop) {
+    CoopScratch& cs = c->cs;
+    cs.grid = grid;
+    cs.nbuckets = k * grid;
+    RBM_CUDA(cudaMalloc(&cs.hist, sizeof(uint32_t) * cs.nbuckets));
+    RBM_CUDA(cudaMemset(cs.hist, 0, sizeof(uint32_t) * cs.nbuckets));
+    RBM_CUDA(cudaMalloc(&cs.tmp, sizeof(uint32_t) * n));
+    RBM_CUDA(cudaMalloc(&cs.bar, sizeof(unsigned long long)));
+    RBM_CUDA(cudaMemset(cs.bar, 0, sizeof(unsigned long long)));
+    cs.perm = s.perm;
+  }
   return RBM_OK;
 }
 
@@ -167,6 +192,31 @@ uint2 seed_of(const rbm_ctx* c) {
 
 // Enqueue one RBM step (mode 1), the permutation only (0) or the forces (2).
 rbm_status enqueue_rbm(rbm_ctx* c, int mode, const int64_t* m_ptr, int64_t m_off, void* fout, cudaStream_t st) {
+  if (c->use_coop) {
+    const uint64_t wait_ns = 1000ull * static_cast<uint64_t>(c->tuning.wait_limit_us > 0 ? c->tuning.wait_limit_us
+                                                                                          : 1000000);
+    const int skip = c->tuning.test_skip_arrival;
+    // Graph replay: the kernel reads the step index from m_ptr and advances
+    // it itself once every block has read it, so each captured step reads
+    // the counter with offset 0.
+    const bool bump = (m_ptr != nullptr);
+    if (bump) m_off = 0;
+    cudaError_t e;
+    if (c->prm.dtype == RBM_F32) {
+      StepParams<float> a = step_params<float>(c, m_ptr, m_off);
+      a.fout = static_cast<float*>(fout);
+      e = launch_coop<float>(c->cs, c->prm.d, mode, &a, wait_ns, skip, bump, c->cfg, st);
+    } else {
+      StepParams<double> a = step_params<double>(c, m_ptr, m_off);
+      a.fout = static_cast<double*>(fout);
+      e = launch_coop<double>(c->cs, c->prm.d, mode, &a, wait_ns, skip, bump, c->cfg, st);
+    }
+    if (e != cudaSuccess) {
+      set_error("cudaLaunchKernelEx (cooperative)", e);
+      return RBM_ERR_CUDA;
+    }
+    return RBM_OK;
+  }
   launch_bucket_scatter(c->ps, static_cast<uint32_t>(c->prm.n), seed_of(c), c->prm.replica, m_ptr, m_off, c->cfg,
                         st);
   if (c->prm.dtype == RBM_F32) {
@@ -218,7 +268,9 @@ rbm_status capture_graph(rbm_ctx* c, int32_t method, int64_t len) {
   RBM_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
   rbm_status st = RBM_OK;
   for (int64_t s = 0; s < len && st == RBM_OK; ++s) st = enqueue_step(c, method, c->m_dev, s, c->cap_stream);
-  if (st == RBM_OK) launch_add_i64(c->m_dev, len, c->cap_stream);
+  // The cooperative RBM kernel advances the device step counter itself.
+  const bool self_bumping = (method == RBM_METHOD_RBM && c->use_coop);
+  if (st == RBM_OK && !self_bumping) launch_add_i64(c->m_dev, len, c->cap_stream);
   cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
   if (st != RBM_OK) {
     if (g) cudaGraphDestroy(g);
@@ -282,7 +334,8 @@ rbm_status rbm_init(const rbm_params* prm, void* x_dev, void* cuda_stream, rbm_c
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
     c->cfg.num_sms = sms;
   {
-    const cudaError_t e = prepare_rbm_kernels();
+    cudaError_t e = prepare_rbm_kernels();
+    if (e == cudaSuccess) e = prepare_coop_kernels(&c->coop_blocks_per_sm);
     if (e != cudaSuccess) {
       set_error("prepare_rbm_kernels", e);
       delete c;
@@ -399,7 +452,8 @@ rbm_status rbm_set_tuning(rbm_ctx* ctx, const rbm_tuning* tuning) {
   if (st != RBM_OK) return st;
   if (!tuning) return RBM_ERR_INVALID;
   if (tuning->bucket_bits < 0 || tuning->bucket_bits > 24 || tuning->slot_cap < 0 || tuning->sort_cap < 0 ||
-      tuning->sort_cap > 4096 || tuning->graph_steps < 0)
+      tuning->sort_cap > 4096 || tuning->graph_steps < 0 || tuning->path < 0 || tuning->path > 2 ||
+      tuning->wait_limit_us < 0 || tuning->test_skip_arrival < 0 || tuning->test_skip_arrival > 1)
     return RBM_ERR_INVALID;
   if ((tuning->block != 0 && tuning->block != 256) ||
       (tuning->direct_block != 0 && (tuning->direct_block < 32 || tuning->direct_block > 1024 ||
@@ -427,6 +481,7 @@ rbm_status rbm_get_tuning(const rbm_ctx* ctx, rbm_tuning* tuning) {
   tuning->sort_cap = static_cast<int32_t>(ctx->ps.sort_cap);
   tuning->block = ctx->cfg.block;
   tuning->direct_block = ctx->cfg.direct_block;
+  tuning->path = ctx->use_coop ? 2 : 1;
   return RBM_OK;
 }
 
@@ -518,7 +573,7 @@ rbm_status rbm_step_profiled(rbm_ctx* ctx, int32_t method, float* kernel_ms, int
 
 rbm_status rbm_launches_per_step(const rbm_ctx* ctx, int32_t method, int32_t* launches) {
   if (!ctx || !launches) return RBM_ERR_INVALID;
-  if (method == RBM_METHOD_RBM) *launches = 1 + rbm_tail_launches(ctx->ps, ctx->prm.p);
+  if (method == RBM_METHOD_RBM) *launches = ctx->use_coop ? 1 : 1 + rbm_tail_launches(ctx->ps, ctx->prm.p);
   else if (method == RBM_METHOD_DIRECT) *launches = 1;
   else return RBM_ERR_INVALID;
   return RBM_OK;

@@ -25,6 +25,16 @@ struct PermScratch {
   bool separate_scan = false;   // large bucket counts: scan and fix-up kernels of their own
 };
 
+// Cooperative single-kernel step scratch.
+struct CoopScratch {
+  uint32_t* hist = nullptr;     // [nbuckets] bucket totals, zero between steps
+  uint32_t* tmp = nullptr;      // [n] ids grouped by bucket
+  uint32_t* perm = nullptr;     // [n] (shared with PermScratch::perm)
+  unsigned long long* bar = nullptr;  // [1] grid barrier arrival counter
+  uint32_t grid = 0;            // blocks (one per SM)
+  uint32_t nbuckets = 0;        // k * grid
+};
+
 struct LaunchCfg {
   int block = 256;
   int direct_block = 256;
@@ -56,6 +66,14 @@ cudaError_t prepare_rbm_kernels();  // per-device kernel attributes, called by r
 void launch_set_i64(int64_t* dst, int64_t value, cudaStream_t st);
 void launch_add_i64(int64_t* dst, int64_t value, cudaStream_t st);
 int rbm_tail_launches(const PermScratch& ps, int p);
+
+// Cooperative step (coop_step.cu): mode as for launch_rbm_tail.
+cudaError_t prepare_coop_kernels(int* blocks_per_sm);
+uint32_t coop_max_buckets();
+uint32_t coop_bucket_target();
+template <typename T>
+cudaError_t launch_coop(const CoopScratch& cs, int d, int mode, const void* params, uint64_t wait_ns, int skip_arrival,
+                        bool bump_step, const LaunchCfg& cfg, cudaStream_t st);
 
 // Direct O(N^2) pieces (direct.cu).  `mode`: 0 = step (into xout), 1 =
 // forces at the particles (into fout), 2 = forces at query points.

@@ -48,7 +48,8 @@ int main(void) {
   F(rbm_params, k_param); F(rbm_params, flags); F(rbm_params, scheme); F(rbm_params, replica);
   printf("rbm_tuning %zu\n", sizeof(rbm_tuning));
   F(rbm_tuning, bucket_bits); F(rbm_tuning, slot_cap); F(rbm_tuning, sort_cap); F(rbm_tuning, block);
-  F(rbm_tuning, direct_block); F(rbm_tuning, graph_steps);
+  F(rbm_tuning, direct_block); F(rbm_tuning, graph_steps); F(rbm_tuning, path); F(rbm_tuning, wait_limit_us);
+  F(rbm_tuning, test_skip_arrival);
   return 0;
 }
 """

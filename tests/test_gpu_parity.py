@@ -46,13 +46,16 @@ def _oprm(n, d, dtype, **kw):
 # ---------------------------------------------------------------------------
 # permutation: bit-exact
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("path", [1, 2])
 @pytest.mark.parametrize("n,seed,m,r", [(2, 0, 0, 0), (3, 1, 5, 0), (7, 3, 9, 2), (513, 0, 1, 0), (1000, 0, 0, 0),
                                         (1001, 5, 17, 3), (4097, 9, 2**31 + 5, 1), (100000, 0, 123, 0),
-                                        (300001, 2**40 + 7, 7, 0)])
-def test_permutation_bit_exact(n, seed, m, r):
+                                        (300001, 2**40 + 7, 7, 0), (900000, 3, 1, 0)])
+def test_permutation_bit_exact(n, seed, m, r, path):
     torch = torch_cuda()
     X = np.zeros((n, 1))
     s, _ = _system(X, 1, "f32", p=2, seed=seed, replica=r)
+    s.set_tuning(path=path)
+    assert s.tuning()["path"] == path
     s.m = m
     perm = s.permutation().cpu().numpy().view(np.uint32)
     s.sync()
@@ -62,10 +65,11 @@ def test_permutation_bit_exact(n, seed, m, r):
     del torch
 
 
-@pytest.mark.parametrize("tuning", [dict(bucket_bits=3, slot_cap=4, sort_cap=8),      # spill + counting sort
-                                    dict(bucket_bits=6, slot_cap=8, sort_cap=4096),   # spill list merged in smem
-                                    dict(bucket_bits=0, sort_cap=4096),               # one bucket
-                                    dict(bucket_bits=12)])                            # separate scan + fix-up
+@pytest.mark.parametrize("tuning", [dict(path=1, bucket_bits=3, slot_cap=4, sort_cap=8),     # spill + counting
+                                    dict(path=1, bucket_bits=6, slot_cap=8, sort_cap=4096),  # spill list in smem
+                                    dict(path=1, bucket_bits=0, sort_cap=4096),              # one bucket
+                                    dict(path=1, bucket_bits=12),                            # separate scan
+                                    dict(path=2)])                                           # cooperative kernel
 @pytest.mark.parametrize("p", [2, 5, 40])
 def test_permutation_and_step_under_forced_bucket_paths(tuning, p):
     n, d = 3000, 2
@@ -95,12 +99,14 @@ def _cases():
     return out
 
 
+@pytest.mark.parametrize("path", [1, 2])
 @pytest.mark.parametrize("k,d,p", _cases())
-def test_rbm_and_direct_forces_fp64(k, d, p):
+def test_rbm_and_direct_forces_fp64(k, d, p, path):
     n = 997
     X = workloads.gaussian(n, d, seed=d * 31 + p)
     kw = dict(p=p, seed=p, k=k, k_param=kparam(k))
     s, x = _system(X, d, "f64", **kw)
+    s.set_tuning(path=path)
     s.m = 5
     f_rbm = from_dev(s.forces("rbm"), d)
     f_dir = from_dev(s.forces("direct"), d)
@@ -139,10 +145,12 @@ def _initial(name, n, d):
     return workloads.gaussian(n, d, seed=3)
 
 
+@pytest.mark.parametrize("path", [1, 2])
 @pytest.mark.parametrize("name,n,d,kw", FP64_RUNS, ids=[r[0] for r in FP64_RUNS])
-def test_rbm_fp64_ten_steps(name, n, d, kw):
+def test_rbm_fp64_ten_steps(name, n, d, kw, path):
     X = _initial(name, n, d)
     s, x = _system(X, d, "f64", seed=0, **kw)
+    s.set_tuning(path=path)
     s.run(10)
     s.sync()
     prm = _oprm(n, d, "f64", seed=0, **kw)
@@ -234,10 +242,12 @@ def _initial32(name, n, d):
     return workloads.gaussian(n, d, seed=0)
 
 
+@pytest.mark.parametrize("path", [1, 2])
 @pytest.mark.parametrize("name,n,d,kw", FP32_RUNS, ids=[r[0] for r in FP32_RUNS])
-def test_rbm_fp32_per_step(name, n, d, kw):
+def test_rbm_fp32_per_step(name, n, d, kw, path):
     X = as_run_precision(_initial32(name, n, d), "f32")
     s, x = _system(X, d, "f32", seed=1, **kw)
+    s.set_tuning(path=path)
     prm = _oprm(n, d, "f32", seed=1, **kw)
     cur = X
     for m in range(3):
@@ -288,13 +298,15 @@ def test_direct_forces_at_queries(dtype):
 # ---------------------------------------------------------------------------
 # behaviour of the boundary
 # ---------------------------------------------------------------------------
-def test_graph_replay_equals_eager_steps():
+@pytest.mark.parametrize("path", [1, 2])
+def test_graph_replay_equals_eager_steps(path):
     n, d = 20000, 3
     X = workloads.gaussian(n, d, seed=5)
     kw = dict(p=2, dt=1e-3, sigma=0.2, v="quadratic", k="reg_attract", k_param=0.01)
     a, xa = _system(X, d, "f32", **kw)
     b, xb = _system(X, d, "f32", **kw)
-    a.set_tuning(graph_steps=7)
+    a.set_tuning(graph_steps=7, path=path)
+    b.set_tuning(path=path)
     a.run(23)                       # 3 graph replays + 2 eager steps
     for _ in range(23):
         b.step()
@@ -347,3 +359,26 @@ def test_invalid_parameters_rejected():
         with pytest.raises(rbm.RbmError) as e:
             rbm.System(x if d == 1 else torch.zeros(100, d, device="cuda", dtype=torch.float64), d=d, **kw)
         assert e.value.status == -1
+
+
+def test_cooperative_barrier_wait_runs_out_and_is_reported():
+    """A bounded grid-barrier wait that runs out: block 0 of the cooperative
+    step is told (host-side hook) to leave before the first barrier, the other
+    blocks' waits end after 20 ms and the step reports RBM_ERR_TIMEOUT.  The
+    first phase writes no positions, so the state is untouched."""
+    n, d = 50000, 2
+    X = workloads.gaussian(n, d, seed=1)
+    s, x = _system(X, d, "f32", p=2, k="gauss_agg")
+    s.set_tuning(path=2, wait_limit_us=20000, test_skip_arrival=1)
+    before = x.clone()
+    s.step()
+    with pytest.raises(rbm.RbmError) as e:
+        s.sync()
+    assert e.value.status == -4
+    assert np.array_equal(before.cpu().numpy(), x.cpu().numpy())
+    s.close()
+    # a fresh context on the same device works normally afterwards
+    t, y = _system(X, d, "f32", p=2, k="gauss_agg")
+    t.set_tuning(path=2)
+    t.step()
+    t.sync()
