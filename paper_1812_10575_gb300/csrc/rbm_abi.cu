@@ -1,5 +1,6 @@
 // C ABI of the library (include/rbm.h): context life cycle, parameter
 // checks, scratch sizing, step dispatch and CUDA-graph replay.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -23,6 +24,8 @@ struct rbm_ctx {
   int32_t* status = nullptr;    // device
   int64_t* m_dev = nullptr;     // device step counter read by graph replays
   void* xtmp = nullptr;         // second position buffer (direct step, generic batches)
+  void* partial = nullptr;      // direct-sum partial forces, partial_rows rows
+  size_t partial_rows = 0;
   PermScratch ps;
   CoopScratch cs;
   bool use_coop = false;
@@ -82,6 +85,9 @@ void free_scratch(rbm_ctx* c) {
   c->cs = CoopScratch{};
   cudaFree(c->xtmp);
   c->xtmp = nullptr;
+  cudaFree(c->partial);
+  c->partial = nullptr;
+  c->partial_rows = 0;
 }
 
 void drop_graphs(rbm_ctx* c) {
@@ -132,6 +138,9 @@ rbm_status alloc_scratch(rbm_ctx* c) {
   RBM_CUDA(cudaMalloc(&s.done, sizeof(uint32_t)));
   RBM_CUDA(cudaMalloc(&s.perm, sizeof(uint32_t) * n));
   RBM_CUDA(cudaMalloc(&c->xtmp, c->row_bytes * n));
+  // Partial sums of the split direct sum: up to 16 chunks of N rows, at most 2^24 rows.
+  c->partial_rows = std::min<size_t>(static_cast<size_t>(n) * 16, size_t(1) << 24);
+  RBM_CUDA(cudaMalloc(&c->partial, c->row_bytes * c->partial_rows));
   RBM_CUDA(cudaMemset(s.cnt, 0, sizeof(uint32_t) * s.nbuckets));
   RBM_CUDA(cudaMemset(s.ovf_cnt, 0, sizeof(uint32_t)));
   RBM_CUDA(cudaMemset(s.done, 0, sizeof(uint32_t)));
@@ -238,11 +247,13 @@ rbm_status enqueue_direct(rbm_ctx* c, int mode, const int64_t* m_ptr, int64_t m_
   if (c->prm.dtype == RBM_F32) {
     StepParams<float> a = step_params<float>(c, m_ptr, m_off);
     a.fout = static_cast<float*>(fout);
-    launch_direct<float>(c->prm.d, mode, &a, static_cast<const float*>(q), nq, c->cfg, st);
+    launch_direct<float>(c->prm.d, mode, &a, static_cast<const float*>(q), nq, c->partial, c->partial_rows, c->cfg,
+                         st);
   } else {
     StepParams<double> a = step_params<double>(c, m_ptr, m_off);
     a.fout = static_cast<double*>(fout);
-    launch_direct<double>(c->prm.d, mode, &a, static_cast<const double*>(q), nq, c->cfg, st);
+    launch_direct<double>(c->prm.d, mode, &a, static_cast<const double*>(q), nq, c->partial, c->partial_rows,
+                          c->cfg, st);
   }
   RBM_CUDA(cudaGetLastError());
   if (mode == 0)
@@ -574,7 +585,7 @@ rbm_status rbm_step_profiled(rbm_ctx* ctx, int32_t method, float* kernel_ms, int
 rbm_status rbm_launches_per_step(const rbm_ctx* ctx, int32_t method, int32_t* launches) {
   if (!ctx || !launches) return RBM_ERR_INVALID;
   if (method == RBM_METHOD_RBM) *launches = ctx->use_coop ? 1 : 1 + rbm_tail_launches(ctx->ps, ctx->prm.p);
-  else if (method == RBM_METHOD_DIRECT) *launches = 1;
+  else if (method == RBM_METHOD_DIRECT) *launches = 2;  // upper bound: sum (+ chunk reduction)
   else return RBM_ERR_INVALID;
   return RBM_OK;
 }

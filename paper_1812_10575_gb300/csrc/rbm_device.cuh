@@ -158,22 +158,38 @@ __device__ __forceinline__ T sqnorm_rn(const T (&x)[D]) {
   return r2;
 }
 
-// s(|x|^2) with K(x) = s x, for a non-zero squared norm r2.
+// Single special-function-unit operations (hand-written PTX): approximate
+// reciprocal and reciprocal square root, with subnormal inputs and results
+// flushed to zero.  Relative error is a few ulp; a zero input gives +inf.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// s(|x|^2) with K(x) = s x, for a non-zero squared norm r2.  FP32 uses the
+// approximate special-function operations above (squared norms below the
+// smallest normal float count as zero there).
 template <int KF>
 __device__ __forceinline__ float kernel_scale(float r2, float kparam, float radius_sq) {
   if constexpr (KF == RBM_K_INV1D) {
-    return __fdividef(1.0f, r2);                 // 1/x = x / x^2
+    return rcp_approx(r2);                       // 1/x = x / x^2
   } else if constexpr (KF == RBM_K_COULOMB) {
-    const float ri = rsqrtf(r2);
+    const float ri = rsqrt_approx(r2);
     return ri * ri * ri;                         // x/|x|^3
   } else if constexpr (KF == RBM_K_BOUNDED_CONF) {
     return (r2 < radius_sq) ? -1.0f : 0.0f;      // -x 1{|x| < R}
   } else if constexpr (KF == RBM_K_GAUSS_AGG) {
     return -__expf(-0.5f * r2);                  // -x exp(-|x|^2/2)
   } else if constexpr (KF == RBM_K_REG_ATTRACT) {
-    return -__fdividef(1.0f, r2 + kparam);       // -x/(|x|^2 + eps)
+    return -rcp_approx(r2 + kparam);             // -x/(|x|^2 + eps)
   } else if constexpr (KF == RBM_K_SMOOTH_TEST) {
-    return __fdividef(1.0f, 1.0f + r2);          // x/(1+|x|^2)
+    return rcp_approx(1.0f + r2);                // x/(1+|x|^2)
   } else {
     return -kparam;                              // -c x
   }

@@ -78,7 +78,7 @@ cudaError_t launch_coop(const CoopScratch& cs, int d, int mode, const void* para
 // Direct O(N^2) pieces (direct.cu).  `mode`: 0 = step (into xout), 1 =
 // forces at the particles (into fout), 2 = forces at query points.
 template <typename T>
-void launch_direct(int d, int mode, const void* params, const T* q, uint32_t nq, const LaunchCfg& cfg,
-                   cudaStream_t st);
+void launch_direct(int d, int mode, const void* params, const T* q, uint32_t nq, void* partial, size_t partial_rows,
+                   const LaunchCfg& cfg, cudaStream_t st);
 
 }  // namespace rbm
