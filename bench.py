@@ -1,18 +1,28 @@
-"""Benchmark: particle-steps/s of RBM-1 on one GB300 (and the direct O(N^2)
-step beside it) on the Thomson-sphere workload of Sec. 5.1 of
-arXiv:1812.10575: N = 100000 points on S^2, K(x) = x/|x|^3, V = 0, sigma = 0,
-positions projected back to the sphere after each step, p = 2, dt = 1e-4,
-FP32.  Inputs are synthetic (uniform points on the sphere from a seeded
-generator).
+"""Benchmark: particle-steps/s of RBM-1 on one GB300, with the direct O(N^2)
+step beside it, on synthetic workloads shaped like the paper's
+(arXiv:1812.10575) examples.  Default workload (the headline line): the
+Thomson problem of Sec. 5.1 -- N = 100000 points on S^2, K(x) = x/|x|^3,
+V = 0, sigma = 0, positions projected back to the sphere after each step,
+p = 2, dt = 1e-4, FP32.
 
 One timed step = one RBM-1 step: Philox keys, random division, in-batch
-forces, Euler update, projection.  The state (1.6 MB) fits in L2, so L2 is
-flushed before every timed step (a 256 MiB write, then a 256 MiB read so the
-flush's dirty lines are written back before the step starts) and each step
-is timed alone with CUDA events on the stream its kernels run on.
+forces, Euler update, projection.  The default state (1.6 MB) fits in L2, so
+L2 is flushed before every timed step (a 256 MiB write, then a 256 MiB read
+so the flush's dirty lines are written back before the step starts) and each
+step is timed alone with CUDA events on the stream its kernels run on.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload thomson|batched_opinion|dyson|large_n]
 
+Other workloads (one JSON line each, same keys):
+  batched_opinion - 4096 independent 2-D bounded-confidence opinion systems
+                    (Sec. 5.2), N_r log-uniform in [256, 65536], sigma = 0.01,
+                    dt = 1e-2, p = 2, one launch per step replayed from a
+                    100-step CUDA graph; inputs (384 MB) exceed L2;
+  dyson           - Dyson Brownian motion (Sec. 4.2), N = 1000, FP64,
+                    splitting scheme, p = 2, dt = 1e-3;
+  large_n         - regularised attraction, d = 3, FP32, N = 2^16 .. 2^24,
+                    p in {2, 4, 8}, RBM and (up to 2^20) direct.
 Under torchrun each rank advances its own replica of the workload (replica
 index = rank; no data-path collective): weak scaling.  ``--impl reference``
 times the CPU oracle on this host's cores instead (rank 0 only).
@@ -36,9 +46,21 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s: RBM vs direct vs surrogate on 1 GB300 at stated W1 error"
 UNIT = "particle-steps/s"
-WORKLOAD = dict(workload="thomson_sphere_rbm1", n=100000, d=3, p=2, dt=1e-4, sigma=0.0, kernel="coulomb",
-                potential="zero", renorm=True, dtype="f32", seed=0)
 L2_FLUSH_BYTES = 256 << 20
+
+WORKLOADS = {
+    "thomson": dict(workload="thomson_sphere_rbm1", n=100000, d=3, p=2, dt=1e-4, sigma=0.0, kernel="coulomb",
+                    potential="zero", v_coef=1.0, k_param=0.0, renorm=True, dtype="f32", seed=0, scheme="euler"),
+    "batched_opinion": dict(workload="batched_opinion_replicas", replicas=4096, n_lo=256, n_hi=65536, d=2, p=2,
+                            dt=1e-2, sigma=0.01, kernel="bounded_conf", potential="zero", v_coef=1.0, k_param=0.25,
+                            renorm=False, dtype="f32", seed=0, scheme="euler", graph_steps=100),
+    "dyson": dict(workload="dyson_brownian_motion", n=1000, d=1, p=2, dt=1e-3, sigma=float(np.sqrt(1.0 / 1000)),
+                  kernel="inv1d", potential="quadratic", v_coef=1.0, k_param=0.0, renorm=False, dtype="f64", seed=0,
+                  scheme="split"),
+    "large_n": dict(workload="large_n_reg_attract", d=3, dt=1e-3, sigma=0.2, kernel="reg_attract",
+                    potential="quadratic", v_coef=1.0, k_param=0.01, renorm=False, dtype="f32", seed=0,
+                    scheme="euler", sizes=[2**16, 2**18, 2**20, 2**22, 2**24], ps=[2, 4, 8], direct_max=2**20),
+}
 
 
 def _env_int(name, default):
@@ -78,7 +100,7 @@ class ClockSampler:
         self.lines = []
         self.thread = None
 
-    def __enter__(self):
+    def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -93,7 +115,7 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
-    def __exit__(self, *exc):
+    def stop(self):
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -118,45 +140,83 @@ class ClockSampler:
             for name, val in zip(names, parts[5:9]):
                 if val.lower().startswith("active"):
                     reasons.add(name)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+               "reasons": sorted(reasons), "samples": len(sm),
+               "window": "sampled every 200 ms from the warm-up soak through the timed, profiled, direct and e2e "
+                         "phases"}
+        return out
 
 
-def _oracle_rbm_rate(n_particles, seconds, steps=None, warmup=0):
-    """Time the CPU oracle's RBM-1 step on the workload (bounded sample)."""
+def _oprm(w, n, replica=0, precision=None):
     import oracle
+
+    return oracle.make_params(n, w["d"], p=w["p"], dt=w["dt"], sigma=w["sigma"], seed=w["seed"], v=w["potential"],
+                              v_coef=w["v_coef"], k=w["kernel"], k_param=w["k_param"], renorm=w["renorm"],
+                              precision=precision or w["dtype"], replica=replica)
+
+
+def _initial(w, n, seed=None):
     import workloads
 
-    w = WORKLOAD
-    prm = oracle.make_params(n_particles, w["d"], p=w["p"], dt=w["dt"], sigma=w["sigma"], seed=w["seed"],
-                             k=w["kernel"], renorm=w["renorm"], precision="f32")
-    X = workloads.sphere(n_particles, w["d"], seed=w["seed"]).astype(np.float32).astype(np.float64)
+    seed = w["seed"] if seed is None else seed
+    if w["workload"].startswith("thomson"):
+        return workloads.sphere(n, w["d"], seed=seed)
+    if w["workload"].startswith("dyson"):
+        return workloads.dyson(n, seed)
+    if w["workload"].startswith("batched"):
+        return workloads.unit_cube(n, w["d"], seed=seed)
+    return workloads.gaussian(n, w["d"], seed=seed)
+
+
+def _oracle_step_fn(w):
+    import oracle
+
+    return oracle.rbm_split_step if w["scheme"] == "split" else oracle.rbm_step
+
+
+def _oracle_rate(w, seconds=None, steps=None, warmup=0):
+    """Time the CPU oracle's RBM-1 step on (a bounded sample of) the workload.
+    Returns (particle-steps/s, steps done, seconds, threads, sample text)."""
+    import oracle
+
+    step = _oracle_step_fn(w)
+    if w["workload"].startswith("batched"):
+        import workloads
+
+        sizes = workloads.replica_sizes(w["replicas"], w["n_lo"], w["n_hi"], seed=w["seed"])
+        pick = list(range(0, len(sizes), max(1, len(sizes) // 16)))[:16]
+        sample = f"replicas {pick[0]}..{pick[-1]} (16 of {len(sizes)}, {int(sum(sizes[pick]))} particles)"
+        systems = [(_oprm(w, int(sizes[r]), replica=r), _initial(w, int(sizes[r]), seed=r)) for r in pick]
+    else:
+        n = w["n"]
+        sample = f"the full N={n} system"
+        X = _initial(w, n)
+        if w["dtype"] == "f32":
+            X = X.astype(np.float32).astype(np.float64)
+        systems = [(_oprm(w, n), X)]
     for m in range(warmup):
-        X = oracle.rbm_step(prm, X, m)
-    done, t0 = 0, time.perf_counter()
+        systems = [(prm, step(prm, X, m)) for prm, X in systems]
+    done, parts, t0 = 0, 0, time.perf_counter()
     while True:
-        X = oracle.rbm_step(prm, X, warmup + done)
+        systems = [(prm, step(prm, X, warmup + done)) for prm, X in systems]
+        parts += sum(prm.n for prm, _ in systems)
         done += 1
         el = time.perf_counter() - t0
         if (steps is not None and done >= steps) or (steps is None and el >= seconds):
             break
-    return n_particles * done / el, done, el, oracle.num_threads()
+    return parts / el, done, el, oracle.num_threads(), sample
 
 
-def run_reference(args):
+def run_reference(args, w):
     rank = _env_int("RANK", 0)
     if rank != 0:
         return 0
-    n = WORKLOAD["n"]
-    rate, done, el, cores = _oracle_rbm_rate(n, None, steps=args.steps, warmup=args.warmup)
-    sample = (f"{done} oracle RBM-1 steps of the full N={n} Thomson workload (FP64 arithmetic, "
-              f"FP32-equivalent noise), after {args.warmup} warm-up steps")
+    rate, done, el, cores, sample = _oracle_rate(w, steps=args.steps, warmup=args.warmup)
+    sample = f"{done} oracle RBM-1 steps of {sample} (FP64 arithmetic), after {args.warmup} warm-up steps"
     line = {
         "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * el / done, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": dict(WORKLOAD), "impl": "reference",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": dict(w), "impl": "reference",
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -164,7 +224,7 @@ def run_reference(args):
     return 0
 
 
-def _traffic_for(kernel_name: str, digest: str):
+def _traffic_for(workload: str, kernel_name: str, digest: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -172,190 +232,310 @@ def _traffic_for(kernel_name: str, digest: str):
         return None
     with open(path) as f:
         data = json.load(f)
-    ent = data.get(WORKLOAD["workload"], {}).get(kernel_name)
+    ent = data.get(workload, {}).get(kernel_name)
     if not ent or ent.get("sources") != digest:
         return None
     return ent.get("dram_bytes_per_launch")
 
 
-def run_ours(args):
-    import torch
-    import torch.distributed as dist
+class Gpu:
+    """Per-rank GPU context: device, stream, L2 flush, barrier."""
 
+    def __init__(self):
+        import torch
+        import torch.distributed as dist
+
+        self.torch, self.dist = torch, dist
+        self.world = _env_int("WORLD_SIZE", 1)
+        self.rank = _env_int("RANK", 0)
+        self.local = _env_int("LOCAL_RANK", 0)
+        if self.world > 1:
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group("nccl")
+        torch.cuda.set_device(self.local)
+        self.dev = torch.device("cuda", self.local)
+        self.stream = torch.cuda.current_stream()
+        self.flush_w = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=self.dev)
+        self.flush_r = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=self.dev)
+        self.sink = torch.empty((), dtype=torch.float32, device=self.dev)
+
+    def flush(self):
+        self.flush_w.zero_()
+        self.sink.copy_(self.flush_r.sum())
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+        self.torch.cuda.synchronize()
+
+    def max_over_ranks(self, v):
+        if self.world == 1:
+            return v
+        t = self.torch.tensor([v], device=self.dev, dtype=self.torch.float64)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def event(self):
+        return self.torch.cuda.Event(enable_timing=True)
+
+    def close(self):
+        if self.world > 1:
+            self.dist.destroy_process_group()
+
+
+def _to_dev(g, X, d, dtype):
+    torch = g.torch
+    ld = 4 if d == 3 else d
+    t = torch.zeros(X.shape[0], ld, dtype=torch.float64)
+    t[:, :d] = torch.from_numpy(np.asarray(X, dtype=np.float64))
+    return t.to(torch.float32 if dtype == "f32" else torch.float64).to(g.dev).contiguous()
+
+
+def _roofline(peaks, peak_src, kernel, alg_bytes, avg_ms, workload, digest):
+    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
+    return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": _traffic_for(workload, kernel, digest),
+            "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
+            "peak_source": f"{peak_src} (hbm_gbs)"}
+
+
+def run_single(args, w, g):
+    """One system (thomson, dyson): each step timed alone after an L2 flush."""
     import paper_1812_10575_gb300 as rbm
-    import workloads
 
-    world = _env_int("WORLD_SIZE", 1)
-    rank = _env_int("RANK", 0)
-    local = _env_int("LOCAL_RANK", 0)
-    if world > 1:
-        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    w = WORKLOAD
     n, d = w["n"], w["d"]
-    stream = torch.cuda.current_stream()
-
-    X0 = workloads.sphere(n, d, seed=w["seed"])
-    x = torch.zeros(n, 4, dtype=torch.float32, device=dev)
-    x[:, :3] = torch.from_numpy(X0).float().to(dev)
-    kw = dict(p=w["p"], dt=w["dt"], sigma=w["sigma"], seed=w["seed"], k=w["kernel"], renorm=w["renorm"],
-              replica=rank)
-    sysm = rbm.System(x, d=d, stream=stream, **kw)
+    row_bytes = (4 if d == 3 else d) * (4 if w["dtype"] == "f32" else 8)
+    x = _to_dev(g, _initial(w, n), d, w["dtype"])
+    kw = dict(p=w["p"], dt=w["dt"], sigma=w["sigma"], seed=w["seed"], v=w["potential"], v_coef=w["v_coef"],
+              k=w["kernel"], k_param=w["k_param"], renorm=w["renorm"], scheme=w["scheme"], replica=g.rank)
+    sysm = rbm.System(x, d=d, stream=g.stream, **kw)
     sysm.set_tuning(graph_steps=1)
-    flush_w = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    flush_r = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    sink = torch.empty((), dtype=torch.float32, device=dev)
-
-    class _Flush:
-        @staticmethod
-        def zero_():
-            flush_w.zero_()
-            sink.copy_(flush_r.sum())
-
-    flush = _Flush()
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    clocks = ClockSampler(local).__enter__()
-    # warm-up: graph capture, caches; then about a second of steps so the
-    # clock record covers the GPU under this load
+    clocks = ClockSampler(g.local).start()
     for _ in range(max(args.warmup, 3)):
         sysm.run(1)
     sysm.sync()
-    soak = rbm.System(x.clone(), d=d, stream=stream, **kw)
+    soak = rbm.System(x.clone(), d=d, stream=g.stream, **kw)
     t_soak = time.perf_counter()
     while time.perf_counter() - t_soak < 1.0:
         soak.run(100)
         soak.sync()
     soak.close()
 
-    # kernels per replayed one-step graph: the step's kernels, plus the
-    # step-counter bump kernel unless the cooperative kernel advances it itself
+    # kernels per replayed one-step graph, plus the counter bump unless the
+    # cooperative kernel advances the step counter itself
     launches = sysm.launches_per_step("rbm") + (0 if sysm.tuning()["path"] == 2 else 1)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    barrier()
-    if True:
-        wall0 = time.perf_counter()
-        for k in range(args.steps):
-            flush.zero_()
-            starts[k].record(stream)
-            sysm.run(1)                    # one RBM-1 step (CUDA graph of one step)
-            ends[k].record(stream)
-        barrier()
-        wall = time.perf_counter() - wall0
-        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-        # per-kernel CUDA-event timing of the same step, on the same stream
-        per_kernel = {}
-        for k in range(args.steps):
-            flush.zero_()
-            for name, ms in sysm.step_profiled("rbm"):
-                per_kernel.setdefault(name, []).append(ms)
-        barrier()
-    sysm.sync()
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * n * args.steps / (total_ms * 1e-3)
+    starts = [g.event() for _ in range(args.steps)]
+    ends = [g.event() for _ in range(args.steps)]
+    g.barrier()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        g.flush()
+        starts[k].record(g.stream)
+        sysm.run(1)                              # one RBM-1 step (CUDA graph of one step)
+        ends[k].record(g.stream)
+    g.barrier()
+    wall = time.perf_counter() - wall0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    per_kernel = {}
+    for k in range(args.steps):                  # the same step, kernel by kernel, same stream
+        g.flush()
+        for name, ms in sysm.step_profiled("rbm"):
+            per_kernel.setdefault(name, []).append(ms)
+    g.barrier()
+    total_ms = g.max_over_ranks(float(sum(step_ms)))
+    value = g.world * n * args.steps / (total_ms * 1e-3)
 
-    # direct O(N^2) step on the same system (a few steps: ~ms each)
+    # direct O(N^2) step on the same system
     nd = min(args.steps, 5)
-    dstart = [torch.cuda.Event(enable_timing=True) for _ in range(nd)]
-    dend = [torch.cuda.Event(enable_timing=True) for _ in range(nd)]
     sysm.direct_step()
     sysm.sync()
+    dstart = [g.event() for _ in range(nd)]
+    dend = [g.event() for _ in range(nd)]
     for k in range(nd):
-        flush.zero_()
-        dstart[k].record(stream)
+        g.flush()
+        dstart[k].record(g.stream)
         sysm.direct_step()
-        dend[k].record(stream)
+        dend[k].record(g.stream)
     sysm.sync()
     direct_ms = float(np.mean([s.elapsed_time(e) for s, e in zip(dstart, dend)]))
-    direct_rate = n / (direct_ms * 1e-3)
     direct_kernel = {}
     for _ in range(2):
         for name, ms in sysm.step_profiled("direct"):
             direct_kernel.setdefault(name, []).append(ms)
 
-    # end to end through the C ABI with host buffers (H2D + step + D2H each step)
+    # end to end through the C ABI with host buffers (H2D + step + D2H)
     host = x.detach().cpu().pin_memory()
     sysm.step_host(host)
     e2e_ms = []
     for k in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
+        g.flush()
+        g.torch.cuda.synchronize()
         t0 = time.perf_counter()
         sysm.step_host(host)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_total = float(sum(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * n * args.steps / (e2e_total * 1e-3)
-    row_bytes = 16
+    e2e_total = g.max_over_ranks(float(sum(e2e_ms)))
+    clocks.stop()
 
-    # roofline of the dominant kernel
     peaks, peak_src = _measured_peaks()
     avg = {k: float(np.mean(v)) for k, v in per_kernel.items()}
     dom = max(avg, key=avg.get)
-    # algorithmic bytes per particle (positions read + written once, one u32
-    # permutation entry written and read): the floor any RBM-1 step moves
-    step_floor = 2 * row_bytes + 8
-    bytes_per_particle = {"k_rbm_coop": step_floor, "k_bucket_sort_step": 4 + 4 + 2 * row_bytes,
-                          "k_bucket_scatter": 4, "k_straddle_fixup": 0, "k_bucket_scan": 0}
-    alg_bytes = n * bytes_per_particle.get(dom, 0)
-    achieved = alg_bytes / (avg[dom] * 1e-3) / 1e9
+    # algorithmic bytes per particle-step: positions read and written once,
+    # one u32 permutation entry written and read
+    floor = 2 * row_bytes + 8
+    per_particle = {"k_rbm_coop": floor, "k_bucket_sort_step": 4 + 4 + 2 * row_bytes, "k_bucket_scatter": 4}
     digest = _kernel_sources_digest()
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": _traffic_for(dom, digest),
-                "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg[dom],
-                "peak_source": f"{peak_src} (hbm_gbs)"}
-    # the direct kernel is bound by the FP32 pipe: 17 flop per pair (Coulomb) over N^2 pairs
-    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    dk = float(np.mean(direct_kernel.get("k_direct", [direct_ms])))
-    direct_tflops = 17.0 * n * n / (dk * 1e-3) / 1e12
-
-    clocks.__exit__(None, None, None)
-    clk = clocks.summary()
-    clk["window"] = "sampled every 200 ms from the warm-up soak through the timed, profiled, direct and e2e phases"
+    roof = _roofline(peaks, peak_src, dom, n * per_particle.get(dom, 0), avg[dom], w["workload"], digest)
+    flop_per_pair = {"coulomb": 17, "inv1d": 6, "reg_attract": 17, "gauss_agg": 18, "smooth_test": 17,
+                     "bounded_conf": 16, "linear": 11}[w["kernel"]]
+    fp_peak = (152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12) / (1 if w["dtype"] == "f32" else 64)
+    dk = float(np.sum([np.mean(v) for v in direct_kernel.values()])) if direct_kernel else direct_ms
+    direct_tflops = flop_per_pair * n * n / (dk * 1e-3) / 1e12
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": g.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(WORKLOAD, l2="flushed before every timed step (256 MiB write + 256 MiB read); "
-                                    "each step timed alone",
-                       parallelism=f"replicas x{world} (one independent system per GPU)"),
-        "roofline": roofline,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * row_bytes,
-                "d2h_bytes_per_step": n * row_bytes},
+        "vs_baseline": None, "dtype": w["dtype"], "data": "synthetic",
+        "config": dict(w, l2="flushed before every timed step (256 MiB write + 256 MiB read); each step timed alone",
+                       parallelism=f"replicas x{g.world} (one independent system per GPU)"),
+        "roofline": roof,
+        "e2e": {"value": g.world * n * args.steps / (e2e_total * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": n * row_bytes, "d2h_bytes_per_step": n * row_bytes},
         "gpu_launches": launches * args.steps,
-        "clocks": clk,
-        "methods": {"rbm": value / world, "direct": direct_rate, "rbm_over_direct": (value / world) / direct_rate,
-                    "direct_ms_per_step": direct_ms,
-                    "direct_kernel": {"bound": "alu", "achieved": direct_tflops, "peak": fp32_peak,
-                                      "unit": "TFLOP/s", "frac": direct_tflops / fp32_peak,
-                                      "flop_per_pair": 17, "peak_source": "152 SMs x 128 FP32 lanes x 2 x max clock"}},
-        "kernels_ms": avg,
-        "wall_s_timed_region": wall,
-        "kernel_sources": digest,
+        "clocks": clocks.summary(),
+        "methods": {"rbm": value / g.world, "direct": n / (direct_ms * 1e-3),
+                    "rbm_over_direct": (value / g.world) / (n / (direct_ms * 1e-3)), "direct_ms_per_step": direct_ms,
+                    "direct_kernel": {"bound": "alu", "achieved": direct_tflops, "peak": fp_peak, "unit": "TFLOP/s",
+                                      "frac": direct_tflops / fp_peak, "flop_per_pair": flop_per_pair,
+                                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x max clock"
+                                                     + ("" if w["dtype"] == "f32" else " / 64 (FP64)")}},
+        "kernels_ms": avg, "direct_kernels_ms": {k: float(np.mean(v)) for k, v in direct_kernel.items()},
+        "wall_s_timed_region": wall, "kernel_sources": digest,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, done, el, cores = _oracle_rbm_rate(n, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"{done} oracle RBM-1 steps of the full N={n} workload in {el:.1f} s"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     sysm.close()
-    if world > 1:
-        dist.destroy_process_group()
+    return line
+
+
+def run_batched(args, w, g):
+    """Batched replicas: K steps replayed from 100-step CUDA graphs; inputs exceed L2."""
+    import paper_1812_10575_gb300 as rbm
+    import workloads
+
+    sizes = [int(v) for v in workloads.replica_sizes(w["replicas"], w["n_lo"], w["n_hi"], seed=w["seed"])]
+    rows, d = sum(sizes), w["d"]
+    row_bytes = d * 4
+    x = _to_dev(g, _initial(w, rows), d, w["dtype"])
+    kw = dict(p=w["p"], dt=w["dt"], sigma=w["sigma"], seed=w["seed"] + 1000 * g.rank, v=w["potential"],
+              v_coef=w["v_coef"], k=w["kernel"], k_param=w["k_param"])
+    rep = rbm.Replicas(x, sizes, d=d, stream=g.stream, **kw)
+    tune = rep.autotune(trial_steps=2, table_path=None)
+    steps = max(args.steps, 1)
+    rep.set_graph_steps(min(w["graph_steps"], steps))
+    clocks = ClockSampler(g.local).start()
+    rep.run(max(args.warmup, 3))
+    rep.sync()
+    t_soak = time.perf_counter()
+    while time.perf_counter() - t_soak < 1.0:
+        rep.run(min(w["graph_steps"], steps))
+        rep.sync()
+    e0, e1 = g.event(), g.event()
+    g.barrier()
+    wall0 = time.perf_counter()
+    e0.record(g.stream)
+    rep.run(steps)
+    e1.record(g.stream)
+    g.barrier()
+    wall = time.perf_counter() - wall0
+    total_ms = g.max_over_ranks(e0.elapsed_time(e1))
+    value = g.world * rows * steps / (total_ms * 1e-3)
+    prof = {}
+    for _ in range(3):
+        for name, ms in rep.step_profiled():
+            prof.setdefault(name, []).append(ms)
+    clocks.stop()
+    host = x.detach().cpu().pin_memory()
+    n_e2e = 3
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        rbm.rbm_step_host(rep.ctx, host)
+    e2e_s = g.max_over_ranks(time.perf_counter() - t0)
+    peaks, peak_src = _measured_peaks()
+    avg = {k: float(np.mean(v)) for k, v in prof.items()}
+    digest = _kernel_sources_digest()
+    roof = _roofline(peaks, peak_src, "k_rbm_batched", rows * (2 * row_bytes + 8), total_ms / steps,
+                     w["workload"], digest)
+    roof["avg_launch_ms_profiled"] = avg.get("k_rbm_batched")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": g.world, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": w["dtype"], "data": "synthetic",
+        "config": dict(w, rows=rows, l2=f"inputs ({rows * row_bytes / 1e6:.0f} MB of positions) exceed L2; "
+                                        "K steps replayed back to back from CUDA graphs",
+                       parallelism=f"replicas x{g.world}", autotune=tune),
+        "roofline": roof,
+        "e2e": {"value": g.world * rows * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": rows * row_bytes,
+                "d2h_bytes_per_step": rows * row_bytes},
+        "gpu_launches": steps + (steps + min(w["graph_steps"], steps) - 1) // min(w["graph_steps"], steps),
+        "clocks": clocks.summary(), "kernels_ms": avg, "wall_s_timed_region": wall, "kernel_sources": digest,
+    }
+    rep.close()
+    return line
+
+
+def run_large_n(args, w, g):
+    """Throughput sweep over N and p (RBM) and N (direct up to 2^20)."""
+    import paper_1812_10575_gb300 as rbm
+
+    rows = []
+    for n in w["sizes"]:
+        X = _initial(w, n)
+        for p in w["ps"]:
+            x = _to_dev(g, X, w["d"], w["dtype"])
+            s = rbm.System(x, d=w["d"], p=p, dt=w["dt"], sigma=w["sigma"], seed=w["seed"], v=w["potential"],
+                           v_coef=w["v_coef"], k=w["kernel"], k_param=w["k_param"], stream=g.stream)
+            s.set_tuning(graph_steps=10)
+            s.run(10)
+            s.sync()
+            e0, e1 = g.event(), g.event()
+            e0.record(g.stream)
+            s.run(20)
+            e1.record(g.stream)
+            s.sync()
+            ms = e0.elapsed_time(e1) / 20
+            ent = {"n": n, "p": p, "method": "rbm", "path": s.tuning()["path"], "ms_per_step": ms,
+                   "particle_steps_per_s": n / (ms * 1e-3),
+                   "hbm_frac_of_floor": n * (2 * 16 + 8) / (ms * 1e-3) / 1e9 / _measured_peaks()[0]["hbm_gbs"]}
+            if p == w["ps"][0] and n <= w["direct_max"]:
+                s.direct_step()
+                s.sync()
+                e0.record(g.stream)
+                s.direct_step()
+                e1.record(g.stream)
+                s.sync()
+                dms = e0.elapsed_time(e1)
+                ent["direct_ms_per_step"] = dms
+                ent["direct_particle_steps_per_s"] = n / (dms * 1e-3)
+            rows.append(ent)
+            s.close()
+    best = max(r["particle_steps_per_s"] for r in rows)
+    return {"metric": METRIC, "value": best, "unit": UNIT, "n_gpus": g.world, "steps": 20, "warmup": 10,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": w["dtype"],
+            "data": "synthetic", "config": dict(w, l2="state larger than L2 from N = 2^23"), "sweep": rows}
+
+
+def run_ours(args, w):
+    g = Gpu()
+    if w["workload"].startswith("batched"):
+        line = run_batched(args, w, g)
+    elif w["workload"].startswith("large_n"):
+        line = run_large_n(args, w, g)
+    else:
+        line = run_single(args, w, g)
+    if g.rank == 0 and g.world == 1 and not args.no_cpu_baseline and "sweep" not in line:
+        rate, done, el, cores, sample = _oracle_rate(w, seconds=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{done} oracle RBM-1 steps of {sample} in {el:.1f} s"}
+    if g.rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
     return 0
 
 
@@ -365,14 +545,16 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="thomson", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    w = WORKLOADS[args.workload]
     if args.impl == "reference":
-        return run_reference(args)
-    return run_ours(args)
+        return run_reference(args, w)
+    return run_ours(args, w)
 
 
 if __name__ == "__main__":

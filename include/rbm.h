@@ -206,6 +206,39 @@ rbm_status rbm_direct_forces_at(rbm_ctx *ctx, const void *q_dev, int64_t nq, voi
 rbm_status rbm_step_profiled(rbm_ctx *ctx, int32_t method, float *kernel_ms, int32_t capacity, int32_t *nkernels,
                              char *names, int32_t names_len);
 
+/* ---- batched replicas --------------------------------------------------- */
+
+/* A context for nrep independent systems advanced together: replica r has
+ * n_host[r] particles (2 .. 2^20) occupying rows [off_r, off_r + n_host[r])
+ * of the concatenated position array x_dev (off_r = sum of the earlier
+ * sizes; layout, alignment and ownership as for rbm_init; base->n must be
+ * the total).  All replicas share base's parameters (p <= 32, Euler scheme);
+ * replica r uses replica index r in its Philox counters, so it follows the
+ * same trajectory as a single system with rbm_params.replica = r.  The paper
+ * has no batched form: it notes that batches can be updated in parallel once
+ * the random division is known (Sec. 2.3 item 3); here whole replicas are the
+ * parallel unit, all of them advanced by one kernel launch per step.
+ * Accepted afterwards: rbm_step, rbm_run (RBM_METHOD_RBM), rbm_permutation
+ * (replica-local ids, replica after replica), rbm_forces (RBM_METHOD_RBM),
+ * rbm_step_host, rbm_get/set_step, rbm_sync, rbm_free, rbm_autotune,
+ * rbm_batched_set_launch; the direct-step calls return RBM_ERR_UNSUPPORTED. */
+rbm_status rbm_batched_init(const rbm_params *base, int32_t nrep, const int64_t *n_host, void *x_dev,
+                            void *cuda_stream, rbm_ctx **out);
+
+/* Launch shape of the batched step: threads per block (256, 512 or 1024) and
+ * the mean bucket size of each replica's sort (64 .. 2048).  Synchronous. */
+rbm_status rbm_batched_set_launch(rbm_ctx *ctx, int32_t threads, int32_t bucket_target);
+
+/* Choose the launch configuration of the RBM step by timing the candidates
+ * (batched: threads x bucket size; single system: bucket-sort kernels vs the
+ * cooperative kernel) for trial_steps steps each on a scratch copy of the
+ * positions (the state and step index are left unchanged), and apply the
+ * fastest.  With table_path, a previous result for the same workload
+ * signature is read from that text file instead of searching, and a new
+ * result is appended to it.  A one-line report is written to `report` (up to
+ * report_len bytes, NUL-terminated) when given.  Synchronous. */
+rbm_status rbm_autotune(rbm_ctx *ctx, int32_t trial_steps, const char *table_path, char *report, int32_t report_len);
+
 /* ---- without allocation ------------------------------------------------ */
 
 /* The random division of step m (the same ids, in the same order, as

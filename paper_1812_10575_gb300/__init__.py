@@ -17,13 +17,87 @@ from ._lib import (  # noqa: F401
     EXPORTS, KERNELS, METHODS, POTENTIALS, SCHEMES, RbmError, RbmParams, RbmTuning, library_path, load,
     make_params, rbm_direct_forces_at, rbm_direct_step, rbm_forces, rbm_free, rbm_get_step, rbm_get_tuning,
     rbm_init, rbm_last_error, rbm_launches_per_step, rbm_permutation, rbm_permutation_noalloc, rbm_run, rbm_set_step, rbm_set_tuning,
-    rbm_status_string, rbm_step, rbm_step_host, rbm_step_profiled, rbm_sync,
+    rbm_status_string, rbm_step, rbm_step_host, rbm_step_profiled, rbm_sync, rbm_batched_init,
+    rbm_batched_set_launch, rbm_autotune,
 )
 
 
 def leading_dim(d: int) -> int:
     """Row length of the position array: d for d = 1, 2 and 4 for d = 3."""
     return 4 if d == 3 else d
+
+
+class Replicas:
+    """Independent systems of sizes ``sizes`` in one caller-owned CUDA tensor
+    ``x`` of shape ``(sum(sizes), leading_dim(d))``, advanced together."""
+
+    def __init__(self, x, sizes, d, p=2, dt=1e-3, sigma=0.0, seed=0, v="zero", v_coef=1.0, k="linear",
+                 k_param=0.0, renorm=False, stream=None):
+        import torch
+
+        self.x = x
+        self.d = d
+        self.sizes = [int(v) for v in sizes]
+        if x.dim() != 2 or x.shape[0] != sum(self.sizes) or x.shape[1] != leading_dim(d):
+            raise ValueError("positions must have shape (sum(sizes), leading_dim(d))")
+        self.params = make_params(sum(self.sizes), d, p=p, dt=dt, sigma=sigma, seed=seed,
+                                  dtype="f32" if x.dtype == torch.float32 else "f64", v=v, v_coef=v_coef, k=k,
+                                  k_param=k_param, renorm=renorm)
+        self.ctx = rbm_batched_init(self.params, self.sizes, x, stream)
+
+    def step(self):
+        rbm_step(self.ctx)
+
+    def run(self, steps):
+        rbm_run(self.ctx, steps, "rbm")
+
+    def sync(self):
+        rbm_sync(self.ctx)
+
+    @property
+    def m(self):
+        return rbm_get_step(self.ctx)
+
+    @m.setter
+    def m(self, value):
+        rbm_set_step(self.ctx, value)
+
+    def permutation(self):
+        import torch
+
+        perm = torch.empty(self.x.shape[0], dtype=torch.int32, device=self.x.device)
+        rbm_permutation(self.ctx, perm)
+        return perm
+
+    def forces(self):
+        import torch
+
+        f = torch.zeros_like(self.x)
+        rbm_forces(self.ctx, "rbm", f)
+        return f
+
+    def set_launch(self, threads, bucket_target):
+        rbm_batched_set_launch(self.ctx, threads, bucket_target)
+
+    def set_graph_steps(self, steps):
+        rbm_set_tuning(self.ctx, RbmTuning(graph_steps=steps))
+
+    def autotune(self, trial_steps=3, table_path=None):
+        return rbm_autotune(self.ctx, trial_steps, table_path)
+
+    def step_profiled(self):
+        return rbm_step_profiled(self.ctx, "rbm")
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            rbm_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class System:
@@ -99,6 +173,9 @@ class System:
 
     def step_profiled(self, method="rbm"):
         return rbm_step_profiled(self.ctx, method)
+
+    def autotune(self, trial_steps=3, table_path=None):
+        return rbm_autotune(self.ctx, trial_steps, table_path)
 
     def launches_per_step(self, method="rbm"):
         return rbm_launches_per_step(self.ctx, method)

@@ -41,7 +41,7 @@ EXPORTS = (
     "rbm_init", "rbm_step", "rbm_direct_step", "rbm_run", "rbm_step_host", "rbm_get_step", "rbm_set_step",
     "rbm_set_tuning", "rbm_get_tuning", "rbm_sync", "rbm_free", "rbm_status_string", "rbm_last_error",
     "rbm_permutation", "rbm_forces", "rbm_direct_forces_at", "rbm_step_profiled", "rbm_launches_per_step",
-    "rbm_permutation_noalloc",
+    "rbm_permutation_noalloc", "rbm_batched_init", "rbm_batched_set_launch", "rbm_autotune",
 )
 
 
@@ -120,6 +120,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "rbm_direct_forces_at": [vp, vp, i64, vp],
         "rbm_launches_per_step": [vp, i32, ctypes.POINTER(i32)],
         "rbm_permutation_noalloc": [i64, ctypes.c_uint64, ctypes.c_uint32, i64, vp, vp],
+        "rbm_batched_init": [P, i32, ctypes.POINTER(i64), vp, vp, ctypes.POINTER(vp)],
+        "rbm_batched_set_launch": [vp, i32, i32],
+        "rbm_autotune": [vp, i32, ctypes.c_char_p, ctypes.c_char_p, i32],
         "rbm_step_profiled": [vp, i32, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(i32), ctypes.c_char_p,
                               i32],
     }
@@ -183,6 +186,26 @@ def rbm_init(params: RbmParams, x, stream=None) -> ctypes.c_void_p:
     _check(load().rbm_init(ctypes.byref(params), ctypes.c_void_p(_dev_ptr(x)),
                            ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(ctx)), "rbm_init")
     return ctx
+
+
+def rbm_batched_init(params: RbmParams, sizes, x, stream=None) -> ctypes.c_void_p:
+    """``sizes``: replica sizes; ``x``: (sum(sizes), ld) CUDA tensor."""
+    n = (ctypes.c_int64 * len(sizes))(*[int(v) for v in sizes])
+    ctx = ctypes.c_void_p()
+    _check(load().rbm_batched_init(ctypes.byref(params), len(sizes), n, ctypes.c_void_p(_dev_ptr(x)),
+                                   ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(ctx)), "rbm_batched_init")
+    return ctx
+
+
+def rbm_batched_set_launch(ctx, threads: int, bucket_target: int) -> None:
+    _check(load().rbm_batched_set_launch(ctx, int(threads), int(bucket_target)), "rbm_batched_set_launch")
+
+
+def rbm_autotune(ctx, trial_steps: int = 3, table_path: str | None = None) -> str:
+    rep = ctypes.create_string_buffer(1024)
+    _check(load().rbm_autotune(ctx, int(trial_steps), table_path.encode() if table_path else None, rep, 1024),
+           "rbm_autotune")
+    return rep.value.decode()
 
 
 def rbm_step(ctx) -> None:

@@ -27,6 +27,7 @@ UNITS = [
     ("direct.cu", ["-DRBM_DIRECT_F64"]),
     ("noalloc.cu", []),
     ("coop_step.cu", []),
+    ("batched.cu", []),
 ]
 
 

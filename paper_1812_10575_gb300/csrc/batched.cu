@@ -1,0 +1,271 @@
+// Batched replicas: many independent particle systems of uneven size N_r,
+// all advanced by one RBM-1 step (Algorithm "randomdiv", Sec. 2.1 of
+// arXiv:1812.10575) in one launch.  The paper notes that batches can be
+// updated in parallel once the random division is known (Sec. 2.3 item 3);
+// here the unit of parallel work is a whole replica.
+//
+// Replica r owns rows [off_r, off_r + N_r) of the concatenated position array
+// and its own ids 0 .. N_r - 1; its random division sorts those ids by the
+// Philox key of counter (id, m, r, 0) with an id tie-break, exactly as a
+// single system with replica index r.  Every block takes a fixed list of
+// replicas (largest first, dealt to the blocks in snake order so the sums of
+// N_r per block stay close) and runs, for each replica, with block-level
+// synchronisation only:
+//   1. keys of all ids (stored once, L2-resident) and a shared-memory
+//      histogram of B_r = ceil(N_r / target) buckets (monotone in the key);
+//   2. scan, scatter of ids to bucket order;
+//   3. per bucket: counting sort in shared memory by the next 11 key bits and
+//      insertion sort of equal sub-buckets by (key, id); the sorted ids form
+//      the replica's permutation;
+//   4. every batch of the replica stepped (groups of p lanes, positions
+//      exchanged by warp shuffles).
+// No block waits on another, so the launch cannot deadlock whatever the
+// residency.
+#include "rbm_batch.cuh"
+#include "rbm_device.cuh"
+#include "rbm_internal.h"
+
+namespace rbm {
+namespace {
+
+constexpr uint32_t kBSubBits = 11;
+constexpr uint32_t kBSub = 1u << kBSubBits;
+constexpr uint32_t kBCap = 2048;       // largest bucket sorted in shared memory
+constexpr uint32_t kBMaxBuckets = 512;  // per replica
+
+struct BatchedArgs {
+  const uint32_t* order;        // replica ids, block-major
+  const uint32_t* block_begin;  // [G + 1] slice of `order` per block
+  const uint64_t* offs;         // [R + 1] first row of each replica
+  uint64_t* keys;               // [rows] key of each row (replica-local id order)
+  uint32_t* tmp;                // [rows] ids grouped by bucket
+  uint32_t* perm;               // [rows] permutation (replica-local ids)
+  uint32_t bucket_target;       // mean members per bucket
+};
+
+__device__ __forceinline__ bool bkey_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
+  return ka < kb || (ka == kb && ia < ib);
+}
+
+// Exclusive scan of a[0, len) for any len by the whole block.
+__device__ void block_scan_any(uint32_t* a, uint32_t len, uint32_t* s_warp) {
+  const uint32_t per = (len + blockDim.x - 1) / blockDim.x;
+  const uint32_t lo = min(len, threadIdx.x * per), hi = min(len, lo + per);
+  uint32_t sum = 0;
+  for (uint32_t i = lo; i < hi; ++i) sum += a[i];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    uint32_t w = (lane < nw) ? s_warp[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    if (lane < nw) s_warp[lane] = w;
+  }
+  __syncthreads();
+  uint32_t run = (warp > 0 ? s_warp[warp - 1] : 0u) + incl - sum;
+  for (uint32_t i = lo; i < hi; ++i) {
+    const uint32_t v = a[i];
+    a[i] = run;
+    run += v;
+  }
+  __syncthreads();
+}
+
+template <typename T, int D, int MODE>
+__global__ void k_rbm_batched(BatchedArgs ba, StepParams<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* a_key = reinterpret_cast<uint64_t*>(smem_raw);  // [kBCap]
+  uint64_t* b_key = a_key + kBCap;                          // [kBCap]
+  uint32_t* a_id = reinterpret_cast<uint32_t*>(b_key + kBCap);
+  uint32_t* b_id = a_id + kBCap;
+  uint32_t* a_sub = b_id + kBCap;
+  uint32_t* s_sub = a_sub + kBCap;                          // [kBSub]
+  __shared__ uint32_t s_hist[kBMaxBuckets + 1];
+  __shared__ uint32_t s_fill[kBMaxBuckets];
+  __shared__ uint32_t s_warp[32];
+
+  const uint32_t m32 = step_index(a);
+  const uint32_t begin = ba.block_begin[blockIdx.x], end_list = ba.block_begin[blockIdx.x + 1];
+  for (uint32_t li = begin; li < end_list; ++li) {
+    const uint32_t r = ba.order[li];
+    const uint64_t off = ba.offs[r];
+    const uint32_t n = static_cast<uint32_t>(ba.offs[r + 1] - off);
+    uint32_t B = (n + ba.bucket_target - 1) / ba.bucket_target;
+    B = max(1u, min(B, kBMaxBuckets));
+    uint64_t* keys = ba.keys + off;
+    uint32_t* tmp = ba.tmp + off;
+    uint32_t* perm = ba.perm + off;
+
+    // 1. keys and bucket histogram
+    for (uint32_t b = threadIdx.x; b <= B; b += blockDim.x) s_hist[b] = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint64_t key = perm_key(i, m32, r, a.seed);
+      keys[i] = key;
+      atomicAdd(&s_hist[static_cast<uint32_t>(__umul64hi(key, B))], 1u);
+    }
+    __syncthreads();
+    // 2. bucket starts (s_hist[B] becomes n), scatter of ids
+    block_scan_any(s_hist, B + 1, s_warp);
+    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) s_fill[b] = s_hist[b];
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint32_t b = static_cast<uint32_t>(__umul64hi(keys[i], B));
+      tmp[atomicAdd(&s_fill[b], 1u)] = i;
+    }
+    __syncthreads();
+    // 3. sort every bucket
+    for (uint32_t b = 0; b < B; ++b) {
+      const uint32_t s = s_hist[b], nb = s_hist[b + 1] - s;
+      if (nb <= kBCap) {
+        for (uint32_t u = threadIdx.x; u < kBSub; u += blockDim.x) s_sub[u] = 0;
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
+          const uint32_t id = tmp[s + j];
+          const uint64_t key = keys[id];
+          const uint32_t sub =
+              static_cast<uint32_t>(__umul64hi(key, static_cast<uint64_t>(B) << kBSubBits)) & (kBSub - 1u);
+          a_key[j] = key;
+          a_id[j] = id;
+          a_sub[j] = sub | (atomicAdd(&s_sub[sub], 1u) << 16);
+        }
+        __syncthreads();
+        block_scan_any(s_sub, kBSub, s_warp);
+        for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
+          const uint32_t pos = s_sub[a_sub[j] & 0xffffu] + (a_sub[j] >> 16);
+          b_key[pos] = a_key[j];
+          b_id[pos] = a_id[j];
+        }
+        __syncthreads();
+        for (uint32_t u = threadIdx.x; u < kBSub; u += blockDim.x) {
+          const uint32_t lo = s_sub[u], hi = (u + 1 < kBSub) ? s_sub[u + 1] : nb;
+          for (uint32_t x = lo + 1; x < hi; ++x) {
+            const uint64_t kx = b_key[x];
+            const uint32_t ix = b_id[x];
+            uint32_t y = x;
+            while (y > lo && bkey_less(kx, ix, b_key[y - 1], b_id[y - 1])) {
+              b_key[y] = b_key[y - 1];
+              b_id[y] = b_id[y - 1];
+              --y;
+            }
+            b_key[y] = kx;
+            b_id[y] = ix;
+          }
+        }
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) perm[s + j] = b_id[j];
+      } else {
+        // a bucket beyond the shared-memory sort: rank by counting
+        for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
+          const uint32_t idj = tmp[s + j];
+          const uint64_t kj = keys[idj];
+          uint32_t rank = 0;
+          for (uint32_t f = 0; f < nb; ++f) {
+            const uint32_t idf = tmp[s + f];
+            rank += bkey_less(keys[idf], idf, kj, idj) ? 1u : 0u;
+          }
+          perm[s + rank] = idj;
+        }
+      }
+      __syncthreads();
+    }
+    // 4. step every batch of the replica
+    if (MODE != kModePerm) {
+      StepParams<T> ar = a;
+      ar.x = a.x + off * Ld<D>::value;
+      ar.fout = a.fout ? a.fout + off * Ld<D>::value : nullptr;
+      ar.n = n;
+      ar.replica = r;
+      const uint32_t nbatch = (n + static_cast<uint32_t>(a.p) - 1) / static_cast<uint32_t>(a.p);
+      step_batches<T, D, MODE>(ar, m32, perm, 0u, 0u, nbatch);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int D>
+size_t batched_smem() {
+  return static_cast<size_t>(kBCap) * (8 + 8 + 4 + 4 + 4) + kBSub * 4;
+}
+
+template <typename T, int D, int MODE>
+cudaError_t launch_batched_k(const BatchedScratch& bs, const StepParams<T>& a, cudaStream_t st) {
+  BatchedArgs ba;
+  ba.order = bs.order;
+  ba.block_begin = bs.block_begin;
+  ba.offs = bs.offs;
+  ba.keys = bs.keys;
+  ba.tmp = bs.tmp;
+  ba.perm = bs.perm;
+  ba.bucket_target = static_cast<uint32_t>(bs.bucket_target);
+  k_rbm_batched<T, D, MODE><<<bs.grid, bs.threads, batched_smem<T, D>(), st>>>(ba, a);
+  return cudaGetLastError();
+}
+
+template <typename T, int D>
+cudaError_t prepare_batched_d(int threads, int* blocks_per_sm) {
+  const int smem = static_cast<int>(batched_smem<T, D>());
+  cudaError_t e = cudaFuncSetAttribute(k_rbm_batched<T, D, kModePerm>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_rbm_batched<T, D, kModeStep>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_rbm_batched<T, D, kModeForces>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_rbm_batched<T, D, kModeStep>, threads, smem);
+  return e;
+}
+
+}  // namespace
+
+int batched_max_buckets() { return static_cast<int>(kBMaxBuckets); }
+
+cudaError_t prepare_batched_kernels(int dtype, int d, int threads, int* blocks_per_sm) {
+  if (dtype == RBM_F32) {
+    if (d == 1) return prepare_batched_d<float, 1>(threads, blocks_per_sm);
+    if (d == 2) return prepare_batched_d<float, 2>(threads, blocks_per_sm);
+    return prepare_batched_d<float, 3>(threads, blocks_per_sm);
+  }
+  if (d == 1) return prepare_batched_d<double, 1>(threads, blocks_per_sm);
+  if (d == 2) return prepare_batched_d<double, 2>(threads, blocks_per_sm);
+  return prepare_batched_d<double, 3>(threads, blocks_per_sm);
+}
+
+template <typename T>
+cudaError_t launch_batched(const BatchedScratch& bs, int d, int mode, const void* params, const LaunchCfg& cfg,
+                           cudaStream_t st) {
+  const StepParams<T>& a = *static_cast<const StepParams<T>*>(params);
+  cudaError_t e;
+  if (d == 1) {
+    e = (mode == kModeStep) ? launch_batched_k<T, 1, kModeStep>(bs, a, st)
+      : (mode == kModeForces) ? launch_batched_k<T, 1, kModeForces>(bs, a, st)
+                              : launch_batched_k<T, 1, kModePerm>(bs, a, st);
+  } else if (d == 2) {
+    e = (mode == kModeStep) ? launch_batched_k<T, 2, kModeStep>(bs, a, st)
+      : (mode == kModeForces) ? launch_batched_k<T, 2, kModeForces>(bs, a, st)
+                              : launch_batched_k<T, 2, kModePerm>(bs, a, st);
+  } else {
+    e = (mode == kModeStep) ? launch_batched_k<T, 3, kModeStep>(bs, a, st)
+      : (mode == kModeForces) ? launch_batched_k<T, 3, kModeForces>(bs, a, st)
+                              : launch_batched_k<T, 3, kModePerm>(bs, a, st);
+  }
+  mark_launch(cfg, st, "k_rbm_batched");
+  return e;
+}
+
+template cudaError_t launch_batched<float>(const BatchedScratch&, int, int, const void*, const LaunchCfg&,
+                                           cudaStream_t);
+template cudaError_t launch_batched<double>(const BatchedScratch&, int, int, const void*, const LaunchCfg&,
+                                            cudaStream_t);
+
+}  // namespace rbm

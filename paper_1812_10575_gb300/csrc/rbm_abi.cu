@@ -4,8 +4,11 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
 #include <new>
+#include <sstream>
 #include <string>
+#include <vector>
 
 #include "rbm_device.cuh"
 #include "rbm_internal.h"
@@ -28,6 +31,10 @@ struct rbm_ctx {
   size_t partial_rows = 0;
   PermScratch ps;
   CoopScratch cs;
+  bool batched = false;
+  BatchedScratch bs;
+  std::vector<int64_t> rep_n;   // replica sizes (batched contexts)
+  int batched_blocks_per_sm = 0;
   bool use_coop = false;
   int coop_blocks_per_sm = 0;
   LaunchCfg cfg;
@@ -83,6 +90,14 @@ void free_scratch(rbm_ctx* c) {
   s = PermScratch{};
   cudaFree(c->cs.hist); cudaFree(c->cs.tmp); cudaFree(c->cs.bar);
   c->cs = CoopScratch{};
+  cudaFree(c->bs.order); cudaFree(c->bs.block_begin); cudaFree(c->bs.offs);
+  cudaFree(c->bs.keys); cudaFree(c->bs.tmp); cudaFree(c->bs.perm);
+  {
+    const int threads = c->bs.threads, target = c->bs.bucket_target;
+    c->bs = BatchedScratch{};
+    c->bs.threads = threads;
+    c->bs.bucket_target = target;
+  }
   cudaFree(c->xtmp);
   c->xtmp = nullptr;
   cudaFree(c->partial);
@@ -201,6 +216,23 @@ uint2 seed_of(const rbm_ctx* c) {
 
 // Enqueue one RBM step (mode 1), the permutation only (0) or the forces (2).
 rbm_status enqueue_rbm(rbm_ctx* c, int mode, const int64_t* m_ptr, int64_t m_off, void* fout, cudaStream_t st) {
+  if (c->batched) {
+    cudaError_t e;
+    if (c->prm.dtype == RBM_F32) {
+      StepParams<float> a = step_params<float>(c, m_ptr, m_off);
+      a.fout = static_cast<float*>(fout);
+      e = launch_batched<float>(c->bs, c->prm.d, mode, &a, c->cfg, st);
+    } else {
+      StepParams<double> a = step_params<double>(c, m_ptr, m_off);
+      a.fout = static_cast<double*>(fout);
+      e = launch_batched<double>(c->bs, c->prm.d, mode, &a, c->cfg, st);
+    }
+    if (e != cudaSuccess) {
+      set_error("k_rbm_batched launch", e);
+      return RBM_ERR_CUDA;
+    }
+    return RBM_OK;
+  }
   if (c->use_coop) {
     const uint64_t wait_ns = 1000ull * static_cast<uint64_t>(c->tuning.wait_limit_us > 0 ? c->tuning.wait_limit_us
                                                                                           : 1000000);
@@ -303,6 +335,63 @@ rbm_status capture_graph(rbm_ctx* c, int32_t method, int64_t len) {
   return RBM_OK;
 }
 
+// Replicas sorted by size (largest first) and dealt to the blocks in snake
+// order (0, 1, .., G-1, G-1, .., 0, ...), so each block's total stays close
+// to the mean; every block then walks its own list.
+rbm_status build_batched_schedule(rbm_ctx* c) {
+  BatchedScratch& bs = c->bs;
+  const int32_t nrep = static_cast<int32_t>(c->rep_n.size());
+  int bpsm = 0;
+  cudaError_t e = prepare_batched_kernels(c->prm.dtype, c->prm.d, bs.threads, &bpsm);
+  if (e != cudaSuccess || bpsm < 1) {
+    set_error("prepare_batched_kernels", e == cudaSuccess ? cudaErrorInvalidConfiguration : e);
+    return RBM_ERR_CUDA;
+  }
+  c->batched_blocks_per_sm = bpsm;
+  uint32_t grid = static_cast<uint32_t>(c->cfg.num_sms) * static_cast<uint32_t>(bpsm);
+  if (grid > static_cast<uint32_t>(nrep)) grid = static_cast<uint32_t>(nrep);
+  std::vector<int32_t> idx(nrep);
+  for (int32_t r = 0; r < nrep; ++r) idx[r] = r;
+  std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) { return c->rep_n[x] > c->rep_n[y]; });
+  std::vector<std::vector<uint32_t>> lists(grid);
+  for (int32_t k = 0; k < nrep; ++k) {
+    const uint32_t round = static_cast<uint32_t>(k) / grid, pos = static_cast<uint32_t>(k) % grid;
+    const uint32_t blk = (round % 2 == 0) ? pos : grid - 1 - pos;
+    lists[blk].push_back(static_cast<uint32_t>(idx[k]));
+  }
+  std::vector<uint32_t> order, begin(grid + 1, 0);
+  for (uint32_t g = 0; g < grid; ++g) {
+    begin[g] = static_cast<uint32_t>(order.size());
+    order.insert(order.end(), lists[g].begin(), lists[g].end());
+  }
+  begin[grid] = static_cast<uint32_t>(order.size());
+  cudaFree(bs.order);
+  cudaFree(bs.block_begin);
+  bs.order = nullptr;
+  bs.block_begin = nullptr;
+  RBM_CUDA(cudaMalloc(&bs.order, sizeof(uint32_t) * order.size()));
+  RBM_CUDA(cudaMalloc(&bs.block_begin, sizeof(uint32_t) * begin.size()));
+  RBM_CUDA(cudaMemcpy(bs.order, order.data(), sizeof(uint32_t) * order.size(), cudaMemcpyHostToDevice));
+  RBM_CUDA(cudaMemcpy(bs.block_begin, begin.data(), sizeof(uint32_t) * begin.size(), cudaMemcpyHostToDevice));
+  bs.grid = grid;
+  return RBM_OK;
+}
+
+rbm_status alloc_batched(rbm_ctx* c) {
+  BatchedScratch& bs = c->bs;
+  const int32_t nrep = static_cast<int32_t>(c->rep_n.size());
+  std::vector<uint64_t> offs(nrep + 1, 0);
+  for (int32_t r = 0; r < nrep; ++r) offs[r + 1] = offs[r] + static_cast<uint64_t>(c->rep_n[r]);
+  const size_t rows = static_cast<size_t>(offs[nrep]);
+  RBM_CUDA(cudaMalloc(&bs.offs, sizeof(uint64_t) * offs.size()));
+  RBM_CUDA(cudaMemcpy(bs.offs, offs.data(), sizeof(uint64_t) * offs.size(), cudaMemcpyHostToDevice));
+  RBM_CUDA(cudaMalloc(&bs.keys, sizeof(uint64_t) * rows));
+  RBM_CUDA(cudaMalloc(&bs.tmp, sizeof(uint32_t) * rows));
+  RBM_CUDA(cudaMalloc(&bs.perm, sizeof(uint32_t) * rows));
+  RBM_CUDA(cudaMalloc(&c->xtmp, c->row_bytes * rows));
+  return build_batched_schedule(c);
+}
+
 }  // namespace
 
 void rbm::set_last_error_text(const char* text) { snprintf(g_last_error, sizeof(g_last_error), "%s", text); }
@@ -391,6 +480,7 @@ rbm_status rbm_step(rbm_ctx* ctx) {
 rbm_status rbm_direct_step(rbm_ctx* ctx) {
   rbm_status st = usable(ctx);
   if (st != RBM_OK) return st;
+  if (ctx->batched) return RBM_ERR_UNSUPPORTED;
   st = enqueue_step(ctx, RBM_METHOD_DIRECT, nullptr, ctx->m, ctx->stream);
   if (st == RBM_OK) ctx->m += 1;
   return st;
@@ -400,6 +490,7 @@ rbm_status rbm_run(rbm_ctx* ctx, int64_t steps, int32_t method) {
   rbm_status st = usable(ctx);
   if (st != RBM_OK) return st;
   if (steps < 0 || (method != RBM_METHOD_RBM && method != RBM_METHOD_DIRECT)) return RBM_ERR_INVALID;
+  if (ctx->batched && method != RBM_METHOD_RBM) return RBM_ERR_UNSUPPORTED;
   const int64_t len = ctx->tuning.graph_steps > 0 ? ctx->tuning.graph_steps : 100;
   while (steps >= len) {
     if (!ctx->graph[method] || ctx->graph_len[method] != len) {
@@ -472,6 +563,10 @@ rbm_status rbm_set_tuning(rbm_ctx* ctx, const rbm_tuning* tuning) {
     return RBM_ERR_INVALID;
   RBM_CUDA(cudaStreamSynchronize(ctx->stream));
   drop_graphs(ctx);
+  if (ctx->batched) {  // batched contexts take only the graph length here
+    ctx->tuning.graph_steps = tuning->graph_steps > 0 ? tuning->graph_steps : 100;
+    return RBM_OK;
+  }
   free_scratch(ctx);
   ctx->tuning = *tuning;
   if (ctx->tuning.graph_steps == 0) ctx->tuning.graph_steps = 100;
@@ -514,7 +609,8 @@ rbm_status rbm_permutation(rbm_ctx* ctx, uint32_t* perm_dev) {
   if (!perm_dev) return RBM_ERR_INVALID;
   st = enqueue_rbm(ctx, 0, nullptr, ctx->m, nullptr, ctx->stream);
   if (st != RBM_OK) return st;
-  RBM_CUDA(cudaMemcpyAsync(perm_dev, ctx->ps.perm, sizeof(uint32_t) * static_cast<size_t>(ctx->prm.n),
+  RBM_CUDA(cudaMemcpyAsync(perm_dev, ctx->batched ? ctx->bs.perm : ctx->ps.perm,
+                           sizeof(uint32_t) * static_cast<size_t>(ctx->prm.n),
                            cudaMemcpyDeviceToDevice, ctx->stream));
   return RBM_OK;
 }
@@ -524,7 +620,10 @@ rbm_status rbm_forces(rbm_ctx* ctx, int32_t method, void* f_dev) {
   if (st != RBM_OK) return st;
   if (!f_dev || (reinterpret_cast<uintptr_t>(f_dev) & 15u)) return RBM_ERR_INVALID;
   if (method == RBM_METHOD_RBM) return enqueue_rbm(ctx, 2, nullptr, ctx->m, f_dev, ctx->stream);
-  if (method == RBM_METHOD_DIRECT) return enqueue_direct(ctx, 1, nullptr, ctx->m, nullptr, 0, f_dev, ctx->stream);
+  if (method == RBM_METHOD_DIRECT) {
+    if (ctx->batched) return RBM_ERR_UNSUPPORTED;
+    return enqueue_direct(ctx, 1, nullptr, ctx->m, nullptr, 0, f_dev, ctx->stream);
+  }
   return RBM_ERR_INVALID;
 }
 
@@ -532,6 +631,7 @@ rbm_status rbm_direct_forces_at(rbm_ctx* ctx, const void* q_dev, int64_t nq, voi
   rbm_status st = usable(ctx);
   if (st != RBM_OK) return st;
   if (nq < 0 || nq > (int64_t(1) << 31)) return RBM_ERR_INVALID;
+  if (ctx->batched) return RBM_ERR_UNSUPPORTED;
   if (nq == 0) return RBM_OK;
   if (!q_dev || !f_dev || (reinterpret_cast<uintptr_t>(q_dev) & 15u) || (reinterpret_cast<uintptr_t>(f_dev) & 15u))
     return RBM_ERR_INVALID;
@@ -582,9 +682,185 @@ rbm_status rbm_step_profiled(rbm_ctx* ctx, int32_t method, float* kernel_ms, int
   return st;
 }
 
+rbm_status rbm_batched_init(const rbm_params* base, int32_t nrep, const int64_t* n_host, void* x_dev,
+                            void* cuda_stream, rbm_ctx** out) {
+  if (!out) return RBM_ERR_INVALID;
+  *out = nullptr;
+  if (!base || !n_host || nrep < 1) return RBM_ERR_INVALID;
+  int64_t total = 0;
+  for (int32_t r = 0; r < nrep; ++r) {
+    if (n_host[r] < 2 || n_host[r] > (int64_t(1) << 20)) return RBM_ERR_INVALID;
+    total += n_host[r];
+  }
+  if (total != base->n) return RBM_ERR_INVALID;
+  rbm_params prm = *base;
+  prm.p = std::max<int32_t>(2, prm.p);
+  // validate the shared parameters as for one system of size max(N_r, p)
+  rbm_params chk = prm;
+  chk.n = std::max<int64_t>(total, prm.p);
+  rbm_status st = check_params(&chk);
+  if (st != RBM_OK) return st;
+  if (prm.p > 32 || prm.scheme != RBM_SCHEME_EULER) return RBM_ERR_INVALID;
+  if (!x_dev || (reinterpret_cast<uintptr_t>(x_dev) & 15u)) return RBM_ERR_INVALID;
+  rbm_ctx* c = new (std::nothrow) rbm_ctx();
+  if (!c) return RBM_ERR_NOMEM;
+  c->prm = prm;
+  c->batched = true;
+  c->rep_n.assign(n_host, n_host + nrep);
+  c->ld = (prm.d == 3) ? 4 : prm.d;
+  c->elem = (prm.dtype == RBM_F32) ? 4 : 8;
+  c->row_bytes = c->elem * c->ld;
+  c->x = x_dev;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+    c->cfg.num_sms = sms;
+  c->tuning.graph_steps = 100;
+  if (cudaMalloc(&c->status, sizeof(int32_t)) != cudaSuccess || cudaMalloc(&c->m_dev, sizeof(int64_t)) != cudaSuccess) {
+    cudaFree(c->status);
+    delete c;
+    return RBM_ERR_NOMEM;
+  }
+  cudaMemset(c->status, 0, sizeof(int32_t));
+  cudaMemset(c->m_dev, 0, sizeof(int64_t));
+  st = alloc_batched(c);
+  if (st != RBM_OK || cudaDeviceSynchronize() != cudaSuccess) {
+    free_scratch(c);
+    cudaFree(c->status);
+    cudaFree(c->m_dev);
+    delete c;
+    return st != RBM_OK ? st : RBM_ERR_CUDA;
+  }
+  *out = c;
+  return RBM_OK;
+}
+
+rbm_status rbm_batched_set_launch(rbm_ctx* ctx, int32_t threads, int32_t bucket_target) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (!ctx->batched) return RBM_ERR_INVALID;
+  if ((threads != 256 && threads != 512 && threads != 1024) || bucket_target < 64 || bucket_target > 2048)
+    return RBM_ERR_INVALID;
+  RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+  drop_graphs(ctx);
+  ctx->bs.threads = threads;
+  ctx->bs.bucket_target = bucket_target;
+  return build_batched_schedule(ctx);
+}
+
+rbm_status rbm_autotune(rbm_ctx* ctx, int32_t trial_steps, const char* table_path, char* report, int32_t report_len) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (trial_steps < 1) return RBM_ERR_INVALID;
+  // workload signature: kind, dtype, d, p, kernel, rows, replicas, size sum of squares
+  std::ostringstream sig;
+  uint64_t sq = 0;
+  for (int64_t n : ctx->rep_n) sq += static_cast<uint64_t>(n) * static_cast<uint64_t>(n);
+  sig << (ctx->batched ? "batched" : "single") << ":" << ctx->prm.dtype << ":" << ctx->prm.d << ":" << ctx->prm.p
+      << ":" << ctx->prm.k << ":" << ctx->prm.n << ":" << ctx->rep_n.size() << ":" << sq;
+  const std::string key = sig.str();
+  std::string found;
+  if (table_path) {
+    std::ifstream in(table_path);
+    std::string line;
+    while (std::getline(in, line))
+      if (line.compare(0, key.size() + 1, key + " ") == 0) found = line.substr(key.size() + 1);
+  }
+  std::string result;
+  if (!found.empty()) {
+    std::istringstream is(found);
+    int a = 0, b = 0;
+    is >> a >> b;
+    if (ctx->batched) st = rbm_batched_set_launch(ctx, a, b);
+    else {
+      rbm_tuning t = ctx->tuning;
+      t.path = a;
+      t.direct_block = 0;
+      st = rbm_set_tuning(ctx, &t);
+    }
+    result = "table " + key + " " + found;
+  } else {
+    // time candidates on a scratch copy of the state (the step index is left as it is)
+    RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+    const size_t bytes = ctx->row_bytes * static_cast<size_t>(ctx->prm.n);
+    void* scratch = nullptr;
+    RBM_CUDA(cudaMalloc(&scratch, bytes));
+    void* real_x = ctx->x;
+    std::vector<std::pair<int, int>> cands;
+    if (ctx->batched) {
+      for (int th : {256, 512, 1024})
+        for (int bt : {512, 1024, 2048}) cands.push_back({th, bt});
+    } else {
+      cands.push_back({1, 0});
+      cands.push_back({2, 0});
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    std::pair<int, int> best_c = cands[0];
+    std::ostringstream rep;
+    for (const auto& cd : cands) {
+      if (ctx->batched) st = rbm_batched_set_launch(ctx, cd.first, cd.second);
+      else {
+        rbm_tuning t = ctx->tuning;
+        t.path = cd.first;
+        st = rbm_set_tuning(ctx, &t);
+        if (st == RBM_OK && ((ctx->use_coop ? 2 : 1) != cd.first)) continue;  // path not available
+      }
+      if (st != RBM_OK) break;
+      cudaMemcpyAsync(scratch, real_x, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+      ctx->x = scratch;
+      const int64_t m0 = ctx->m;
+      enqueue_step(ctx, RBM_METHOD_RBM, nullptr, m0, ctx->stream);  // warm-up
+      cudaEventRecord(e0, ctx->stream);
+      for (int32_t s = 0; s < trial_steps; ++s) enqueue_step(ctx, RBM_METHOD_RBM, nullptr, m0, ctx->stream);
+      cudaEventRecord(e1, ctx->stream);
+      cudaEventSynchronize(e1);
+      ctx->x = real_x;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= static_cast<float>(trial_steps);
+      rep << cd.first << "," << cd.second << "=" << ms << "ms ";
+      if (ms < best) {
+        best = ms;
+        best_c = cd;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(scratch);
+    ctx->x = real_x;
+    if (st == RBM_OK) {
+      if (ctx->batched) st = rbm_batched_set_launch(ctx, best_c.first, best_c.second);
+      else {
+        rbm_tuning t = ctx->tuning;
+        t.path = best_c.first;
+        st = rbm_set_tuning(ctx, &t);
+      }
+    }
+    if (st == RBM_OK && table_path) {
+      std::ofstream outf(table_path, std::ios::app);
+      outf << key << " " << best_c.first << " " << best_c.second << "\n";
+    }
+    std::ostringstream r2;
+    r2 << "searched " << key << " best " << best_c.first << " " << best_c.second << " (" << best << " ms/step): "
+       << rep.str();
+    result = r2.str();
+  }
+  if (report && report_len > 0) {
+    std::strncpy(report, result.c_str(), static_cast<size_t>(report_len) - 1);
+    report[report_len - 1] = 0;
+  }
+  return st;
+}
+
 rbm_status rbm_launches_per_step(const rbm_ctx* ctx, int32_t method, int32_t* launches) {
   if (!ctx || !launches) return RBM_ERR_INVALID;
-  if (method == RBM_METHOD_RBM) *launches = ctx->use_coop ? 1 : 1 + rbm_tail_launches(ctx->ps, ctx->prm.p);
+  if (method == RBM_METHOD_RBM)
+    *launches = (ctx->use_coop || ctx->batched) ? 1 : 1 + rbm_tail_launches(ctx->ps, ctx->prm.p);
   else if (method == RBM_METHOD_DIRECT) *launches = 2;  // upper bound: sum (+ chunk reduction)
   else return RBM_ERR_INVALID;
   return RBM_OK;

@@ -35,6 +35,19 @@ struct CoopScratch {
   uint32_t nbuckets = 0;        // k * grid
 };
 
+// Batched-replica scratch.
+struct BatchedScratch {
+  uint32_t* order = nullptr;        // replica ids, block-major
+  uint32_t* block_begin = nullptr;  // [grid + 1]
+  uint64_t* offs = nullptr;         // [nrep + 1] first row of each replica
+  uint64_t* keys = nullptr;         // [rows]
+  uint32_t* tmp = nullptr;          // [rows]
+  uint32_t* perm = nullptr;         // [rows]
+  uint32_t grid = 0;
+  int threads = 512;
+  int bucket_target = 1024;
+};
+
 struct LaunchCfg {
   int block = 256;
   int direct_block = 256;
@@ -74,6 +87,13 @@ uint32_t coop_bucket_target();
 template <typename T>
 cudaError_t launch_coop(const CoopScratch& cs, int d, int mode, const void* params, uint64_t wait_ns, int skip_arrival,
                         bool bump_step, const LaunchCfg& cfg, cudaStream_t st);
+
+// Batched replicas (batched.cu): mode as for launch_rbm_tail.
+int batched_max_buckets();
+cudaError_t prepare_batched_kernels(int dtype, int d, int threads, int* blocks_per_sm);
+template <typename T>
+cudaError_t launch_batched(const BatchedScratch& bs, int d, int mode, const void* params, const LaunchCfg& cfg,
+                           cudaStream_t st);
 
 // Direct O(N^2) pieces (direct.cu).  `mode`: 0 = step (into xout), 1 =
 // forces at the particles (into fout), 2 = forces at query points.
