@@ -1,0 +1,121 @@
+"""FP64 oracle of the mean-field surrogate: a 2 -> 64 -> 64 -> 2 ReLU MLP that
+approximates the interaction force F(x) = 1/(N-1) sum_j K(x - X^j) (the mean-
+field force K * mu of eq. "nonlinearfp" in arXiv:1812.10575, evaluated on the
+empirical measure), its mean-squared-error gradient and one Adam step.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  The paper has no
+surrogate; this module fixes the definitions the CUDA path must match:
+
+  xh = (x - mu) / s                               input normalisation
+  z1 = W1 xh + b1,       h1 = relu(z1)            (64)
+  z2 = W2 h1 + b2,       h2 = relu(z2)            (64)
+  y  = W3 h2 + b3                                 (2)
+  F(x) = sF * y                                   output scale
+  loss = 1/B sum_s |y_s - t_s|^2,  t_s = F_target,s / sF
+
+Weights enter every product rounded to bfloat16 (the precision the tensor-core
+kernels read them in); the hidden activations that feed the 64 x 64 products
+(h1 forward; h1 and dz2 in the weight gradient; dz2 in dh1) are rounded to
+bfloat16 as well.  Rounding is round-to-nearest-even of the float32 value.
+Everything else is FP64.  Parameter vector layout (float32 masters, 4482):
+W1[64][2], b1[64], W2[64][64], b2[64], W3[2][64], b3[2].
+"""
+from __future__ import annotations
+
+import numpy as np
+
+H = 64
+SIZES = [("W1", (H, 2)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (2, H)), ("b3", (2,))]
+N_PARAMS = sum(int(np.prod(s)) for _, s in SIZES)
+
+
+def unpack(theta):
+    theta = np.asarray(theta, dtype=np.float64)
+    out, o = {}, 0
+    for name, shape in SIZES:
+        k = int(np.prod(shape))
+        out[name] = theta[o:o + k].reshape(shape)
+        o += k
+    return out
+
+
+def pack(p):
+    return np.concatenate([np.asarray(p[name], dtype=np.float64).ravel() for name, _ in SIZES])
+
+
+def bf16(a):
+    """Round to bfloat16 (nearest, ties to even) through float32; returns float64."""
+    f = np.asarray(a, dtype=np.float64).astype(np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    nan = np.isnan(f)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    out = r.view(np.float32).astype(np.float64)
+    out[nan] = np.nan
+    return out
+
+
+def forward(theta, x, norm, emulate_bf16=True):
+    """Returns the output y (B x 2) and the activations needed by backward."""
+    p = unpack(theta)
+    q = bf16 if emulate_bf16 else (lambda a: np.asarray(a, dtype=np.float64))
+    mu, s = np.asarray(norm[:2], dtype=np.float64), float(norm[2])
+    xh = (np.asarray(x, dtype=np.float64) - mu) / s
+    z1 = xh @ q(p["W1"]).T + p["b1"]
+    h1 = np.maximum(z1, 0.0)
+    z2 = q(h1) @ q(p["W2"]).T + p["b2"]
+    h2 = np.maximum(z2, 0.0)
+    y = h2 @ q(p["W3"]).T + p["b3"]
+    return y, dict(xh=xh, z1=z1, h1=h1, z2=z2, h2=h2)
+
+
+def predict_force(theta, x, norm, emulate_bf16=True):
+    y, _ = forward(theta, x, norm, emulate_bf16)
+    return float(norm[3]) * y
+
+
+def loss_and_grad(theta, x, f_target, norm, emulate_bf16=True):
+    """MSE loss and its gradient with respect to the float parameters."""
+    p = unpack(theta)
+    q = bf16 if emulate_bf16 else (lambda a: np.asarray(a, dtype=np.float64))
+    y, a = forward(theta, x, norm, emulate_bf16)
+    t = np.asarray(f_target, dtype=np.float64) / float(norm[3])
+    B = y.shape[0]
+    r = y - t
+    loss = float(np.sum(r * r) / B)
+    dy = 2.0 * r / B                                   # B x 2
+    g = {}
+    g["W3"] = dy.T @ a["h2"]                           # 2 x 64
+    g["b3"] = dy.sum(axis=0)
+    dh2 = dy @ q(p["W3"])                              # B x 64
+    dz2 = dh2 * (a["z2"] > 0)
+    g["W2"] = q(dz2).T @ q(a["h1"])                    # 64 x 64
+    g["b2"] = dz2.sum(axis=0)
+    dh1 = q(dz2) @ q(p["W2"])                          # B x 64
+    dz1 = dh1 * (a["z1"] > 0)
+    g["W1"] = dz1.T @ a["xh"]                          # 64 x 2
+    g["b1"] = dz1.sum(axis=0)
+    return loss, pack(g)
+
+
+def adam_step(theta, m, v, grad, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015) at step t >= 1; returns (theta, m, v)."""
+    m = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * grad
+    v = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * grad * grad
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    theta = np.asarray(theta, dtype=np.float64) - lr * mhat / (np.sqrt(vhat) + eps)
+    return theta, m, v
+
+
+def init_params(seed=0):
+    """He-uniform initial weights, zero biases (a seeded draw; both sides load
+    the same values)."""
+    g = np.random.default_rng(np.random.SeedSequence([int(seed), 0x4D4C50]))
+    p = {}
+    p["W1"] = g.uniform(-1, 1, (H, 2)) * np.sqrt(6.0 / 2)
+    p["b1"] = np.zeros(H)
+    p["W2"] = g.uniform(-1, 1, (H, H)) * np.sqrt(6.0 / H)
+    p["b2"] = np.zeros(H)
+    p["W3"] = g.uniform(-1, 1, (2, H)) * np.sqrt(6.0 / H)
+    p["b3"] = np.zeros(2)
+    return pack(p).astype(np.float32).astype(np.float64)
