@@ -1,4 +1,4 @@
-"""FP64 oracle of the mean-field surrogate: a 2 -> 64 -> 64 -> 2 ReLU MLP that
+"""FP64 oracle of the mean-field surrogate: a 2 -> 64 -> 64 -> 2 tanh MLP that
 approximates the interaction force F(x) = 1/(N-1) sum_j K(x - X^j) (the mean-
 field force K * mu of eq. "nonlinearfp" in arXiv:1812.10575, evaluated on the
 empirical measure), its mean-squared-error gradient and one Adam step.
@@ -7,8 +7,8 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  The paper has no
 surrogate; this module fixes the definitions the CUDA path must match:
 
   xh = (x - mu) / s                               input normalisation
-  z1 = W1 xh + b1,       h1 = relu(z1)            (64)
-  z2 = W2 h1 + b2,       h2 = relu(z2)            (64)
+  z1 = W1 xh + b1,       h1 = tanh(z1)            (64)
+  z2 = W2 h1 + b2,       h2 = tanh(z2)            (64)
   y  = W3 h2 + b3                                 (2)
   F(x) = sF * y                                   output scale
   loss = 1/B sum_s |y_s - t_s|^2,  t_s = F_target,s / sF
@@ -61,9 +61,9 @@ def forward(theta, x, norm, emulate_bf16=True):
     mu, s = np.asarray(norm[:2], dtype=np.float64), float(norm[2])
     xh = (np.asarray(x, dtype=np.float64) - mu) / s
     z1 = xh @ q(p["W1"]).T + p["b1"]
-    h1 = np.maximum(z1, 0.0)
+    h1 = np.tanh(z1)
     z2 = q(h1) @ q(p["W2"]).T + p["b2"]
-    h2 = np.maximum(z2, 0.0)
+    h2 = np.tanh(z2)
     y = h2 @ q(p["W3"]).T + p["b3"]
     return y, dict(xh=xh, z1=z1, h1=h1, z2=z2, h2=h2)
 
@@ -87,14 +87,21 @@ def loss_and_grad(theta, x, f_target, norm, emulate_bf16=True):
     g["W3"] = dy.T @ a["h2"]                           # 2 x 64
     g["b3"] = dy.sum(axis=0)
     dh2 = dy @ q(p["W3"])                              # B x 64
-    dz2 = dh2 * (a["z2"] > 0)
+    dz2 = dh2 * (1.0 - a["h2"] * a["h2"])             # tanh' = 1 - tanh^2
     g["W2"] = q(dz2).T @ q(a["h1"])                    # 64 x 64
     g["b2"] = dz2.sum(axis=0)
     dh1 = q(dz2) @ q(p["W2"])                          # B x 64
-    dz1 = dh1 * (a["z1"] > 0)
+    dz1 = dh1 * (1.0 - a["h1"] * a["h1"])
     g["W1"] = dz1.T @ a["xh"]                          # 64 x 2
     g["b1"] = dz1.sum(axis=0)
     return loss, pack(g)
+
+
+def lr_at(lr, it, iters, round_=0):
+    """Rate of iteration it (0-based) of training round `round_` (0-based) of
+    `iters` Adam steps: a geometric decay from lr/2^round_ to lr/(100 2^round_)
+    over the round."""
+    return lr * 0.5 ** round_ * 0.01 ** (it / max(iters - 1, 1))
 
 
 def adam_step(theta, m, v, grad, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
@@ -108,14 +115,14 @@ def adam_step(theta, m, v, grad, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
 
 
 def init_params(seed=0):
-    """He-uniform initial weights, zero biases (a seeded draw; both sides load
-    the same values)."""
+    """Initial parameters: each weight and bias of a layer uniform in
+    +-c/sqrt(fan_in), c = 3 for the input layer and 1 otherwise (a seeded
+    draw; the CUDA path draws its own start and tests load the same values
+    into both sides)."""
     g = np.random.default_rng(np.random.SeedSequence([int(seed), 0x4D4C50]))
     p = {}
-    p["W1"] = g.uniform(-1, 1, (H, 2)) * np.sqrt(6.0 / 2)
-    p["b1"] = np.zeros(H)
-    p["W2"] = g.uniform(-1, 1, (H, H)) * np.sqrt(6.0 / H)
-    p["b2"] = np.zeros(H)
-    p["W3"] = g.uniform(-1, 1, (2, H)) * np.sqrt(6.0 / H)
-    p["b3"] = np.zeros(2)
+    for name, shape in SIZES:
+        fan_in = 2 if name in ("W1", "b1") else H
+        c = 3.0 if name in ("W1", "b1") else 1.0
+        p[name] = g.uniform(-1, 1, shape) * c / np.sqrt(fan_in)
     return pack(p).astype(np.float32).astype(np.float64)

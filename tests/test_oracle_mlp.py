@@ -25,23 +25,60 @@ def test_gradient_matches_finite_differences():
         assert abs(fd - g[i]) <= 1e-7 + 1e-6 * abs(fd), (i, fd, g[i])
 
 
-def test_hand_built_network_computes_known_function():
-    """W1 = [[1,0],[-1,0],[0,1],[0,-1],0...], W2 = I, W3 picks |x0| - |x1|
-    through relu(x) + relu(-x) = |x|; with mu = 0, s = 1, sF = 2."""
+def test_saturated_network_computes_known_function():
+    """Weights large enough that every tanh saturates to exactly +-1 or sits
+    at tanh(0) = 0, so the output is a known step function of the input; W2 is
+    not symmetric, so a transposed W2 changes the answer.  All weights are
+    exact in bfloat16.  mu = (0.5, -0.25), s = 2, sF = 4."""
     p = {k: np.zeros(s) for k, s in mlp.SIZES}
-    p["W1"][0] = [1, 0]
-    p["W1"][1] = [-1, 0]
-    p["W1"][2] = [0, 1]
-    p["W1"][3] = [0, -1]
-    p["W2"] = np.eye(mlp.H)
-    p["W3"][0, :4] = [1, 1, -1, -1]
-    p["W3"][1, :4] = [0, 0, 1, 1]
-    p["b3"] = [0.5, 0.0]
+    p["W1"][0] = [256, 0]           # h1[0] = sign(x0 - 0.5)
+    p["W1"][1] = [0, 256]           # h1[1] = sign(x1 + 0.25)
+    p["W1"][2] = [256, 256]         # h1[2] = sign(x0 + x1 - 0.25)
+    p["b1"][3] = 64                 # h1[3] = 1
+    p["W2"][5, 0] = 512             # h2[5] = h1[0]
+    p["W2"][6, 1] = -512            # h2[6] = -h1[1]
+    p["W2"][7, 2] = 512
+    p["W2"][7, 3] = 512             # h2[7] = 1 if h1[2] = 1 else tanh(0) = 0
+    p["W3"][0, 5:8] = [1, 2, 0.5]
+    p["W3"][1, 5:8] = [-1, 0, 4]
+    p["b3"] = [0.25, -0.5]
     theta = mlp.pack(p)
-    x = np.array([[0.75, -2.5], [-1.5, 0.25]])
-    f = mlp.predict_force(theta, x, np.array([0.0, 0.0, 1.0, 2.0]))
-    # y0 = |x0| - |x1| + 0.5, y1 = |x1|; F = 2 y (all values exact in bfloat16)
-    np.testing.assert_array_equal(f, [[2 * (0.75 - 2.5 + 0.5), 2 * 2.5], [2 * (1.5 - 0.25 + 0.5), 2 * 0.25]])
+    x = np.array([[1.5, 0.75], [-1.0, 0.5], [0.0, -2.0], [3.0, -1.0]])
+    f = mlp.predict_force(theta, x, np.array([0.5, -0.25, 2.0, 4.0]))
+    # (h2[5], h2[6], h2[7]) = (+1, -1, 1), (-1, -1, 0), (-1, +1, 0), (+1, +1, 1)
+    want = 4 * np.array([[1 - 2 + 0.5 + 0.25, -1 + 4 - 0.5],
+                         [-1 - 2 + 0.25, 1 - 0.5],
+                         [-1 + 2 + 0.25, 1 - 0.5],
+                         [1 + 2 + 0.5 + 0.25, -1 + 4 - 0.5]])
+    np.testing.assert_array_equal(f, want)
+
+
+def test_tanh_layers_at_closed_form_points():
+    """tanh(ln a) = (a^2 - 1)/(a^2 + 1): an input of ln 2 gives h1 = 3/5 and
+    W2 = ln 3 / 0.6 gives h2 = tanh(ln 3) = 4/5 (FP64, no bfloat16)."""
+    p = {k: np.zeros(s) for k, s in mlp.SIZES}
+    p["W1"][9] = [0, 1]
+    p["W2"][4, 9] = np.log(3.0) / 0.6
+    p["W3"][:, 4] = [1.0, -3.0]
+    p["b3"] = [0.5, 0.0]
+    f = mlp.predict_force(mlp.pack(p), np.array([[7.0, np.log(2.0)]]), np.array([0.0, 0.0, 1.0, 2.0]),
+                          emulate_bf16=False)
+    np.testing.assert_allclose(f, [[2 * (0.8 + 0.5), 2 * (-2.4)]], rtol=1e-13)
+
+
+def test_small_inputs_see_the_linearised_network():
+    """Zero biases and |z| ~ 1e-4: tanh(z) = z - z^3/3 + ..., so the force is
+    sF W3 W2 W1 (x - mu)/s to relative O(z^2)."""
+    rng = np.random.default_rng(5)
+    p = {k: np.zeros(s) for k, s in mlp.SIZES}
+    p["W1"] = rng.normal(0, 1, (mlp.H, 2))
+    p["W2"] = rng.normal(0, 0.3, (mlp.H, mlp.H))
+    p["W3"] = rng.normal(0, 1, (2, mlp.H))
+    mu, s, sF = np.array([1.0, -2.0]), 3.0, 0.7
+    x = mu + s * rng.normal(0, 1e-5, (5, 2))
+    f = mlp.predict_force(mlp.pack(p), x, np.array([mu[0], mu[1], s, sF]), emulate_bf16=False)
+    lin = sF * ((x - mu) / s) @ (p["W3"] @ p["W2"] @ p["W1"]).T
+    np.testing.assert_allclose(f, lin, rtol=1e-6)
 
 
 def test_bf16_rounding_matches_torch():
