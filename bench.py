@@ -12,7 +12,7 @@ so the flush's dirty lines are written back before the step starts) and each
 step is timed alone with CUDA events on the stream its kernels run on.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload thomson|batched_opinion|dyson|large_n]
+                    [--workload thomson|batched_opinion|dyson|large_n|surrogate]
 
 Other workloads (one JSON line each, same keys):
   batched_opinion - 4096 independent 2-D bounded-confidence opinion systems
@@ -22,7 +22,13 @@ Other workloads (one JSON line each, same keys):
   dyson           - Dyson Brownian motion (Sec. 4.2), N = 1000, FP64,
                     splitting scheme, p = 2, dt = 1e-3;
   large_n         - regularised attraction, d = 3, FP32, N = 2^16 .. 2^24,
-                    p in {2, 4, 8}, RBM and (up to 2^20) direct.
+                    p in {2, 4, 8}, RBM and (up to 2^20) direct;
+  surrogate       - the learned mean-field surrogate, N = 2^22, d = 2,
+                    Gaussian aggregation with confinement from a 4-cluster
+                    mixture, sigma = 0.1, dt = 1e-3: whole 100-step cycles
+                    (checkpoint training + 100 network steps), the network
+                    step alone, RBM-1 and direct at the same N, and the
+                    accuracy of each at N = 2^16 against the direct method.
 Under torchrun each rank advances its own replica of the workload (replica
 index = rank; no data-path collective): weak scaling.  ``--impl reference``
 times the CPU oracle on this host's cores instead (rank 0 only).
@@ -60,6 +66,11 @@ WORKLOADS = {
     "large_n": dict(workload="large_n_reg_attract", d=3, dt=1e-3, sigma=0.2, kernel="reg_attract",
                     potential="quadratic", v_coef=1.0, k_param=0.01, renorm=False, dtype="f32", seed=0,
                     scheme="euler", sizes=[2**16, 2**18, 2**20, 2**22, 2**24], ps=[2, 4, 8], direct_max=2**20),
+    "surrogate": dict(workload="surrogate_mixture_aggregation", n=2**22, d=2, p=2, dt=1e-3, sigma=0.1,
+                      kernel="gauss_agg", potential="quadratic", v_coef=1.0, k_param=0.0, renorm=False, dtype="f32",
+                      seed=0, scheme="euler", train_every=100, n_queries=16384, iters_first=12000,
+                      iters_per_checkpoint=2000, max_rounds=8, lr=3e-3, fallback_tol=1e-2, accuracy_n=2**16,
+                      accuracy_steps=300),
 }
 
 
@@ -165,6 +176,8 @@ def _initial(w, n, seed=None):
         return workloads.dyson(n, seed)
     if w["workload"].startswith("batched"):
         return workloads.unit_cube(n, w["d"], seed=seed)
+    if w["workload"].startswith("surrogate"):
+        return workloads.mixture(n, w["d"], seed=seed)
     return workloads.gaussian(n, w["d"], seed=seed)
 
 
@@ -521,10 +534,174 @@ def run_large_n(args, w, g):
             "data": "synthetic", "config": dict(w, l2="state larger than L2 from N = 2^23"), "sweep": rows}
 
 
+def _w1_marginals(A, B):
+    """Wasserstein-1 distance of each coordinate's empirical distribution
+    (equal sample sizes: the mean absolute difference of the sorted values)."""
+    return [float(np.mean(np.abs(np.sort(A[:, k]) - np.sort(B[:, k])))) for k in range(A.shape[1])]
+
+
+def run_surrogate(args, w, g):
+    """The learned mean-field surrogate on the 4-cluster aggregation workload:
+    whole 100-step cycles (checkpoint: queries, direct forces at them, Adam
+    rounds until the held-out error is within tolerance; then 100 network
+    steps replayed from a graph), the network step alone, RBM-1 and one direct
+    step at the same N, and the accuracy of each method at N = 2^16 against
+    the direct method with the same Brownian increments."""
+    import paper_1812_10575_gb300 as rbm
+
+    n, d = w["n"], w["d"]
+    kw = dict(p=w["p"], dt=w["dt"], sigma=w["sigma"], seed=w["seed"], v=w["potential"], v_coef=w["v_coef"],
+              k=w["kernel"], k_param=w["k_param"], replica=g.rank)
+    cfg = dict(train_every=w["train_every"], fallback_tol=w["fallback_tol"], n_queries=w["n_queries"],
+               iters_first=w["iters_first"], iters_per_checkpoint=w["iters_per_checkpoint"],
+               max_rounds=w["max_rounds"], lr=w["lr"])
+    every = w["train_every"]
+    X0 = _initial(w, n)
+    x = _to_dev(g, X0, d, "f32")
+    sysm = rbm.System(x, d=d, stream=g.stream, **kw)
+    sysm.surrogate_config(**cfg)
+    clocks = ClockSampler(g.local).start()
+    e0, e1 = g.event(), g.event()
+    e0.record(g.stream)
+    sysm.run(every, "surrogate")                 # first checkpoint (training from scratch) + one cycle
+    e1.record(g.stream)
+    sysm.sync()
+    first_cycle_ms = e0.elapsed_time(e1)
+    st0 = sysm.surrogate_stats()
+    cycles = max(2, -(-args.steps // every))
+    starts = [g.event() for _ in range(cycles)]
+    ends = [g.event() for _ in range(cycles)]
+    g.barrier()
+    wall0 = time.perf_counter()
+    for k in range(cycles):
+        starts[k].record(g.stream)
+        sysm.run(every, "surrogate")             # checkpoint + `every` steps
+        ends[k].record(g.stream)
+    g.barrier()
+    wall = time.perf_counter() - wall0
+    cyc_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    st1 = sysm.surrogate_stats()
+    total_ms = g.max_over_ranks(float(sum(cyc_ms)))
+    value = g.world * n * every * cycles / (total_ms * 1e-3)
+
+    # the network step alone, kernel by kernel (inputs 32 MiB: L2 flushed first)
+    per_kernel = {}
+    for _ in range(max(args.warmup, 3) + 5):
+        g.flush()
+        for name, ms in sysm.step_profiled("surrogate"):
+            per_kernel.setdefault(name, []).append(ms)
+    avg = {k: float(np.mean(v[3:])) for k, v in per_kernel.items()}
+    step_ms = float(sum(avg.values()))
+    # the same step through the C ABI with host buffers
+    host = x.detach().cpu().pin_memory()
+    sysm.step_host(host, "surrogate")
+    e2e_ms = []
+    for _ in range(5):
+        g.torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sysm.step_host(host, "surrogate")
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_total = g.max_over_ranks(float(np.mean(e2e_ms)))
+    launches = sysm.launches_per_step("surrogate")
+    sysm.close()
+
+    # RBM-1 and one direct step at the same N
+    xr = _to_dev(g, X0, d, "f32")
+    rb = rbm.System(xr, d=d, stream=g.stream, **kw)
+    rb.run(every)
+    rb.sync()
+    e0.record(g.stream)
+    rb.run(every)
+    e1.record(g.stream)
+    rb.sync()
+    rbm_ms = e0.elapsed_time(e1) / every
+    e0.record(g.stream)
+    rb.direct_step()
+    e1.record(g.stream)
+    rb.sync()
+    direct_ms = e0.elapsed_time(e1)
+    rb.close()
+    clocks.stop()
+
+    # accuracy at N = 2^16 after `accuracy_steps` steps, same X0 and increments
+    na, steps = w["accuracy_n"], w["accuracy_steps"]
+    Xa = _initial(w, na)
+    # the surrogate as configured (retrained every train_every steps) and
+    # retrained every 25 steps in rounds of 1000 Adam iterations
+    variants = {"rbm": None, "surrogate": cfg,
+                "surrogate_every25": dict(cfg, train_every=25, iters_per_checkpoint=1000)}
+    out, stats, secs = {}, {}, {}
+    for method in ("direct",) + tuple(variants):
+        xa = _to_dev(g, Xa, d, "f32")
+        sa = rbm.System(xa, d=d, stream=g.stream, **kw)
+        if variants.get(method):
+            sa.surrogate_config(**variants[method])
+        g.torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sa.run(steps, "surrogate" if variants.get(method) else method)
+        sa.sync()
+        secs[method] = time.perf_counter() - t0
+        out[method] = xa[:, :d].double().cpu().numpy()
+        if variants.get(method):
+            stats[method] = sa.surrogate_stats()
+        sa.close()
+    acc = {"direct": {"wall_s": secs["direct"]}}
+    for method in variants:
+        diff = out[method] - out["direct"]
+        acc[method] = {"E_T": float(np.sqrt(np.mean(np.sum(diff ** 2, axis=1)))),
+                       "w1_marginals_vs_direct": _w1_marginals(out[method], out["direct"]),
+                       "wall_s": secs[method]}
+        if method in stats:
+            acc[method]["stats"] = stats[method]
+
+    # launches in the timed cycles: the network step and the gated RBM-1
+    # kernels per step; per checkpoint the query sample and the direct sum
+    # (2); per round 2 per Adam iteration, the step-count bump, the network
+    # forces at the queries and the error check
+    adam = st1["adam_steps"] - st0["adam_steps"]
+    rounds = adam // max(1, w["iters_per_checkpoint"])
+    gpu_launches = cycles * (every * launches + 3) + 2 * adam + 3 * rounds
+    peaks, peak_src = _measured_peaks()
+    dom = "k_sur_step"
+    # special-function unit: 2 operations per tanh (exponential, reciprocal),
+    # 128 tanh per particle, plus 4 for the Gaussian pair (log, sqrt, sin, cos)
+    mufu_per_particle = 2 * 128 + 4
+    mufu_peak = 152 * 16 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = mufu_per_particle * n / (avg[dom] * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": g.world, "steps": every * cycles,
+        "warmup": every, "ms_per_step": total_ms / (every * cycles), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (bf16 tensor-core operands)", "data": "synthetic",
+        "config": dict(w, l2="state 32 MiB: L2 not flushed inside a cycle (a cycle is one graph); "
+                             "flushed before each profiled network step",
+                       parallelism=f"replicas x{g.world} (one independent system per GPU)"),
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": mufu_peak,
+                     "unit": "T special-function ops/s", "frac": achieved / mufu_peak, "traffic": None,
+                     "ops_per_particle": mufu_per_particle, "avg_launch_ms": avg[dom],
+                     "peak_source": "152 SMs x 16 special-function results per clock x max SM clock"},
+        "e2e": {"value": g.world * n / (e2e_total * 1e-3), "unit": UNIT, "h2d_bytes_per_step": n * 8,
+                "d2h_bytes_per_step": n * 8, "note": "one network step through rbm_step_host"},
+        "gpu_launches": gpu_launches,
+        "clocks": clocks.summary(),
+        "methods": {"surrogate_cycle": value / g.world, "surrogate_step_only": n / (step_ms * 1e-3),
+                    "rbm": n / (rbm_ms * 1e-3), "direct": n / (direct_ms * 1e-3),
+                    "surrogate_step_ms": step_ms, "rbm_ms_per_step": rbm_ms, "direct_ms_per_step": direct_ms,
+                    "cycle_ms": cyc_ms, "first_cycle_ms": first_cycle_ms,
+                    "adam_steps_per_cycle": adam / cycles,
+                    "stats_after": st1},
+        "accuracy": dict(acc, n=na, steps=steps),
+        "kernels_ms": avg, "launches_per_network_step": launches,
+        "wall_s_timed_region": wall, "kernel_sources": _kernel_sources_digest(),
+    }
+    return line
+
+
 def run_ours(args, w):
     g = Gpu()
     if w["workload"].startswith("batched"):
         line = run_batched(args, w, g)
+    elif w["workload"].startswith("surrogate"):
+        line = run_surrogate(args, w, g)
     elif w["workload"].startswith("large_n"):
         line = run_large_n(args, w, g)
     else:

@@ -85,8 +85,10 @@ typedef enum {
 } rbm_kernel;
 
 typedef enum {
-    RBM_METHOD_RBM = 0,    /* RBM-1 step (Algorithm "randomdiv")            */
-    RBM_METHOD_DIRECT = 1  /* direct O(N^2) forward-Euler step (Sec. 4.1)   */
+    RBM_METHOD_RBM = 0,       /* RBM-1 step (Algorithm "randomdiv")            */
+    RBM_METHOD_DIRECT = 1,    /* direct O(N^2) forward-Euler step (Sec. 4.1)   */
+    RBM_METHOD_SURROGATE = 2  /* learned mean-field force with the RBM-1 step
+                                 as fallback (see rbm_surrogate_config)        */
 } rbm_method;
 
 /* Time scheme of the RBM step. */
@@ -205,6 +207,61 @@ rbm_status rbm_direct_forces_at(rbm_ctx *ctx, const void *q_dev, int64_t nq, voi
  * Synchronous.  Used by the benchmark to time kernels on their own stream. */
 rbm_status rbm_step_profiled(rbm_ctx *ctx, int32_t method, float *kernel_ms, int32_t capacity, int32_t *nkernels,
                              char *names, int32_t names_len);
+
+/* ---- learned mean-field surrogate ---------------------------------------- */
+/* The paper has no surrogate.  Its mean-field limit (Sec. 1, eq.
+ * "nonlinearfp") drives each particle by the force K * mu; here a
+ * 2 -> 64 -> 64 -> 2 tanh network F(x) is trained on the direct-sum force
+ * F(x) = 1/(N-1) sum_j K(x - X^j) at sampled particles and, while its held-out
+ * relative error stays at or below `fallback_tol`, replaces the random-batch
+ * force in the Euler-Maruyama step (-grad V and the Brownian increment as in
+ * rbm_step); otherwise the RBM-1 step runs.  The choice is a device-side flag
+ * set at each checkpoint; no host synchronisation is involved.
+ *   network: xh = (x - mu)/s, h1 = tanh(W1 xh + b1), h2 = tanh(W2 h1 + b2),
+ *            F = sF (W3 h2 + b3); weights read as bfloat16; the 64 x 64
+ *            products on the tensor cores with FP32 accumulation;
+ *   training: MSE on F/sF, Adam (beta 0.9, 0.999, eps 1e-8), FP32 masters,
+ *            minibatches of 4096 of the 3/4 training share of the queries,
+ *            in round r (0-based) of a checkpoint the rate decays
+ *            geometrically from lr/2^r to lr/(100 2^r);
+ *   checkpoint (every `train_every` steps, and before the first step):
+ *            n_queries particle ids drawn by Philox (id q, step m, stream 2),
+ *            direct forces at them, mu, s, sF fixed at the first checkpoint
+ *            (unless given by rbm_surrogate_set_params),
+ *            a round of iters_first (first checkpoint) or
+ *            iters_per_checkpoint Adam steps, the error on the held-out
+ *            quarter = ||F_net - F||_2 / ||F||_2, then further rounds of
+ *            iters_per_checkpoint while that error is above fallback_tol, at
+ *            most max_rounds rounds in all (the error is read back after each
+ *            round: the only host synchronisation of the method).
+ * Requires d = 2, FP32, the Euler scheme, a single (not batched) system.
+ * Synchronous (allocates the network state). */
+rbm_status rbm_surrogate_config(rbm_ctx *ctx, int32_t train_every, double fallback_tol, int64_t n_queries,
+                                int32_t iters_first, int32_t iters_per_checkpoint, int32_t max_rounds, double lr);
+
+/* One checkpoint round now (sample, direct forces, `iters` Adam steps, error). */
+rbm_status rbm_surrogate_train(rbm_ctx *ctx, int32_t iters);
+
+/* Last held-out relative error, steps taken by the network and by the RBM
+ * fallback so far, whether the network is selected, and the Adam iterations
+ * run so far.  Any output pointer may be NULL.  Synchronous. */
+rbm_status rbm_surrogate_stats(rbm_ctx *ctx, double *last_rel_err, int64_t *n_surrogate_steps,
+                               int64_t *n_fallback_steps, int32_t *active, int64_t *n_adam_steps);
+
+/* Network parameters (4482 floats: W1[64][2], b1[64], W2[64][64], b2[64],
+ * W3[2][64], b3[2]) and normalisation (mu_x, mu_y, s, sF), host buffers;
+ * set_params also clears the Adam state.  Synchronous. */
+rbm_status rbm_surrogate_params(rbm_ctx *ctx, float *theta_host, float *norm_host);
+rbm_status rbm_surrogate_set_params(rbm_ctx *ctx, const float *theta_host, const float *norm_host);
+
+/* Network force at nq points q_dev (nq x 2 FP32, device) into f_dev. */
+rbm_status rbm_surrogate_forces(rbm_ctx *ctx, const void *q_dev, int64_t nq, void *f_dev);
+
+/* Loss and its gradient (host, 4482 floats) on nb samples: positions x_dev
+ * and target forces f_target_dev (nb x 2 FP32, device), nb <= 65536; the
+ * network's own tensor-core kernels, no update.  Synchronous. */
+rbm_status rbm_surrogate_gradient(rbm_ctx *ctx, const void *x_dev, const void *f_target_dev, int64_t nb,
+                                  float *grad_host, double *loss_host);
 
 /* ---- batched replicas --------------------------------------------------- */
 

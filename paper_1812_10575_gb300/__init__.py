@@ -18,7 +18,9 @@ from ._lib import (  # noqa: F401
     make_params, rbm_direct_forces_at, rbm_direct_step, rbm_forces, rbm_free, rbm_get_step, rbm_get_tuning,
     rbm_init, rbm_last_error, rbm_launches_per_step, rbm_permutation, rbm_permutation_noalloc, rbm_run, rbm_set_step, rbm_set_tuning,
     rbm_status_string, rbm_step, rbm_step_host, rbm_step_profiled, rbm_sync, rbm_batched_init,
-    rbm_batched_set_launch, rbm_autotune,
+    rbm_batched_set_launch, rbm_autotune, rbm_surrogate_config, rbm_surrogate_train, rbm_surrogate_stats,
+    rbm_surrogate_params, rbm_surrogate_set_params, rbm_surrogate_forces, rbm_surrogate_gradient,
+    N_SURROGATE_PARAMS,
 )
 
 
@@ -84,6 +86,7 @@ class Replicas:
 
     def autotune(self, trial_steps=3, table_path=None):
         return rbm_autotune(self.ctx, trial_steps, table_path)
+
 
     def step_profiled(self):
         return rbm_step_profiled(self.ctx, "rbm")
@@ -179,6 +182,32 @@ class System:
 
     def launches_per_step(self, method="rbm"):
         return rbm_launches_per_step(self.ctx, method)
+
+    # learned mean-field surrogate (d = 2, FP32)
+    def surrogate_config(self, **kw):
+        rbm_surrogate_config(self.ctx, **kw)
+
+    def surrogate_train(self, iters):
+        rbm_surrogate_train(self.ctx, iters)
+
+    def surrogate_stats(self):
+        return rbm_surrogate_stats(self.ctx)
+
+    def surrogate_params(self):
+        return rbm_surrogate_params(self.ctx)
+
+    def surrogate_set_params(self, theta, norm=None):
+        rbm_surrogate_set_params(self.ctx, theta, norm)
+
+    def surrogate_forces(self, q):
+        import torch
+
+        f = torch.zeros_like(q)
+        rbm_surrogate_forces(self.ctx, q, f)
+        return f
+
+    def surrogate_gradient(self, x, f_target):
+        return rbm_surrogate_gradient(self.ctx, x, f_target)
 
     def close(self):
         if getattr(self, "ctx", None) is not None:

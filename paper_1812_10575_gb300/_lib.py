@@ -31,7 +31,7 @@ KERNELS = {"inv1d": 0, "coulomb": 1, "bounded_conf": 2, "gauss_agg": 3, "reg_att
            "linear": 6}
 POTENTIALS = {"zero": 0, "quadratic": 1}
 RBM_METHOD_RBM, RBM_METHOD_DIRECT = 0, 1
-METHODS = {"rbm": 0, "direct": 1}
+METHODS = {"rbm": 0, "direct": 1, "surrogate": 2}
 RBM_SCHEME_EULER, RBM_SCHEME_SPLIT = 0, 1
 SCHEMES = {"euler": 0, "split": 1}
 RBM_FLAG_RENORM_SPHERE = 1
@@ -42,7 +42,10 @@ EXPORTS = (
     "rbm_set_tuning", "rbm_get_tuning", "rbm_sync", "rbm_free", "rbm_status_string", "rbm_last_error",
     "rbm_permutation", "rbm_forces", "rbm_direct_forces_at", "rbm_step_profiled", "rbm_launches_per_step",
     "rbm_permutation_noalloc", "rbm_batched_init", "rbm_batched_set_launch", "rbm_autotune",
+    "rbm_surrogate_config", "rbm_surrogate_train", "rbm_surrogate_stats", "rbm_surrogate_params",
+    "rbm_surrogate_set_params", "rbm_surrogate_forces", "rbm_surrogate_gradient",
 )
+N_SURROGATE_PARAMS = 4482
 
 
 class RbmParams(ctypes.Structure):
@@ -123,6 +126,14 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "rbm_batched_init": [P, i32, ctypes.POINTER(i64), vp, vp, ctypes.POINTER(vp)],
         "rbm_batched_set_launch": [vp, i32, i32],
         "rbm_autotune": [vp, i32, ctypes.c_char_p, ctypes.c_char_p, i32],
+        "rbm_surrogate_config": [vp, i32, ctypes.c_double, i64, i32, i32, i32, ctypes.c_double],
+        "rbm_surrogate_train": [vp, i32],
+        "rbm_surrogate_stats": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                ctypes.POINTER(i32), ctypes.POINTER(i64)],
+        "rbm_surrogate_params": [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
+        "rbm_surrogate_set_params": [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
+        "rbm_surrogate_forces": [vp, vp, i64, vp],
+        "rbm_surrogate_gradient": [vp, vp, vp, i64, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double)],
         "rbm_step_profiled": [vp, i32, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(i32), ctypes.c_char_p,
                               i32],
     }
@@ -206,6 +217,71 @@ def rbm_autotune(ctx, trial_steps: int = 3, table_path: str | None = None) -> st
     _check(load().rbm_autotune(ctx, int(trial_steps), table_path.encode() if table_path else None, rep, 1024),
            "rbm_autotune")
     return rep.value.decode()
+
+
+def rbm_surrogate_config(ctx, train_every=100, fallback_tol=1e-2, n_queries=65536, iters_first=8000,
+                         iters_per_checkpoint=1000, max_rounds=8, lr=3e-3) -> None:
+    _check(load().rbm_surrogate_config(ctx, int(train_every), float(fallback_tol), int(n_queries), int(iters_first),
+                                       int(iters_per_checkpoint), int(max_rounds), float(lr)), "rbm_surrogate_config")
+
+
+def rbm_surrogate_train(ctx, iters: int) -> None:
+    _check(load().rbm_surrogate_train(ctx, int(iters)), "rbm_surrogate_train")
+
+
+def rbm_surrogate_stats(ctx) -> dict:
+    err = ctypes.c_double()
+    ns, nf = ctypes.c_int64(), ctypes.c_int64()
+    act = ctypes.c_int32()
+    na = ctypes.c_int64()
+    _check(load().rbm_surrogate_stats(ctx, ctypes.byref(err), ctypes.byref(ns), ctypes.byref(nf), ctypes.byref(act),
+                                      ctypes.byref(na)), "rbm_surrogate_stats")
+    return {"rel_err": err.value, "surrogate_steps": ns.value, "fallback_steps": nf.value, "active": bool(act.value),
+            "adam_steps": na.value}
+
+
+def rbm_surrogate_params(ctx):
+    import numpy as np
+
+    th = np.zeros(N_SURROGATE_PARAMS, dtype=np.float32)
+    nm = np.zeros(4, dtype=np.float32)
+    _check(load().rbm_surrogate_params(ctx, th.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                       nm.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), "rbm_surrogate_params")
+    return th, nm
+
+
+def rbm_surrogate_set_params(ctx, theta, norm=None) -> None:
+    """Load parameters (4482 floats) and, unless None, the normalisation
+    (mu_x, mu_y, s, sF), which is then kept at the first checkpoint."""
+    import numpy as np
+
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float32))
+    if th.size != N_SURROGATE_PARAMS:
+        raise ValueError("expected 4482 parameters")
+    nm_ptr = None
+    if norm is not None:
+        nm = np.ascontiguousarray(np.asarray(norm, dtype=np.float32))
+        if nm.size != 4:
+            raise ValueError("expected 4 normalisation values")
+        nm_ptr = nm.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    _check(load().rbm_surrogate_set_params(ctx, th.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), nm_ptr),
+           "rbm_surrogate_set_params")
+
+
+def rbm_surrogate_forces(ctx, q, f) -> None:
+    _check(load().rbm_surrogate_forces(ctx, ctypes.c_void_p(_dev_ptr(q)), int(q.shape[0]),
+                                       ctypes.c_void_p(_dev_ptr(f))), "rbm_surrogate_forces")
+
+
+def rbm_surrogate_gradient(ctx, x, f_target):
+    import numpy as np
+
+    g = np.zeros(N_SURROGATE_PARAMS, dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(load().rbm_surrogate_gradient(ctx, ctypes.c_void_p(_dev_ptr(x)), ctypes.c_void_p(_dev_ptr(f_target)),
+                                         int(x.shape[0]), g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                         ctypes.byref(loss)), "rbm_surrogate_gradient")
+    return g, loss.value
 
 
 def rbm_step(ctx) -> None:

@@ -28,6 +28,7 @@ UNITS = [
     ("noalloc.cu", []),
     ("coop_step.cu", []),
     ("batched.cu", []),
+    ("surrogate.cu", []),
 ]
 
 

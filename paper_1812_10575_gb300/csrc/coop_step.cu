@@ -266,6 +266,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
   __shared__ Row<T, D> s_selrow[kMaxAdjacentPick];
   __shared__ int s_general;
 
+  if (skipped(a)) return;  // uniform: the flag does not change during the launch
   const uint32_t G = gridDim.x, c = blockIdx.x;
   const uint32_t m32 = step_index(a);
   const uint32_t per = (ca.n + G - 1) / G;

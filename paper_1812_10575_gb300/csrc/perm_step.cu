@@ -52,7 +52,10 @@ struct PermArgs {
   uint32_t replica;
   const int64_t* m_ptr;
   int64_t m_off;
+  const int* skip;
 };
+
+__device__ __forceinline__ bool perm_skipped(const PermArgs& a) { return a.skip != nullptr && *a.skip != 0; }
 
 __device__ __forceinline__ uint32_t perm_step_index(const PermArgs& a) {
   const int64_t m = (a.m_ptr ? *a.m_ptr : 0) + a.m_off;
@@ -65,7 +68,7 @@ PermArgs make_perm_args(const PermScratch& ps, uint32_t n, uint2 seed, uint32_t 
   a.cnt = ps.cnt; a.start = ps.start; a.slots = ps.slots; a.ovf_cnt = ps.ovf_cnt; a.ovf = ps.ovf;
   a.done = ps.done; a.perm = ps.perm; a.n = n; a.bits = ps.bucket_bits; a.nbuckets = ps.nbuckets;
   a.slot_cap = ps.slot_cap; a.sort_cap = ps.sort_cap; a.separate_scan = ps.separate_scan ? 1 : 0;
-  a.seed = seed; a.replica = replica; a.m_ptr = m_ptr; a.m_off = m_off;
+  a.seed = seed; a.replica = replica; a.m_ptr = m_ptr; a.m_off = m_off; a.skip = ps.skip;
   return a;
 }
 
@@ -73,6 +76,7 @@ PermArgs make_perm_args(const PermScratch& ps, uint32_t n, uint2 seed, uint32_t 
 // Pass 1: bucket every particle by the top bits of its key.
 // ---------------------------------------------------------------------------
 __global__ void k_bucket_scatter(PermArgs a) {
+  if (perm_skipped(a)) return;
   const uint32_t m32 = perm_step_index(a);
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
@@ -90,6 +94,7 @@ __global__ void k_bucket_scatter(PermArgs a) {
 
 // Exclusive scan of the bucket counts by one block (many-bucket case).
 __global__ void k_bucket_scan(PermArgs a) {
+  if (perm_skipped(a)) return;
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_carry;
   if (threadIdx.x == 0) s_carry = 0;
@@ -208,6 +213,7 @@ __global__ void __launch_bounds__(256) k_bucket_sort_step(PermArgs pa, StepParam
   __shared__ uint32_t s_red[32];
   __shared__ uint32_t s_fill;
   __shared__ int s_last;
+  if (perm_skipped(pa)) return;
 
   const uint32_t b = blockIdx.x;
   const uint32_t m32 = perm_step_index(pa);
@@ -312,6 +318,7 @@ __global__ void __launch_bounds__(256) k_bucket_sort_step(PermArgs pa, StepParam
 // Many-bucket case: straddling batches over a grid, then the spill counter reset.
 template <typename T, int D, int MODE>
 __global__ void __launch_bounds__(256) k_straddle_fixup(PermArgs pa, StepParams<T> a) {
+  if (perm_skipped(pa)) return;
   const uint32_t m32 = perm_step_index(pa);
   const int gpw = 32 / a.p;
   const uint32_t per_block = static_cast<uint32_t>(gpw * (blockDim.x >> 5));
@@ -324,6 +331,7 @@ __global__ void __launch_bounds__(256) k_straddle_fixup(PermArgs pa, StepParams<
 // new positions staged in xout before any is written back.
 template <typename T, int D, int MODE>
 __global__ void __launch_bounds__(256) k_batch_generic(PermArgs pa, StepParams<T> a) {
+  if (perm_skipped(pa)) return;
   const uint32_t m32 = step_index(a);
   const uint32_t up = static_cast<uint32_t>(a.p);
   const uint32_t lo = blockIdx.x * up;

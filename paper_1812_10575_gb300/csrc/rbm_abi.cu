@@ -34,6 +34,16 @@ struct rbm_ctx {
   bool batched = false;
   BatchedScratch bs;
   std::vector<int64_t> rep_n;   // replica sizes (batched contexts)
+  // surrogate
+  bool sur_on = false;
+  SurrogateScratch ss;
+  int32_t sur_every = 100, sur_iters_first = 2000, sur_iters = 200, sur_max_rounds = 1;
+  int64_t sur_adam_total = 0;    // Adam iterations run so far
+  bool sur_trained = false;
+  bool sur_norm_given = false;   // normalisation set by the caller: keep it
+  int64_t sur_last = 0;          // step of the last checkpoint
+  cudaGraphExec_t sur_graph = nullptr;
+  int64_t sur_graph_len = 0;
   int batched_blocks_per_sm = 0;
   bool use_coop = false;
   int coop_blocks_per_sm = 0;
@@ -215,7 +225,8 @@ uint2 seed_of(const rbm_ctx* c) {
 }
 
 // Enqueue one RBM step (mode 1), the permutation only (0) or the forces (2).
-rbm_status enqueue_rbm(rbm_ctx* c, int mode, const int64_t* m_ptr, int64_t m_off, void* fout, cudaStream_t st) {
+rbm_status enqueue_rbm(rbm_ctx* c, int mode, const int64_t* m_ptr, int64_t m_off, void* fout, cudaStream_t st,
+                       const int* skip = nullptr) {
   if (c->batched) {
     cudaError_t e;
     if (c->prm.dtype == RBM_F32) {
@@ -236,21 +247,23 @@ rbm_status enqueue_rbm(rbm_ctx* c, int mode, const int64_t* m_ptr, int64_t m_off
   if (c->use_coop) {
     const uint64_t wait_ns = 1000ull * static_cast<uint64_t>(c->tuning.wait_limit_us > 0 ? c->tuning.wait_limit_us
                                                                                           : 1000000);
-    const int skip = c->tuning.test_skip_arrival;
+    const int skip_hook = c->tuning.test_skip_arrival;
     // Graph replay: the kernel reads the step index from m_ptr and advances
     // it itself once every block has read it, so each captured step reads
     // the counter with offset 0.
-    const bool bump = (m_ptr != nullptr);
+    const bool bump = (m_ptr != nullptr) && skip == nullptr;
     if (bump) m_off = 0;
     cudaError_t e;
     if (c->prm.dtype == RBM_F32) {
       StepParams<float> a = step_params<float>(c, m_ptr, m_off);
       a.fout = static_cast<float*>(fout);
-      e = launch_coop<float>(c->cs, c->prm.d, mode, &a, wait_ns, skip, bump, c->cfg, st);
+      a.skip = skip;
+      e = launch_coop<float>(c->cs, c->prm.d, mode, &a, wait_ns, skip_hook, bump, c->cfg, st);
     } else {
       StepParams<double> a = step_params<double>(c, m_ptr, m_off);
       a.fout = static_cast<double*>(fout);
-      e = launch_coop<double>(c->cs, c->prm.d, mode, &a, wait_ns, skip, bump, c->cfg, st);
+      a.skip = skip;
+      e = launch_coop<double>(c->cs, c->prm.d, mode, &a, wait_ns, skip_hook, bump, c->cfg, st);
     }
     if (e != cudaSuccess) {
       set_error("cudaLaunchKernelEx (cooperative)", e);
@@ -258,17 +271,21 @@ rbm_status enqueue_rbm(rbm_ctx* c, int mode, const int64_t* m_ptr, int64_t m_off
     }
     return RBM_OK;
   }
+  c->ps.skip = skip;
   launch_bucket_scatter(c->ps, static_cast<uint32_t>(c->prm.n), seed_of(c), c->prm.replica, m_ptr, m_off, c->cfg,
                         st);
   if (c->prm.dtype == RBM_F32) {
     StepParams<float> a = step_params<float>(c, m_ptr, m_off);
     a.fout = static_cast<float*>(fout);
+    a.skip = skip;
     launch_rbm_tail<float>(c->ps, c->prm.d, mode, &a, c->cfg, st);
   } else {
     StepParams<double> a = step_params<double>(c, m_ptr, m_off);
     a.fout = static_cast<double*>(fout);
+    a.skip = skip;
     launch_rbm_tail<double>(c->ps, c->prm.d, mode, &a, c->cfg, st);
   }
+  c->ps.skip = nullptr;
   RBM_CUDA(cudaGetLastError());
   return RBM_OK;
 }
@@ -294,8 +311,12 @@ rbm_status enqueue_direct(rbm_ctx* c, int mode, const int64_t* m_ptr, int64_t m_
   return RBM_OK;
 }
 
+rbm_status enqueue_surrogate_step(rbm_ctx* c, const int64_t* m_ptr, int64_t m_off, cudaStream_t st);
+rbm_status enqueue_train_round(rbm_ctx* c, int32_t iters, int32_t round, cudaStream_t st);
+
 rbm_status enqueue_step(rbm_ctx* c, int32_t method, const int64_t* m_ptr, int64_t m_off, cudaStream_t st) {
   if (method == RBM_METHOD_RBM) return enqueue_rbm(c, 1, m_ptr, m_off, nullptr, st);
+  if (method == RBM_METHOD_SURROGATE) return enqueue_surrogate_step(c, m_ptr, m_off, st);
   return enqueue_direct(c, 0, m_ptr, m_off, nullptr, 0, nullptr, st);
 }
 
@@ -330,8 +351,13 @@ rbm_status capture_graph(rbm_ctx* c, int32_t method, int64_t len) {
     set_error("cudaGraphInstantiate", e);
     return RBM_ERR_CUDA;
   }
-  c->graph[method] = ex;
-  c->graph_len[method] = len;
+  if (method == RBM_METHOD_SURROGATE) {
+    c->sur_graph = ex;
+    c->sur_graph_len = len;
+  } else {
+    c->graph[method] = ex;
+    c->graph_len[method] = len;
+  }
   return RBM_OK;
 }
 
@@ -390,6 +416,98 @@ rbm_status alloc_batched(rbm_ctx* c) {
   RBM_CUDA(cudaMalloc(&bs.perm, sizeof(uint32_t) * rows));
   RBM_CUDA(cudaMalloc(&c->xtmp, c->row_bytes * rows));
   return build_batched_schedule(c);
+}
+
+// One step of the surrogate method: the network step (runs when the flag is
+// set) and the RBM step gated on the same flag (runs when it is clear).
+rbm_status enqueue_surrogate_step(rbm_ctx* c, const int64_t* m_ptr, int64_t m_off, cudaStream_t st) {
+  StepParams<float> a = step_params<float>(c, m_ptr, m_off);
+  cudaError_t e = sur_step(c->ss, &a, c->cfg, st);
+  if (e != cudaSuccess) {
+    set_error("surrogate step", e);
+    return RBM_ERR_CUDA;
+  }
+  return enqueue_rbm(c, 1, m_ptr, m_off, nullptr, st, c->ss.flag);
+}
+
+void free_surrogate(rbm_ctx* c) {
+  SurrogateScratch& s = c->ss;
+  cudaFree(s.theta); cudaFree(s.mom1); cudaFree(s.mom2); cudaFree(s.wq); cudaFree(s.w2f); cudaFree(s.w2b);
+  cudaFree(s.norm); cudaFree(s.adam_t); cudaFree(s.flag); cudaFree(s.err); cudaFree(s.counters);
+  cudaFree(s.partial); cudaFree(s.qidx); cudaFree(s.q); cudaFree(s.fq); cudaFree(s.fpred);
+  s = SurrogateScratch{};
+  if (c->sur_graph) cudaGraphExecDestroy(c->sur_graph);
+  c->sur_graph = nullptr;
+  c->sur_on = false;
+}
+
+// A checkpoint at the current step: sample queries, direct forces at them,
+// (first time) the normalisation, `iters` Adam iterations on 3/4 of them,
+// then the held-out error and the selection flag.
+rbm_status enqueue_checkpoint(rbm_ctx* c, int32_t iters, bool first, cudaStream_t st) {
+  SurrogateScratch& s = c->ss;
+  StepParams<float> a = step_params<float>(c, nullptr, c->m);
+  cudaError_t e = sur_sample(s, &a, st);
+  if (e != cudaSuccess) {
+    set_error("surrogate sample", e);
+    return RBM_ERR_CUDA;
+  }
+  rbm_status r = enqueue_direct(c, 2, nullptr, c->m, s.q, s.nq, s.fq, st);
+  if (r != RBM_OK) return r;
+  if (first && !c->sur_norm_given) e = sur_norm(s, c->status, st);
+  if (e != cudaSuccess) {
+    set_error("surrogate checkpoint", e);
+    return RBM_ERR_CUDA;
+  }
+  return enqueue_train_round(c, iters, 0, st);
+}
+
+// Round `round` (0-based) of a checkpoint: `iters` Adam iterations on the
+// current queries (minibatches continue cyclically through the training
+// share) with the peak rate lr / 2^round, then the held-out error and flag.
+rbm_status enqueue_train_round(rbm_ctx* c, int32_t iters, int32_t round, cudaStream_t st) {
+  SurrogateScratch& s = c->ss;
+  const uint32_t batch = std::min<uint32_t>(4096u, s.ntrain);
+  cudaError_t e = cudaSuccess;
+  if (iters > 0) {
+    const uint32_t begin0 = static_cast<uint32_t>((static_cast<uint64_t>(c->sur_adam_total) * batch) % s.ntrain);
+    e = sur_train(s, c->status, s.q, s.fq, s.ntrain, iters, batch, begin0, std::ldexp(1.0f, -std::min(round, 60)),
+                  c->cfg, st);
+    c->sur_adam_total += iters;
+  }
+  if (e == cudaSuccess) e = sur_forces(s, c->status, s.q, s.nq, s.fpred, c->cfg, st);
+  if (e == cudaSuccess) e = sur_check(s, c->status, st);
+  if (e != cudaSuccess) {
+    set_error("surrogate training", e);
+    return RBM_ERR_CUDA;
+  }
+  return RBM_OK;
+}
+
+// A full checkpoint: the first round (iters_first at the first checkpoint,
+// iters_per_checkpoint later), then further rounds of iters_per_checkpoint
+// while the held-out error is above the tolerance, up to max_rounds rounds.
+// Each round restarts the geometric rate decay from a peak halved at every
+// restart (warm restarts as in SGDR, Loshchilov & Hutter 2017, with a
+// geometric instead of a cosine decay), so a restart cannot undo the
+// convergence of the round before it.
+// Reading the error back after each round is the one host synchronisation of
+// the surrogate method; the steps themselves never wait on the host.
+rbm_status run_checkpoint(rbm_ctx* c) {
+  const bool first = !c->sur_trained;
+  rbm_status st = enqueue_checkpoint(c, first ? c->sur_iters_first : c->sur_iters, first, c->stream);
+  if (st != RBM_OK) return st;
+  c->sur_trained = true;
+  c->sur_last = c->m;
+  for (int32_t round = 1; round < c->sur_max_rounds && c->sur_iters > 0; ++round) {
+    float err = 0.0f;
+    RBM_CUDA(cudaMemcpyAsync(&err, c->ss.err, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    RBM_CUDA(cudaStreamSynchronize(c->stream));
+    if (std::isfinite(err) && err <= c->ss.tol) break;
+    st = enqueue_train_round(c, c->sur_iters, round, c->stream);
+    if (st != RBM_OK) return st;
+  }
+  return RBM_OK;
 }
 
 }  // namespace
@@ -489,8 +607,39 @@ rbm_status rbm_direct_step(rbm_ctx* ctx) {
 rbm_status rbm_run(rbm_ctx* ctx, int64_t steps, int32_t method) {
   rbm_status st = usable(ctx);
   if (st != RBM_OK) return st;
-  if (steps < 0 || (method != RBM_METHOD_RBM && method != RBM_METHOD_DIRECT)) return RBM_ERR_INVALID;
+  if (steps < 0 || (method != RBM_METHOD_RBM && method != RBM_METHOD_DIRECT && method != RBM_METHOD_SURROGATE))
+    return RBM_ERR_INVALID;
   if (ctx->batched && method != RBM_METHOD_RBM) return RBM_ERR_UNSUPPORTED;
+  if (method == RBM_METHOD_SURROGATE) {
+    if (!ctx->sur_on) return RBM_ERR_STATE;
+    while (steps > 0) {
+      if (!ctx->sur_trained || ctx->m - ctx->sur_last >= ctx->sur_every) {
+        st = run_checkpoint(ctx);
+        if (st != RBM_OK) return st;
+      }
+      const int64_t cycle = std::min<int64_t>(steps, ctx->sur_every - (ctx->m - ctx->sur_last));
+      if (cycle == ctx->sur_every) {  // a whole cycle: replay its graph
+        if (!ctx->sur_graph || ctx->sur_graph_len != cycle) {
+          if (ctx->sur_graph) cudaGraphExecDestroy(ctx->sur_graph);
+          ctx->sur_graph = nullptr;
+          st = capture_graph(ctx, RBM_METHOD_SURROGATE, cycle);
+          if (st != RBM_OK) return st;
+        }
+        if (ctx->m_dev_value != ctx->m) launch_set_i64(ctx->m_dev, ctx->m, ctx->stream);
+        RBM_CUDA(cudaGraphLaunch(ctx->sur_graph, ctx->stream));
+        ctx->m += cycle;
+        ctx->m_dev_value = ctx->m;
+      } else {
+        for (int64_t s2 = 0; s2 < cycle; ++s2) {
+          st = enqueue_step(ctx, RBM_METHOD_SURROGATE, nullptr, ctx->m, ctx->stream);
+          if (st != RBM_OK) return st;
+          ctx->m += 1;
+        }
+      }
+      steps -= cycle;
+    }
+    return RBM_OK;
+  }
   const int64_t len = ctx->tuning.graph_steps > 0 ? ctx->tuning.graph_steps : 100;
   while (steps >= len) {
     if (!ctx->graph[method] || ctx->graph_len[method] != len) {
@@ -525,7 +674,9 @@ rbm_status rbm_sync(rbm_ctx* ctx) {
 rbm_status rbm_step_host(rbm_ctx* ctx, void* x_host, int32_t method) {
   rbm_status st = usable(ctx);
   if (st != RBM_OK) return st;
-  if (!x_host || (method != RBM_METHOD_RBM && method != RBM_METHOD_DIRECT)) return RBM_ERR_INVALID;
+  if (!x_host || (method != RBM_METHOD_RBM && method != RBM_METHOD_DIRECT && method != RBM_METHOD_SURROGATE))
+    return RBM_ERR_INVALID;
+  if (method == RBM_METHOD_SURROGATE && !ctx->sur_on) return RBM_ERR_STATE;
   const size_t bytes = ctx->row_bytes * static_cast<size_t>(ctx->prm.n);
   RBM_CUDA(cudaMemcpyAsync(ctx->x, x_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
   st = enqueue_step(ctx, method, nullptr, ctx->m, ctx->stream);
@@ -595,6 +746,7 @@ rbm_status rbm_free(rbm_ctx* ctx) {
   if (!ctx) return RBM_ERR_INVALID;
   cudaStreamSynchronize(ctx->stream);
   drop_graphs(ctx);
+  free_surrogate(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   free_scratch(ctx);
   cudaFree(ctx->status);
@@ -642,8 +794,10 @@ rbm_status rbm_step_profiled(rbm_ctx* ctx, int32_t method, float* kernel_ms, int
                              char* names, int32_t names_len) {
   rbm_status st = usable(ctx);
   if (st != RBM_OK) return st;
-  if (!kernel_ms || !nkernels || capacity < 1 || (method != RBM_METHOD_RBM && method != RBM_METHOD_DIRECT))
+  if (!kernel_ms || !nkernels || capacity < 1 ||
+      (method != RBM_METHOD_RBM && method != RBM_METHOD_DIRECT && method != RBM_METHOD_SURROGATE))
     return RBM_ERR_INVALID;
+  if (method == RBM_METHOD_SURROGATE && !ctx->sur_on) return RBM_ERR_STATE;
   constexpr int kMax = 16;
   cudaEvent_t ev[kMax + 1];
   const char* nm[kMax + 1] = {};
@@ -857,11 +1011,190 @@ rbm_status rbm_autotune(rbm_ctx* ctx, int32_t trial_steps, const char* table_pat
   return st;
 }
 
+rbm_status rbm_surrogate_config(rbm_ctx* ctx, int32_t train_every, double fallback_tol, int64_t n_queries,
+                                int32_t iters_first, int32_t iters_per_checkpoint, int32_t max_rounds, double lr) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (ctx->batched || ctx->prm.d != 2 || ctx->prm.dtype != RBM_F32 || ctx->prm.scheme != RBM_SCHEME_EULER)
+    return RBM_ERR_UNSUPPORTED;
+  if (train_every < 1 || !(fallback_tol > 0) || n_queries < 8 || n_queries > (int64_t(1) << 24) || iters_first < 0 ||
+      iters_per_checkpoint < 0 || max_rounds < 1 || !(lr > 0))
+    return RBM_ERR_INVALID;
+  RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+  free_surrogate(ctx);
+  {
+    cudaError_t e = prepare_surrogate_kernels();
+    if (e != cudaSuccess) {
+      set_error("prepare_surrogate_kernels", e);
+      return RBM_ERR_CUDA;
+    }
+  }
+  SurrogateScratch& s = ctx->ss;
+  const int np = surrogate_param_count();
+  s.nq = static_cast<uint32_t>(n_queries);
+  s.ntrain = std::max<uint32_t>(1u, s.nq - s.nq / 4);
+  s.lr = static_cast<float>(lr);
+  s.tol = static_cast<float>(fallback_tol);
+  s.partial_blocks = std::max<uint32_t>(32u, 512u);
+  RBM_CUDA(cudaMalloc(&s.theta, sizeof(float) * np));
+  RBM_CUDA(cudaMalloc(&s.mom1, sizeof(float) * np));
+  RBM_CUDA(cudaMalloc(&s.mom2, sizeof(float) * np));
+  RBM_CUDA(cudaMalloc(&s.wq, sizeof(float) * np));
+  RBM_CUDA(cudaMalloc(&s.w2f, 64 * 64 * 2));
+  RBM_CUDA(cudaMalloc(&s.w2b, 64 * 64 * 2));
+  RBM_CUDA(cudaMalloc(&s.norm, sizeof(float) * 4));
+  RBM_CUDA(cudaMalloc(&s.adam_t, sizeof(int)));
+  RBM_CUDA(cudaMalloc(&s.flag, sizeof(int)));
+  RBM_CUDA(cudaMalloc(&s.err, sizeof(float)));
+  RBM_CUDA(cudaMalloc(&s.counters, 2 * sizeof(unsigned long long)));
+  RBM_CUDA(cudaMalloc(&s.partial, sizeof(float) * (np + 1) * s.partial_blocks));
+  RBM_CUDA(cudaMalloc(&s.qidx, sizeof(uint32_t) * s.nq));
+  RBM_CUDA(cudaMalloc(&s.q, sizeof(float) * 2 * s.nq));
+  RBM_CUDA(cudaMalloc(&s.fq, sizeof(float) * 2 * s.nq));
+  RBM_CUDA(cudaMalloc(&s.fpred, sizeof(float) * 2 * s.nq));
+  const float norm0[4] = {0.0f, 0.0f, 1.0f, 1.0f};
+  RBM_CUDA(cudaMemcpy(s.norm, norm0, sizeof(norm0), cudaMemcpyHostToDevice));
+  RBM_CUDA(cudaMemset(s.adam_t, 0, sizeof(int)));
+  RBM_CUDA(cudaMemset(s.flag, 0, sizeof(int)));
+  RBM_CUDA(cudaMemset(s.err, 0, sizeof(float)));
+  RBM_CUDA(cudaMemset(s.counters, 0, 2 * sizeof(unsigned long long)));
+  {
+    cudaError_t e = sur_init(s, ctx->status, ctx->prm.seed ^ 0x5EED5EEDull, ctx->stream);
+    if (e != cudaSuccess) {
+      set_error("surrogate init", e);
+      return RBM_ERR_CUDA;
+    }
+  }
+  RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->sur_on = true;
+  ctx->sur_every = train_every;
+  ctx->sur_iters_first = iters_first;
+  ctx->sur_iters = iters_per_checkpoint;
+  ctx->sur_max_rounds = max_rounds;
+  ctx->sur_adam_total = 0;
+  ctx->sur_trained = false;
+  ctx->sur_norm_given = false;
+  return RBM_OK;
+}
+
+rbm_status rbm_surrogate_train(rbm_ctx* ctx, int32_t iters) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (!ctx->sur_on) return RBM_ERR_STATE;
+  if (iters < 0) return RBM_ERR_INVALID;
+  st = enqueue_checkpoint(ctx, iters, !ctx->sur_trained, ctx->stream);
+  if (st == RBM_OK) {
+    ctx->sur_trained = true;
+    ctx->sur_last = ctx->m;
+  }
+  return st;
+}
+
+rbm_status rbm_surrogate_stats(rbm_ctx* ctx, double* last_rel_err, int64_t* n_surrogate_steps,
+                               int64_t* n_fallback_steps, int32_t* active, int64_t* n_adam_steps) {
+  if (!ctx) return RBM_ERR_INVALID;
+  if (!ctx->sur_on) return RBM_ERR_STATE;
+  RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+  float err = 0.0f;
+  unsigned long long cnt[2] = {0, 0};
+  int flag = 0;
+  RBM_CUDA(cudaMemcpy(&err, ctx->ss.err, sizeof(float), cudaMemcpyDeviceToHost));
+  RBM_CUDA(cudaMemcpy(cnt, ctx->ss.counters, sizeof(cnt), cudaMemcpyDeviceToHost));
+  RBM_CUDA(cudaMemcpy(&flag, ctx->ss.flag, sizeof(int), cudaMemcpyDeviceToHost));
+  if (last_rel_err) *last_rel_err = err;
+  if (n_surrogate_steps) *n_surrogate_steps = static_cast<int64_t>(cnt[0]);
+  if (n_fallback_steps) *n_fallback_steps = static_cast<int64_t>(cnt[1]);
+  if (active) *active = flag;
+  if (n_adam_steps) *n_adam_steps = ctx->sur_adam_total;
+  return RBM_OK;
+}
+
+rbm_status rbm_surrogate_params(rbm_ctx* ctx, float* theta_host, float* norm_host) {
+  if (!ctx) return RBM_ERR_INVALID;
+  if (!ctx->sur_on) return RBM_ERR_STATE;
+  RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (theta_host)
+    RBM_CUDA(cudaMemcpy(theta_host, ctx->ss.theta, sizeof(float) * surrogate_param_count(), cudaMemcpyDeviceToHost));
+  if (norm_host) RBM_CUDA(cudaMemcpy(norm_host, ctx->ss.norm, sizeof(float) * 4, cudaMemcpyDeviceToHost));
+  return RBM_OK;
+}
+
+rbm_status rbm_surrogate_set_params(rbm_ctx* ctx, const float* theta_host, const float* norm_host) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (!ctx->sur_on) return RBM_ERR_STATE;
+  RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+  const int np = surrogate_param_count();
+  if (theta_host) {
+    RBM_CUDA(cudaMemcpy(ctx->ss.theta, theta_host, sizeof(float) * np, cudaMemcpyHostToDevice));
+    RBM_CUDA(cudaMemset(ctx->ss.mom1, 0, sizeof(float) * np));
+    RBM_CUDA(cudaMemset(ctx->ss.mom2, 0, sizeof(float) * np));
+    RBM_CUDA(cudaMemset(ctx->ss.adam_t, 0, sizeof(int)));
+  }
+  if (norm_host) {
+    RBM_CUDA(cudaMemcpy(ctx->ss.norm, norm_host, sizeof(float) * 4, cudaMemcpyHostToDevice));
+    ctx->sur_norm_given = true;
+  }
+  cudaError_t e = sur_publish(ctx->ss, ctx->status, ctx->stream);
+  if (e != cudaSuccess) {
+    set_error("surrogate publish", e);
+    return RBM_ERR_CUDA;
+  }
+  RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+  return RBM_OK;
+}
+
+rbm_status rbm_surrogate_forces(rbm_ctx* ctx, const void* q_dev, int64_t nq, void* f_dev) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (!ctx->sur_on) return RBM_ERR_STATE;
+  if (nq < 0 || nq > (int64_t(1) << 31) || (nq > 0 && (!q_dev || !f_dev))) return RBM_ERR_INVALID;
+  if (nq == 0) return RBM_OK;
+  cudaError_t e = sur_forces(ctx->ss, ctx->status, static_cast<const float*>(q_dev), static_cast<uint32_t>(nq),
+                             static_cast<float*>(f_dev), ctx->cfg, ctx->stream);
+  if (e != cudaSuccess) {
+    set_error("surrogate forces", e);
+    return RBM_ERR_CUDA;
+  }
+  return RBM_OK;
+}
+
+rbm_status rbm_surrogate_gradient(rbm_ctx* ctx, const void* x_dev, const void* f_target_dev, int64_t nb,
+                                  float* grad_host, double* loss_host) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (!ctx->sur_on) return RBM_ERR_STATE;
+  if (nb < 1 || nb > static_cast<int64_t>(ctx->ss.partial_blocks) * 128 || !x_dev || !f_target_dev || !grad_host)
+    return RBM_ERR_INVALID;
+  cudaError_t e = sur_gradient(ctx->ss, ctx->status, static_cast<const float*>(x_dev),
+                               static_cast<const float*>(f_target_dev), static_cast<uint32_t>(nb), ctx->stream);
+  if (e != cudaSuccess) {
+    set_error("surrogate gradient", e);
+    return RBM_ERR_CUDA;
+  }
+  const int np = surrogate_param_count();
+  const uint32_t nblocks = static_cast<uint32_t>((nb + 127) / 128);
+  std::vector<float> part(static_cast<size_t>(nblocks) * (np + 1));
+  RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+  RBM_CUDA(cudaMemcpy(part.data(), ctx->ss.partial, sizeof(float) * part.size(), cudaMemcpyDeviceToHost));
+  double loss = 0.0;
+  for (int i = 0; i <= np; ++i) {
+    double g = 0.0;
+    for (uint32_t b = 0; b < nblocks; ++b) g += part[static_cast<size_t>(b) * (np + 1) + i];
+    if (i < np) grad_host[i] = static_cast<float>(g);
+    else loss = g;
+  }
+  if (loss_host) *loss_host = loss;
+  return rbm_sync(ctx);
+}
+
 rbm_status rbm_launches_per_step(const rbm_ctx* ctx, int32_t method, int32_t* launches) {
   if (!ctx || !launches) return RBM_ERR_INVALID;
   if (method == RBM_METHOD_RBM)
     *launches = (ctx->use_coop || ctx->batched) ? 1 : 1 + rbm_tail_launches(ctx->ps, ctx->prm.p);
   else if (method == RBM_METHOD_DIRECT) *launches = 2;  // upper bound: sum (+ chunk reduction)
+  else if (method == RBM_METHOD_SURROGATE)
+    *launches = 1 + (ctx->use_coop ? 1 : 1 + rbm_tail_launches(ctx->ps, ctx->prm.p));
   else return RBM_ERR_INVALID;
   return RBM_OK;
 }

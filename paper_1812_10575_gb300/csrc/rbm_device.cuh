@@ -262,7 +262,13 @@ struct StepParams {
   uint32_t replica;
   const int64_t* m_ptr;  // step counter in device memory (graph replay) or null
   int64_t m_off;         // added to *m_ptr (or the step itself when m_ptr is null)
+  const int* skip;       // when set and non-zero, the RBM step kernels do nothing (surrogate mode)
 };
+
+template <typename T>
+__device__ __forceinline__ bool skipped(const StepParams<T>& a) {
+  return a.skip != nullptr && *a.skip != 0;
+}
 
 template <typename T>
 __device__ __forceinline__ uint32_t step_index(const StepParams<T>& a) {

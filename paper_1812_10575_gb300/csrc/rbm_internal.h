@@ -23,6 +23,7 @@ struct PermScratch {
   uint32_t slot_cap = 0;
   uint32_t sort_cap = 0;
   bool separate_scan = false;   // large bucket counts: scan and fix-up kernels of their own
+  const int* skip = nullptr;    // when set and non-zero the kernels do nothing (surrogate mode)
 };
 
 // Cooperative single-kernel step scratch.
@@ -46,6 +47,29 @@ struct BatchedScratch {
   uint32_t grid = 0;
   int threads = 512;
   int bucket_target = 1024;
+};
+
+// Surrogate-network state (surrogate.cu); all device pointers.
+struct SurrogateScratch {
+  float* theta = nullptr;
+  float* mom1 = nullptr;
+  float* mom2 = nullptr;
+  float* wq = nullptr;
+  uint16_t* w2f = nullptr;
+  uint16_t* w2b = nullptr;
+  float* norm = nullptr;
+  int* adam_t = nullptr;
+  int* flag = nullptr;
+  float* err = nullptr;
+  unsigned long long* counters = nullptr;
+  float* partial = nullptr;
+  uint32_t partial_blocks = 0;
+  uint32_t* qidx = nullptr;
+  float* q = nullptr;
+  float* fq = nullptr;
+  float* fpred = nullptr;
+  uint32_t nq = 0, ntrain = 0;
+  float lr = 1e-3f, tol = 1e-2f;
 };
 
 struct LaunchCfg {
@@ -94,6 +118,23 @@ cudaError_t prepare_batched_kernels(int dtype, int d, int threads, int* blocks_p
 template <typename T>
 cudaError_t launch_batched(const BatchedScratch& bs, int d, int mode, const void* params, const LaunchCfg& cfg,
                            cudaStream_t st);
+
+// Surrogate network (surrogate.cu).
+int surrogate_param_count();
+cudaError_t prepare_surrogate_kernels();
+cudaError_t sur_init(const SurrogateScratch& ss, int32_t* status, uint64_t seed, cudaStream_t st);
+cudaError_t sur_publish(const SurrogateScratch& ss, int32_t* status, cudaStream_t st);
+cudaError_t sur_sample(const SurrogateScratch& ss, const void* params, cudaStream_t st);
+cudaError_t sur_norm(const SurrogateScratch& ss, int32_t* status, cudaStream_t st);
+cudaError_t sur_train(const SurrogateScratch& ss, int32_t* status, const float* xs, const float* ts, uint32_t ntrain,
+                      int iters, uint32_t batch, uint32_t begin0, float lr_scale, const LaunchCfg& cfg,
+                      cudaStream_t st);
+cudaError_t sur_gradient(const SurrogateScratch& ss, int32_t* status, const float* xs, const float* ts, uint32_t nb,
+                         cudaStream_t st);
+cudaError_t sur_forces(const SurrogateScratch& ss, int32_t* status, const float* q, uint32_t nq, float* fout,
+                       const LaunchCfg& cfg, cudaStream_t st);
+cudaError_t sur_check(const SurrogateScratch& ss, int32_t* status, cudaStream_t st);
+cudaError_t sur_step(const SurrogateScratch& ss, const void* params, const LaunchCfg& cfg, cudaStream_t st);
 
 // Direct O(N^2) pieces (direct.cu).  `mode`: 0 = step (into xout), 1 =
 // forces at the particles (into fout), 2 = forces at query points.
