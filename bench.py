@@ -13,6 +13,7 @@ step is timed alone with CUDA events on the stream its kernels run on.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload thomson|batched_opinion|dyson|large_n|surrogate]
+                    [--sizes 20,22 (large_n)] [--no-cpu-baseline]
 
 Other workloads (one JSON line each, same keys):
   batched_opinion - 4096 independent 2-D bounded-confidence opinion systems
@@ -498,7 +499,8 @@ def run_large_n(args, w, g):
     import paper_1812_10575_gb300 as rbm
 
     rows = []
-    for n in w["sizes"]:
+    sizes = [1 << int(v) for v in args.sizes.split(",")] if args.sizes else w["sizes"]
+    for n in sizes:
         X = _initial(w, n)
         for p in w["ps"]:
             x = _to_dev(g, X, w["d"], w["dtype"])
@@ -676,7 +678,8 @@ def run_surrogate(args, w, g):
                              "flushed before each profiled network step",
                        parallelism=f"replicas x{g.world} (one independent system per GPU)"),
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": mufu_peak,
-                     "unit": "T special-function ops/s", "frac": achieved / mufu_peak, "traffic": None,
+                     "unit": "T special-function ops/s", "frac": achieved / mufu_peak,
+                     "traffic": _traffic_for(w["workload"], dom, _kernel_sources_digest()),
                      "ops_per_particle": mufu_per_particle, "avg_launch_ms": avg[dom],
                      "peak_source": "152 SMs x 16 special-function results per clock x max SM clock"},
         "e2e": {"value": g.world * n / (e2e_total * 1e-3), "unit": UNIT, "h2d_bytes_per_step": n * 8,
@@ -725,6 +728,7 @@ def main():
     ap.add_argument("--workload", default="thomson", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sizes", default="", help="large_n only: comma-separated log2 N (default 16,18,20,22,24)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -11,11 +11,13 @@
 // The sort runs in two passes over buckets of the top `bucket_bits` key bits:
 //   k_bucket_scatter  - one Philox per particle, an atomic slot in its bucket
 //                       (overflowing members go to a spill list);
-//   k_bucket_sort_step - one block per bucket: regenerate the keys, bitonic
-//                       sort of (key, id) in shared memory, write the bucket's
-//                       stretch of the permutation, and step every batch that
-//                       lies wholly inside the bucket (p <= 32: one group of p
-//                       lanes per batch, positions exchanged by warp shuffles).
+//   k_bucket_sort_step - one block per bucket: regenerate the keys, counting
+//                       sort by the next kSubBits key bits in shared memory,
+//                       insertion sort of the few members sharing a sub-bucket
+//                       by (key, id), write the bucket's stretch of the
+//                       permutation, and step every batch that lies wholly
+//                       inside the bucket (p <= 32: one group of p lanes per
+//                       batch, positions exchanged by warp shuffles).
 // Batches that straddle a bucket boundary are stepped afterwards by the last
 // block to finish (few buckets) or by k_straddle_fixup (many buckets).  They
 // read only positions no other batch writes, so every update uses the
@@ -32,6 +34,17 @@ namespace {
 
 __device__ __forceinline__ uint32_t bucket_of(uint64_t key, int bits) {
   return bits ? static_cast<uint32_t>(key >> (64 - bits)) : 0u;
+}
+
+constexpr int kSortThreads = 256;
+constexpr int kSortPer = 8;                              // members per thread
+constexpr uint32_t kSortCapMax = kSortThreads * kSortPer;  // largest bucket sorted in shared memory
+constexpr int kSubBits = 10;
+constexpr uint32_t kSub = 1u << kSubBits;                // sub-buckets of a bucket
+
+// The kSubBits key bits below the bucket bits (monotone in the key inside a bucket).
+__device__ __forceinline__ uint32_t sub_of(uint64_t key, int bits) {
+  return static_cast<uint32_t>((key << bits) >> (64 - kSubBits));
 }
 
 struct PermArgs {
@@ -146,25 +159,34 @@ __device__ __forceinline__ bool key_less(uint64_t ka, uint32_t ia, uint64_t kb, 
   return ka < kb || (ka == kb && ia < ib);
 }
 
-// Bitonic sort of (skey, sid)[0, p2) ascending; p2 a power of two.
-__device__ void bitonic_sort(uint64_t* skey, uint32_t* sid, uint32_t p2) {
-  for (uint32_t k = 2; k <= p2; k <<= 1) {
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t t = threadIdx.x; t < (p2 >> 1); t += blockDim.x) {
-        const uint32_t i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
-        const uint32_t l = i + j;
-        const bool up = (i & k) == 0;
-        const uint64_t ki = skey[i], kl = skey[l];
-        const uint32_t ii = sid[i], il = sid[l];
-        const bool gt = key_less(kl, il, ki, ii);
-        if (gt == up) {
-          skey[i] = kl; skey[l] = ki;
-          sid[i] = il; sid[l] = ii;
-        }
-      }
-      __syncthreads();
-    }
+// Exclusive scan of a[0, kSub) in shared memory by the whole block.
+__device__ void sub_exclusive_scan(uint32_t* a, uint32_t* s_warp) {
+  constexpr uint32_t per = kSub / kSortThreads;
+  const uint32_t lo = threadIdx.x * per;
+  uint32_t v[per];
+  uint32_t sum = 0;
+#pragma unroll
+  for (uint32_t i = 0; i < per; ++i) {
+    v[i] = a[lo + i];
+    sum += v[i];
   }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  uint32_t run = incl - sum;
+  for (int w = 0; w < warp; ++w) run += s_warp[w];
+#pragma unroll
+  for (uint32_t i = 0; i < per; ++i) {
+    a[lo + i] = run;
+    run += v[i];
+  }
+  __syncthreads();
 }
 
 // Steps the batches that straddle bucket boundaries b in [b_begin, b_end)
@@ -206,10 +228,11 @@ __device__ void step_straddling(const StepParams<T>& a, uint32_t m32, const Perm
 // Pass 2: one block per bucket.
 // ---------------------------------------------------------------------------
 template <typename T, int D, int MODE>
-__global__ void __launch_bounds__(256) k_bucket_sort_step(PermArgs pa, StepParams<T> a) {
+__global__ void __launch_bounds__(kSortThreads) k_bucket_sort_step(PermArgs pa, StepParams<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint64_t* skey = reinterpret_cast<uint64_t*>(smem_raw);
-  uint32_t* sid = reinterpret_cast<uint32_t*>(skey + pa.sort_cap);
+  uint64_t* skey = reinterpret_cast<uint64_t*>(smem_raw);       // [sort_cap] keys, sorted
+  uint32_t* sid = reinterpret_cast<uint32_t*>(skey + pa.sort_cap);  // [sort_cap] ids, sorted
+  uint32_t* ssub = sid + pa.sort_cap;                            // [kSub] sub-bucket counts, then starts
   __shared__ uint32_t s_red[32];
   __shared__ uint32_t s_fill;
   __shared__ int s_last;
@@ -232,33 +255,58 @@ __global__ void __launch_bounds__(256) k_bucket_sort_step(PermArgs pa, StepParam
   const uint32_t* ids;
 
   if (nb <= pa.sort_cap) {
-    for (uint32_t t = threadIdx.x; t < nslot; t += blockDim.x) {
-      const uint32_t id = pa.slots[static_cast<size_t>(b) * pa.slot_cap + t];
-      sid[t] = id;
-      skey[t] = perm_key(id, m32, pa.replica, pa.seed);
-    }
-    if (nb > nslot) {  // members that spilled to the overflow list
+    for (uint32_t u = threadIdx.x; u < kSub; u += blockDim.x) ssub[u] = 0;
+    if (nb > nslot) {  // members that spilled to the overflow list, staged after the slot members
       if (threadIdx.x == 0) s_fill = nslot;
       __syncthreads();
       const uint32_t novf = *pa.ovf_cnt;
       for (uint32_t t = threadIdx.x; t < novf; t += blockDim.x) {
         const uint32_t id = pa.ovf[t];
-        const uint64_t key = perm_key(id, m32, pa.replica, pa.seed);
-        if (bucket_of(key, pa.bits) == b) {
-          const uint32_t pos = atomicAdd(&s_fill, 1u);
-          sid[pos] = id;
-          skey[pos] = key;
-        }
+        if (bucket_of(perm_key(id, m32, pa.replica, pa.seed), pa.bits) == b) sid[atomicAdd(&s_fill, 1u)] = id;
       }
     }
-    uint32_t p2 = 1;
-    while (p2 < nb) p2 <<= 1;
-    for (uint32_t t = nb + threadIdx.x; t < p2; t += blockDim.x) {
-      skey[t] = ~0ull;
-      sid[t] = ~0u;
+    __syncthreads();
+    // keys in registers; rank of each member inside its sub-bucket
+    uint64_t key[kSortPer];
+    uint32_t idr[kSortPer], subr[kSortPer];
+#pragma unroll
+    for (int k = 0; k < kSortPer; ++k) {
+      const uint32_t t = threadIdx.x + k * kSortThreads;
+      if (t < nb) {
+        idr[k] = (t < nslot) ? pa.slots[static_cast<size_t>(b) * pa.slot_cap + t] : sid[t];
+        key[k] = perm_key(idr[k], m32, pa.replica, pa.seed);
+        const uint32_t sub = sub_of(key[k], pa.bits);
+        subr[k] = sub | (atomicAdd(&ssub[sub], 1u) << 16);
+      }
     }
     __syncthreads();
-    bitonic_sort(skey, sid, p2);
+    sub_exclusive_scan(ssub, s_red);
+#pragma unroll
+    for (int k = 0; k < kSortPer; ++k) {
+      const uint32_t t = threadIdx.x + k * kSortThreads;
+      if (t < nb) {
+        const uint32_t pos = ssub[subr[k] & 0xffffu] + (subr[k] >> 16);
+        skey[pos] = key[k];
+        sid[pos] = idr[k];
+      }
+    }
+    __syncthreads();
+    for (uint32_t u = threadIdx.x; u < kSub; u += blockDim.x) {  // insertion sort of each sub-bucket
+      const uint32_t lo = ssub[u], hi = (u + 1 < kSub) ? ssub[u + 1] : nb;
+      for (uint32_t x = lo + 1; x < hi; ++x) {
+        const uint64_t kx = skey[x];
+        const uint32_t ix = sid[x];
+        uint32_t y = x;
+        while (y > lo && key_less(kx, ix, skey[y - 1], sid[y - 1])) {
+          skey[y] = skey[y - 1];
+          sid[y] = sid[y - 1];
+          --y;
+        }
+        skey[y] = kx;
+        sid[y] = ix;
+      }
+    }
+    __syncthreads();
     for (uint32_t t = threadIdx.x; t < nb; t += blockDim.x) pa.perm[start + t] = sid[t];
     ids = sid;
   } else {
@@ -374,18 +422,22 @@ __global__ void __launch_bounds__(256) k_batch_generic(PermArgs pa, StepParams<T
 __global__ void k_set_i64(int64_t* dst, int64_t v) { *dst = v; }
 __global__ void k_add_i64(int64_t* dst, int64_t v) { *dst += v; }
 
+size_t sort_smem_bytes(uint32_t sort_cap) {
+  return static_cast<size_t>(sort_cap) * (sizeof(uint64_t) + sizeof(uint32_t)) + kSub * sizeof(uint32_t);
+}
+
 template <typename T, int D>
 void launch_tail_d(const PermScratch& ps, int mode, const StepParams<T>& a, const LaunchCfg& cfg, cudaStream_t st) {
   const PermArgs pa = make_perm_args(ps, a.n, a.seed, a.replica, a.m_ptr, a.m_off);
-  const size_t smem = static_cast<size_t>(ps.sort_cap) * (sizeof(uint64_t) + sizeof(uint32_t));
+  const size_t smem = sort_smem_bytes(ps.sort_cap);
   const bool small_p = a.p <= 32;
-  const int block = 256;
+  const int block = kSortThreads;
   if (ps.separate_scan) {
     k_bucket_scan<<<1, 1024, 0, st>>>(pa);
     mark_launch(cfg, st, "k_bucket_scan");
   }
   const int kmode = small_p ? mode : kModePerm;
-  auto launch_sort = [&](auto kern) { kern<<<ps.nbuckets, block, smem, st>>>(pa, a); };
+  auto launch_sort = [&](auto kern) { kern<<<ps.nbuckets, kSortThreads, smem, st>>>(pa, a); };
   if (kmode == kModeStep) launch_sort(k_bucket_sort_step<T, D, kModeStep>);
   else if (kmode == kModeForces) launch_sort(k_bucket_sort_step<T, D, kModeForces>);
   else launch_sort(k_bucket_sort_step<T, D, kModePerm>);
@@ -431,6 +483,8 @@ void launch_rbm_tail(const PermScratch& ps, int d, int mode, const void* params,
 template void launch_rbm_tail<float>(const PermScratch&, int, int, const void*, const LaunchCfg&, cudaStream_t);
 template void launch_rbm_tail<double>(const PermScratch&, int, int, const void*, const LaunchCfg&, cudaStream_t);
 
+uint32_t max_sort_cap() { return kSortCapMax; }
+
 int rbm_tail_launches(const PermScratch& ps, int p) {
   int n = 1;                      // sort (+ fused step)
   if (ps.separate_scan) n += 2;   // scan, straddle fix-up
@@ -453,8 +507,8 @@ cudaError_t allow_sort_smem_d(int bytes) {
 }  // namespace
 
 cudaError_t prepare_rbm_kernels() {
-  // The largest shared-memory sort (4096 keys + ids) plus static shared data.
-  const int bytes = 4096 * static_cast<int>(sizeof(uint64_t) + sizeof(uint32_t)) + 1024;
+  // The largest shared-memory sort plus static shared data.
+  const int bytes = static_cast<int>(sort_smem_bytes(kSortCapMax)) + 1024;
   cudaError_t e = allow_sort_smem_d<float, 1>(bytes);
   if (e == cudaSuccess) e = allow_sort_smem_d<float, 2>(bytes);
   if (e == cudaSuccess) e = allow_sort_smem_d<float, 3>(bytes);

@@ -131,7 +131,7 @@ uint32_t next_pow2(uint32_t v) {
 
 // Bucket geometry: about 512 members per bucket by default; slots hold the
 // mean plus eight standard deviations plus 64, the shared-memory sort twice
-// that (power of two, at most 4096); members beyond either bound take the
+// that (power of two, at most max_sort_cap()); members beyond either bound take the
 // spill list and the counting fallback, so any bucket size stays correct.
 rbm_status alloc_scratch(rbm_ctx* c) {
   const uint32_t n = static_cast<uint32_t>(c->prm.n);
@@ -151,7 +151,7 @@ rbm_status alloc_scratch(rbm_ctx* c) {
   s.slot_cap = cap;
   uint32_t sc = c->tuning.sort_cap > 0 ? next_pow2(static_cast<uint32_t>(c->tuning.sort_cap))
                                        : next_pow2(2 * cap);
-  if (sc > 4096) sc = 4096;
+  if (sc > max_sort_cap()) sc = max_sort_cap();
   if (sc < 2) sc = 2;
   s.sort_cap = sc;
   s.separate_scan = s.nbuckets > 1024;

@@ -103,6 +103,8 @@ cudaError_t prepare_rbm_kernels();  // per-device kernel attributes, called by r
 void launch_set_i64(int64_t* dst, int64_t value, cudaStream_t st);
 void launch_add_i64(int64_t* dst, int64_t value, cudaStream_t st);
 int rbm_tail_launches(const PermScratch& ps, int p);
+// Largest bucket the shared-memory sort of the multi-kernel path takes.
+uint32_t max_sort_cap();
 
 // Cooperative step (coop_step.cu): mode as for launch_rbm_tail.
 cudaError_t prepare_coop_kernels(int* blocks_per_sm);
