@@ -12,7 +12,7 @@ so the flush's dirty lines are written back before the step starts) and each
 step is timed alone with CUDA events on the stream its kernels run on.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload thomson|batched_opinion|dyson|large_n|surrogate]
+                    [--workload thomson|batched_opinion|dyson|large_n|surrogate|w1_sweep]
                     [--sizes 20,22 (large_n)] [--no-cpu-baseline]
 
 Other workloads (one JSON line each, same keys):
@@ -29,7 +29,11 @@ Other workloads (one JSON line each, same keys):
                     mixture, sigma = 0.1, dt = 1e-3: whole 100-step cycles
                     (checkpoint training + 100 network steps), the network
                     step alone, RBM-1 and direct at the same N, and the
-                    accuracy of each at N = 2^16 against the direct method.
+                    accuracy of each at N = 2^16 against the direct method;
+  w1_sweep        - equal-accuracy comparison at N = 2^16: sliced W1 to a
+                    direct reference at dt/16 for RBM-1, direct and the
+                    surrogate at dt * {1, 1/2, 1/4, ...}, and the time to T
+                    at W1 <= 1e-2 for each method.
 Under torchrun each rank advances its own replica of the workload (replica
 index = rank; no data-path collective): weak scaling.  ``--impl reference``
 times the CPU oracle on this host's cores instead (rank 0 only).
@@ -72,6 +76,19 @@ WORKLOADS = {
                       seed=0, scheme="euler", train_every=100, n_queries=16384, iters_first=12000,
                       iters_per_checkpoint=2000, max_rounds=8, lr=3e-3, fallback_tol=1e-2, accuracy_n=2**16,
                       accuracy_steps=300),
+    "w1_sweep": dict(workload="equal_w1_sweep", n=2**16, eps=1e-2, ref_refine=16, refines=[1, 2, 4, 8],
+                     direct_refines=[1, 2, 4], slices=16, seed=0, dtype="f32"),
+}
+
+# The two systems of the equal-W1 sweep (N = 2^16 for accuracy): the large-N
+# workload (d = 3, regularised attraction) and the surrogate workload (d = 2,
+# Gaussian aggregation from the 4-cluster mixture).
+W1_SYSTEMS = {
+    "large_n_reg_attract": dict(d=3, dt=1e-3, steps=200, sigma=0.2, kernel="reg_attract", potential="quadratic",
+                                v_coef=1.0, k_param=0.01, p=2, init="gaussian", surrogate=False),
+    "surrogate_mixture_aggregation": dict(d=2, dt=1e-3, steps=300, sigma=0.1, kernel="gauss_agg",
+                                          potential="quadratic", v_coef=1.0, k_param=0.0, p=2, init="mixture",
+                                          surrogate=True),
 }
 
 
@@ -330,7 +347,7 @@ def run_single(args, w, g):
     sysm.sync()
     soak = rbm.System(x.clone(), d=d, stream=g.stream, **kw)
     t_soak = time.perf_counter()
-    while time.perf_counter() - t_soak < 1.0:
+    while time.perf_counter() - t_soak < args.soak_seconds:
         soak.run(100)
         soak.sync()
     soak.close()
@@ -447,7 +464,7 @@ def run_batched(args, w, g):
     rep.run(max(args.warmup, 3))
     rep.sync()
     t_soak = time.perf_counter()
-    while time.perf_counter() - t_soak < 1.0:
+    while time.perf_counter() - t_soak < args.soak_seconds:
         rep.run(min(w["graph_steps"], steps))
         rep.sync()
     e0, e1 = g.event(), g.event()
@@ -699,17 +716,100 @@ def run_surrogate(args, w, g):
     return line
 
 
+def _sliced_w1(A, B, k, seed=0):
+    """Mean over k random unit directions (and the coordinate axes) of the
+    1-D Wasserstein-1 distance of the projected samples (equal sizes)."""
+    rng = np.random.default_rng(seed)
+    dirs = rng.standard_normal((k, A.shape[1]))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    dirs = np.concatenate([np.eye(A.shape[1]), dirs])
+    return float(np.mean([np.mean(np.abs(np.sort(A @ v) - np.sort(B @ v))) for v in dirs]))
+
+
+def run_w1_sweep(args, w, g):
+    """Equal-accuracy comparison: for each system, a direct reference at
+    dt/16 to the same final time T, then RBM-1 (and direct, and the surrogate
+    where it applies) at dt * {1, 1/2, 1/4, ...}; W1 of each final empirical
+    distribution to the reference's (sliced), the measured particle-steps/s
+    of each run, and the time to reach T with the coarsest dt whose W1 is
+    within eps.  The Brownian increments of different dt are independent
+    draws, so W1 has a sampling floor of order N^-1/2."""
+    import paper_1812_10575_gb300 as rbm
+    import workloads
+
+    n, eps = w["n"], w["eps"]
+    out = {}
+    clocks = ClockSampler(g.local).start()
+    for name, sy in W1_SYSTEMS.items():
+        d = sy["d"]
+        X0 = workloads.gaussian(n, d, seed=w["seed"]) if sy["init"] == "gaussian" else \
+            workloads.mixture(n, d, seed=w["seed"])
+        T = sy["dt"] * sy["steps"]
+
+        def final(method, refine):
+            x = _to_dev(g, X0, d, "f32")
+            dt = sy["dt"] / refine
+            s = rbm.System(x, d=d, p=sy["p"], dt=dt, sigma=sy["sigma"], seed=w["seed"], v=sy["potential"],
+                           v_coef=sy["v_coef"], k=sy["kernel"], k_param=sy["k_param"], stream=g.stream)
+            if method == "surrogate":
+                s.surrogate_config(train_every=25, fallback_tol=1e-2, n_queries=16384, iters_first=12000,
+                                   iters_per_checkpoint=1000, max_rounds=8, lr=3e-3)
+            steps = sy["steps"] * refine
+            e0, e1 = g.event(), g.event()
+            e0.record(g.stream)
+            s.run(steps, method)
+            e1.record(g.stream)
+            s.sync()
+            ms = e0.elapsed_time(e1)
+            st = s.surrogate_stats() if method == "surrogate" else None
+            X = x[:, :d].double().cpu().numpy()
+            s.close()
+            return X, ms, steps, st
+
+        Xref, ref_ms, ref_steps, _ = final("direct", w["ref_refine"])
+        methods = {"rbm": w["refines"], "direct": w["direct_refines"]}
+        if sy["surrogate"]:
+            methods["surrogate"] = w["direct_refines"]
+        res = {"T": T, "reference": {"method": "direct", "dt": sy["dt"] / w["ref_refine"], "steps": ref_steps,
+                                     "seconds": ref_ms / 1e3}}
+        for method, refines in methods.items():
+            curve = []
+            for rf in refines:
+                X, ms, steps, st = final(method, rf)
+                ent = {"dt": sy["dt"] / rf, "steps": steps, "w1": _sliced_w1(X, Xref, w["slices"]),
+                       "seconds_to_T": ms / 1e3, "particle_steps_per_s": n * steps / (ms * 1e-3)}
+                if st:
+                    ent["surrogate_steps"], ent["fallback_steps"] = st["surrogate_steps"], st["fallback_steps"]
+                curve.append(ent)
+            ok = [c for c in curve if c["w1"] <= eps]
+            best = min(ok, key=lambda c: c["seconds_to_T"]) if ok else None
+            res[method] = {"curve": curve, "time_to_T_at_eps_s": best["seconds_to_T"] if best else None,
+                           "dt_at_eps": best["dt"] if best else None,
+                           "particle_steps_per_s_at_eps": best["particle_steps_per_s"] if best else None}
+        out[name] = res
+    clocks.stop()
+    head = out["large_n_reg_attract"]
+    value = head["rbm"]["particle_steps_per_s_at_eps"] or 0.0
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": g.world, "steps": None, "warmup": 0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(w, systems=W1_SYSTEMS, l2="state 1-2 MB (L2-resident); whole runs timed with events",
+                           value_is="RBM-1 particle-steps/s at the coarsest dt with sliced W1 <= eps, large-N system"),
+            "clocks": clocks.summary(), "sweeps": out}
+
+
 def run_ours(args, w):
     g = Gpu()
     if w["workload"].startswith("batched"):
         line = run_batched(args, w, g)
     elif w["workload"].startswith("surrogate"):
         line = run_surrogate(args, w, g)
+    elif w["workload"].startswith("equal_w1"):
+        line = run_w1_sweep(args, w, g)
     elif w["workload"].startswith("large_n"):
         line = run_large_n(args, w, g)
     else:
         line = run_single(args, w, g)
-    if g.rank == 0 and g.world == 1 and not args.no_cpu_baseline and "sweep" not in line:
+    if g.rank == 0 and g.world == 1 and not args.no_cpu_baseline and "sweep" not in line and "sweeps" not in line:
         rate, done, el, cores, sample = _oracle_rate(w, seconds=args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{done} oracle RBM-1 steps of {sample} in {el:.1f} s"}
@@ -728,6 +828,8 @@ def main():
     ap.add_argument("--workload", default="thomson", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--soak-seconds", type=float, default=1.0,
+                    help="untimed load before the timed steps (brings the clocks up; 0 for short profiling runs)")
     ap.add_argument("--sizes", default="", help="large_n only: comma-separated log2 N (default 16,18,20,22,24)")
     args = ap.parse_args()
     if args.warmup < 3:
