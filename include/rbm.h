@@ -283,7 +283,9 @@ rbm_status rbm_batched_init(const rbm_params *base, int32_t nrep, const int64_t 
                             void *cuda_stream, rbm_ctx **out);
 
 /* Launch shape of the batched step: threads per block (256, 512 or 1024) and
- * the mean bucket size of each replica's sort (64 .. 2048).  Synchronous. */
+ * the mean bucket size of each replica's sort (64 .. 2048).  Synchronous.
+ * RBM_ERR_UNSUPPORTED (shape unchanged) when the kernel for this dtype and d
+ * cannot run that many threads per block (its registers do not fit). */
 rbm_status rbm_batched_set_launch(rbm_ctx *ctx, int32_t threads, int32_t bucket_target);
 
 /* Choose the launch configuration of the RBM step by timing the candidates

@@ -11,14 +11,19 @@
 // replicas (largest first, dealt to the blocks in snake order so the sums of
 // N_r per block stay close) and runs, for each replica, with block-level
 // synchronisation only:
-//   1. keys of all ids (stored once, L2-resident) and a shared-memory
-//      histogram of B_r = ceil(N_r / target) buckets (monotone in the key);
+//   1. a shared-memory histogram of B_r = ceil(N_r / target) buckets
+//      (monotone in the key; keys are regenerated from Philox wherever they
+//      are needed, never stored);
 //   2. scan, scatter of ids to bucket order;
 //   3. per bucket: counting sort in shared memory by the next 11 key bits and
 //      insertion sort of equal sub-buckets by (key, id); the sorted ids form
-//      the replica's permutation;
-//   4. every batch of the replica stepped (groups of p lanes, positions
-//      exchanged by warp shuffles).
+//      the replica's stretch of the permutation, and the batches lying wholly
+//      inside the bucket are stepped at once from the sorted ids (groups of p
+//      lanes, positions exchanged by warp shuffles);
+//   4. the batches straddling bucket boundaries, from the permutation.
+// A replica of at most one bucket skips 1-2 and sorts its ids directly.  If a
+// bucket outgrows shared memory or holds fewer than p members, the replica
+// takes the general mode: whole permutation first, then every batch.
 // No block waits on another, so the launch cannot deadlock whatever the
 // residency.
 #include "rbm_batch.cuh"
@@ -37,7 +42,6 @@ struct BatchedArgs {
   const uint32_t* order;        // replica ids, block-major
   const uint32_t* block_begin;  // [G + 1] slice of `order` per block
   const uint64_t* offs;         // [R + 1] first row of each replica
-  uint64_t* keys;               // [rows] key of each row (replica-local id order)
   uint32_t* tmp;                // [rows] ids grouped by bucket
   uint32_t* perm;               // [rows] permutation (replica-local ids)
   uint32_t bucket_target;       // mean members per bucket
@@ -82,8 +86,58 @@ __device__ void block_scan_any(uint32_t* a, uint32_t len, uint32_t* s_warp) {
   __syncthreads();
 }
 
+// Sorts the nb members of one bucket, given by ids[0, nb) in arbitrary order
+// (or the identity 0 .. nb-1 when ids is null), into b_id[0, nb) by
+// (key, id): counting sort by the kBSubBits key bits below the bucket bits,
+// then insertion sort inside each sub-bucket.  Keys are regenerated.
+__device__ void sort_bucket(const uint32_t* ids, uint32_t nb, uint32_t B, uint32_t m32, uint32_t r, uint2 seed,
+                            uint64_t* a_key, uint64_t* b_key, uint32_t* a_id, uint32_t* b_id, uint32_t* a_sub,
+                            uint32_t* s_sub, uint32_t* s_warp) {
+  for (uint32_t u = threadIdx.x; u < kBSub; u += blockDim.x) s_sub[u] = 0;
+  __syncthreads();
+  for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
+    const uint32_t id = ids ? ids[j] : j;
+    const uint64_t key = perm_key(id, m32, r, seed);
+    const uint32_t sub = static_cast<uint32_t>(__umul64hi(key, static_cast<uint64_t>(B) << kBSubBits)) & (kBSub - 1u);
+    a_key[j] = key;
+    a_id[j] = id;
+    a_sub[j] = sub | (atomicAdd(&s_sub[sub], 1u) << 16);
+  }
+  __syncthreads();
+  block_scan_any(s_sub, kBSub, s_warp);
+  for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
+    const uint32_t pos = s_sub[a_sub[j] & 0xffffu] + (a_sub[j] >> 16);
+    b_key[pos] = a_key[j];
+    b_id[pos] = a_id[j];
+  }
+  __syncthreads();
+  for (uint32_t u = threadIdx.x; u < kBSub; u += blockDim.x) {
+    const uint32_t lo = s_sub[u], hi = (u + 1 < kBSub) ? s_sub[u + 1] : nb;
+    for (uint32_t x = lo + 1; x < hi; ++x) {
+      const uint64_t kx = b_key[x];
+      const uint32_t ix = b_id[x];
+      uint32_t y = x;
+      while (y > lo && bkey_less(kx, ix, b_key[y - 1], b_id[y - 1])) {
+        b_key[y] = b_key[y - 1];
+        b_id[y] = b_id[y - 1];
+        --y;
+      }
+      b_key[y] = kx;
+      b_id[y] = ix;
+    }
+  }
+  __syncthreads();
+}
+
+// FP32 rows of one or two coordinates: registers capped so that two blocks
+// of 1024 threads fit on an SM (64 warps resident).
+template <typename T, int D>
+constexpr int batched_min_blocks() {
+  return (sizeof(T) == 4 && D <= 2) ? 2 : 1;
+}
+
 template <typename T, int D, int MODE>
-__global__ void k_rbm_batched(BatchedArgs ba, StepParams<T> a) {
+__global__ void __launch_bounds__(1024, batched_min_blocks<T, D>()) k_rbm_batched(BatchedArgs ba, StepParams<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t* a_key = reinterpret_cast<uint64_t*>(smem_raw);  // [kBCap]
   uint64_t* b_key = a_key + kBCap;                          // [kBCap]
@@ -94,101 +148,119 @@ __global__ void k_rbm_batched(BatchedArgs ba, StepParams<T> a) {
   __shared__ uint32_t s_hist[kBMaxBuckets + 1];
   __shared__ uint32_t s_fill[kBMaxBuckets];
   __shared__ uint32_t s_warp[32];
+  __shared__ int s_general;
 
   const uint32_t m32 = step_index(a);
+  const uint32_t up = static_cast<uint32_t>(a.p);
   const uint32_t begin = ba.block_begin[blockIdx.x], end_list = ba.block_begin[blockIdx.x + 1];
-  for (uint32_t li = begin; li < end_list; ++li) {
+  const uint32_t count_list = end_list - begin;
+  for (uint32_t k = 0; k < count_list; ++k) {
+    // odd blocks walk their list backwards: large and small replicas are in
+    // flight together, so the replicas being worked on fit in L2
+    const uint32_t li = (blockIdx.x & 1u) ? end_list - 1u - k : begin + k;
     const uint32_t r = ba.order[li];
     const uint64_t off = ba.offs[r];
     const uint32_t n = static_cast<uint32_t>(ba.offs[r + 1] - off);
     uint32_t B = (n + ba.bucket_target - 1) / ba.bucket_target;
     B = max(1u, min(B, kBMaxBuckets));
-    uint64_t* keys = ba.keys + off;
     uint32_t* tmp = ba.tmp + off;
     uint32_t* perm = ba.perm + off;
+    StepParams<T> ar = a;
+    ar.x = a.x + off * Ld<D>::value;
+    ar.fout = a.fout ? a.fout + off * Ld<D>::value : nullptr;
+    ar.n = n;
+    ar.replica = r;
 
-    // 1. keys and bucket histogram
+    if (B == 1 && n <= kBCap) {
+      // the whole replica is one bucket: sort the ids directly, step every batch
+      sort_bucket(nullptr, n, 1u, m32, r, a.seed, a_key, b_key, a_id, b_id, a_sub, s_sub, s_warp);
+      for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) perm[j] = b_id[j];
+      if (MODE != kModePerm) step_batches<T, D, MODE>(ar, m32, b_id, 0u, 0u, (n + up - 1) / up);
+      __syncthreads();
+      continue;
+    }
+
+    // 1. bucket histogram (keys regenerated, never stored)
     for (uint32_t b = threadIdx.x; b <= B; b += blockDim.x) s_hist[b] = 0;
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const uint64_t key = perm_key(i, m32, r, a.seed);
-      keys[i] = key;
-      atomicAdd(&s_hist[static_cast<uint32_t>(__umul64hi(key, B))], 1u);
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
+      atomicAdd(&s_hist[static_cast<uint32_t>(__umul64hi(perm_key(i, m32, r, a.seed), B))], 1u);
+    __syncthreads();
+    // 2. bucket starts (s_hist[B] becomes n), scatter of ids; a bucket too
+    //    large for shared memory or smaller than a batch selects the general
+    //    mode (whole permutation first, then every batch from it)
+    block_scan_any(s_hist, B + 1, s_warp);
+    if (threadIdx.x == 0) s_general = 0;
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) {
+      s_fill[b] = s_hist[b];
+      const uint32_t nb = s_hist[b + 1] - s_hist[b];
+      if (nb > kBCap || nb < up) s_general = 1;
     }
     __syncthreads();
-    // 2. bucket starts (s_hist[B] becomes n), scatter of ids
-    block_scan_any(s_hist, B + 1, s_warp);
-    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) s_fill[b] = s_hist[b];
-    __syncthreads();
+    const bool general = (MODE == kModePerm) || s_general != 0;
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const uint32_t b = static_cast<uint32_t>(__umul64hi(keys[i], B));
+      const uint32_t b = static_cast<uint32_t>(__umul64hi(perm_key(i, m32, r, a.seed), B));
       tmp[atomicAdd(&s_fill[b], 1u)] = i;
     }
     __syncthreads();
-    // 3. sort every bucket
+    // 3. sort every bucket; outside the general mode step the batches lying
+    //    wholly inside it straight from the sorted ids in shared memory
     for (uint32_t b = 0; b < B; ++b) {
       const uint32_t s = s_hist[b], nb = s_hist[b + 1] - s;
       if (nb <= kBCap) {
-        for (uint32_t u = threadIdx.x; u < kBSub; u += blockDim.x) s_sub[u] = 0;
-        __syncthreads();
-        for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
-          const uint32_t id = tmp[s + j];
-          const uint64_t key = keys[id];
-          const uint32_t sub =
-              static_cast<uint32_t>(__umul64hi(key, static_cast<uint64_t>(B) << kBSubBits)) & (kBSub - 1u);
-          a_key[j] = key;
-          a_id[j] = id;
-          a_sub[j] = sub | (atomicAdd(&s_sub[sub], 1u) << 16);
-        }
-        __syncthreads();
-        block_scan_any(s_sub, kBSub, s_warp);
-        for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
-          const uint32_t pos = s_sub[a_sub[j] & 0xffffu] + (a_sub[j] >> 16);
-          b_key[pos] = a_key[j];
-          b_id[pos] = a_id[j];
-        }
-        __syncthreads();
-        for (uint32_t u = threadIdx.x; u < kBSub; u += blockDim.x) {
-          const uint32_t lo = s_sub[u], hi = (u + 1 < kBSub) ? s_sub[u + 1] : nb;
-          for (uint32_t x = lo + 1; x < hi; ++x) {
-            const uint64_t kx = b_key[x];
-            const uint32_t ix = b_id[x];
-            uint32_t y = x;
-            while (y > lo && bkey_less(kx, ix, b_key[y - 1], b_id[y - 1])) {
-              b_key[y] = b_key[y - 1];
-              b_id[y] = b_id[y - 1];
-              --y;
-            }
-            b_key[y] = kx;
-            b_id[y] = ix;
-          }
-        }
-        __syncthreads();
+        sort_bucket(tmp + s, nb, B, m32, r, a.seed, a_key, b_key, a_id, b_id, a_sub, s_sub, s_warp);
         for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) perm[s + j] = b_id[j];
+        if (!general) {
+          const uint32_t end = s + nb;
+          const uint32_t q0 = (s + up - 1) / up;
+          const uint32_t q_end = (end == n) ? (n + up - 1) / up : end / up;
+          step_batches<T, D, MODE>(ar, m32, b_id, s, q0, (q_end > q0) ? q_end - q0 : 0u);
+        }
       } else {
-        // a bucket beyond the shared-memory sort: rank by counting
+        // a bucket beyond the shared-memory sort (general mode): rank by counting
         for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
           const uint32_t idj = tmp[s + j];
-          const uint64_t kj = keys[idj];
+          const uint64_t kj = perm_key(idj, m32, r, a.seed);
           uint32_t rank = 0;
           for (uint32_t f = 0; f < nb; ++f) {
             const uint32_t idf = tmp[s + f];
-            rank += bkey_less(keys[idf], idf, kj, idj) ? 1u : 0u;
+            rank += bkey_less(perm_key(idf, m32, r, a.seed), idf, kj, idj) ? 1u : 0u;
           }
           perm[s + rank] = idj;
         }
       }
       __syncthreads();
     }
-    // 4. step every batch of the replica
+    // 4. the batches not stepped yet: those straddling a bucket boundary
+    //    (each from the first boundary strictly inside it), or all of them in
+    //    the general mode; members read from the permutation just written
     if (MODE != kModePerm) {
-      StepParams<T> ar = a;
-      ar.x = a.x + off * Ld<D>::value;
-      ar.fout = a.fout ? a.fout + off * Ld<D>::value : nullptr;
-      ar.n = n;
-      ar.replica = r;
-      const uint32_t nbatch = (n + static_cast<uint32_t>(a.p) - 1) / static_cast<uint32_t>(a.p);
-      step_batches<T, D, MODE>(ar, m32, perm, 0u, 0u, nbatch);
+      if (general) {
+        step_batches<T, D, MODE>(ar, m32, perm, 0u, 0u, (n + up - 1) / up);
+      } else {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int gpw = 32 / a.p, nwarps = blockDim.x >> 5;
+        const int g = lane / a.p, lg = lane - g * a.p;
+        const uint32_t per_round = static_cast<uint32_t>(gpw * nwarps);
+        for (uint32_t r0 = 1; r0 < B; r0 += per_round) {
+          const uint32_t b = r0 + static_cast<uint32_t>(warp * gpw + g);
+          bool valid = (g < gpw) && (b < B);
+          uint32_t id = 0;
+          int bs = a.p;
+          if (valid) {
+            const uint32_t sb = s_hist[b];
+            valid = (sb % up) != 0;                 // buckets hold >= p members: one boundary per batch
+            if (valid) {
+              const uint32_t lo = (sb / up) * up, hi = min(lo + up, n);
+              bs = static_cast<int>(hi - lo);
+              valid = lg < bs;
+              if (valid) id = perm[lo + lg];
+            }
+          }
+          batch_group<T, D, MODE>(ar, m32, id, valid, lg, bs);
+        }
+      }
     }
     __syncthreads();
   }
@@ -205,7 +277,6 @@ cudaError_t launch_batched_k(const BatchedScratch& bs, const StepParams<T>& a, c
   ba.order = bs.order;
   ba.block_begin = bs.block_begin;
   ba.offs = bs.offs;
-  ba.keys = bs.keys;
   ba.tmp = bs.tmp;
   ba.perm = bs.perm;
   ba.bucket_target = static_cast<uint32_t>(bs.bucket_target);

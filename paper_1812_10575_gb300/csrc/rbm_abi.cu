@@ -101,7 +101,7 @@ void free_scratch(rbm_ctx* c) {
   cudaFree(c->cs.hist); cudaFree(c->cs.tmp); cudaFree(c->cs.bar);
   c->cs = CoopScratch{};
   cudaFree(c->bs.order); cudaFree(c->bs.block_begin); cudaFree(c->bs.offs);
-  cudaFree(c->bs.keys); cudaFree(c->bs.tmp); cudaFree(c->bs.perm);
+  cudaFree(c->bs.tmp); cudaFree(c->bs.perm);
   {
     const int threads = c->bs.threads, target = c->bs.bucket_target;
     c->bs = BatchedScratch{};
@@ -411,7 +411,6 @@ rbm_status alloc_batched(rbm_ctx* c) {
   const size_t rows = static_cast<size_t>(offs[nrep]);
   RBM_CUDA(cudaMalloc(&bs.offs, sizeof(uint64_t) * offs.size()));
   RBM_CUDA(cudaMemcpy(bs.offs, offs.data(), sizeof(uint64_t) * offs.size(), cudaMemcpyHostToDevice));
-  RBM_CUDA(cudaMalloc(&bs.keys, sizeof(uint64_t) * rows));
   RBM_CUDA(cudaMalloc(&bs.tmp, sizeof(uint32_t) * rows));
   RBM_CUDA(cudaMalloc(&bs.perm, sizeof(uint32_t) * rows));
   RBM_CUDA(cudaMalloc(&c->xtmp, c->row_bytes * rows));
@@ -897,6 +896,9 @@ rbm_status rbm_batched_set_launch(rbm_ctx* ctx, int32_t threads, int32_t bucket_
   if (!ctx->batched) return RBM_ERR_INVALID;
   if ((threads != 256 && threads != 512 && threads != 1024) || bucket_target < 64 || bucket_target > 2048)
     return RBM_ERR_INVALID;
+  int bpsm = 0;
+  if (prepare_batched_kernels(ctx->prm.dtype, ctx->prm.d, threads, &bpsm) != cudaSuccess || bpsm < 1)
+    return RBM_ERR_UNSUPPORTED;  // this block size does not fit the kernel's registers; shape unchanged
   RBM_CUDA(cudaStreamSynchronize(ctx->stream));
   drop_graphs(ctx);
   ctx->bs.threads = threads;
@@ -944,8 +946,10 @@ rbm_status rbm_autotune(rbm_ctx* ctx, int32_t trial_steps, const char* table_pat
     void* real_x = ctx->x;
     std::vector<std::pair<int, int>> cands;
     if (ctx->batched) {
+      // mean bucket sizes well below the 2048-member shared-memory sort, so
+      // the counting fallback for an oversized bucket stays out of the trial
       for (int th : {256, 512, 1024})
-        for (int bt : {512, 1024, 2048}) cands.push_back({th, bt});
+        for (int bt : {256, 512, 1024}) cands.push_back({th, bt});
     } else {
       cands.push_back({1, 0});
       cands.push_back({2, 0});
@@ -957,8 +961,13 @@ rbm_status rbm_autotune(rbm_ctx* ctx, int32_t trial_steps, const char* table_pat
     std::pair<int, int> best_c = cands[0];
     std::ostringstream rep;
     for (const auto& cd : cands) {
-      if (ctx->batched) st = rbm_batched_set_launch(ctx, cd.first, cd.second);
-      else {
+      if (ctx->batched) {
+        st = rbm_batched_set_launch(ctx, cd.first, cd.second);
+        if (st == RBM_ERR_UNSUPPORTED) {  // block size not available for this kernel
+          st = RBM_OK;
+          continue;
+        }
+      } else {
         rbm_tuning t = ctx->tuning;
         t.path = cd.first;
         st = rbm_set_tuning(ctx, &t);

@@ -41,7 +41,6 @@ struct BatchedScratch {
   uint32_t* order = nullptr;        // replica ids, block-major
   uint32_t* block_begin = nullptr;  // [grid + 1]
   uint64_t* offs = nullptr;         // [nrep + 1] first row of each replica
-  uint64_t* keys = nullptr;         // [rows]
   uint32_t* tmp = nullptr;          // [rows]
   uint32_t* perm = nullptr;         // [rows]
   uint32_t grid = 0;

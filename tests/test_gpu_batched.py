@@ -91,6 +91,27 @@ def test_batched_fp32_per_step_opinion_workload():
         cur = got
 
 
+@pytest.mark.parametrize("p,bucket_target", [(8, 64), (32, 64), (4, 2048)])
+def test_batched_bucket_shapes_fp64(p, bucket_target):
+    """Small buckets (a batch straddles almost every bucket boundary, stepped
+    after the buckets) and buckets of mean ~2048 (some beyond the
+    shared-memory sort: the replica takes the general mode) give the oracle's
+    trajectory."""
+    torch_cuda()
+    sizes = [4100, 6000, 300, 33, 40, 2049, 2100, 31]
+    kw = dict(p=p, seed=5, **OPINION)
+    rep, x, X = _replicas(sizes, 2, "f64", data_seed=4, **kw)
+    rep.set_launch(256, bucket_target)
+    rep.run(5)
+    rep.sync()
+    got = from_dev(x, 2)
+    for r, (lo, hi) in enumerate(_slices(sizes)):
+        prm = oracle.make_params(hi - lo, 2, p=p, dt=OPINION["dt"], sigma=OPINION["sigma"], seed=5,
+                                 k="bounded_conf", k_param=0.25, replica=r)
+        ref = oracle.run(prm, X[lo:hi], 0, 5)
+        assert_close_per_particle(got[lo:hi], ref, 1e-10, what=f"replica {r} (N={hi - lo})")
+
+
 def test_batched_replica_equals_single_system_bitwise():
     torch = torch_cuda()
     sizes = [700, 5000, 1234, 4]
