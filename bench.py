@@ -61,7 +61,8 @@ L2_FLUSH_BYTES = 256 << 20
 
 WORKLOADS = {
     "thomson": dict(workload="thomson_sphere_rbm1", n=100000, d=3, p=2, dt=1e-4, sigma=0.0, kernel="coulomb",
-                    potential="zero", v_coef=1.0, k_param=0.0, renorm=True, dtype="f32", seed=0, scheme="euler"),
+                    potential="zero", v_coef=1.0, k_param=0.0, renorm=True, dtype="f32", seed=0, scheme="euler",
+                    quality_steps=2000),
     "batched_opinion": dict(workload="batched_opinion_replicas", replicas=4096, n_lo=256, n_hi=65536, d=2, p=2,
                             dt=1e-2, sigma=0.01, kernel="bounded_conf", potential="zero", v_coef=1.0, k_param=0.25,
                             renorm=False, dtype="f32", seed=0, scheme="euler", graph_steps=100),
@@ -442,7 +443,60 @@ def run_single(args, w, g):
         "wall_s_timed_region": wall, "kernel_sources": digest,
     }
     sysm.close()
+    if w.get("quality_steps"):
+        line["quality"] = _thomson_quality(g, w, kw)
     return line
+
+
+def _coulomb_energy(torch, X, chunk=512):
+    """E = sum_{i<j} 1/|x_i - x_j| on the GPU with torch (a diagnostic of the
+    run, not part of the timed path)."""
+    e = torch.zeros((), dtype=torch.float64, device=X.device)
+    for a in range(0, X.shape[0], chunk):
+        dist = torch.cdist(X[a:a + chunk].double(), X.double())
+        idx = torch.arange(a, min(a + chunk, X.shape[0]), device=X.device)
+        dist[idx - a, idx] = float("inf")
+        e += (1.0 / dist).sum()
+    return float(e) / 2.0
+
+
+def _sliced_w1_uniform(X, k=16, seed=0):
+    """Mean over k random directions of W1 between the projections X v and
+    U[-1, 1], the law of the projection of a uniform point of S^2 onto any
+    axis (Archimedes): mean |y_(k) - q_k| with the uniform quantiles q_k."""
+    rng = np.random.default_rng(seed)
+    dirs = rng.standard_normal((k, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    n = X.shape[0]
+    q = -1.0 + 2.0 * (np.arange(n) + 0.5) / n
+    return float(np.mean([np.mean(np.abs(np.sort(X @ v) - q)) for v in dirs]))
+
+
+def _thomson_quality(g, w, kw):
+    """The Thomson run's own figures of merit after `quality_steps` steps of
+    RBM-1 and of the direct method from the same X0: the Coulomb energy and
+    the sliced W1 of the points to the uniform law on the sphere."""
+    import paper_1812_10575_gb300 as rbm
+
+    torch, n, d = g.torch, w["n"], w["d"]
+    X0 = _initial(w, n)
+    out = {"steps": w["quality_steps"], "T": w["quality_steps"] * w["dt"]}
+    x0 = _to_dev(g, X0, d, w["dtype"])
+    out["energy_x0"] = _coulomb_energy(torch, x0[:, :3])
+    out["sliced_w1_uniform_x0"] = _sliced_w1_uniform(x0[:, :3].double().cpu().numpy())
+    for method in ("rbm", "direct"):
+        x = _to_dev(g, X0, d, w["dtype"])
+        s = rbm.System(x, d=d, stream=g.stream, **kw)
+        e0, e1 = g.event(), g.event()
+        e0.record(g.stream)
+        s.run(w["quality_steps"], method)
+        e1.record(g.stream)
+        s.sync()
+        out[method] = {"energy": _coulomb_energy(torch, x[:, :3]),
+                       "sliced_w1_uniform": _sliced_w1_uniform(x[:, :3].double().cpu().numpy()),
+                       "seconds": e0.elapsed_time(e1) / 1e3}
+        s.close()
+    return out
 
 
 def run_batched(args, w, g):
@@ -498,6 +552,9 @@ def run_batched(args, w, g):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": g.world, "steps": steps, "warmup": args.warmup,
         "ms_per_step": total_ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": w["dtype"], "data": "synthetic",
+        "replica_size_histogram": {f"[2^{k}, 2^{k + 1})": int(np.sum((np.array(sizes) >= 2 ** k) &
+                                                                     (np.array(sizes) < 2 ** (k + 1))))
+                                   for k in range(8, 17)},
         "config": dict(w, rows=rows, l2=f"inputs ({rows * row_bytes / 1e6:.0f} MB of positions) exceed L2; "
                                         "K steps replayed back to back from CUDA graphs",
                        parallelism=f"replicas x{g.world}", autotune=tune),

@@ -102,6 +102,11 @@ def lib() -> ctypes.CDLL:
             L.orc_rbm_split_step.argtypes = [P, dp, ctypes.c_int64]
             L.orc_split_pair_solve.argtypes = [P, dp, dp, dp, dp]
             L.orc_direct_step.argtypes = [P, dp, ctypes.c_int64]
+            L.orc_rbmr_iterations_per_step.argtypes = [P]
+            L.orc_rbmr_iterations_per_step.restype = ctypes.c_int64
+            L.orc_rbmr_set.argtypes = [P, ctypes.c_int64, u32p]
+            L.orc_rbmr_iteration.argtypes = [P, dp, ctypes.c_int64]
+            L.orc_rbmr_step.argtypes = [P, dp, ctypes.c_int64]
             L.orc_direct_forces_at.argtypes = [P, dp, dp, ctypes.c_int64, dp]
             L.orc_direct_step_sampled.argtypes = [P, dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                                   ctypes.c_int64, dp]
@@ -240,8 +245,34 @@ def direct_step(prm: OrcParams, X, m: int) -> np.ndarray:
     return Y
 
 
+def rbmr_iterations_per_step(prm: OrcParams) -> int:
+    """RBM-r iterations per step: floor(N/p), at least 1."""
+    return int(lib().orc_rbmr_iterations_per_step(ctypes.byref(prm)))
+
+
+def rbmr_set(prm: OrcParams, k: int) -> np.ndarray:
+    """The p members (slot order) of RBM-r iteration ``k``."""
+    out = np.zeros(prm.p, dtype=np.uint32)
+    lib().orc_rbmr_set(ctypes.byref(prm), int(k), _ptr(out, ctypes.c_uint32))
+    return out
+
+
+def rbmr_iteration(prm: OrcParams, X, k: int) -> np.ndarray:
+    """One RBM-r iteration (Algorithm "fullyrandom"); returns the new positions."""
+    Y = _x(X, prm).copy()
+    lib().orc_rbmr_iteration(ctypes.byref(prm), _ptr(Y, ctypes.c_double), int(k))
+    return Y
+
+
+def rbmr_step(prm: OrcParams, X, m: int) -> np.ndarray:
+    """One RBM-r step m -> m+1: iterations m K .. m K + K - 1, K = floor(N/p)."""
+    Y = _x(X, prm).copy()
+    lib().orc_rbmr_step(ctypes.byref(prm), _ptr(Y, ctypes.c_double), int(m))
+    return Y
+
+
 def run(prm: OrcParams, X, m0: int, steps: int, method: str = "rbm") -> np.ndarray:
-    step = {"rbm": rbm_step, "direct": direct_step, "split": rbm_split_step}[method]
+    step = {"rbm": rbm_step, "direct": direct_step, "split": rbm_split_step, "rbmr": rbmr_step}[method]
     Y = _x(X, prm).copy()
     for s in range(steps):
         Y = step(prm, Y, m0 + s)

@@ -388,6 +388,115 @@ void orc_direct_step(const orc_params *prm, double *X, int64_t m)
     free(FK);
 }
 
+/* ------------------------------------------------------------------------ */
+/* RBM-r (Sec. 2.2, Algorithm "fullyrandom"): iteration k picks a set C of p  */
+/* distinct particles at random and moves its members by one Euler-Maruyama   */
+/* step of size tau of the p-particle system of eq. "secondalgB", every force */
+/* taken from the positions before the iteration; iterations run strictly in */
+/* order, each seeing the positions the previous ones left.  floor(N/p)       */
+/* iterations (at least one) carry the pseudo-time of one RBM-1 step, as the  */
+/* paper's RBM-r' form (Algorithm "randomreplacement") spells out.            */
+/* Readings (the paper says only "randomly"):                                */
+/*   - the set: the words w0..w3 of the Philox blocks at counters             */
+/*     (k mod 2^32, k div 2^32, r, 7*256 + c), c = 0, 1, ..., 255, in order,  */
+/*     each mapped to the id floor(w N / 2^32); an id already taken is        */
+/*     skipped; the first p distinct ids, in the order drawn, are the slots   */
+/*     0..p-1 (the smallest ids not yet taken fill any slot still empty after */
+/*     1024 words, which needs p close to N and never happens for p <= 32);   */
+/*   - the noise of slot s: Box-Muller as for RBM-1 from the blocks at        */
+/*     counters (k mod 2^32, k div 2^32, r, 8*256 + 2 s + t), t < ceil(d/2);  */
+/*   - the in-set sum runs over the other slots in slot order.               */
+/* ------------------------------------------------------------------------ */
+#define ORC_STREAM_RBMR_SET 7u
+#define ORC_STREAM_RBMR_NOISE 8u
+
+int64_t orc_rbmr_iterations_per_step(const orc_params *prm)
+{
+    int64_t k = prm->n / prm->p;
+    return k > 0 ? k : 1;
+}
+
+void orc_rbmr_set(const orc_params *prm, int64_t k, uint32_t *set)
+{
+    uint32_t key[2] = {(uint32_t)prm->seed, (uint32_t)(prm->seed >> 32)};
+    int p = prm->p, got = 0;
+    for (uint32_t c = 0; c < 256u && got < p; ++c) {
+        uint32_t ctr[4] = {(uint32_t)(uint64_t)k, (uint32_t)((uint64_t)k >> 32), prm->replica,
+                           ORC_STREAM_RBMR_SET * 256u + c};
+        uint32_t w[4];
+        orc_philox4x32_10(ctr, key, w);
+        for (int q = 0; q < 4 && got < p; ++q) {
+            uint32_t id = (uint32_t)(((uint64_t)w[q] * (uint64_t)prm->n) >> 32);
+            int taken = 0;
+            for (int s = 0; s < got; ++s) taken |= (set[s] == id);
+            if (!taken) set[got++] = id;
+        }
+    }
+    for (uint32_t id = 0; got < p; ++id) {
+        int taken = 0;
+        for (int s = 0; s < got; ++s) taken |= (set[s] == id);
+        if (!taken) set[got++] = id;
+    }
+}
+
+static void orc_rbmr_normals(const orc_params *prm, int64_t k, int slot, double *z)
+{
+    uint32_t key[2] = {(uint32_t)prm->seed, (uint32_t)(prm->seed >> 32)};
+    for (int t = 0; 2 * t < prm->d; ++t) {
+        uint32_t ctr[4] = {(uint32_t)(uint64_t)k, (uint32_t)((uint64_t)k >> 32), prm->replica,
+                           ORC_STREAM_RBMR_NOISE * 256u + 2u * (uint32_t)slot + (uint32_t)t};
+        uint32_t a[4];
+        orc_philox4x32_10(ctr, key, a);
+        double u1 = orc_uniform(a[0], a[1], prm->ubits);
+        double u2 = orc_uniform(a[2], a[3], prm->ubits);
+        double rad = sqrt(-2.0 * log(u1));
+        double ang = 2.0 * M_PI * u2;
+        z[2 * t] = rad * cos(ang);
+        if (2 * t + 1 < prm->d) z[2 * t + 1] = rad * sin(ang);
+    }
+}
+
+void orc_rbmr_iteration(const orc_params *prm, double *X, int64_t k)
+{
+    int p = prm->p, d = prm->d;
+    uint32_t *set = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)p);
+    double *F = (double *)malloc(sizeof(double) * 3 * (size_t)p);
+    orc_rbmr_set(prm, k, set);
+    for (int s = 0; s < p; ++s) {
+        double acc[3] = {0.0, 0.0, 0.0}, kst[3];
+        for (int t = 0; t < p; ++t) {
+            if (t == s) continue;
+            orc_kernel_pair(prm, X + (size_t)set[s] * d, X + (size_t)set[t] * d, kst);
+            for (int c = 0; c < d; ++c) acc[c] += kst[c];
+        }
+        for (int c = 0; c < d; ++c) F[3 * s + c] = acc[c] / (double)(p - 1);
+    }
+    double sq = prm->sigma * sqrt(prm->dt);
+    for (int s = 0; s < p; ++s) {
+        double *x = X + (size_t)set[s] * d;
+        double z[4] = {0.0, 0.0, 0.0, 0.0}, fv[3], y[3];
+        orc_rbmr_normals(prm, k, s, z);
+        orc_confining(prm, x, fv);
+        for (int c = 0; c < d; ++c) y[c] = x[c] + prm->dt * (F[3 * s + c] + fv[c]) + sq * z[c];
+        if (prm->renorm) {
+            double nrm = 0.0;
+            for (int c = 0; c < d; ++c) nrm += y[c] * y[c];
+            nrm = sqrt(nrm);
+            for (int c = 0; c < d; ++c) y[c] /= nrm;
+        }
+        for (int c = 0; c < d; ++c) x[c] = y[c];
+    }
+    free(F);
+    free(set);
+}
+
+/* One RBM-r step m -> m+1: iterations m K .. m K + K - 1, K = floor(N/p). */
+void orc_rbmr_step(const orc_params *prm, double *X, int64_t m)
+{
+    int64_t K = orc_rbmr_iterations_per_step(prm);
+    for (int64_t j = 0; j < K; ++j) orc_rbmr_iteration(prm, X, m * K + j);
+}
+
 /* The direct step of the listed particles only: Y[a] = new position of
  * particle idx[a] after one direct step from X (same arithmetic as
  * orc_direct_step, restricted to a sample so large N stays affordable). */
