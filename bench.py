@@ -23,7 +23,8 @@ Other workloads (one JSON line each, same keys):
   dyson           - Dyson Brownian motion (Sec. 4.2), N = 1000, FP64,
                     splitting scheme, p = 2, dt = 1e-3;
   large_n         - regularised attraction, d = 3, FP32, N = 2^16 .. 2^24,
-                    p in {2, 4, 8}, RBM and (up to 2^20) direct;
+                    p in {2, 4, 8}, RBM-1, RBM-r (up to 2^22, p = 2) and
+                    direct (up to 2^20);
   surrogate       - the learned mean-field surrogate, N = 2^22, d = 2,
                     Gaussian aggregation with confinement from a 4-cluster
                     mixture, sigma = 0.1, dt = 1e-3: whole 100-step cycles
@@ -71,7 +72,8 @@ WORKLOADS = {
                   scheme="split"),
     "large_n": dict(workload="large_n_reg_attract", d=3, dt=1e-3, sigma=0.2, kernel="reg_attract",
                     potential="quadratic", v_coef=1.0, k_param=0.01, renorm=False, dtype="f32", seed=0,
-                    scheme="euler", sizes=[2**16, 2**18, 2**20, 2**22, 2**24], ps=[2, 4, 8], direct_max=2**20),
+                    scheme="euler", sizes=[2**16, 2**18, 2**20, 2**22, 2**24], ps=[2, 4, 8], direct_max=2**20,
+                    rbmr_max=2**22),
     "surrogate": dict(workload="surrogate_mixture_aggregation", n=2**22, d=2, p=2, dt=1e-3, sigma=0.1,
                       kernel="gauss_agg", potential="quadratic", v_coef=1.0, k_param=0.0, renorm=False, dtype="f32",
                       seed=0, scheme="euler", train_every=100, n_queries=16384, iters_first=12000,
@@ -592,6 +594,18 @@ def run_large_n(args, w, g):
             ent = {"n": n, "p": p, "method": "rbm", "path": s.tuning()["path"], "ms_per_step": ms,
                    "particle_steps_per_s": n / (ms * 1e-3),
                    "hbm_frac_of_floor": n * (2 * 16 + 8) / (ms * 1e-3) / 1e9 / _measured_peaks()[0]["hbm_gbs"]}
+            if p == w["ps"][0] and n <= w.get("rbmr_max", 0):
+                # RBM-r: a step = floor(N/p) iterations in conflict-free rounds
+                s.run(1, "rbmr")
+                s.sync()
+                e0.record(g.stream)
+                s.run(5, "rbmr")
+                e1.record(g.stream)
+                s.sync()
+                rms = e0.elapsed_time(e1) / 5
+                ent["rbmr_ms_per_step"] = rms
+                ent["rbmr_particle_steps_per_s"] = n / (rms * 1e-3)
+                ent["rbmr_rounds_per_step"] = s.rbmr_info()["rounds_last"]
             if p == w["ps"][0] and n <= w["direct_max"]:
                 s.direct_step()
                 s.sync()

@@ -87,8 +87,10 @@ typedef enum {
 typedef enum {
     RBM_METHOD_RBM = 0,       /* RBM-1 step (Algorithm "randomdiv")            */
     RBM_METHOD_DIRECT = 1,    /* direct O(N^2) forward-Euler step (Sec. 4.1)   */
-    RBM_METHOD_SURROGATE = 2  /* learned mean-field force with the RBM-1 step
+    RBM_METHOD_SURROGATE = 2, /* learned mean-field force with the RBM-1 step
                                  as fallback (see rbm_surrogate_config)        */
+    RBM_METHOD_RBMR = 3       /* RBM-r: floor(N/p) iterations per step of
+                                 Algorithm "fullyrandom" (see below)           */
 } rbm_method;
 
 /* Time scheme of the RBM step. */
@@ -182,6 +184,28 @@ const char *rbm_status_string(int32_t status);
 /* Text of the last CUDA runtime failure seen by the calling thread (the call
  * and the runtime's message), or "" if none.  Thread-local, static storage. */
 const char *rbm_last_error(void);
+
+/* ---- RBM-r (Sec. 2.2, Algorithm "fullyrandom") --------------------------- */
+/* One step of RBM_METHOD_RBMR (rbm_run, rbm_step_host, rbm_step_profiled) is
+ * K = floor(N/p) (at least 1) iterations k = m K .. m K + K - 1, in order:
+ * iteration k draws p distinct ids (Philox4x32-10 blocks at counters
+ * (k mod 2^32, k div 2^32, replica, 7*256 + c), words in order, id =
+ * floor(w N / 2^32), repeats skipped, slots in draw order) and moves each
+ * member i by X^i += dt (1/(p-1) sum_{j in C, j != i} K(X^i - X^j) - grad V)
+ * + sigma sqrt(dt) z, z of slot s from the blocks (k mod 2^32, k div 2^32,
+ * replica, 8*256 + 2 s + t), all forces from the positions before the
+ * iteration.  The GPU runs disjoint iterations together in rounds that keep
+ * every particle's iterations in order, so the result is the sequential one.
+ * Requires p <= 32, the Euler scheme, a single (not batched) system.  The
+ * first RBM-r call allocates about N (16 + 9 p / p) bytes of scratch. */
+
+/* The sets of step m (K x p uint32 ids, slot order) into sets_dev (device,
+ * caller-owned, K p entries).  Does not advance m. */
+rbm_status rbm_rbmr_sets(rbm_ctx *ctx, int64_t m, uint32_t *sets_dev);
+
+/* Iterations per step and the number of rounds the last RBM-r step took
+ * (0 before the first).  Synchronous. */
+rbm_status rbm_rbmr_info(rbm_ctx *ctx, int64_t *iterations_per_step, int32_t *rounds_last);
 
 /* ---- diagnostics (same conventions; used by the tests) ------------------ */
 

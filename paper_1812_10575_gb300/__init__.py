@@ -20,6 +20,7 @@ from ._lib import (  # noqa: F401
     rbm_status_string, rbm_step, rbm_step_host, rbm_step_profiled, rbm_sync, rbm_batched_init,
     rbm_batched_set_launch, rbm_autotune, rbm_surrogate_config, rbm_surrogate_train, rbm_surrogate_stats,
     rbm_surrogate_params, rbm_surrogate_set_params, rbm_surrogate_forces, rbm_surrogate_gradient,
+    rbm_rbmr_sets, rbm_rbmr_info,
     N_SURROGATE_PARAMS,
 )
 
@@ -182,6 +183,18 @@ class System:
 
     def launches_per_step(self, method="rbm"):
         return rbm_launches_per_step(self.ctx, method)
+
+    # RBM-r (Algorithm "fullyrandom"): run(steps, "rbmr")
+    def rbmr_info(self):
+        return rbm_rbmr_info(self.ctx)
+
+    def rbmr_sets(self, m):
+        import torch
+
+        k = rbm_rbmr_info(self.ctx)["iterations_per_step"]
+        sets = torch.empty(k, self.params.p, dtype=torch.int32, device=self.x.device)
+        rbm_rbmr_sets(self.ctx, m, sets)
+        return sets
 
     # learned mean-field surrogate (d = 2, FP32)
     def surrogate_config(self, **kw):

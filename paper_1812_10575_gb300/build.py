@@ -29,6 +29,7 @@ UNITS = [
     ("coop_step.cu", []),
     ("batched.cu", []),
     ("surrogate.cu", []),
+    ("rbmr.cu", []),
 ]
 
 

@@ -35,6 +35,7 @@
 // RBM_ERR_TIMEOUT and the kernel returns.
 #include "rbm_batch.cuh"
 #include "rbm_device.cuh"
+#include "rbm_grid.cuh"
 #include "rbm_internal.h"
 
 namespace rbm {
@@ -60,61 +61,10 @@ struct CoopArgs {
   int64_t* m_bump;             // graph replay: step counter block 0 advances once every block has read it
 };
 
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ unsigned long long atom_add_acq_rel_gpu(unsigned long long* p, unsigned long long v) {
-  unsigned long long old;
-  asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
-  return old;
-}
-
-// Grid-wide barrier over all (co-resident) blocks on a monotonic arrival
-// counter: the G arrivals of one barrier occupy counter values [t - G, t),
-// t a multiple of G, so each block's thread 0 arrives with an acquire-release
-// add and polls (acquire) until the counter reaches the next multiple of G.
-// Returns false when the wait ran out (RBM_ERR_TIMEOUT latched) or this block
-// was told to leave.
+// Grid barrier of this kernel (rbm_grid.cuh), with the test hook that lets
+// block 0 leave without arriving.
 __device__ bool grid_barrier(const CoopArgs& ca, int32_t* status, bool leave) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    if (leave) {
-      ok = 0;
-    } else {
-      const unsigned long long g = gridDim.x;
-      const unsigned long long old = atom_add_acq_rel_gpu(ca.bar, 1ull);
-      const unsigned long long target = (old / g + 1ull) * g;
-      if (old + 1ull != target) {
-        const unsigned long long t0 = global_ns();
-        // The iteration bound holds even if the timer were not advancing.
-        const unsigned long long max_iter = ca.wait_ns / 8 + 4096;
-        unsigned long long iter = 0;
-        while (ld_acquire_gpu(ca.bar) < target) {
-          ++iter;
-          if (iter > 2048) __nanosleep(32);
-          if (iter >= max_iter || ((iter & 63u) == 0 && global_ns() - t0 > ca.wait_ns)) {
-            ok = 0;
-            latch_status(status, RBM_ERR_TIMEOUT);
-            break;
-          }
-        }
-      }
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
+  return ::rbm::grid_barrier(ca.bar, ca.wait_ns, status, leave);
 }
 
 // Exclusive scan of a[0, len) in shared memory by the whole block.

@@ -51,8 +51,9 @@ struct rbm_ctx {
   rbm_tuning tuning{};
   int32_t latched = RBM_OK;     // host copy of a device error
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  int64_t graph_len[2] = {0, 0};
+  cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};  // by method (surrogate: sur_graph)
+  int64_t graph_len[4] = {0, 0, 0, 0};
+  RbmrScratch rs;                // RBM-r scratch, allocated on first use
 };
 
 namespace {
@@ -108,6 +109,12 @@ void free_scratch(rbm_ctx* c) {
     c->bs.threads = threads;
     c->bs.bucket_target = target;
   }
+  {
+    RbmrScratch& rs = c->rs;
+    cudaFree(rs.set); cudaFree(rs.cnt); cudaFree(rs.start); cudaFree(rs.occ); cudaFree(rs.next);
+    cudaFree(rs.flag); cudaFree(rs.btot); cudaFree(rs.remaining); cudaFree(rs.rounds); cudaFree(rs.bar);
+    rs = RbmrScratch{};
+  }
   cudaFree(c->xtmp);
   c->xtmp = nullptr;
   cudaFree(c->partial);
@@ -116,7 +123,7 @@ void free_scratch(rbm_ctx* c) {
 }
 
 void drop_graphs(rbm_ctx* c) {
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < 4; ++i) {
     if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
     c->graph[i] = nullptr;
     c->graph_len[i] = 0;
@@ -314,8 +321,59 @@ rbm_status enqueue_direct(rbm_ctx* c, int mode, const int64_t* m_ptr, int64_t m_
 rbm_status enqueue_surrogate_step(rbm_ctx* c, const int64_t* m_ptr, int64_t m_off, cudaStream_t st);
 rbm_status enqueue_train_round(rbm_ctx* c, int32_t iters, int32_t round, cudaStream_t st);
 
+// RBM-r scratch for this context (once; not during graph capture).
+rbm_status ensure_rbmr(rbm_ctx* c) {
+  if (c->rs.set) return RBM_OK;
+  if (c->batched) return RBM_ERR_UNSUPPORTED;
+  if (c->prm.p > 32 || c->prm.scheme != RBM_SCHEME_EULER) return RBM_ERR_UNSUPPORTED;
+  int nb = 0;
+  cudaError_t e = rbmr_blocks_per_sm(c->prm.dtype, c->prm.d, &nb);
+  if (e != cudaSuccess || nb < 1) {
+    set_error("rbmr_blocks_per_sm", e == cudaSuccess ? cudaErrorInvalidConfiguration : e);
+    return RBM_ERR_CUDA;
+  }
+  RbmrScratch& rs = c->rs;
+  const uint64_t n = static_cast<uint64_t>(c->prm.n), p = static_cast<uint64_t>(c->prm.p);
+  const uint64_t K = std::max<uint64_t>(1, n / p);
+  rs.K = static_cast<uint32_t>(K);
+  rs.grid = static_cast<uint32_t>(c->cfg.num_sms);
+  RBM_CUDA(cudaMalloc(&rs.set, sizeof(uint32_t) * K * p));
+  RBM_CUDA(cudaMalloc(&rs.cnt, sizeof(uint32_t) * n));
+  RBM_CUDA(cudaMemset(rs.cnt, 0, sizeof(uint32_t) * n));
+  RBM_CUDA(cudaMalloc(&rs.start, sizeof(uint32_t) * (n + 1)));
+  RBM_CUDA(cudaMalloc(&rs.occ, sizeof(uint32_t) * K * p));
+  RBM_CUDA(cudaMalloc(&rs.next, sizeof(uint32_t) * n));
+  RBM_CUDA(cudaMalloc(&rs.flag, K));
+  RBM_CUDA(cudaMalloc(&rs.btot, sizeof(uint32_t) * rs.grid));
+  RBM_CUDA(cudaMalloc(&rs.remaining, sizeof(uint32_t)));
+  RBM_CUDA(cudaMalloc(&rs.rounds, sizeof(uint32_t)));
+  RBM_CUDA(cudaMemset(rs.rounds, 0, sizeof(uint32_t)));
+  RBM_CUDA(cudaMalloc(&rs.bar, sizeof(unsigned long long)));
+  RBM_CUDA(cudaMemset(rs.bar, 0, sizeof(unsigned long long)));
+  return RBM_OK;
+}
+
+rbm_status enqueue_rbmr(rbm_ctx* c, const int64_t* m_ptr, int64_t m_off, cudaStream_t st) {
+  const uint64_t wait_ns = 1000ull * static_cast<uint64_t>(c->tuning.wait_limit_us > 0 ? c->tuning.wait_limit_us
+                                                                                        : 1000000);
+  cudaError_t e;
+  if (c->prm.dtype == RBM_F32) {
+    StepParams<float> a = step_params<float>(c, m_ptr, m_off);
+    e = launch_rbmr<float>(c->rs, c->prm.d, &a, wait_ns, c->cfg, st);
+  } else {
+    StepParams<double> a = step_params<double>(c, m_ptr, m_off);
+    e = launch_rbmr<double>(c->rs, c->prm.d, &a, wait_ns, c->cfg, st);
+  }
+  if (e != cudaSuccess) {
+    set_error("cudaLaunchKernelEx (RBM-r)", e);
+    return RBM_ERR_CUDA;
+  }
+  return RBM_OK;
+}
+
 rbm_status enqueue_step(rbm_ctx* c, int32_t method, const int64_t* m_ptr, int64_t m_off, cudaStream_t st) {
   if (method == RBM_METHOD_RBM) return enqueue_rbm(c, 1, m_ptr, m_off, nullptr, st);
+  if (method == RBM_METHOD_RBMR) return enqueue_rbmr(c, m_ptr, m_off, st);
   if (method == RBM_METHOD_SURROGATE) return enqueue_surrogate_step(c, m_ptr, m_off, st);
   return enqueue_direct(c, 0, m_ptr, m_off, nullptr, 0, nullptr, st);
 }
@@ -606,9 +664,14 @@ rbm_status rbm_direct_step(rbm_ctx* ctx) {
 rbm_status rbm_run(rbm_ctx* ctx, int64_t steps, int32_t method) {
   rbm_status st = usable(ctx);
   if (st != RBM_OK) return st;
-  if (steps < 0 || (method != RBM_METHOD_RBM && method != RBM_METHOD_DIRECT && method != RBM_METHOD_SURROGATE))
+  if (steps < 0 || (method != RBM_METHOD_RBM && method != RBM_METHOD_DIRECT && method != RBM_METHOD_SURROGATE &&
+                     method != RBM_METHOD_RBMR))
     return RBM_ERR_INVALID;
   if (ctx->batched && method != RBM_METHOD_RBM) return RBM_ERR_UNSUPPORTED;
+  if (method == RBM_METHOD_RBMR) {
+    st = ensure_rbmr(ctx);
+    if (st != RBM_OK) return st;
+  }
   if (method == RBM_METHOD_SURROGATE) {
     if (!ctx->sur_on) return RBM_ERR_STATE;
     while (steps > 0) {
@@ -673,9 +736,14 @@ rbm_status rbm_sync(rbm_ctx* ctx) {
 rbm_status rbm_step_host(rbm_ctx* ctx, void* x_host, int32_t method) {
   rbm_status st = usable(ctx);
   if (st != RBM_OK) return st;
-  if (!x_host || (method != RBM_METHOD_RBM && method != RBM_METHOD_DIRECT && method != RBM_METHOD_SURROGATE))
+  if (!x_host || (method != RBM_METHOD_RBM && method != RBM_METHOD_DIRECT && method != RBM_METHOD_SURROGATE &&
+                  method != RBM_METHOD_RBMR))
     return RBM_ERR_INVALID;
   if (method == RBM_METHOD_SURROGATE && !ctx->sur_on) return RBM_ERR_STATE;
+  if (method == RBM_METHOD_RBMR) {
+    st = ensure_rbmr(ctx);
+    if (st != RBM_OK) return st;
+  }
   const size_t bytes = ctx->row_bytes * static_cast<size_t>(ctx->prm.n);
   RBM_CUDA(cudaMemcpyAsync(ctx->x, x_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
   st = enqueue_step(ctx, method, nullptr, ctx->m, ctx->stream);
@@ -794,9 +862,14 @@ rbm_status rbm_step_profiled(rbm_ctx* ctx, int32_t method, float* kernel_ms, int
   rbm_status st = usable(ctx);
   if (st != RBM_OK) return st;
   if (!kernel_ms || !nkernels || capacity < 1 ||
-      (method != RBM_METHOD_RBM && method != RBM_METHOD_DIRECT && method != RBM_METHOD_SURROGATE))
+      (method != RBM_METHOD_RBM && method != RBM_METHOD_DIRECT && method != RBM_METHOD_SURROGATE &&
+       method != RBM_METHOD_RBMR))
     return RBM_ERR_INVALID;
   if (method == RBM_METHOD_SURROGATE && !ctx->sur_on) return RBM_ERR_STATE;
+  if (method == RBM_METHOD_RBMR) {
+    st = ensure_rbmr(ctx);
+    if (st != RBM_OK) return st;
+  }
   constexpr int kMax = 16;
   cudaEvent_t ev[kMax + 1];
   const char* nm[kMax + 1] = {};
@@ -1197,6 +1270,34 @@ rbm_status rbm_surrogate_gradient(rbm_ctx* ctx, const void* x_dev, const void* f
   return rbm_sync(ctx);
 }
 
+rbm_status rbm_rbmr_sets(rbm_ctx* ctx, int64_t m, uint32_t* sets_dev) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (!sets_dev || m < 0) return RBM_ERR_INVALID;
+  st = ensure_rbmr(ctx);
+  if (st != RBM_OK) return st;
+  cudaError_t e = launch_rbmr_sets(sets_dev, ctx->rs.K, static_cast<uint32_t>(ctx->prm.n), ctx->prm.p,
+                                   static_cast<uint32_t>(ctx->prm.replica), ctx->prm.seed, m, ctx->stream);
+  if (e != cudaSuccess) {
+    set_error("k_rbmr_sets", e);
+    return RBM_ERR_CUDA;
+  }
+  return RBM_OK;
+}
+
+rbm_status rbm_rbmr_info(rbm_ctx* ctx, int64_t* iterations_per_step, int32_t* rounds_last) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  st = ensure_rbmr(ctx);
+  if (st != RBM_OK) return st;
+  RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+  uint32_t rounds = 0;
+  RBM_CUDA(cudaMemcpy(&rounds, ctx->rs.rounds, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  if (iterations_per_step) *iterations_per_step = ctx->rs.K;
+  if (rounds_last) *rounds_last = static_cast<int32_t>(rounds);
+  return RBM_OK;
+}
+
 rbm_status rbm_launches_per_step(const rbm_ctx* ctx, int32_t method, int32_t* launches) {
   if (!ctx || !launches) return RBM_ERR_INVALID;
   if (method == RBM_METHOD_RBM)
@@ -1204,6 +1305,7 @@ rbm_status rbm_launches_per_step(const rbm_ctx* ctx, int32_t method, int32_t* la
   else if (method == RBM_METHOD_DIRECT) *launches = 2;  // upper bound: sum (+ chunk reduction)
   else if (method == RBM_METHOD_SURROGATE)
     *launches = 1 + (ctx->use_coop ? 1 : 1 + rbm_tail_launches(ctx->ps, ctx->prm.p));
+  else if (method == RBM_METHOD_RBMR) *launches = 1;
   else return RBM_ERR_INVALID;
   return RBM_OK;
 }

@@ -282,18 +282,12 @@ __device__ __forceinline__ void latch_status(int32_t* status, int32_t code) {
 
 template <typename T> __device__ __forceinline__ bool finite_val(T v) { return isfinite(v); }
 
-// y = x + dt (fk - grad V(x)) + sigma sqrt(dt) z, then the optional projection
-// onto the unit sphere; latches RBM_ERR_NONFINITE on a non-finite result.
+// y = x + dt (fk - grad V(x)) + sigma sqrt(dt) z for given increments z, then
+// the optional projection onto the unit sphere; latches RBM_ERR_NONFINITE on a
+// non-finite result.
 template <typename T, int D>
-__device__ __forceinline__ void euler_update(const StepParams<T>& a, uint32_t id, uint32_t m32, const T (&x)[D],
-                                             const T (&fk)[D], T (&y)[D]) {
-  T z[D];
-  if (a.sq != T(0)) {
-    brownian<T, D>(id, m32, a.replica, a.seed, z);
-  } else {
-#pragma unroll
-    for (int k = 0; k < D; ++k) z[k] = T(0);
-  }
+__device__ __forceinline__ void euler_apply(const StepParams<T>& a, const T (&x)[D], const T (&fk)[D],
+                                            const T (&z)[D], T (&y)[D]) {
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     const T fv = (a.vkind == RBM_V_QUADRATIC) ? -a.vcoef * x[k] : T(0);
@@ -311,6 +305,21 @@ __device__ __forceinline__ void euler_update(const StepParams<T>& a, uint32_t id
 #pragma unroll
   for (int k = 0; k < D; ++k) ok = ok && finite_val(y[k]);
   if (!ok) latch_status(a.status, RBM_ERR_NONFINITE);
+}
+
+// The Euler-Maruyama update of particle `id` at step m with its Brownian
+// increment (id, m) (synchronous coupling of RBM-1 and the direct step).
+template <typename T, int D>
+__device__ __forceinline__ void euler_update(const StepParams<T>& a, uint32_t id, uint32_t m32, const T (&x)[D],
+                                             const T (&fk)[D], T (&y)[D]) {
+  T z[D];
+  if (a.sq != T(0)) {
+    brownian<T, D>(id, m32, a.replica, a.seed, z);
+  } else {
+#pragma unroll
+    for (int k = 0; k < D; ++k) z[k] = T(0);
+  }
+  euler_apply<T, D>(a, x, fk, z, y);
 }
 
 }  // namespace rbm

@@ -48,6 +48,22 @@ struct BatchedScratch {
   int bucket_target = 1024;
 };
 
+// RBM-r scratch (rbmr.cu); all device pointers.
+struct RbmrScratch {
+  uint32_t* set = nullptr;        // [K p]
+  uint32_t* cnt = nullptr;        // [N] zero between steps
+  uint32_t* start = nullptr;      // [N + 1]
+  uint32_t* occ = nullptr;        // [K p]
+  uint32_t* next = nullptr;       // [N]
+  uint8_t* flag = nullptr;        // [K]
+  uint32_t* btot = nullptr;       // [grid]
+  uint32_t* remaining = nullptr;  // [1]
+  uint32_t* rounds = nullptr;     // [1]
+  unsigned long long* bar = nullptr;  // [1] grid barrier counter
+  uint32_t K = 0;                 // iterations per step
+  uint32_t grid = 0;              // blocks (one per SM)
+};
+
 // Surrogate-network state (surrogate.cu); all device pointers.
 struct SurrogateScratch {
   float* theta = nullptr;
@@ -142,5 +158,14 @@ cudaError_t sur_step(const SurrogateScratch& ss, const void* params, const Launc
 template <typename T>
 void launch_direct(int d, int mode, const void* params, const T* q, uint32_t nq, void* partial, size_t partial_rows,
                    const LaunchCfg& cfg, cudaStream_t st);
+
+// RBM-r (rbmr.cu).
+int rbmr_threads();
+cudaError_t rbmr_blocks_per_sm(int dtype, int d, int* nb);
+template <typename T>
+cudaError_t launch_rbmr(const RbmrScratch& rs, int d, const void* params, uint64_t wait_ns, const LaunchCfg& cfg,
+                        cudaStream_t st);
+cudaError_t launch_rbmr_sets(uint32_t* set, uint32_t K, uint32_t n, int p, uint32_t replica, uint64_t seed,
+                             int64_t m, cudaStream_t st);
 
 }  // namespace rbm
