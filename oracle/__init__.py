@@ -102,6 +102,8 @@ def lib() -> ctypes.CDLL:
             L.orc_rbm_split_step.argtypes = [P, dp, ctypes.c_int64]
             L.orc_split_pair_solve.argtypes = [P, dp, dp, dp, dp]
             L.orc_direct_step.argtypes = [P, dp, ctypes.c_int64]
+            L.orc_rbm_verlet_step.argtypes = [P, dp, dp, ctypes.c_int64, ctypes.c_int]
+            L.orc_direct_verlet_step.argtypes = [P, dp, dp, ctypes.c_int]
             L.orc_rbmr_iterations_per_step.argtypes = [P]
             L.orc_rbmr_iterations_per_step.restype = ctypes.c_int64
             L.orc_rbmr_set.argtypes = [P, ctypes.c_int64, u32p]
@@ -243,6 +245,22 @@ def direct_step(prm: OrcParams, X, m: int) -> np.ndarray:
     Y = _x(X, prm).copy()
     lib().orc_direct_step(ctypes.byref(prm), _ptr(Y, ctypes.c_double), int(m))
     return Y
+
+
+def verlet_run(prm: OrcParams, X0, V0, m0: int, steps: int, method: str = "rbm"):
+    """Verlet scheme of the second-order system (Appendix A, Sec. 4.1):
+    ``steps`` steps from positions X0 and velocities V0 at step index m0 (the
+    first step is the Taylor start); returns (X_n, X_{n-1})."""
+    X = _x(X0, prm).copy()
+    P = _x(V0, prm).copy()
+    for s in range(steps):
+        if method == "rbm":
+            lib().orc_rbm_verlet_step(ctypes.byref(prm), _ptr(X, ctypes.c_double), _ptr(P, ctypes.c_double),
+                                      int(m0 + s), int(s == 0))
+        else:
+            lib().orc_direct_verlet_step(ctypes.byref(prm), _ptr(X, ctypes.c_double), _ptr(P, ctypes.c_double),
+                                         int(s == 0))
+    return X, P
 
 
 def rbmr_iterations_per_step(prm: OrcParams) -> int:

@@ -389,6 +389,55 @@ void orc_direct_step(const orc_params *prm, double *X, int64_t m)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Second-order (Hamiltonian) system of Appendix A, eq. "Hamil1":            */
+/*   dX/dt = V,  dV/dt = b(X) + 1/(N-1) sum_j K(X^i - X^j),  b = -grad V,    */
+/* integrated by the Verlet scheme of Sec. 4.1 (end):                         */
+/*   X_1 = X_0 + tau V_0 + tau^2 F_0 / 2,                                    */
+/*   X_{n+1} = 2 X_n - X_{n-1} + tau^2 F_n,  n >= 1,                          */
+/* F_n = b(X_n) + the interaction of step n: the in-batch sum of RBM-1        */
+/* (eq. "Hamilrand", the random division of step n) or the full sum.          */
+/* P holds V_0 before the first step (first = 1) and X_{n-1} afterwards; the */
+/* step writes X_{n+1} to X and X_n to P.  No noise.                          */
+/* ------------------------------------------------------------------------ */
+static void orc_verlet_update(const orc_params *prm, double *X, double *P, const double *FK, int first)
+{
+    int d = prm->d;
+    double tau = prm->dt;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < prm->n; ++i) {
+        double fv[3];
+        orc_confining(prm, X + i * d, fv);
+        for (int k = 0; k < d; ++k) {
+            double x = X[i * d + k], q = P[i * d + k], f = FK[i * d + k] + fv[k];
+            double y = first ? x + tau * q + 0.5 * tau * tau * f : 2.0 * x - q + tau * tau * f;
+            P[i * d + k] = x;
+            X[i * d + k] = y;
+        }
+    }
+}
+
+void orc_rbm_verlet_step(const orc_params *prm, double *X, double *P, int64_t m, int first)
+{
+    size_t nd = (size_t)prm->n * (size_t)prm->d;
+    uint32_t *perm = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)prm->n);
+    double *FK = (double *)malloc(sizeof(double) * nd);
+    orc_permutation(prm, m, perm);
+    orc_rbm_interaction(prm, X, perm, FK);
+    orc_verlet_update(prm, X, P, FK, first);
+    free(FK);
+    free(perm);
+}
+
+void orc_direct_verlet_step(const orc_params *prm, double *X, double *P, int first)
+{
+    size_t nd = (size_t)prm->n * (size_t)prm->d;
+    double *FK = (double *)malloc(sizeof(double) * nd);
+    orc_direct_interaction(prm, X, FK);
+    orc_verlet_update(prm, X, P, FK, first);
+    free(FK);
+}
+
+/* ------------------------------------------------------------------------ */
 /* RBM-r (Sec. 2.2, Algorithm "fullyrandom"): iteration k picks a set C of p  */
 /* distinct particles at random and moves its members by one Euler-Maruyama   */
 /* step of size tau of the p-particle system of eq. "secondalgB", every force */

@@ -59,6 +59,8 @@ void orc_direct_step(const orc_params *prm, double *X, int64_t m);
 void orc_direct_step_sampled(const orc_params *prm, const double *X, int64_t m, const int64_t *idx, int64_t nidx,
                              double *Y);
 void orc_direct_forces_at(const orc_params *prm, const double *X, const double *Q, int64_t nq, double *F);
+void orc_rbm_verlet_step(const orc_params *prm, double *X, double *P, int64_t m, int first);
+void orc_direct_verlet_step(const orc_params *prm, double *X, double *P, int first);
 int64_t orc_rbmr_iterations_per_step(const orc_params *prm);
 void orc_rbmr_set(const orc_params *prm, int64_t k, uint32_t *set);
 void orc_rbmr_iteration(const orc_params *prm, double *X, int64_t k);
