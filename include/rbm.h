@@ -96,11 +96,19 @@ typedef enum {
 /* Time scheme of the RBM step. */
 typedef enum {
     RBM_SCHEME_EULER = 0, /* explicit Euler-Maruyama of eq. "firstalgorithm" */
-    RBM_SCHEME_SPLIT = 1  /* splitting, Sec. 2.3 item 5: the p = 2 pair flow of
+    RBM_SCHEME_SPLIT = 1, /* splitting, Sec. 2.3 item 5: the p = 2 pair flow of
                              K solved exactly (K = 1/x: |delta|^2 += 4 dt;
                              K = x/|x|^3: |delta|^3 += 6 dt, Secs. 4.2, 5.1),
                              then Euler-Maruyama for -grad V and the noise.
                              Requires p = 2 and K = INV1D or COULOMB.      */
+    RBM_SCHEME_VERLET = 2 /* the second-order system of Appendix A (eq.
+                             "Hamil1": dX = V dt, dV = (-grad V + interaction)
+                             dt) by the Verlet scheme of Sec. 4.1: X_1 = X_0 +
+                             dt V_0 + dt^2 F_0 / 2, X_{n+1} = 2 X_n - X_{n-1}
+                             + dt^2 F_n, F_n from the RBM-1 batches of step n
+                             (eq. "Hamilrand") or the full sum.  Requires
+                             sigma = 0, no projection, p <= 32, and
+                             rbm_verlet_set_velocity before the first step. */
 } rbm_scheme;
 
 #define RBM_FLAG_RENORM_SPHERE 1u /* X^i <- X^i/|X^i| after each step (Sec. 5.1) */
@@ -184,6 +192,15 @@ const char *rbm_status_string(int32_t status);
 /* Text of the last CUDA runtime failure seen by the calling thread (the call
  * and the runtime's message), or "" if none.  Thread-local, static storage. */
 const char *rbm_last_error(void);
+
+/* ---- second-order system (RBM_SCHEME_VERLET) --------------------------- */
+/* Velocities V_0 (N x ld, run dtype, device, copied) at the current step m:
+ * the next step (rbm_step, rbm_direct_step, rbm_run) is the Taylor start,
+ * the ones after it the two-step recurrence (the Taylor start is the step
+ * whose index equals the current m modulo 2^32).  The context keeps X_{n-1}
+ * in a buffer of its own.  Synchronous.  RBM_ERR_STATE when the scheme is not
+ * Verlet. */
+rbm_status rbm_verlet_set_velocity(rbm_ctx *ctx, const void *v_dev);
 
 /* ---- RBM-r (Sec. 2.2, Algorithm "fullyrandom") --------------------------- */
 /* One step of RBM_METHOD_RBMR (rbm_run, rbm_step_host, rbm_step_profiled) is

@@ -20,7 +20,7 @@ from ._lib import (  # noqa: F401
     rbm_status_string, rbm_step, rbm_step_host, rbm_step_profiled, rbm_sync, rbm_batched_init,
     rbm_batched_set_launch, rbm_autotune, rbm_surrogate_config, rbm_surrogate_train, rbm_surrogate_stats,
     rbm_surrogate_params, rbm_surrogate_set_params, rbm_surrogate_forces, rbm_surrogate_gradient,
-    rbm_rbmr_sets, rbm_rbmr_info,
+    rbm_rbmr_sets, rbm_rbmr_info, rbm_verlet_set_velocity,
     N_SURROGATE_PARAMS,
 )
 
@@ -183,6 +183,12 @@ class System:
 
     def launches_per_step(self, method="rbm"):
         return rbm_launches_per_step(self.ctx, method)
+
+    # second-order system, scheme="verlet": velocities before the first step
+    def verlet_set_velocity(self, v):
+        if v.shape != self.x.shape or v.dtype != self.x.dtype or not v.is_contiguous():
+            raise ValueError("velocities must match the positions' shape, dtype and layout")
+        rbm_verlet_set_velocity(self.ctx, v)
 
     # RBM-r (Algorithm "fullyrandom"): run(steps, "rbmr")
     def rbmr_info(self):

@@ -32,8 +32,8 @@ KERNELS = {"inv1d": 0, "coulomb": 1, "bounded_conf": 2, "gauss_agg": 3, "reg_att
 POTENTIALS = {"zero": 0, "quadratic": 1}
 RBM_METHOD_RBM, RBM_METHOD_DIRECT = 0, 1
 METHODS = {"rbm": 0, "direct": 1, "surrogate": 2, "rbmr": 3}
-RBM_SCHEME_EULER, RBM_SCHEME_SPLIT = 0, 1
-SCHEMES = {"euler": 0, "split": 1}
+RBM_SCHEME_EULER, RBM_SCHEME_SPLIT, RBM_SCHEME_VERLET = 0, 1, 2
+SCHEMES = {"euler": 0, "split": 1, "verlet": 2}
 RBM_FLAG_RENORM_SPHERE = 1
 
 # Every symbol include/rbm.h declares.
@@ -44,7 +44,7 @@ EXPORTS = (
     "rbm_permutation_noalloc", "rbm_batched_init", "rbm_batched_set_launch", "rbm_autotune",
     "rbm_surrogate_config", "rbm_surrogate_train", "rbm_surrogate_stats", "rbm_surrogate_params",
     "rbm_surrogate_set_params", "rbm_surrogate_forces", "rbm_surrogate_gradient",
-    "rbm_rbmr_sets", "rbm_rbmr_info",
+    "rbm_rbmr_sets", "rbm_rbmr_info", "rbm_verlet_set_velocity",
 )
 N_SURROGATE_PARAMS = 4482
 
@@ -124,6 +124,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "rbm_direct_forces_at": [vp, vp, i64, vp],
         "rbm_launches_per_step": [vp, i32, ctypes.POINTER(i32)],
         "rbm_rbmr_sets": [vp, i64, vp],
+        "rbm_verlet_set_velocity": [vp, vp],
         "rbm_rbmr_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)],
         "rbm_permutation_noalloc": [i64, ctypes.c_uint64, ctypes.c_uint32, i64, vp, vp],
         "rbm_batched_init": [P, i32, ctypes.POINTER(i64), vp, vp, ctypes.POINTER(vp)],
@@ -372,6 +373,12 @@ def rbm_permutation_noalloc(n: int, seed: int, replica: int, m: int, perm, strea
 def rbm_rbmr_sets(ctx, m, sets) -> None:
     """RBM-r sets of step ``m`` into ``sets`` (a CUDA int32 tensor of K x p)."""
     _check(load().rbm_rbmr_sets(ctx, int(m), ctypes.c_void_p(int(sets.data_ptr()))), "rbm_rbmr_sets")
+
+
+def rbm_verlet_set_velocity(ctx, v) -> None:
+    """Velocities V_0 (a CUDA tensor shaped like the positions) for the
+    Verlet scheme; the next step is the Taylor start."""
+    _check(load().rbm_verlet_set_velocity(ctx, ctypes.c_void_p(int(v.data_ptr()))), "rbm_verlet_set_velocity")
 
 
 def rbm_rbmr_info(ctx) -> dict:

@@ -110,7 +110,7 @@ __device__ __forceinline__ void finish_target(const StepParams<T>& a, uint32_t i
   }
   const uint32_t m32 = step_index(a);
   T y[D];
-  euler_update<T, D>(a, i, m32, ri.x, fk, y);
+  scheme_update<T, D>(a, i, m32, ri.x, fk, y);
   Row<T, D> out = ri;
 #pragma unroll
   for (int k = 0; k < D; ++k) out.x[k] = y[k];

@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(256) k_batch_generic(PermArgs pa, StepParams<T
       store_row<T, D>(a.fout, id, f);
     } else {
       T y[D];
-      euler_update<T, D>(a, id, m32, r.x, fk, y);
+      scheme_update<T, D>(a, id, m32, r.x, fk, y);
 #pragma unroll
       for (int k = 0; k < D; ++k) r.x[k] = y[k];
       store_row<T, D>(a.xout, lo + e, r);

@@ -27,6 +27,8 @@ struct rbm_ctx {
   int32_t* status = nullptr;    // device
   int64_t* m_dev = nullptr;     // device step counter read by graph replays
   void* xtmp = nullptr;         // second position buffer (direct step, generic batches)
+  void* xprev = nullptr;        // Verlet: V_0 before the first step, X_{n-1} afterwards
+  int64_t verlet_m0 = -1;       // Verlet: step index of the Taylor start
   void* partial = nullptr;      // direct-sum partial forces, partial_rows rows
   size_t partial_rows = 0;
   PermScratch ps;
@@ -88,7 +90,11 @@ rbm_status check_params(const rbm_params* p) {
   if (p->k == RBM_K_INV1D && p->d != 1) return RBM_ERR_INVALID;
   if (!std::isfinite(p->v_coef) || !std::isfinite(p->k_param)) return RBM_ERR_INVALID;
   if (p->flags & ~RBM_FLAG_RENORM_SPHERE) return RBM_ERR_INVALID;
-  if (p->scheme != RBM_SCHEME_EULER && p->scheme != RBM_SCHEME_SPLIT) return RBM_ERR_INVALID;
+  if (p->scheme != RBM_SCHEME_EULER && p->scheme != RBM_SCHEME_SPLIT && p->scheme != RBM_SCHEME_VERLET)
+    return RBM_ERR_INVALID;
+  // the second-order system carries no noise and no projection (Appendix A)
+  if (p->scheme == RBM_SCHEME_VERLET && (p->sigma != 0.0 || (p->flags & RBM_FLAG_RENORM_SPHERE)))
+    return RBM_ERR_INVALID;
   if (p->scheme == RBM_SCHEME_SPLIT && (p->p != 2 || (p->k != RBM_K_INV1D && p->k != RBM_K_COULOMB)))
     return RBM_ERR_INVALID;
   return RBM_OK;
@@ -224,6 +230,8 @@ StepParams<T> step_params(const rbm_ctx* c, const int64_t* m_ptr, int64_t m_off)
   a.replica = p.replica;
   a.m_ptr = m_ptr;
   a.m_off = m_off;
+  a.xprev = static_cast<T*>(c->xprev);
+  a.verlet_m0 = c->verlet_m0;
   return a;
 }
 
@@ -372,6 +380,7 @@ rbm_status enqueue_rbmr(rbm_ctx* c, const int64_t* m_ptr, int64_t m_off, cudaStr
 }
 
 rbm_status enqueue_step(rbm_ctx* c, int32_t method, const int64_t* m_ptr, int64_t m_off, cudaStream_t st) {
+  if (c->prm.scheme == RBM_SCHEME_VERLET && !c->xprev) return RBM_ERR_STATE;  // no velocities yet
   if (method == RBM_METHOD_RBM) return enqueue_rbm(c, 1, m_ptr, m_off, nullptr, st);
   if (method == RBM_METHOD_RBMR) return enqueue_rbmr(c, m_ptr, m_off, st);
   if (method == RBM_METHOD_SURROGATE) return enqueue_surrogate_step(c, m_ptr, m_off, st);
@@ -816,6 +825,7 @@ rbm_status rbm_free(rbm_ctx* ctx) {
   free_surrogate(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   free_scratch(ctx);
+  cudaFree(ctx->xprev);
   cudaFree(ctx->status);
   cudaFree(ctx->m_dev);
   delete ctx;
@@ -1268,6 +1278,21 @@ rbm_status rbm_surrogate_gradient(rbm_ctx* ctx, const void* x_dev, const void* f
   }
   if (loss_host) *loss_host = loss;
   return rbm_sync(ctx);
+}
+
+rbm_status rbm_verlet_set_velocity(rbm_ctx* ctx, const void* v_dev) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (!v_dev) return RBM_ERR_INVALID;
+  if (ctx->prm.scheme != RBM_SCHEME_VERLET) return RBM_ERR_STATE;
+  const size_t bytes = ctx->row_bytes * static_cast<size_t>(ctx->prm.n);
+  RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (!ctx->xprev) RBM_CUDA(cudaMalloc(&ctx->xprev, bytes));
+  RBM_CUDA(cudaMemcpyAsync(ctx->xprev, v_dev, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  ctx->verlet_m0 = ctx->m;
+  drop_graphs(ctx);  // captured steps hold the index of the Taylor start
+  RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+  return RBM_OK;
 }
 
 rbm_status rbm_rbmr_sets(rbm_ctx* ctx, int64_t m, uint32_t* sets_dev) {

@@ -94,7 +94,7 @@ __device__ __forceinline__ void batch_group_row(const StepParams<T>& a, uint32_t
     return;
   }
   T y[D];
-  euler_update<T, D>(a, id, m32, r.x, fk, y);
+  scheme_update<T, D>(a, id, m32, r.x, fk, y);
 #pragma unroll
   for (int k = 0; k < D; ++k) r.x[k] = y[k];
   store_row<T, D>(a.x, id, r);

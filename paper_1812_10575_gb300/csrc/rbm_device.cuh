@@ -263,6 +263,8 @@ struct StepParams {
   const int64_t* m_ptr;  // step counter in device memory (graph replay) or null
   int64_t m_off;         // added to *m_ptr (or the step itself when m_ptr is null)
   const int* skip;       // when set and non-zero, the RBM step kernels do nothing (surrogate mode)
+  T* xprev;              // Verlet: V_0 before the first step, X_{n-1} afterwards (N x ld)
+  int64_t verlet_m0;     // Verlet: the step index of the Taylor start
 };
 
 template <typename T>
@@ -307,6 +309,33 @@ __device__ __forceinline__ void euler_apply(const StepParams<T>& a, const T (&x)
   if (!ok) latch_status(a.status, RBM_ERR_NONFINITE);
 }
 
+// Verlet scheme of the second-order system (Appendix A, Sec. 4.1): with
+// F = fk - grad V(x), y = x + dt v + dt^2 F / 2 at the first step (xprev
+// holds v = V_0) and y = 2 x - x_prev + dt^2 F afterwards; x becomes the new
+// x_prev.  m32 is the step index the kernel read when it started (a graph
+// replay advances the device counter during the step); the Taylor start is
+// the step whose index agrees with verlet_m0 mod 2^32.  Latches
+// RBM_ERR_NONFINITE on a non-finite result.
+template <typename T, int D>
+__device__ __forceinline__ void verlet_update(const StepParams<T>& a, uint32_t id, uint32_t m32, const T (&x)[D],
+                                              const T (&fk)[D], T (&y)[D]) {
+  const bool first = (m32 == static_cast<uint32_t>(static_cast<uint64_t>(a.verlet_m0)));
+  const T* q = a.xprev + static_cast<uint64_t>(id) * Ld<D>::value;
+  T* w = a.xprev + static_cast<uint64_t>(id) * Ld<D>::value;
+  const T tt = a.dt * a.dt;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const T fv = (a.vkind == RBM_V_QUADRATIC) ? -a.vcoef * x[k] : T(0);
+    const T f = fk[k] + fv;
+    const T pk = q[k];
+    y[k] = first ? x[k] + a.dt * pk + T(0.5) * tt * f : T(2) * x[k] - pk + tt * f;
+    w[k] = x[k];
+    ok = ok && finite_val(y[k]);
+  }
+  if (!ok) latch_status(a.status, RBM_ERR_NONFINITE);
+}
+
 // The Euler-Maruyama update of particle `id` at step m with its Brownian
 // increment (id, m) (synchronous coupling of RBM-1 and the direct step).
 template <typename T, int D>
@@ -320,6 +349,14 @@ __device__ __forceinline__ void euler_update(const StepParams<T>& a, uint32_t id
     for (int k = 0; k < D; ++k) z[k] = T(0);
   }
   euler_apply<T, D>(a, x, fk, z, y);
+}
+
+// The update of the configured scheme after the interaction force fk.
+template <typename T, int D>
+__device__ __forceinline__ void scheme_update(const StepParams<T>& a, uint32_t id, uint32_t m32, const T (&x)[D],
+                                              const T (&fk)[D], T (&y)[D]) {
+  if (a.scheme == RBM_SCHEME_VERLET) verlet_update<T, D>(a, id, m32, x, fk, y);
+  else euler_update<T, D>(a, id, m32, x, fk, y);
 }
 
 }  // namespace rbm

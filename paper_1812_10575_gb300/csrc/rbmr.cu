@@ -112,30 +112,44 @@ __device__ __forceinline__ void slot_noise(uint64_t k, int s, uint32_t replica, 
 
 // One iteration by one thread: forces of all members from their positions
 // before the iteration (sum over the other slots in slot order), then each
-// member's Euler-Maruyama update.
+// member's Euler-Maruyama update.  PMAX = 4 keeps the members in registers
+// (loops unrolled); PMAX = 32 keeps them in local memory (loops rolled).
 template <typename T, int D, int PMAX>
 __device__ void run_iteration(const StepParams<T>& a, uint64_t k, const uint32_t* set) {
+  constexpr bool kSmall = PMAX <= 4;
   const int p = a.p;
   uint32_t id[PMAX];
   Row<T, D> row[PMAX];
+  if constexpr (kSmall) {
 #pragma unroll
-  for (int s = 0; s < PMAX; ++s) {
-    if (s < p) {
+    for (int s = 0; s < PMAX; ++s) {
+      if (s < p) {
+        id[s] = ldcg(set + s);
+        row[s] = load_row_cg<T, D>(a.x, id[s]);
+      }
+    }
+  } else {
+#pragma unroll 1
+    for (int s = 0; s < p; ++s) {
       id[s] = ldcg(set + s);
       row[s] = load_row_cg<T, D>(a.x, id[s]);
     }
   }
   const T inv = T(1) / static_cast<T>(p - 1);
-#pragma unroll
-  for (int s = 0; s < PMAX; ++s) {
-    if (s >= p) break;
+  auto member = [&](int s) {
     T acc[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) acc[c] = T(0);
+    if constexpr (kSmall) {
 #pragma unroll
-    for (int t = 0; t < PMAX; ++t) {
-      if (t >= p) break;
-      if (t != s) add_pair_force_rt<T, D>(a.kf, a.kparam, a.radius_sq, row[s].x, row[t].x, acc);
+      for (int t = 0; t < PMAX; ++t) {
+        if (t < p && t != s) add_pair_force_rt<T, D>(a.kf, a.kparam, a.radius_sq, row[s].x, row[t].x, acc);
+      }
+    } else {
+#pragma unroll 1
+      for (int t = 0; t < p; ++t) {
+        if (t != s) add_pair_force_rt<T, D>(a.kf, a.kparam, a.radius_sq, row[s].x, row[t].x, acc);
+      }
     }
     T fk[D], z[D], y[D];
 #pragma unroll
@@ -151,6 +165,15 @@ __device__ void run_iteration(const StepParams<T>& a, uint64_t k, const uint32_t
 #pragma unroll
     for (int c = 0; c < D; ++c) out.x[c] = y[c];
     store_row<T, D>(a.x, id[s], out);
+  };
+  if constexpr (kSmall) {
+#pragma unroll
+    for (int s = 0; s < PMAX; ++s) {
+      if (s < p) member(s);
+    }
+  } else {
+#pragma unroll 1
+    for (int s = 0; s < p; ++s) member(s);
   }
 }
 
