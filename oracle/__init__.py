@@ -52,6 +52,7 @@ class OrcParams(ctypes.Structure):
         ("ubits", ctypes.c_int32),
         ("decide_f32", ctypes.c_int32),
         ("replica", ctypes.c_uint32),
+        ("gbm", ctypes.c_int32),
     ]
 
 
@@ -127,7 +128,7 @@ def _ptr(a: np.ndarray, ctype):
 
 
 def make_params(n, d, p=2, dt=1e-3, sigma=0.0, seed=0, v="zero", v_coef=1.0, k="linear",
-                k_param=0.0, renorm=False, precision="f64", replica=0) -> OrcParams:
+                k_param=0.0, renorm=False, precision="f64", replica=0, gbm=False) -> OrcParams:
     """Build an :class:`OrcParams`.
 
     ``precision`` names the precision of the run the oracle is compared with:
@@ -143,7 +144,7 @@ def make_params(n, d, p=2, dt=1e-3, sigma=0.0, seed=0, v="zero", v_coef=1.0, k="
         k_kind=K_KINDS[k] if isinstance(k, str) else int(k),
         v_coef=float(v_coef), k_param=float(k_param), renorm=int(bool(renorm)),
         ubits=53 if precision == "f64" else 24, decide_f32=int(precision == "f32"),
-        replica=int(replica),
+        replica=int(replica), gbm=int(bool(gbm)),
     )
 
 
@@ -223,9 +224,9 @@ def rbm_step(prm: OrcParams, X, m: int) -> np.ndarray:
 
 
 def rbm_split_step(prm: OrcParams, X, m: int) -> np.ndarray:
-    """One RBM-1 step of the splitting scheme (p = 2, K = 1/x or Coulomb)."""
-    if prm.p != 2 or prm.k_kind not in (K_KINDS["inv1d"], K_KINDS["coulomb"]):
-        raise ValueError("the splitting scheme needs p = 2 and K = 1/x or x/|x|^3")
+    """One RBM-1 step of the splitting scheme (p = 2, K = 1/x, Coulomb or -c x)."""
+    if prm.p != 2 or prm.k_kind not in (K_KINDS["inv1d"], K_KINDS["coulomb"], K_KINDS["linear"]):
+        raise ValueError("the splitting scheme needs p = 2 and K = 1/x, x/|x|^3 or -c x")
     Y = _x(X, prm).copy()
     lib().orc_rbm_split_step(ctypes.byref(prm), _ptr(Y, ctypes.c_double), int(m))
     return Y

@@ -279,15 +279,24 @@ void orc_rbm_interaction(const orc_params *prm, const double *X, const uint32_t 
 /*   X'^i = X^i + dt (FK_i - grad V(X^i)) + sigma sqrt(dt) z_i               */
 /*   RENORM: X'^i <- X'^i / |X'^i|                                           */
 /* ------------------------------------------------------------------------ */
+/* With multiplicative noise (gbm = 1, the wealth model of Sec. 5.2, eq.     */
+/* "wealth": sigma X dB) the noise term is sigma sqrt(tau) x z in the Euler-  */
+/* Maruyama step; after the exact pair flow of the splitting scheme the noise */
+/* sub-step is the exact geometric Brownian flow x exp(-sigma^2 tau/2 +       */
+/* sigma sqrt(tau) z) (Ito), which keeps the expected wealth.                 */
 static void orc_euler_update_one(const orc_params *prm, uint32_t id, const double *x, const double *fk, int64_t m,
-                                 double *y)
+                                 double *y, int split_flow)
 {
     int d = prm->d;
     double sq = prm->sigma * sqrt(prm->dt);
     double z[4] = {0.0, 0.0, 0.0, 0.0}, fv[3];
     orc_normals_one(prm, id, m, z);
     orc_confining(prm, x, fv);
-    for (int k = 0; k < d; ++k) y[k] = x[k] + prm->dt * (fk[k] + fv[k]) + sq * z[k];
+    for (int k = 0; k < d; ++k) {
+        if (!prm->gbm)      y[k] = x[k] + prm->dt * (fk[k] + fv[k]) + sq * z[k];
+        else if (split_flow) y[k] = x[k] * exp(-0.5 * sq * sq + sq * z[k]) + prm->dt * (fk[k] + fv[k]);
+        else                y[k] = x[k] + prm->dt * (fk[k] + fv[k]) + sq * x[k] * z[k];
+    }
     if (prm->renorm) {
         double nrm = 0.0;
         for (int k = 0; k < d; ++k) nrm += y[k] * y[k];
@@ -296,15 +305,20 @@ static void orc_euler_update_one(const orc_params *prm, uint32_t id, const doubl
     }
 }
 
-void orc_euler_update(const orc_params *prm, double *X, const double *FK, int64_t m)
+static void orc_update_all(const orc_params *prm, double *X, const double *FK, int64_t m, int split_flow)
 {
     int d = prm->d;
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < prm->n; ++i) {
         double y[3];
-        orc_euler_update_one(prm, (uint32_t)i, X + i * d, FK + i * d, m, y);
+        orc_euler_update_one(prm, (uint32_t)i, X + i * d, FK + i * d, m, y, split_flow);
         for (int k = 0; k < d; ++k) X[i * d + k] = y[k];
     }
+}
+
+void orc_euler_update(const orc_params *prm, double *X, const double *FK, int64_t m)
+{
+    orc_update_all(prm, X, FK, m, 0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -317,6 +331,8 @@ void orc_euler_update(const orc_params *prm, double *X, const double *FK, int64_
 /*     Y^i,j = (X^i + X^j)/2 +- sgn(delta) sqrt(delta^2 + 4 tau) / 2.         */
 /*   K = x/|x|^3: the direction of delta is fixed and d|delta|^3/dt = 6, so   */
 /*     Y^i,j = (X^i + X^j)/2 +- (delta/|delta|) (|delta|^3 + 6 tau)^(1/3) / 2.*/
+/*   K = -c x (the wealth model's quadratic trading, Sec. 5.2): d delta/dt =  */
+/*     -2 c delta, so delta shrinks by exp(-2 c tau) about the fixed mean.    */
 /* (The paper prints both formulas without the factors 1/2; the ODE fixes    */
 /* them.)  A singleton batch and a coincident pair (delta = 0, K(0) = 0) keep */
 /* Y = X.                                                                     */
@@ -335,8 +351,9 @@ void orc_split_pair_solve(const orc_params *prm, const double *xi, const double 
         return;
     }
     double len = sqrt(len2), newlen;
-    if (prm->k_kind == ORC_K_INV1D) newlen = sqrt(len2 + 4.0 * prm->dt);
-    else                            newlen = cbrt(len2 * len + 6.0 * prm->dt);
+    if (prm->k_kind == ORC_K_INV1D)       newlen = sqrt(len2 + 4.0 * prm->dt);
+    else if (prm->k_kind == ORC_K_LINEAR) newlen = len * exp(-2.0 * prm->k_param * prm->dt);
+    else                                  newlen = cbrt(len2 * len + 6.0 * prm->dt);
     for (int k = 0; k < d; ++k) {
         double half = 0.5 * newlen * (delta[k] / len);
         yi[k] = mid[k] + half;
@@ -358,7 +375,7 @@ void orc_rbm_split_step(const orc_params *prm, double *X, int64_t m)
         if (j < i) { uint32_t t = i; i = j; j = t; }   /* smaller id first */
         orc_split_pair_solve(prm, X + (int64_t)i * d, X + (int64_t)j * d, Y + (int64_t)i * d, Y + (int64_t)j * d);
     }
-    orc_euler_update(prm, Y, zero, m);               /* -grad V(Y), noise, renorm */
+    orc_update_all(prm, Y, zero, m, 1);              /* -grad V(Y), noise, renorm */
     memcpy(X, Y, sizeof(double) * (size_t)n * (size_t)d);
     free(zero);
     free(Y);
@@ -558,7 +575,7 @@ void orc_direct_step_sampled(const orc_params *prm, const double *X, int64_t m, 
         double fk[3];
         int64_t i = idx[a];
         orc_direct_interaction_one(prm, X, i, fk);
-        orc_euler_update_one(prm, (uint32_t)i, X + i * d, fk, m, Y + a * d);
+        orc_euler_update_one(prm, (uint32_t)i, X + i * d, fk, m, Y + a * d, 0);
     }
 }
 

@@ -41,6 +41,7 @@ typedef struct {
     int32_t ubits;    /* uniform bits per Box-Muller input: 53 or 24        */
     int32_t decide_f32; /* 1: kernel decisions on the FP32 squared norm     */
     uint32_t replica; /* replica index r (third counter word)               */
+    int32_t gbm;      /* 1: multiplicative noise sigma X dB (wealth model)  */
 } orc_params;
 
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
