@@ -100,7 +100,10 @@ typedef enum {
                              K solved exactly (K = 1/x: |delta|^2 += 4 dt;
                              K = x/|x|^3: |delta|^3 += 6 dt, Secs. 4.2, 5.1),
                              then Euler-Maruyama for -grad V and the noise.
-                             Requires p = 2 and K = INV1D or COULOMB.      */
+                             K = LINEAR (-c x): the gap shrinks by
+                             exp(-2 c dt) about the fixed mean (the wealth
+                             model's exchange, Sec. 5.2).
+                             Requires p = 2 and K = INV1D, COULOMB or LINEAR. */
     RBM_SCHEME_VERLET = 2 /* the second-order system of Appendix A (eq.
                              "Hamil1": dX = V dt, dV = (-grad V + interaction)
                              dt) by the Verlet scheme of Sec. 4.1: X_1 = X_0 +
@@ -112,6 +115,12 @@ typedef enum {
 } rbm_scheme;
 
 #define RBM_FLAG_RENORM_SPHERE 1u /* X^i <- X^i/|X^i| after each step (Sec. 5.1) */
+#define RBM_FLAG_GBM_NOISE 2u     /* multiplicative noise sigma X^i dB^i (the wealth
+                                     model, Sec. 5.2, eq. "wealth"): the Euler-
+                                     Maruyama term becomes sigma sqrt(dt) X z; with
+                                     RBM_SCHEME_SPLIT the noise sub-step is the exact
+                                     geometric flow X exp(-sigma^2 dt/2 + sigma
+                                     sqrt(dt) z)                                    */
 
 typedef struct {
     int64_t n;        /* particles N >= 2                                    */
@@ -213,8 +222,8 @@ rbm_status rbm_verlet_set_velocity(rbm_ctx *ctx, const void *v_dev);
  * replica, 8*256 + 2 s + t), all forces from the positions before the
  * iteration.  The GPU runs disjoint iterations together in rounds that keep
  * every particle's iterations in order, so the result is the sequential one.
- * Requires p <= 32, the Euler scheme, a single (not batched) system.  The
- * first RBM-r call allocates about N (16 + 9 p / p) bytes of scratch. */
+ * Requires p <= 32, the Euler scheme, additive noise, a single (not batched)
+ * system.  The first RBM-r call allocates about N (16 + 9 p / p) bytes of scratch. */
 
 /* The sets of step m (K x p uint32 ids, slot order) into sets_dev (device,
  * caller-owned, K p entries).  Does not advance m. */
@@ -275,7 +284,8 @@ rbm_status rbm_step_profiled(rbm_ctx *ctx, int32_t method, float *kernel_ms, int
  *            iters_per_checkpoint while that error is above fallback_tol, at
  *            most max_rounds rounds in all (the error is read back after each
  *            round: the only host synchronisation of the method).
- * Requires d = 2, FP32, the Euler scheme, a single (not batched) system.
+ * Requires d = 2, FP32, the Euler scheme, additive noise, a single (not
+ * batched) system.
  * Synchronous (allocates the network state). */
 rbm_status rbm_surrogate_config(rbm_ctx *ctx, int32_t train_every, double fallback_tol, int64_t n_queries,
                                 int32_t iters_first, int32_t iters_per_checkpoint, int32_t max_rounds, double lr);

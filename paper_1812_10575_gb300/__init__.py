@@ -109,7 +109,7 @@ class System:
     ``(N, leading_dim(d))``.  Methods map one-to-one onto the C entry points."""
 
     def __init__(self, x, d, p=2, dt=1e-3, sigma=0.0, seed=0, v="zero", v_coef=1.0, k="linear",
-                 k_param=0.0, renorm=False, scheme="euler", replica=0, stream=None):
+                 k_param=0.0, renorm=False, scheme="euler", replica=0, gbm=False, stream=None):
         import torch
 
         if x.dtype not in (torch.float32, torch.float64):
@@ -120,7 +120,7 @@ class System:
         self.d = d
         self.params = make_params(x.shape[0], d, p=p, dt=dt, sigma=sigma, seed=seed,
                                   dtype="f32" if x.dtype == torch.float32 else "f64", v=v, v_coef=v_coef,
-                                  k=k, k_param=k_param, renorm=renorm, scheme=scheme, replica=replica)
+                                  k=k, k_param=k_param, renorm=renorm, scheme=scheme, replica=replica, gbm=gbm)
         self.ctx = rbm_init(self.params, x, stream)
 
     def step(self):

@@ -35,6 +35,7 @@ METHODS = {"rbm": 0, "direct": 1, "surrogate": 2, "rbmr": 3}
 RBM_SCHEME_EULER, RBM_SCHEME_SPLIT, RBM_SCHEME_VERLET = 0, 1, 2
 SCHEMES = {"euler": 0, "split": 1, "verlet": 2}
 RBM_FLAG_RENORM_SPHERE = 1
+RBM_FLAG_GBM_NOISE = 2
 
 # Every symbol include/rbm.h declares.
 EXPORTS = (
@@ -171,13 +172,13 @@ def rbm_last_error() -> str:
 
 
 def make_params(n, d, p=2, dt=1e-3, sigma=0.0, seed=0, dtype="f32", v="zero", v_coef=1.0, k="linear",
-                k_param=0.0, renorm=False, scheme="euler", replica=0) -> RbmParams:
+                k_param=0.0, renorm=False, scheme="euler", replica=0, gbm=False) -> RbmParams:
     return RbmParams(
         n=int(n), d=int(d), p=int(p), dt=float(dt), sigma=float(sigma), seed=int(seed),
         dtype=RBM_F32 if dtype in ("f32", "float32") else RBM_F64,
         v=POTENTIALS[v] if isinstance(v, str) else int(v), v_coef=float(v_coef),
         k=KERNELS[k] if isinstance(k, str) else int(k), k_param=float(k_param),
-        flags=RBM_FLAG_RENORM_SPHERE if renorm else 0,
+        flags=(RBM_FLAG_RENORM_SPHERE if renorm else 0) | (RBM_FLAG_GBM_NOISE if gbm else 0),
         scheme=SCHEMES[scheme] if isinstance(scheme, str) else int(scheme), replica=int(replica),
     )
 

@@ -89,13 +89,14 @@ rbm_status check_params(const rbm_params* p) {
   if (!valid_kernel(p->k)) return RBM_ERR_INVALID;
   if (p->k == RBM_K_INV1D && p->d != 1) return RBM_ERR_INVALID;
   if (!std::isfinite(p->v_coef) || !std::isfinite(p->k_param)) return RBM_ERR_INVALID;
-  if (p->flags & ~RBM_FLAG_RENORM_SPHERE) return RBM_ERR_INVALID;
+  if (p->flags & ~(RBM_FLAG_RENORM_SPHERE | RBM_FLAG_GBM_NOISE)) return RBM_ERR_INVALID;
   if (p->scheme != RBM_SCHEME_EULER && p->scheme != RBM_SCHEME_SPLIT && p->scheme != RBM_SCHEME_VERLET)
     return RBM_ERR_INVALID;
   // the second-order system carries no noise and no projection (Appendix A)
   if (p->scheme == RBM_SCHEME_VERLET && (p->sigma != 0.0 || (p->flags & RBM_FLAG_RENORM_SPHERE)))
     return RBM_ERR_INVALID;
-  if (p->scheme == RBM_SCHEME_SPLIT && (p->p != 2 || (p->k != RBM_K_INV1D && p->k != RBM_K_COULOMB)))
+  if (p->scheme == RBM_SCHEME_SPLIT &&
+      (p->p != 2 || (p->k != RBM_K_INV1D && p->k != RBM_K_COULOMB && p->k != RBM_K_LINEAR)))
     return RBM_ERR_INVALID;
   return RBM_OK;
 }
@@ -220,6 +221,7 @@ StepParams<T> step_params(const rbm_ctx* c, const int64_t* m_ptr, int64_t m_off)
   a.kf = p.k;
   a.vkind = p.v;
   a.renorm = (p.flags & RBM_FLAG_RENORM_SPHERE) ? 1 : 0;
+  a.gbm = (p.flags & RBM_FLAG_GBM_NOISE) ? 1 : 0;
   a.scheme = p.scheme;
   a.dt = static_cast<T>(p.dt);
   a.sq = static_cast<T>(p.sigma * std::sqrt(p.dt));
@@ -333,7 +335,8 @@ rbm_status enqueue_train_round(rbm_ctx* c, int32_t iters, int32_t round, cudaStr
 rbm_status ensure_rbmr(rbm_ctx* c) {
   if (c->rs.set) return RBM_OK;
   if (c->batched) return RBM_ERR_UNSUPPORTED;
-  if (c->prm.p > 32 || c->prm.scheme != RBM_SCHEME_EULER) return RBM_ERR_UNSUPPORTED;
+  if (c->prm.p > 32 || c->prm.scheme != RBM_SCHEME_EULER || (c->prm.flags & RBM_FLAG_GBM_NOISE))
+    return RBM_ERR_UNSUPPORTED;
   int nb = 0;
   cudaError_t e = rbmr_blocks_per_sm(c->prm.dtype, c->prm.d, &nb);
   if (e != cudaSuccess || nb < 1) {
@@ -1107,7 +1110,8 @@ rbm_status rbm_surrogate_config(rbm_ctx* ctx, int32_t train_every, double fallba
                                 int32_t iters_first, int32_t iters_per_checkpoint, int32_t max_rounds, double lr) {
   rbm_status st = usable(ctx);
   if (st != RBM_OK) return st;
-  if (ctx->batched || ctx->prm.d != 2 || ctx->prm.dtype != RBM_F32 || ctx->prm.scheme != RBM_SCHEME_EULER)
+  if (ctx->batched || ctx->prm.d != 2 || ctx->prm.dtype != RBM_F32 || ctx->prm.scheme != RBM_SCHEME_EULER ||
+      (ctx->prm.flags & RBM_FLAG_GBM_NOISE))
     return RBM_ERR_UNSUPPORTED;
   if (train_every < 1 || !(fallback_tol > 0) || n_queries < 8 || n_queries > (int64_t(1) << 24) || iters_first < 0 ||
       iters_per_checkpoint < 0 || max_rounds < 1 || !(lr > 0))

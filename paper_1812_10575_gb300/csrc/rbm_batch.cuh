@@ -60,13 +60,15 @@ __device__ __forceinline__ void batch_group_row(const StepParams<T>& a, uint32_t
       for (int k = 0; k < D; ++k) dd[k] = fsub_rn(r.x[k], xj[k]);
       if (sqnorm_rn<T, D>(dd) != T(0)) {
         const T len = sqrt(len2);
-        const T newlen = (a.kf == RBM_K_INV1D) ? sqrt(len2 + T(4) * a.dt) : cbrt(len2 * len + T(6) * a.dt);
+        const T newlen = (a.kf == RBM_K_INV1D)    ? sqrt(len2 + T(4) * a.dt)
+                         : (a.kf == RBM_K_LINEAR) ? len * exp_rt(T(-2) * a.kparam * a.dt)
+                                                  : cbrt(len2 * len + T(6) * a.dt);
 #pragma unroll
         for (int k = 0; k < D; ++k) y0[k] = mid[k] + T(0.5) * newlen * (delta[k] / len);
       }
     }
     T y[D];
-    euler_update<T, D>(a, id, m32, y0, fk, y);
+    euler_update<T, D>(a, id, m32, y0, fk, y, true);
 #pragma unroll
     for (int k = 0; k < D; ++k) r.x[k] = y[k];
     store_row<T, D>(a.x, id, r);

@@ -255,6 +255,7 @@ struct StepParams {
   int32_t kf;         // rbm_kernel
   int32_t vkind;      // rbm_potential
   int32_t renorm;
+  int32_t gbm;        // 1: multiplicative noise sigma X dB
   int32_t scheme;     // rbm_scheme
   T dt, sq;           // tau, sigma sqrt(tau)
   T vcoef, kparam, radius_sq;
@@ -284,16 +285,24 @@ __device__ __forceinline__ void latch_status(int32_t* status, int32_t code) {
 
 template <typename T> __device__ __forceinline__ bool finite_val(T v) { return isfinite(v); }
 
+__device__ __forceinline__ float exp_rt(float v) { return expf(v); }
+__device__ __forceinline__ double exp_rt(double v) { return exp(v); }
+
 // y = x + dt (fk - grad V(x)) + sigma sqrt(dt) z for given increments z, then
 // the optional projection onto the unit sphere; latches RBM_ERR_NONFINITE on a
-// non-finite result.
+// non-finite result.  Multiplicative noise (gbm): the noise term is
+// sigma sqrt(dt) x z, or, after the exact pair flow of the splitting scheme
+// (split_flow), the exact geometric flow y = x exp(-s^2/2 + s z) + dt (fk -
+// grad V(x)), s = sigma sqrt(dt) (Ito).
 template <typename T, int D>
 __device__ __forceinline__ void euler_apply(const StepParams<T>& a, const T (&x)[D], const T (&fk)[D],
-                                            const T (&z)[D], T (&y)[D]) {
+                                            const T (&z)[D], T (&y)[D], bool split_flow = false) {
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     const T fv = (a.vkind == RBM_V_QUADRATIC) ? -a.vcoef * x[k] : T(0);
-    y[k] = x[k] + a.dt * (fk[k] + fv) + a.sq * z[k];
+    if (!a.gbm) y[k] = x[k] + a.dt * (fk[k] + fv) + a.sq * z[k];
+    else if (split_flow) y[k] = x[k] * exp_rt(T(-0.5) * a.sq * a.sq + a.sq * z[k]) + a.dt * (fk[k] + fv);
+    else y[k] = x[k] + a.dt * (fk[k] + fv) + a.sq * x[k] * z[k];
   }
   if (a.renorm) {
     T nrm = T(0);
@@ -340,7 +349,7 @@ __device__ __forceinline__ void verlet_update(const StepParams<T>& a, uint32_t i
 // increment (id, m) (synchronous coupling of RBM-1 and the direct step).
 template <typename T, int D>
 __device__ __forceinline__ void euler_update(const StepParams<T>& a, uint32_t id, uint32_t m32, const T (&x)[D],
-                                             const T (&fk)[D], T (&y)[D]) {
+                                             const T (&fk)[D], T (&y)[D], bool split_flow = false) {
   T z[D];
   if (a.sq != T(0)) {
     brownian<T, D>(id, m32, a.replica, a.seed, z);
@@ -348,7 +357,7 @@ __device__ __forceinline__ void euler_update(const StepParams<T>& a, uint32_t id
 #pragma unroll
     for (int k = 0; k < D; ++k) z[k] = T(0);
   }
-  euler_apply<T, D>(a, x, fk, z, y);
+  euler_apply<T, D>(a, x, fk, z, y, split_flow);
 }
 
 // The update of the configured scheme after the interaction force fk.
