@@ -147,8 +147,9 @@ typedef struct {
     int32_t block;        /* threads per block of the fused step kernel      */
     int32_t direct_block; /* threads per block of the direct kernel          */
     int32_t graph_steps;  /* steps captured per CUDA graph by rbm_run        */
-    int32_t path;         /* RBM step: 0 automatic, 1 bucket-sort kernels, 2 one
-                             cooperative kernel (N up to about 1.2 million, p <= 32;
+    int32_t path;         /* RBM step: 0 automatic (2 up to about 2.3 million
+                             particles, 1 beyond), 1 bucket-sort kernels, 2 one
+                             cooperative kernel (N up to about 8 million, p <= 32;
                              falls back to 1 when it does not fit)            */
     int32_t wait_limit_us;/* bound of a grid-barrier wait in the cooperative
                              kernel (0 = 1 second); a wait that runs out

@@ -1,5 +1,5 @@
-// RBM-1 step as one cooperative persistent kernel (systems of up to about a
-// million particles): one block per SM, all blocks resident, two grid-wide
+// RBM-1 step as one cooperative persistent kernel (systems of up to about
+// eight million particles): one block per SM, all blocks resident, two grid-wide
 // barriers per step in the common case and no atomics outside shared memory
 // except one per (block, bucket).
 //
@@ -424,27 +424,29 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
   if (!grid_barrier(ca, a.status, false)) return;
 
   // phase 4 (general mode): batches straddling a bucket boundary; warp w
-  // takes boundary c + w G, the first boundary inside a batch takes it
-  const uint32_t b = c + static_cast<uint32_t>(warp) * G;
-  if (static_cast<uint32_t>(warp) * G >= B) return;  // warp-uniform
-  bool valid = (b > 0) && (b < B);
-  uint32_t id = 0;
-  int bs = a.p;
-  if (valid) {
-    const uint32_t s = sm.s_start[b];
-    valid = (s % up != 0) && (s < a.n);
+  // takes boundaries c + w G, c + (w + W) G, ... (W warps per block); the
+  // first boundary inside a batch takes it
+  const uint32_t nwarps = blockDim.x >> 5;
+  for (uint32_t b = c + static_cast<uint32_t>(warp) * G; b < B; b += nwarps * G) {  // warp-uniform
+    bool valid = b > 0;
+    uint32_t id = 0;
+    int bs = a.p;
     if (valid) {
-      const uint32_t q = s / up;
-      valid = sm.s_start[b - 1] <= q * up;
+      const uint32_t s = sm.s_start[b];
+      valid = (s % up != 0) && (s < a.n);
       if (valid) {
-        const uint32_t lo = q * up, hi = min(lo + up, a.n);
-        bs = static_cast<int>(hi - lo);
-        valid = lane < bs;
-        if (valid) id = ca.perm[lo + lane];
+        const uint32_t q = s / up;
+        valid = sm.s_start[b - 1] <= q * up;
+        if (valid) {
+          const uint32_t lo = q * up, hi = min(lo + up, a.n);
+          bs = static_cast<int>(hi - lo);
+          valid = lane < bs;
+          if (valid) id = ca.perm[lo + lane];
+        }
       }
     }
+    batch_group<T, D, MODE>(a, m32, id, valid, lane < a.p ? lane : 0, bs);
   }
-  batch_group<T, D, MODE>(a, m32, id, valid, lane < a.p ? lane : 0, bs);
 }
 
 template <typename T, int D, int MODE>
@@ -464,7 +466,7 @@ cudaError_t launch_coop_k(const CoopScratch& cs, const StepParams<T>& a, const C
 
 template <typename T, int D>
 cudaError_t set_attr_d(int* min_blocks) {
-  const int bytes = static_cast<int>(coop_smem_bytes_t<T, D>(1024));
+  const int bytes = static_cast<int>(coop_smem_bytes_t<T, D>(coop_max_buckets()));
   cudaError_t e =
       cudaFuncSetAttribute(k_rbm_coop<T, D, kModePerm>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
@@ -480,7 +482,7 @@ cudaError_t set_attr_d(int* min_blocks) {
 
 }  // namespace
 
-uint32_t coop_max_buckets() { return 1024; }
+uint32_t coop_max_buckets() { return 8192; }
 uint32_t coop_bucket_target() { return 1024; }
 
 cudaError_t prepare_coop_kernels(int* blocks_per_sm) {

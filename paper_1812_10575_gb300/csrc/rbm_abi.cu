@@ -187,13 +187,16 @@ rbm_status alloc_scratch(rbm_ctx* c) {
   c->cfg.direct_block = c->tuning.direct_block > 0 ? c->tuning.direct_block : 256;
 
   // Cooperative single-kernel path: one block per SM, B = k * grid buckets of
-  // at most ~2048 members on average, B <= 1024; batches of at most a warp.
+  // about 1024 members on average, B <= coop_max_buckets() (N up to about
+  // 8M); batches of at most a warp.  Chosen automatically up to 15 buckets
+  // per block (N about 2.3M): beyond that the multi-kernel path is faster
+  // (measured crossover between 2^20 and 2^22); path = 2 forces it.
   const uint32_t grid = static_cast<uint32_t>(c->cfg.num_sms);
   const uint32_t k = static_cast<uint32_t>((static_cast<uint64_t>(n) + static_cast<uint64_t>(grid) *
                                             coop_bucket_target() - 1) / (static_cast<uint64_t>(grid) *
                                                                          coop_bucket_target()));
   const bool coop_fits = c->coop_blocks_per_sm >= 1 && c->prm.p <= 32 && k >= 1 && k * grid <= coop_max_buckets();
-  c->use_coop = (c->tuning.path == 2 || c->tuning.path == 0) && coop_fits;
+  c->use_coop = (c->tuning.path == 2 || (c->tuning.path == 0 && k <= 15)) && coop_fits;
   if (c->use_coop) {
     CoopScratch& cs = c->cs;
     cs.grid = grid;

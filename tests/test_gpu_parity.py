@@ -261,6 +261,28 @@ def test_rbm_fp32_per_step(name, n, d, kw, path):
         cur = got
 
 
+@pytest.mark.parametrize("p", [2, 16])
+def test_cooperative_path_at_millions_of_particles(p):
+    """N = 5e6 on the single-kernel path (about 5000 buckets, more than the
+    152 x 32 warps of one pass): the permutation bit-exact and one FP32 step
+    within the per-step bar; p = 16 needs more than 7 picks for a straddling
+    batch, so the general mode's boundary loop runs."""
+    n, d = 5_000_000, 3
+    kw = dict(p=p, dt=1e-3, sigma=0.2, v="quadratic", k="reg_attract", k_param=0.01)
+    X = as_run_precision(workloads.gaussian(n, d, seed=7), "f32")
+    s, x = _system(X, d, "f32", seed=3, **kw)
+    s.set_tuning(path=2)                      # beyond the automatic crossover
+    assert s.tuning()["path"] == 2
+    prm = _oprm(n, d, "f32", seed=3, **kw)
+    perm = oracle.permutation(prm, 0)
+    assert np.array_equal(s.permutation().cpu().numpy().view(np.uint32), perm)
+    s.step()
+    s.sync()
+    FK = oracle.rbm_interaction(prm, X, perm)
+    ref = oracle.euler_update(prm, X, FK, 0)
+    assert_close_per_particle(from_dev(x, d), ref, 1e-5, extra=_fp32_bound(prm, X, FK, 0), what=f"p = {p}")
+
+
 def test_direct_fp32_full_size_sampled():
     """Thomson N = 1e5, FP32, the launch the benchmark times: 256 sampled particles."""
     n, d = 100000, 3
