@@ -147,10 +147,13 @@ typedef struct {
     int32_t block;        /* threads per block of the fused step kernel      */
     int32_t direct_block; /* threads per block of the direct kernel          */
     int32_t graph_steps;  /* steps captured per CUDA graph by rbm_run        */
-    int32_t path;         /* RBM step: 0 automatic (2 up to about 2.3 million
-                             particles, 1 beyond), 1 bucket-sort kernels, 2 one
-                             cooperative kernel (N up to about 8 million, p <= 32;
-                             falls back to 1 when it does not fit)            */
+    int32_t path;         /* RBM step: 0 automatic (3 up to 1536 particles in
+                             FP32 / 384 in FP64, 2 up to about 2.3 million,
+                             1 beyond), 1 bucket-sort
+                             kernels, 2 one cooperative kernel (N up to about 8
+                             million, p <= 32), 3 one block for the whole system
+                             (N <= 2048, p <= 32); a path that does not fit
+                             falls back to 1                                   */
     int32_t wait_limit_us;/* bound of a grid-barrier wait in the cooperative
                              kernel (0 = 1 second); a wait that runs out
                              latches RBM_ERR_TIMEOUT                           */

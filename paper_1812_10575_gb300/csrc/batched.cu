@@ -45,6 +45,7 @@ struct BatchedArgs {
   uint32_t* tmp;                // [rows] ids grouped by bucket
   uint32_t* perm;               // [rows] permutation (replica-local ids)
   uint32_t bucket_target;       // mean members per bucket
+  uint32_t rep_base;            // replica index in the counters = list index + rep_base
 };
 
 __device__ __forceinline__ bool bkey_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
@@ -150,6 +151,7 @@ __global__ void __launch_bounds__(1024, batched_min_blocks<T, D>()) k_rbm_batche
   __shared__ uint32_t s_warp[32];
   __shared__ int s_general;
 
+  if (skipped(a)) return;  // uniform: the flag does not change during the launch
   const uint32_t m32 = step_index(a);
   const uint32_t up = static_cast<uint32_t>(a.p);
   const uint32_t begin = ba.block_begin[blockIdx.x], end_list = ba.block_begin[blockIdx.x + 1];
@@ -158,9 +160,10 @@ __global__ void __launch_bounds__(1024, batched_min_blocks<T, D>()) k_rbm_batche
     // odd blocks walk their list backwards: large and small replicas are in
     // flight together, so the replicas being worked on fit in L2
     const uint32_t li = (blockIdx.x & 1u) ? end_list - 1u - k : begin + k;
-    const uint32_t r = ba.order[li];
-    const uint64_t off = ba.offs[r];
-    const uint32_t n = static_cast<uint32_t>(ba.offs[r + 1] - off);
+    const uint32_t ri = ba.order[li];
+    const uint32_t r = ri + ba.rep_base;  // replica index of the Philox counters
+    const uint64_t off = ba.offs[ri];
+    const uint32_t n = static_cast<uint32_t>(ba.offs[ri + 1] - off);
     uint32_t B = (n + ba.bucket_target - 1) / ba.bucket_target;
     B = max(1u, min(B, kBMaxBuckets));
     uint32_t* tmp = ba.tmp + off;
@@ -280,6 +283,7 @@ cudaError_t launch_batched_k(const BatchedScratch& bs, const StepParams<T>& a, c
   ba.tmp = bs.tmp;
   ba.perm = bs.perm;
   ba.bucket_target = static_cast<uint32_t>(bs.bucket_target);
+  ba.rep_base = bs.rep_base;
   k_rbm_batched<T, D, MODE><<<bs.grid, bs.threads, batched_smem<T, D>(), st>>>(ba, a);
   return cudaGetLastError();
 }

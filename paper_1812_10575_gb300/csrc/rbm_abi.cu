@@ -48,6 +48,7 @@ struct rbm_ctx {
   int64_t sur_graph_len = 0;
   int batched_blocks_per_sm = 0;
   bool use_coop = false;
+  bool use_small = false;       // N <= 2048: the whole step in one block (the replica kernel)
   int coop_blocks_per_sm = 0;
   LaunchCfg cfg;
   rbm_tuning tuning{};
@@ -197,6 +198,40 @@ rbm_status alloc_scratch(rbm_ctx* c) {
                                                                          coop_bucket_target()));
   const bool coop_fits = c->coop_blocks_per_sm >= 1 && c->prm.p <= 32 && k >= 1 && k * grid <= coop_max_buckets();
   c->use_coop = (c->tuning.path == 2 || (c->tuning.path == 0 && k <= 15)) && coop_fits;
+  // Small systems: one block sorts all N keys in shared memory and steps
+  // every batch (no grid barrier); the replica kernel with one replica.
+  // Chosen automatically up to N = 1536 in FP32 and N = 384 in FP64 (the
+  // measured crossovers with the cooperative kernel: FP32 14.3 vs 17.7 us at
+  // N = 1000, even near 2048; FP64 25 vs 31 us at N = 256 but 52 vs 25 us at
+  // N = 1000, where the FP64 transcendental work of Box-Muller and the split
+  // pair flow on one SM outweighs the grid barriers).
+  const bool small_fits = !c->batched && n <= 2048 && c->prm.p <= 32;
+  const bool small_auto = n <= (c->prm.dtype == RBM_F32 ? 1536u : 384u);
+  c->use_small = (c->tuning.path == 3 || (c->tuning.path == 0 && small_auto)) && small_fits;
+  if (c->use_small) {
+    c->use_coop = false;
+    BatchedScratch& bs = c->bs;
+    int bpsm = 0;
+    cudaError_t e = prepare_batched_kernels(c->prm.dtype, c->prm.d, 1024, &bpsm);
+    if (e != cudaSuccess || bpsm < 1) {
+      set_error("prepare_batched_kernels", e == cudaSuccess ? cudaErrorInvalidConfiguration : e);
+      return RBM_ERR_CUDA;
+    }
+    bs.threads = 1024;
+    bs.bucket_target = 2048;
+    bs.grid = 1;
+    bs.rep_base = static_cast<uint32_t>(c->prm.replica);
+    const uint32_t order0 = 0, begin01[2] = {0, 1};
+    const uint64_t offs01[2] = {0, n};
+    RBM_CUDA(cudaMalloc(&bs.order, sizeof(uint32_t)));
+    RBM_CUDA(cudaMalloc(&bs.block_begin, 2 * sizeof(uint32_t)));
+    RBM_CUDA(cudaMalloc(&bs.offs, 2 * sizeof(uint64_t)));
+    RBM_CUDA(cudaMemcpy(bs.order, &order0, sizeof(uint32_t), cudaMemcpyHostToDevice));
+    RBM_CUDA(cudaMemcpy(bs.block_begin, begin01, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    RBM_CUDA(cudaMemcpy(bs.offs, offs01, 2 * sizeof(uint64_t), cudaMemcpyHostToDevice));
+    RBM_CUDA(cudaMalloc(&bs.tmp, sizeof(uint32_t) * n));
+    RBM_CUDA(cudaMalloc(&bs.perm, sizeof(uint32_t) * n));
+  }
   if (c->use_coop) {
     CoopScratch& cs = c->cs;
     cs.grid = grid;
@@ -247,15 +282,17 @@ uint2 seed_of(const rbm_ctx* c) {
 // Enqueue one RBM step (mode 1), the permutation only (0) or the forces (2).
 rbm_status enqueue_rbm(rbm_ctx* c, int mode, const int64_t* m_ptr, int64_t m_off, void* fout, cudaStream_t st,
                        const int* skip = nullptr) {
-  if (c->batched) {
+  if (c->batched || c->use_small) {
     cudaError_t e;
     if (c->prm.dtype == RBM_F32) {
       StepParams<float> a = step_params<float>(c, m_ptr, m_off);
       a.fout = static_cast<float*>(fout);
+      a.skip = skip;
       e = launch_batched<float>(c->bs, c->prm.d, mode, &a, c->cfg, st);
     } else {
       StepParams<double> a = step_params<double>(c, m_ptr, m_off);
       a.fout = static_cast<double*>(fout);
+      a.skip = skip;
       e = launch_batched<double>(c->bs, c->prm.d, mode, &a, c->cfg, st);
     }
     if (e != cudaSuccess) {
@@ -787,7 +824,7 @@ rbm_status rbm_set_tuning(rbm_ctx* ctx, const rbm_tuning* tuning) {
   if (st != RBM_OK) return st;
   if (!tuning) return RBM_ERR_INVALID;
   if (tuning->bucket_bits < 0 || tuning->bucket_bits > 24 || tuning->slot_cap < 0 || tuning->sort_cap < 0 ||
-      tuning->sort_cap > 4096 || tuning->graph_steps < 0 || tuning->path < 0 || tuning->path > 2 ||
+      tuning->sort_cap > 4096 || tuning->graph_steps < 0 || tuning->path < 0 || tuning->path > 3 ||
       tuning->wait_limit_us < 0 || tuning->test_skip_arrival < 0 || tuning->test_skip_arrival > 1)
     return RBM_ERR_INVALID;
   if ((tuning->block != 0 && tuning->block != 256) ||
@@ -820,7 +857,7 @@ rbm_status rbm_get_tuning(const rbm_ctx* ctx, rbm_tuning* tuning) {
   tuning->sort_cap = static_cast<int32_t>(ctx->ps.sort_cap);
   tuning->block = ctx->cfg.block;
   tuning->direct_block = ctx->cfg.direct_block;
-  tuning->path = ctx->use_coop ? 2 : 1;
+  tuning->path = ctx->use_small ? 3 : ctx->use_coop ? 2 : 1;
   return RBM_OK;
 }
 
@@ -844,7 +881,7 @@ rbm_status rbm_permutation(rbm_ctx* ctx, uint32_t* perm_dev) {
   if (!perm_dev) return RBM_ERR_INVALID;
   st = enqueue_rbm(ctx, 0, nullptr, ctx->m, nullptr, ctx->stream);
   if (st != RBM_OK) return st;
-  RBM_CUDA(cudaMemcpyAsync(perm_dev, ctx->batched ? ctx->bs.perm : ctx->ps.perm,
+  RBM_CUDA(cudaMemcpyAsync(perm_dev, (ctx->batched || ctx->use_small) ? ctx->bs.perm : ctx->ps.perm,
                            sizeof(uint32_t) * static_cast<size_t>(ctx->prm.n),
                            cudaMemcpyDeviceToDevice, ctx->stream));
   return RBM_OK;
@@ -1042,6 +1079,7 @@ rbm_status rbm_autotune(rbm_ctx* ctx, int32_t trial_steps, const char* table_pat
     } else {
       cands.push_back({1, 0});
       cands.push_back({2, 0});
+      cands.push_back({3, 0});
     }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -1060,7 +1098,7 @@ rbm_status rbm_autotune(rbm_ctx* ctx, int32_t trial_steps, const char* table_pat
         rbm_tuning t = ctx->tuning;
         t.path = cd.first;
         st = rbm_set_tuning(ctx, &t);
-        if (st == RBM_OK && ((ctx->use_coop ? 2 : 1) != cd.first)) continue;  // path not available
+        if (st == RBM_OK && ((ctx->use_small ? 3 : ctx->use_coop ? 2 : 1) != cd.first)) continue;  // not available
       }
       if (st != RBM_OK) break;
       cudaMemcpyAsync(scratch, real_x, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
@@ -1333,10 +1371,10 @@ rbm_status rbm_rbmr_info(rbm_ctx* ctx, int64_t* iterations_per_step, int32_t* ro
 rbm_status rbm_launches_per_step(const rbm_ctx* ctx, int32_t method, int32_t* launches) {
   if (!ctx || !launches) return RBM_ERR_INVALID;
   if (method == RBM_METHOD_RBM)
-    *launches = (ctx->use_coop || ctx->batched) ? 1 : 1 + rbm_tail_launches(ctx->ps, ctx->prm.p);
+    *launches = (ctx->use_coop || ctx->batched || ctx->use_small) ? 1 : 1 + rbm_tail_launches(ctx->ps, ctx->prm.p);
   else if (method == RBM_METHOD_DIRECT) *launches = 2;  // upper bound: sum (+ chunk reduction)
   else if (method == RBM_METHOD_SURROGATE)
-    *launches = 1 + (ctx->use_coop ? 1 : 1 + rbm_tail_launches(ctx->ps, ctx->prm.p));
+    *launches = 1 + ((ctx->use_coop || ctx->use_small) ? 1 : 1 + rbm_tail_launches(ctx->ps, ctx->prm.p));
   else if (method == RBM_METHOD_RBMR) *launches = 1;
   else return RBM_ERR_INVALID;
   return RBM_OK;

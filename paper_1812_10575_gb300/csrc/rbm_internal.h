@@ -46,6 +46,7 @@ struct BatchedScratch {
   uint32_t grid = 0;
   int threads = 512;
   int bucket_target = 1024;
+  uint32_t rep_base = 0;            // added to the replica index in the Philox counters
 };
 
 // RBM-r scratch (rbmr.cu); all device pointers.

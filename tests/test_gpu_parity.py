@@ -46,7 +46,7 @@ def _oprm(n, d, dtype, **kw):
 # ---------------------------------------------------------------------------
 # permutation: bit-exact
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("path", [1, 2, 3])
 @pytest.mark.parametrize("n,seed,m,r", [(2, 0, 0, 0), (3, 1, 5, 0), (7, 3, 9, 2), (513, 0, 1, 0), (1000, 0, 0, 0),
                                         (1001, 5, 17, 3), (4097, 9, 2**31 + 5, 1), (100000, 0, 123, 0),
                                         (300001, 2**40 + 7, 7, 0), (900000, 3, 1, 0)])
@@ -55,7 +55,7 @@ def test_permutation_bit_exact(n, seed, m, r, path):
     X = np.zeros((n, 1))
     s, _ = _system(X, 1, "f32", p=2, seed=seed, replica=r)
     s.set_tuning(path=path)
-    assert s.tuning()["path"] == path
+    assert s.tuning()["path"] == (1 if path == 3 and n > 2048 else path)   # one block: N <= 2048 only
     s.m = m
     perm = s.permutation().cpu().numpy().view(np.uint32)
     s.sync()
@@ -99,7 +99,7 @@ def _cases():
     return out
 
 
-@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("path", [1, 2, 3])
 @pytest.mark.parametrize("k,d,p", _cases())
 def test_rbm_and_direct_forces_fp64(k, d, p, path):
     n = 997
@@ -145,7 +145,7 @@ def _initial(name, n, d):
     return workloads.gaussian(n, d, seed=3)
 
 
-@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("path", [1, 2, 3])
 @pytest.mark.parametrize("name,n,d,kw", FP64_RUNS, ids=[r[0] for r in FP64_RUNS])
 def test_rbm_fp64_ten_steps(name, n, d, kw, path):
     X = _initial(name, n, d)
@@ -242,7 +242,7 @@ def _initial32(name, n, d):
     return workloads.gaussian(n, d, seed=0)
 
 
-@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("path", [1, 2, 3])
 @pytest.mark.parametrize("name,n,d,kw", FP32_RUNS, ids=[r[0] for r in FP32_RUNS])
 def test_rbm_fp32_per_step(name, n, d, kw, path):
     X = as_run_precision(_initial32(name, n, d), "f32")
@@ -320,9 +320,9 @@ def test_direct_forces_at_queries(dtype):
 # ---------------------------------------------------------------------------
 # behaviour of the boundary
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("path", [1, 2, 3])
 def test_graph_replay_equals_eager_steps(path):
-    n, d = 20000, 3
+    n, d = (2000 if path == 3 else 20000), 3
     X = workloads.gaussian(n, d, seed=5)
     kw = dict(p=2, dt=1e-3, sigma=0.2, v="quadratic", k="reg_attract", k_param=0.01)
     a, xa = _system(X, d, "f32", **kw)
