@@ -224,8 +224,9 @@ void launch_direct_k(int mode, const StepParams<T>& a, const T* q, uint32_t nq, 
   const uint32_t per_block = kDirectThreads * R;
   const uint32_t tiles = (nt + per_block - 1) / per_block;
   // Split the sources so the grid fills whole waves of resident blocks:
-  // the smallest split (<= 32) whose last wave is at least 90 % full, among
-  // splits that give every SM work and keep chunks of >= 4 tiles.
+  // the smallest split (<= 64) whose last wave is at least 90 % full, among
+  // splits that give every SM work and keep chunks of >= 16 sources; when no
+  // split gives every SM work (small systems), the largest one allowed.
   static int resident = 0;  // blocks of this instantiation per SM
   if (resident == 0) {
     int nb = 0;
@@ -235,28 +236,32 @@ void launch_direct_k(int mode, const StepParams<T>& a, const T* q, uint32_t nq, 
     resident = nb;
   }
   const uint64_t wave = static_cast<uint64_t>(cfg.num_sms) * resident;
-  uint32_t split = 1;
+  uint32_t split = 1, largest = 1;
   double best = -1.0;
-  for (uint32_t sp = 1; sp <= 32; ++sp) {
+  for (uint32_t sp = 1; sp <= 64; ++sp) {
     if (static_cast<uint64_t>(sp) * nt > partial_rows && sp > 1) break;
-    if (sp > 1 && a.n / sp < 4u * kDirectThreads) break;
+    if (sp > 1 && a.n / sp < 16u) break;
+    largest = sp;
     const uint64_t blocks = static_cast<uint64_t>(tiles) * sp;
     const double waves = static_cast<double>(blocks) / static_cast<double>(wave);
     const double eff = waves / static_cast<double>((blocks + wave - 1) / wave);
-    if (blocks < static_cast<uint64_t>(cfg.num_sms) && sp < 32) continue;
+    if (blocks < static_cast<uint64_t>(cfg.num_sms) && sp < 64) continue;
     if (eff > best + 1e-9) {
       best = eff;
       split = sp;
     }
     if (eff >= 0.9) break;
   }
+  if (best < 0.0) split = largest;  // no split reaches every SM: as many chunks as allowed
   DirectArgs da;
   da.q = q;
   da.nq = nq;
   da.partial = partial;
   da.split = split;
-  const uint32_t chunk_tiles = ((a.n + kDirectThreads - 1) / kDirectThreads + split - 1) / split;
-  da.chunk = chunk_tiles * kDirectThreads;
+  // chunks of whole 16-row multiples (a tile multiple when the chunks are large)
+  const uint32_t chunk_rows = (a.n + split - 1) / split;
+  da.chunk = (chunk_rows >= kDirectThreads) ? (chunk_rows + kDirectThreads - 1) / kDirectThreads * kDirectThreads
+                                           : (chunk_rows + 15u) / 16u * 16u;
   const dim3 grid(tiles, split);
   if (mode == kDirectStep) k_direct<T, D, KF, kDirectStep, R><<<grid, kDirectThreads, 0, st>>>(a, da);
   else if (mode == kDirectForces) k_direct<T, D, KF, kDirectForces, R><<<grid, kDirectThreads, 0, st>>>(a, da);

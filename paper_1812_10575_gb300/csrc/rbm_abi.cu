@@ -178,8 +178,8 @@ rbm_status alloc_scratch(rbm_ctx* c) {
   RBM_CUDA(cudaMalloc(&s.done, sizeof(uint32_t)));
   RBM_CUDA(cudaMalloc(&s.perm, sizeof(uint32_t) * n));
   RBM_CUDA(cudaMalloc(&c->xtmp, c->row_bytes * n));
-  // Partial sums of the split direct sum: up to 16 chunks of N rows, at most 2^24 rows.
-  c->partial_rows = std::min<size_t>(static_cast<size_t>(n) * 16, size_t(1) << 24);
+  // Partial sums of the split direct sum: up to 64 chunks of N rows, at most 2^24 rows.
+  c->partial_rows = std::min<size_t>(static_cast<size_t>(n) * 64, size_t(1) << 24);
   RBM_CUDA(cudaMalloc(&c->partial, c->row_bytes * c->partial_rows));
   RBM_CUDA(cudaMemset(s.cnt, 0, sizeof(uint32_t) * s.nbuckets));
   RBM_CUDA(cudaMemset(s.ovf_cnt, 0, sizeof(uint32_t)));
