@@ -272,6 +272,21 @@ def _traffic_for(workload: str, kernel_name: str, digest: str):
     return ent.get("dram_bytes_per_launch")
 
 
+def max_over_ranks(dist, v, device):
+    """The largest of every rank's v (the job's time is its slowest rank's)."""
+    import torch
+
+    t = torch.tensor([float(v)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(world, n_per_rank, steps, total_ms):
+    """Whole-job particle-steps/s: every rank advances its own replica of N
+    particles (no data-path collective), the job takes the slowest rank's time."""
+    return world * n_per_rank * steps / (total_ms * 1e-3)
+
+
 class Gpu:
     """Per-rank GPU context: device, stream, L2 flush, barrier."""
 
@@ -305,9 +320,7 @@ class Gpu:
     def max_over_ranks(self, v):
         if self.world == 1:
             return v
-        t = self.torch.tensor([v], device=self.dev, dtype=self.torch.float64)
-        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(self.dist, v, self.dev)
 
     def event(self):
         return self.torch.cuda.Event(enable_timing=True)
@@ -377,7 +390,7 @@ def run_single(args, w, g):
             per_kernel.setdefault(name, []).append(ms)
     g.barrier()
     total_ms = g.max_over_ranks(float(sum(step_ms)))
-    value = g.world * n * args.steps / (total_ms * 1e-3)
+    value = weak_value(g.world, n, args.steps, total_ms)
 
     # direct O(N^2) step on the same system
     nd = min(args.steps, 5)
