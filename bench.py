@@ -22,7 +22,7 @@ Other workloads (one JSON line each, same keys):
                     100-step CUDA graph; inputs (384 MB) exceed L2;
   dyson           - Dyson Brownian motion (Sec. 4.2), N = 1000, FP64,
                     splitting scheme, p = 2, dt = 1e-3;
-  large_n         - regularised attraction, d = 3, FP32, N = 2^16 .. 2^24,
+  large_n         - regularised attraction, d = 3, FP32, N = 2^16 .. 2^26,
                     p in {2, 4, 8}, RBM-1, RBM-r (up to 2^22, p = 2) and
                     direct (up to 2^20);
   surrogate       - the learned mean-field surrogate, N = 2^22, d = 2,
@@ -72,7 +72,7 @@ WORKLOADS = {
                   scheme="split"),
     "large_n": dict(workload="large_n_reg_attract", d=3, dt=1e-3, sigma=0.2, kernel="reg_attract",
                     potential="quadratic", v_coef=1.0, k_param=0.01, renorm=False, dtype="f32", seed=0,
-                    scheme="euler", sizes=[2**16, 2**18, 2**20, 2**22, 2**24], ps=[2, 4, 8], direct_max=2**20,
+                    scheme="euler", sizes=[2**16, 2**18, 2**20, 2**22, 2**24, 2**26], ps=[2, 4, 8], direct_max=2**20,
                     rbmr_max=2**22),
     "surrogate": dict(workload="surrogate_mixture_aggregation", n=2**22, d=2, p=2, dt=1e-3, sigma=0.1,
                       kernel="gauss_agg", potential="quadratic", v_coef=1.0, k_param=0.0, renorm=False, dtype="f32",
@@ -914,7 +914,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--soak-seconds", type=float, default=1.0,
                     help="untimed load before the timed steps (brings the clocks up; 0 for short profiling runs)")
-    ap.add_argument("--sizes", default="", help="large_n only: comma-separated log2 N (default 16,18,20,22,24)")
+    ap.add_argument("--sizes", default="", help="large_n only: comma-separated log2 N (default 16,18,20,22,24,26)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -215,6 +215,12 @@ const char *rbm_last_error(void);
  * Verlet. */
 rbm_status rbm_verlet_set_velocity(rbm_ctx *ctx, const void *v_dev);
 
+/* The Verlet buffer for checkpoint/resume: X_{n-1} (or V_0 while the Taylor
+ * start is pending, *taylor_pending = 1) into prev_dev (N x ld, device);
+ * set_previous restores it at the current step m.  Synchronous. */
+rbm_status rbm_verlet_get_previous(rbm_ctx *ctx, void *prev_dev, int32_t *taylor_pending);
+rbm_status rbm_verlet_set_previous(rbm_ctx *ctx, const void *prev_dev, int32_t taylor_pending);
+
 /* ---- RBM-r (Sec. 2.2, Algorithm "fullyrandom") --------------------------- */
 /* One step of RBM_METHOD_RBMR (rbm_run, rbm_step_host, rbm_step_profiled) is
  * K = floor(N/p) (at least 1) iterations k = m K .. m K + K - 1, in order:
@@ -317,6 +323,17 @@ rbm_status rbm_surrogate_forces(rbm_ctx *ctx, const void *q_dev, int64_t nq, voi
  * network's own tensor-core kernels, no update.  Synchronous. */
 rbm_status rbm_surrogate_gradient(rbm_ctx *ctx, const void *x_dev, const void *f_target_dev, int64_t nb,
                                   float *grad_host, double *loss_host);
+
+/* Checkpoint/resume of the surrogate: everything later steps and checkpoints
+ * read (FP32 masters, Adam moments and step count, normalisation, selection
+ * flag, last error, step counters, the checkpoint schedule) as a
+ * self-describing host buffer of rbm_surrogate_state_size bytes.  Load into a
+ * context configured with the same rbm_surrogate_config; together with the
+ * positions and rbm_set_step the run continues bit for bit.  RBM_ERR_INVALID
+ * for a short or foreign buffer.  Synchronous. */
+rbm_status rbm_surrogate_state_size(const rbm_ctx *ctx, int64_t *bytes);
+rbm_status rbm_surrogate_save(rbm_ctx *ctx, void *host_buf, int64_t bytes);
+rbm_status rbm_surrogate_load(rbm_ctx *ctx, const void *host_buf, int64_t bytes);
 
 /* ---- batched replicas --------------------------------------------------- */
 

@@ -20,7 +20,8 @@ from ._lib import (  # noqa: F401
     rbm_status_string, rbm_step, rbm_step_host, rbm_step_profiled, rbm_sync, rbm_batched_init,
     rbm_batched_set_launch, rbm_autotune, rbm_surrogate_config, rbm_surrogate_train, rbm_surrogate_stats,
     rbm_surrogate_params, rbm_surrogate_set_params, rbm_surrogate_forces, rbm_surrogate_gradient,
-    rbm_rbmr_sets, rbm_rbmr_info, rbm_verlet_set_velocity,
+    rbm_rbmr_sets, rbm_rbmr_info, rbm_verlet_set_velocity, rbm_verlet_get_previous, rbm_verlet_set_previous,
+    rbm_surrogate_save, rbm_surrogate_load,
     N_SURROGATE_PARAMS,
 )
 
@@ -189,6 +190,23 @@ class System:
         if v.shape != self.x.shape or v.dtype != self.x.dtype or not v.is_contiguous():
             raise ValueError("velocities must match the positions' shape, dtype and layout")
         rbm_verlet_set_velocity(self.ctx, v)
+
+    def verlet_get_previous(self):
+        """(X_{n-1} or V_0, Taylor start pending) for checkpoint/resume."""
+        import torch
+
+        prev = torch.empty_like(self.x)
+        pending = rbm_verlet_get_previous(self.ctx, prev)
+        return prev, pending
+
+    def verlet_set_previous(self, prev, taylor_pending):
+        rbm_verlet_set_previous(self.ctx, prev.contiguous(), taylor_pending)
+
+    def surrogate_save(self):
+        return rbm_surrogate_save(self.ctx)
+
+    def surrogate_load(self, state):
+        rbm_surrogate_load(self.ctx, state)
 
     # RBM-r (Algorithm "fullyrandom"): run(steps, "rbmr")
     def rbmr_info(self):

@@ -45,7 +45,8 @@ EXPORTS = (
     "rbm_permutation_noalloc", "rbm_batched_init", "rbm_batched_set_launch", "rbm_autotune",
     "rbm_surrogate_config", "rbm_surrogate_train", "rbm_surrogate_stats", "rbm_surrogate_params",
     "rbm_surrogate_set_params", "rbm_surrogate_forces", "rbm_surrogate_gradient",
-    "rbm_rbmr_sets", "rbm_rbmr_info", "rbm_verlet_set_velocity",
+    "rbm_rbmr_sets", "rbm_rbmr_info", "rbm_verlet_set_velocity", "rbm_verlet_get_previous",
+    "rbm_verlet_set_previous", "rbm_surrogate_state_size", "rbm_surrogate_save", "rbm_surrogate_load",
 )
 N_SURROGATE_PARAMS = 4482
 
@@ -126,6 +127,11 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "rbm_launches_per_step": [vp, i32, ctypes.POINTER(i32)],
         "rbm_rbmr_sets": [vp, i64, vp],
         "rbm_verlet_set_velocity": [vp, vp],
+        "rbm_verlet_get_previous": [vp, vp, ctypes.POINTER(i32)],
+        "rbm_verlet_set_previous": [vp, vp, i32],
+        "rbm_surrogate_state_size": [vp, ctypes.POINTER(i64)],
+        "rbm_surrogate_save": [vp, vp, i64],
+        "rbm_surrogate_load": [vp, vp, i64],
         "rbm_rbmr_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)],
         "rbm_permutation_noalloc": [i64, ctypes.c_uint64, ctypes.c_uint32, i64, vp, vp],
         "rbm_batched_init": [P, i32, ctypes.POINTER(i64), vp, vp, ctypes.POINTER(vp)],
@@ -380,6 +386,34 @@ def rbm_verlet_set_velocity(ctx, v) -> None:
     """Velocities V_0 (a CUDA tensor shaped like the positions) for the
     Verlet scheme; the next step is the Taylor start."""
     _check(load().rbm_verlet_set_velocity(ctx, ctypes.c_void_p(int(v.data_ptr()))), "rbm_verlet_set_velocity")
+
+
+def rbm_verlet_get_previous(ctx, prev) -> bool:
+    """X_{n-1} (or V_0 while the Taylor start is pending) into ``prev``; returns
+    whether the Taylor start is pending."""
+    pend = ctypes.c_int32()
+    _check(load().rbm_verlet_get_previous(ctx, ctypes.c_void_p(int(prev.data_ptr())), ctypes.byref(pend)),
+           "rbm_verlet_get_previous")
+    return bool(pend.value)
+
+
+def rbm_verlet_set_previous(ctx, prev, taylor_pending) -> None:
+    _check(load().rbm_verlet_set_previous(ctx, ctypes.c_void_p(int(prev.data_ptr())), int(bool(taylor_pending))),
+           "rbm_verlet_set_previous")
+
+
+def rbm_surrogate_save(ctx) -> bytes:
+    """The surrogate's state as bytes (checkpoint/resume)."""
+    n = ctypes.c_int64()
+    _check(load().rbm_surrogate_state_size(ctx, ctypes.byref(n)), "rbm_surrogate_state_size")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(load().rbm_surrogate_save(ctx, buf, n.value), "rbm_surrogate_save")
+    return buf.raw
+
+
+def rbm_surrogate_load(ctx, state: bytes) -> None:
+    buf = ctypes.create_string_buffer(state, len(state))
+    _check(load().rbm_surrogate_load(ctx, buf, len(state)), "rbm_surrogate_load")
 
 
 def rbm_rbmr_info(ctx) -> dict:

@@ -1340,6 +1340,114 @@ rbm_status rbm_verlet_set_velocity(rbm_ctx* ctx, const void* v_dev) {
   return RBM_OK;
 }
 
+rbm_status rbm_verlet_get_previous(rbm_ctx* ctx, void* prev_dev, int32_t* taylor_pending) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (!prev_dev || !taylor_pending) return RBM_ERR_INVALID;
+  if (ctx->prm.scheme != RBM_SCHEME_VERLET || !ctx->xprev) return RBM_ERR_STATE;
+  const size_t bytes = ctx->row_bytes * static_cast<size_t>(ctx->prm.n);
+  RBM_CUDA(cudaMemcpyAsync(prev_dev, ctx->xprev, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+  *taylor_pending = (ctx->verlet_m0 == ctx->m) ? 1 : 0;
+  return RBM_OK;
+}
+
+rbm_status rbm_verlet_set_previous(rbm_ctx* ctx, const void* prev_dev, int32_t taylor_pending) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (!prev_dev || (taylor_pending != 0 && taylor_pending != 1)) return RBM_ERR_INVALID;
+  if (ctx->prm.scheme != RBM_SCHEME_VERLET) return RBM_ERR_STATE;
+  st = rbm_verlet_set_velocity(ctx, prev_dev);            // copies the buffer, drops graphs
+  if (st != RBM_OK) return st;
+  if (!taylor_pending) ctx->verlet_m0 = ctx->m - 1;       // the Taylor start lies behind
+  return RBM_OK;
+}
+
+// Surrogate state: every value a later checkpoint or step reads, so that a
+// run saved after step m and loaded into a context configured the same way
+// continues bit for bit.
+namespace {
+constexpr uint32_t kSurStateMagic = 0x52425347u;  // "RBSG"
+struct SurStateHeader {
+  uint32_t magic, version, np, pad;
+  int32_t adam_t, flag, trained, norm_given;
+  float err, pad2;
+  uint64_t counters[2];
+  int64_t last, adam_total;
+  float norm[4];
+};
+size_t sur_state_bytes() {
+  return sizeof(SurStateHeader) + 3 * sizeof(float) * static_cast<size_t>(surrogate_param_count());
+}
+}  // namespace
+
+rbm_status rbm_surrogate_state_size(const rbm_ctx* ctx, int64_t* bytes) {
+  if (!ctx || !bytes) return RBM_ERR_INVALID;
+  *bytes = static_cast<int64_t>(sur_state_bytes());
+  return RBM_OK;
+}
+
+rbm_status rbm_surrogate_save(rbm_ctx* ctx, void* host_buf, int64_t bytes) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (!ctx->sur_on) return RBM_ERR_STATE;
+  if (!host_buf || bytes < static_cast<int64_t>(sur_state_bytes())) return RBM_ERR_INVALID;
+  RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+  const size_t np = static_cast<size_t>(surrogate_param_count());
+  SurStateHeader h{};
+  h.magic = kSurStateMagic;
+  h.version = 1;
+  h.np = static_cast<uint32_t>(np);
+  RBM_CUDA(cudaMemcpy(&h.adam_t, ctx->ss.adam_t, sizeof(int), cudaMemcpyDeviceToHost));
+  RBM_CUDA(cudaMemcpy(&h.flag, ctx->ss.flag, sizeof(int), cudaMemcpyDeviceToHost));
+  RBM_CUDA(cudaMemcpy(&h.err, ctx->ss.err, sizeof(float), cudaMemcpyDeviceToHost));
+  RBM_CUDA(cudaMemcpy(h.counters, ctx->ss.counters, sizeof(h.counters), cudaMemcpyDeviceToHost));
+  RBM_CUDA(cudaMemcpy(h.norm, ctx->ss.norm, sizeof(h.norm), cudaMemcpyDeviceToHost));
+  h.trained = ctx->sur_trained ? 1 : 0;
+  h.norm_given = ctx->sur_norm_given ? 1 : 0;
+  h.last = ctx->sur_last;
+  h.adam_total = ctx->sur_adam_total;
+  unsigned char* out = static_cast<unsigned char*>(host_buf);
+  std::memcpy(out, &h, sizeof(h));
+  float* f = reinterpret_cast<float*>(out + sizeof(h));
+  RBM_CUDA(cudaMemcpy(f, ctx->ss.theta, sizeof(float) * np, cudaMemcpyDeviceToHost));
+  RBM_CUDA(cudaMemcpy(f + np, ctx->ss.mom1, sizeof(float) * np, cudaMemcpyDeviceToHost));
+  RBM_CUDA(cudaMemcpy(f + 2 * np, ctx->ss.mom2, sizeof(float) * np, cudaMemcpyDeviceToHost));
+  return RBM_OK;
+}
+
+rbm_status rbm_surrogate_load(rbm_ctx* ctx, const void* host_buf, int64_t bytes) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (!ctx->sur_on) return RBM_ERR_STATE;
+  if (!host_buf || bytes < static_cast<int64_t>(sur_state_bytes())) return RBM_ERR_INVALID;
+  SurStateHeader h;
+  std::memcpy(&h, host_buf, sizeof(h));
+  const size_t np = static_cast<size_t>(surrogate_param_count());
+  if (h.magic != kSurStateMagic || h.version != 1 || h.np != np) return RBM_ERR_INVALID;
+  RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+  const float* f = reinterpret_cast<const float*>(static_cast<const unsigned char*>(host_buf) + sizeof(h));
+  RBM_CUDA(cudaMemcpy(ctx->ss.theta, f, sizeof(float) * np, cudaMemcpyHostToDevice));
+  RBM_CUDA(cudaMemcpy(ctx->ss.mom1, f + np, sizeof(float) * np, cudaMemcpyHostToDevice));
+  RBM_CUDA(cudaMemcpy(ctx->ss.mom2, f + 2 * np, sizeof(float) * np, cudaMemcpyHostToDevice));
+  RBM_CUDA(cudaMemcpy(ctx->ss.adam_t, &h.adam_t, sizeof(int), cudaMemcpyHostToDevice));
+  RBM_CUDA(cudaMemcpy(ctx->ss.flag, &h.flag, sizeof(int), cudaMemcpyHostToDevice));
+  RBM_CUDA(cudaMemcpy(ctx->ss.err, &h.err, sizeof(float), cudaMemcpyHostToDevice));
+  RBM_CUDA(cudaMemcpy(ctx->ss.counters, h.counters, sizeof(h.counters), cudaMemcpyHostToDevice));
+  RBM_CUDA(cudaMemcpy(ctx->ss.norm, h.norm, sizeof(h.norm), cudaMemcpyHostToDevice));
+  ctx->sur_trained = h.trained != 0;
+  ctx->sur_norm_given = h.norm_given != 0;
+  ctx->sur_last = h.last;
+  ctx->sur_adam_total = h.adam_total;
+  cudaError_t e = sur_publish(ctx->ss, ctx->status, ctx->stream);  // the bf16 views of theta
+  if (e != cudaSuccess) {
+    set_error("surrogate publish", e);
+    return RBM_ERR_CUDA;
+  }
+  RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+  return RBM_OK;
+}
+
 rbm_status rbm_rbmr_sets(rbm_ctx* ctx, int64_t m, uint32_t* sets_dev) {
   rbm_status st = usable(ctx);
   if (st != RBM_OK) return st;
