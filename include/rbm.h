@@ -268,6 +268,14 @@ rbm_status rbm_direct_forces_at(rbm_ctx *ctx, const void *q_dev, int64_t nq, voi
 rbm_status rbm_step_profiled(rbm_ctx *ctx, int32_t method, float *kernel_ms, int32_t capacity, int32_t *nkernels,
                              char *names, int32_t names_len);
 
+/* The latency floor of the cooperative RBM-1 step's launch shape: the mean
+ * time (microseconds, 20 back-to-back launches after one warm-up, CUDA events
+ * on the context's stream) of the same cooperative launch (grid, block,
+ * dynamic shared memory) doing only its two bounded grid barriers.  The
+ * benchmark sets it beside the step kernel's time.  RBM_ERR_STATE when the
+ * context does not use the cooperative kernel.  Synchronous. */
+rbm_status rbm_latency_floor(rbm_ctx *ctx, float *us);
+
 /* ---- learned mean-field surrogate ---------------------------------------- */
 /* The paper has no surrogate.  Its mean-field limit (Sec. 1, eq.
  * "nonlinearfp") drives each particle by the force K * mu; here a

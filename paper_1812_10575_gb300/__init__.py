@@ -21,7 +21,7 @@ from ._lib import (  # noqa: F401
     rbm_batched_set_launch, rbm_autotune, rbm_surrogate_config, rbm_surrogate_train, rbm_surrogate_stats,
     rbm_surrogate_params, rbm_surrogate_set_params, rbm_surrogate_forces, rbm_surrogate_gradient,
     rbm_rbmr_sets, rbm_rbmr_info, rbm_verlet_set_velocity, rbm_verlet_get_previous, rbm_verlet_set_previous,
-    rbm_surrogate_save, rbm_surrogate_load,
+    rbm_surrogate_save, rbm_surrogate_load, rbm_latency_floor,
     N_SURROGATE_PARAMS,
 )
 
@@ -201,6 +201,9 @@ class System:
 
     def verlet_set_previous(self, prev, taylor_pending):
         rbm_verlet_set_previous(self.ctx, prev.contiguous(), taylor_pending)
+
+    def latency_floor(self):
+        return rbm_latency_floor(self.ctx)
 
     def surrogate_save(self):
         return rbm_surrogate_save(self.ctx)

@@ -47,6 +47,7 @@ EXPORTS = (
     "rbm_surrogate_set_params", "rbm_surrogate_forces", "rbm_surrogate_gradient",
     "rbm_rbmr_sets", "rbm_rbmr_info", "rbm_verlet_set_velocity", "rbm_verlet_get_previous",
     "rbm_verlet_set_previous", "rbm_surrogate_state_size", "rbm_surrogate_save", "rbm_surrogate_load",
+    "rbm_latency_floor",
 )
 N_SURROGATE_PARAMS = 4482
 
@@ -127,6 +128,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "rbm_launches_per_step": [vp, i32, ctypes.POINTER(i32)],
         "rbm_rbmr_sets": [vp, i64, vp],
         "rbm_verlet_set_velocity": [vp, vp],
+        "rbm_latency_floor": [vp, ctypes.POINTER(ctypes.c_float)],
         "rbm_verlet_get_previous": [vp, vp, ctypes.POINTER(i32)],
         "rbm_verlet_set_previous": [vp, vp, i32],
         "rbm_surrogate_state_size": [vp, ctypes.POINTER(i64)],
@@ -414,6 +416,13 @@ def rbm_surrogate_save(ctx) -> bytes:
 def rbm_surrogate_load(ctx, state: bytes) -> None:
     buf = ctypes.create_string_buffer(state, len(state))
     _check(load().rbm_surrogate_load(ctx, buf, len(state)), "rbm_surrogate_load")
+
+
+def rbm_latency_floor(ctx) -> float:
+    """Microseconds of the cooperative step's launch shape with no work (two grid barriers)."""
+    us = ctypes.c_float()
+    _check(load().rbm_latency_floor(ctx, ctypes.byref(us)), "rbm_latency_floor")
+    return us.value
 
 
 def rbm_rbmr_info(ctx) -> dict:

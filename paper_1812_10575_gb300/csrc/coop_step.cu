@@ -449,6 +449,15 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
   }
 }
 
+// The latency floor of the step kernel's launch shape: the same cooperative
+// launch (grid, block, dynamic shared memory) and the same two bounded grid
+// barriers with no work between them.
+__global__ void __launch_bounds__(kCoopThreads, 1) k_coop_floor(unsigned long long* bar, unsigned long long wait_ns,
+                                                                int32_t* status) {
+  if (!::rbm::grid_barrier(bar, wait_ns, status, false)) return;
+  ::rbm::grid_barrier(bar, wait_ns, status, false);
+}
+
 template <typename T, int D, int MODE>
 cudaError_t launch_coop_k(const CoopScratch& cs, const StepParams<T>& a, const CoopArgs& ca, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
@@ -483,6 +492,35 @@ cudaError_t set_attr_d(int* min_blocks) {
 }  // namespace
 
 uint32_t coop_max_buckets() { return 8192; }
+
+cudaError_t launch_coop_floor(const CoopScratch& cs, size_t smem_bytes, uint64_t wait_ns, int32_t* status,
+                              cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_coop_floor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(coop_smem_bytes_t<double, 3>(coop_max_buckets())));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cs.grid);
+  cfg.blockDim = dim3(kCoopThreads);
+  cfg.dynamicSmemBytes = smem_bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_coop_floor, cs.bar, static_cast<unsigned long long>(wait_ns), status);
+}
+
+size_t coop_smem_bytes(int dtype, int d, uint32_t nbuckets) {
+  if (dtype == RBM_F32) return d == 1 ? coop_smem_bytes_t<float, 1>(nbuckets) : d == 2 ? coop_smem_bytes_t<float, 2>(nbuckets)
+                                                                                        : coop_smem_bytes_t<float, 3>(nbuckets);
+  return d == 1 ? coop_smem_bytes_t<double, 1>(nbuckets) : d == 2 ? coop_smem_bytes_t<double, 2>(nbuckets)
+                                                                  : coop_smem_bytes_t<double, 3>(nbuckets);
+}
 uint32_t coop_bucket_target() { return 1024; }
 
 cudaError_t prepare_coop_kernels(int* blocks_per_sm) {

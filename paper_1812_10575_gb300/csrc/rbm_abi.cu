@@ -1476,6 +1476,34 @@ rbm_status rbm_rbmr_info(rbm_ctx* ctx, int64_t* iterations_per_step, int32_t* ro
   return RBM_OK;
 }
 
+rbm_status rbm_latency_floor(rbm_ctx* ctx, float* us) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (!us) return RBM_ERR_INVALID;
+  if (!ctx->use_coop) return RBM_ERR_STATE;
+  const size_t smem = coop_smem_bytes(ctx->prm.dtype, ctx->prm.d, ctx->cs.nbuckets);
+  const uint64_t wait_ns = 1000ull * 1000000ull;
+  cudaEvent_t e0, e1;
+  RBM_CUDA(cudaEventCreate(&e0));
+  RBM_CUDA(cudaEventCreate(&e1));
+  cudaError_t e = launch_coop_floor(ctx->cs, smem, wait_ns, ctx->status, ctx->stream);  // warm-up
+  constexpr int kReps = 20;
+  if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+  for (int r = 0; r < kReps && e == cudaSuccess; ++r) e = launch_coop_floor(ctx->cs, smem, wait_ns, ctx->status, ctx->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    set_error("latency floor", e);
+    return RBM_ERR_CUDA;
+  }
+  *us = 1000.0f * ms / kReps;
+  return rbm_sync(ctx);
+}
+
 rbm_status rbm_launches_per_step(const rbm_ctx* ctx, int32_t method, int32_t* launches) {
   if (!ctx || !launches) return RBM_ERR_INVALID;
   if (method == RBM_METHOD_RBM)

@@ -125,6 +125,9 @@ uint32_t max_sort_cap();
 // Cooperative step (coop_step.cu): mode as for launch_rbm_tail.
 cudaError_t prepare_coop_kernels(int* blocks_per_sm);
 uint32_t coop_max_buckets();
+size_t coop_smem_bytes(int dtype, int d, uint32_t nbuckets);
+cudaError_t launch_coop_floor(const CoopScratch& cs, size_t smem_bytes, uint64_t wait_ns, int32_t* status,
+                              cudaStream_t st);
 uint32_t coop_bucket_target();
 template <typename T>
 cudaError_t launch_coop(const CoopScratch& cs, int d, int mode, const void* params, uint64_t wait_ns, int skip_arrival,
