@@ -102,10 +102,24 @@ def _env_int(name, default):
         return default
 
 
-def _kernel_sources_digest() -> str:
+# The source files each timed kernel is built from: a profile's counters stay
+# valid while these files are unchanged.
+KERNEL_SOURCES = {
+    "k_rbm_coop": ["coop_step.cu", "rbm_grid.cuh", "rbm_batch.cuh", "rbm_device.cuh", "rbm_internal.h"],
+    "k_rbm_batched": ["batched.cu", "rbm_batch.cuh", "rbm_device.cuh", "rbm_internal.h"],
+    "k_sur_step": ["surrogate.cu", "tc.cuh", "rbm_device.cuh", "rbm_internal.h"],
+    "k_bucket_sort_step": ["perm_step.cu", "rbm_batch.cuh", "rbm_device.cuh", "rbm_internal.h"],
+    "k_rbmr_step": ["rbmr.cu", "rbm_grid.cuh", "rbm_device.cuh", "rbm_internal.h"],
+}
+
+
+def _kernel_sources_digest(kernel: str = "") -> str:
+    """Digest of the kernel sources: of the files `kernel` is built from, or of
+    every file when no kernel is named."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1812_10575_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    files = KERNEL_SOURCES.get(kernel) or sorted(os.listdir(csrc))
+    for f in sorted(files):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -260,14 +274,15 @@ def run_reference(args, w):
 
 def _traffic_for(workload: str, kernel_name: str, digest: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources."""
+    on the current sources of that kernel (`digest`, of all sources, is kept
+    for the line's record)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         data = json.load(f)
     ent = data.get(workload, {}).get(kernel_name)
-    if not ent or ent.get("sources") != digest:
+    if not ent or ent.get("sources") != _kernel_sources_digest(kernel_name):
         return None
     return ent.get("dram_bytes_per_launch")
 
