@@ -142,7 +142,10 @@ typedef struct {
 /* Optional launch and scratch tuning (zero = library default). */
 typedef struct {
     int32_t bucket_bits;  /* log2 of the number of permutation buckets       */
-    int32_t slot_cap;     /* slots per bucket before spilling to the overflow list */
+    int32_t slot_cap;     /* slots per bucket before spilling to the overflow
+                             list (path 1) or regrouping every id compactly
+                             behind one more grid barrier (path 2, at most
+                             and by default 2048)                              */
     int32_t sort_cap;     /* largest bucket sorted in shared memory (power of 2) */
     int32_t block;        /* threads per block of the fused step kernel      */
     int32_t direct_block; /* threads per block of the direct kernel          */
@@ -271,7 +274,8 @@ rbm_status rbm_step_profiled(rbm_ctx *ctx, int32_t method, float *kernel_ms, int
 /* The latency floor of the cooperative RBM-1 step's launch shape: the mean
  * time (microseconds, 20 back-to-back launches after one warm-up, CUDA events
  * on the context's stream) of the same cooperative launch (grid, block,
- * dynamic shared memory) doing only its two bounded grid barriers.  The
+ * dynamic shared memory) doing only the one bounded grid barrier of a step
+ * (common case: no bucket overflow, no general mode).  The
  * benchmark sets it beside the step kernel's time.  RBM_ERR_STATE when the
  * context does not use the cooperative kernel.  Synchronous. */
 rbm_status rbm_latency_floor(rbm_ctx *ctx, float *us);

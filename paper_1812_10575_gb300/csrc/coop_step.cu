@@ -1,7 +1,7 @@
 // RBM-1 step as one cooperative persistent kernel (systems of up to about
-// eight million particles): one block per SM, all blocks resident, two grid-wide
-// barriers per step in the common case and no atomics outside shared memory
-// except one per (block, bucket).
+// eight million particles): one block per SM, all blocks resident, one
+// grid-wide barrier per step in the common case and no atomics outside shared
+// memory except one per (block, bucket).
 //
 // The random division is the id list sorted by the 64-bit Philox key with an
 // id tie-break (Algorithm "randomdiv", Sec. 2.1 of arXiv:1812.10575; any
@@ -10,13 +10,14 @@
 // so concatenating the buckets in order after sorting each one gives the
 // global order.  Per step:
 //   phase 1: every block histograms the buckets of its contiguous id range
-//            (shared-memory counters) and reserves its stretch of each bucket
+//            (shared-memory counters), reserves its stretch of each bucket
 //            with one global atomicAdd per bucket (the order of blocks inside
-//            a bucket is arbitrary: phase 3 sorts every bucket completely);
+//            a bucket is arbitrary: phase 3 sorts every bucket completely)
+//            and scatters its ids into the buckets' slots (kCap per bucket
+//            by default);
 //   barrier
-//   phase 2: every block scans the bucket totals into bucket starts and
-//            scatters its ids to the bucket-grouped array;
-//   barrier
+//   phase 2: every block scans the bucket totals into bucket starts (the
+//            global position of each bucket in the permutation);
 //   phase 3: block c takes buckets c, c + G, ...: loads the members' ids and
 //            positions into shared memory, sorts them (a counting sort by the
 //            next 11 key bits, then insertion sort of the few ids sharing a
@@ -27,9 +28,15 @@
 //            next bucket, selected by block-wide argmin rounds.
 // When some straddling batch reaches beyond the two buckets around its
 // boundary (tiny buckets: small N or large p) or a bucket outgrows shared
-// memory, every block sees it in the bucket starts, and instead a third
+// memory, every block sees it in the bucket starts, and instead a further
 // barrier and a phase 4 step those batches, one warp each, from the
-// permutation in global memory.  Every update reads the positions of step m
+// permutation in global memory.  A bucket that outgrows its slots (with
+// kCap slots, a deviation of many standard deviations from the mean of about
+// 1024) makes
+// every block regroup its ids compactly at the bucket starts behind one more
+// barrier before phase 3.  The bucket totals are double-buffered by the
+// parity of a launch counter, so each launch clears the buffer the previous
+// launch used and no barrier is spent on clearing.  Every update reads the positions of step m
 // only (explicit scheme); no particle is written by two blocks.  Barrier
 // waits are bounded by wall time; a wait that runs out latches
 // RBM_ERR_TIMEOUT and the kernel returns.
@@ -42,14 +49,17 @@ namespace rbm {
 namespace {
 
 constexpr int kCoopThreads = 1024;
-constexpr uint32_t kSubBits = 11;
-constexpr uint32_t kSub = 1u << kSubBits;  // sub-buckets inside a bucket
-constexpr uint32_t kCap = 2048;            // largest bucket sorted in shared memory
+constexpr uint32_t kSubBits = 10;
+constexpr uint32_t kSub = 1u << kSubBits;  // sub-buckets inside a bucket (one per thread)
+constexpr uint32_t kCap = 2048;            // largest bucket sorted in shared memory; slots per bucket
 constexpr int kMaxAdjacentPick = 7;        // straddling batches handled in phase 3 need <= 7 picks
 
 struct CoopArgs {
-  uint32_t* hist;              // [B] bucket totals (zero between steps)
-  uint32_t* tmp;               // [N] ids grouped by bucket
+  uint32_t* hist;              // [2 B] bucket totals, two buffers by launch parity
+  uint32_t* slots;             // [B slot_cap] ids grouped by bucket
+  uint32_t slot_cap;           // slots per bucket (<= kCap)
+  uint32_t* tmp;               // [N] ids grouped by bucket, compact (bucket overflow only)
+  uint32_t* epoch;             // [1] launch counter: its parity selects the hist buffer
   uint32_t* perm;              // [N] the permutation
   unsigned long long* bar;     // [1] barrier arrival counter (monotonic)
   uint32_t n;
@@ -213,18 +223,22 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
   __shared__ uint64_t s_wkey[64];
   __shared__ uint32_t s_wid[64];
   __shared__ uint32_t s_sel[kMaxAdjacentPick];
-  __shared__ Row<T, D> s_selrow[kMaxAdjacentPick];
-  __shared__ int s_general;
+  __shared__ int s_general, s_compact;
 
   if (skipped(a)) return;  // uniform: the flag does not change during the launch
   const uint32_t G = gridDim.x, c = blockIdx.x;
   const uint32_t m32 = step_index(a);
+  // Every block reads the launch counter before it arrives at the barrier;
+  // block 0 advances it after the barrier.
+  const uint32_t parity = *static_cast<volatile uint32_t*>(ca.epoch) & 1u;
+  uint32_t* hist = ca.hist + parity * B;
   const uint32_t per = (ca.n + G - 1) / G;
   const uint32_t i_lo = min(ca.n, c * per), i_hi = min(ca.n, i_lo + per);
   const uint32_t up = static_cast<uint32_t>(a.p);
 
-  // phase 1: bucket histogram of ids [i_lo, i_hi); reserve this block's
-  // stretch of every bucket it touches
+  // phase 1: bucket histogram of ids [i_lo, i_hi) (counts kept in s_start
+  // until the barrier); reserve this block's stretch of every bucket it
+  // touches; scatter the ids into the buckets' slots
   for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) sm.s_cnt[b] = 0;
   __syncthreads();
   for (uint32_t i = i_lo + threadIdx.x; i < i_hi; i += blockDim.x) {
@@ -234,24 +248,51 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
   __syncthreads();
   for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) {
     const uint32_t cnt = sm.s_cnt[b];
-    sm.s_cnt[b] = cnt ? atomicAdd(&ca.hist[b], cnt) : 0u;  // offset of this block inside bucket b
+    sm.s_start[b] = cnt;
+    sm.s_cnt[b] = b * ca.slot_cap + (cnt ? atomicAdd(&hist[b], cnt) : 0u);  // this block's first slot in bucket b
+  }
+  __syncthreads();
+  for (uint32_t i = i_lo + threadIdx.x; i < i_hi; i += blockDim.x) {
+    const uint64_t key = perm_key(i, m32, ca.replica, ca.seed);
+    const uint32_t b = static_cast<uint32_t>(fine_index(key, B) >> kSubBits);
+    const uint32_t slot = atomicAdd(&sm.s_cnt[b], 1u);
+    if (slot < (b + 1u) * ca.slot_cap) ca.slots[slot] = i;  // an overflowing bucket is regrouped below
   }
   if (!grid_barrier(ca, a.status, ca.skip_arrival && c == 0)) return;
-  if (ca.m_bump && c == 0 && threadIdx.x == 0) *ca.m_bump += 1;  // every block has read the step index
+  if (c == 0 && threadIdx.x == 0) {
+    if (ca.m_bump) *ca.m_bump += 1;  // every block has read the step index
+    *ca.epoch += 1u;                 // and the launch counter
+  }
+  {
+    // the buffer the previous launch used (it has completed): cleared for the next launch
+    uint32_t* other = ca.hist + (parity ^ 1u) * B;
+    for (uint32_t b = c * blockDim.x + threadIdx.x; b < B; b += G * blockDim.x) other[b] = 0;
+  }
 
-  // phase 2: bucket starts, scatter of ids
-  for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) sm.s_start[b] = ca.hist[b];
+  // phase 2: bucket starts; this block's offset inside each bucket (for the
+  // compact regrouping) is its first slot minus the bucket's slot base
+  for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) {
+    sm.s_cnt[b] -= b * ca.slot_cap + sm.s_start[b];
+    sm.s_start[b] = hist[b];
+  }
   if (threadIdx.x == 0) {
     sm.s_start[B] = 0;
     s_general = 0;
+    s_compact = 0;
   }
   __syncthreads();
   block_exclusive_scan(sm.s_start, B + 1, s_warp);  // s_start[B] becomes N
-  for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) sm.s_cnt[b] += sm.s_start[b];
+  if (sm.s_start[B] != ca.n) {
+    // totals left over by a launch whose barrier wait ran out: every block
+    // sees the same sum and leaves; nothing has been written but slots
+    if (threadIdx.x == 0) latch_status(a.status, RBM_ERR_STATE);
+    return;
+  }
   // Can every straddling batch be completed from its two adjacent buckets?
-  if (MODE != kModePerm) {
-    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) {
-      const uint32_t nb = sm.s_start[b + 1] - sm.s_start[b];
+  for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) {
+    const uint32_t nb = sm.s_start[b + 1] - sm.s_start[b];
+    if (nb > ca.slot_cap) s_compact = 1;
+    if (MODE != kModePerm) {
       bool general = nb > kCap;
       const uint32_t s = sm.s_start[b];
       if (b > 0 && s % up != 0 && s < a.n) {
@@ -264,15 +305,20 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
   }
   __syncthreads();
   const bool general = s_general != 0;
-  for (uint32_t i = i_lo + threadIdx.x; i < i_hi; i += blockDim.x) {
-    const uint64_t key = perm_key(i, m32, ca.replica, ca.seed);
-    const uint32_t b = static_cast<uint32_t>(fine_index(key, B) >> kSubBits);
-    ca.tmp[atomicAdd(&sm.s_cnt[b], 1u)] = i;
+  const bool compact = s_compact != 0;
+  if (compact) {
+    // some bucket outgrew its slots: every block regroups its ids compactly
+    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) sm.s_cnt[b] += sm.s_start[b];
+    __syncthreads();
+    for (uint32_t i = i_lo + threadIdx.x; i < i_hi; i += blockDim.x) {
+      const uint64_t key = perm_key(i, m32, ca.replica, ca.seed);
+      const uint32_t b = static_cast<uint32_t>(fine_index(key, B) >> kSubBits);
+      ca.tmp[atomicAdd(&sm.s_cnt[b], 1u)] = i;
+    }
+    if (!grid_barrier(ca, a.status, false)) return;
   }
-  if (!grid_barrier(ca, a.status, false)) return;
 
   // phase 3: sort each of this block's buckets, write the permutation, step
-  for (uint32_t b = c + threadIdx.x * G; b < B && threadIdx.x * G < B; b += blockDim.x * G) ca.hist[b] = 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint32_t b = c; b < B; b += G) {
     const uint32_t s = sm.s_start[b], nb = sm.s_start[b + 1] - s;
@@ -285,11 +331,13 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
       for (uint32_t u = threadIdx.x; u < kSub; u += blockDim.x) sm.s_sub[u] = 0;
       // issue every global load of this bucket first: ids, positions, the next bucket's ids
       const uint32_t t0 = threadIdx.x, t1 = threadIdx.x + blockDim.x;  // nb, n1 <= kCap = 2 * blockDim
-      const uint32_t id0 = (t0 < nb) ? ca.tmp[s + t0] : 0u;
-      const uint32_t id1 = (t1 < nb) ? ca.tmp[s + t1] : 0u;
-      const uint32_t nid0 = (t0 < n1) ? ca.tmp[end + t0] : 0u;
-      const uint32_t nid1 = (t1 < n1) ? ca.tmp[end + t1] : 0u;
-      Row<T, D> x0{}, x1{};
+      const uint32_t* ids = compact ? ca.tmp + s : ca.slots + static_cast<size_t>(b) * ca.slot_cap;
+      const uint32_t* next_ids = compact ? ca.tmp + end : ca.slots + static_cast<size_t>(b + 1) * ca.slot_cap;
+      const uint32_t id0 = (t0 < nb) ? ids[t0] : 0u;
+      const uint32_t id1 = (t1 < nb) ? ids[t1] : 0u;
+      const uint32_t nid0 = (t0 < n1) ? next_ids[t0] : 0u;
+      const uint32_t nid1 = (t1 < n1) ? next_ids[t1] : 0u;
+      Row<T, D> x0{}, x1{}, selrow{};
       if (MODE != kModePerm) {
         if (t0 < nb) x0 = load_row<T, D>(a.x, id0);
         if (t1 < nb) x1 = load_row<T, D>(a.x, id1);
@@ -317,7 +365,11 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
         const uint64_t nk0 = (t0 < n1) ? perm_key(nid0, m32, ca.replica, ca.seed) : ~0ull;
         const uint64_t nk1 = (t1 < n1) ? perm_key(nid1, m32, ca.replica, ca.seed) : ~0ull;
         select_smallest(nk0, nid0, t0 < n1, nk1, nid1, t1 < n1, pick, s_sel, s_wkey, s_wid);
-        if (threadIdx.x < static_cast<uint32_t>(pick)) s_selrow[threadIdx.x] = load_row<T, D>(a.x, s_sel[threadIdx.x]);
+        // the lanes of the last warp that step the picked members load their
+        // rows now; the registers are read only at the straddling step
+        const int own = static_cast<int>(end - lo);
+        if (warp == (static_cast<int>(blockDim.x) >> 5) - 1 && lane >= own && lane < own + pick)
+          selrow = load_row<T, D>(a.x, s_sel[lane - own]);
       }
       if (MODE != kModePerm) {
         if (t0 < nb) rows[t0] = x0;
@@ -393,14 +445,14 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
             row = rows[sm.b_j[t]];
           } else if (v) {
             idv = s_sel[lane - own];
-            row = s_selrow[lane - own];
+            row = selrow;
           }
           batch_group_row<T, D, MODE>(a, m32, idv, v, lane < a.p ? lane : 0, own + pick, row);
         }
       }
     } else {
-      // A bucket beyond the shared-memory sort (general mode): rank each
-      // member by counting the members before it.
+      // A bucket beyond the shared-memory sort (general and compact mode):
+      // rank each member by counting the members before it.
       for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
         const uint32_t idj = ca.tmp[s + j];
         const uint64_t kj = perm_key(idj, m32, ca.replica, ca.seed);
@@ -450,11 +502,10 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
 }
 
 // The latency floor of the step kernel's launch shape: the same cooperative
-// launch (grid, block, dynamic shared memory) and the same two bounded grid
-// barriers with no work between them.
+// launch (grid, block, dynamic shared memory) and the same bounded grid
+// barrier (one, as a step in the common case) with no work around it.
 __global__ void __launch_bounds__(kCoopThreads, 1) k_coop_floor(unsigned long long* bar, unsigned long long wait_ns,
                                                                 int32_t* status) {
-  if (!::rbm::grid_barrier(bar, wait_ns, status, false)) return;
   ::rbm::grid_barrier(bar, wait_ns, status, false);
 }
 
@@ -492,6 +543,7 @@ cudaError_t set_attr_d(int* min_blocks) {
 }  // namespace
 
 uint32_t coop_max_buckets() { return 8192; }
+uint32_t coop_slot_capacity() { return kCap; }
 
 cudaError_t launch_coop_floor(const CoopScratch& cs, size_t smem_bytes, uint64_t wait_ns, int32_t* status,
                               cudaStream_t st) {
@@ -541,7 +593,10 @@ cudaError_t launch_coop(const CoopScratch& cs, int d, int mode, const void* para
   const StepParams<T>& a = *static_cast<const StepParams<T>*>(params);
   CoopArgs ca;
   ca.hist = cs.hist;
+  ca.slots = cs.slots;
+  ca.slot_cap = cs.slot_cap;
   ca.tmp = cs.tmp;
+  ca.epoch = cs.epoch;
   ca.perm = cs.perm;
   ca.bar = cs.bar;
   ca.n = a.n;

@@ -107,7 +107,7 @@ void free_scratch(rbm_ctx* c) {
   cudaFree(s.cnt); cudaFree(s.start); cudaFree(s.slots); cudaFree(s.ovf_cnt); cudaFree(s.ovf);
   cudaFree(s.done); cudaFree(s.perm);
   s = PermScratch{};
-  cudaFree(c->cs.hist); cudaFree(c->cs.tmp); cudaFree(c->cs.bar);
+  cudaFree(c->cs.hist); cudaFree(c->cs.slots); cudaFree(c->cs.tmp); cudaFree(c->cs.epoch); cudaFree(c->cs.bar);
   c->cs = CoopScratch{};
   cudaFree(c->bs.order); cudaFree(c->bs.block_begin); cudaFree(c->bs.offs);
   cudaFree(c->bs.tmp); cudaFree(c->bs.perm);
@@ -236,9 +236,15 @@ rbm_status alloc_scratch(rbm_ctx* c) {
     CoopScratch& cs = c->cs;
     cs.grid = grid;
     cs.nbuckets = k * grid;
-    RBM_CUDA(cudaMalloc(&cs.hist, sizeof(uint32_t) * cs.nbuckets));
-    RBM_CUDA(cudaMemset(cs.hist, 0, sizeof(uint32_t) * cs.nbuckets));
+    RBM_CUDA(cudaMalloc(&cs.hist, sizeof(uint32_t) * 2 * cs.nbuckets));
+    RBM_CUDA(cudaMemset(cs.hist, 0, sizeof(uint32_t) * 2 * cs.nbuckets));
+    cs.slot_cap = coop_slot_capacity();
+    if (c->tuning.slot_cap > 0 && static_cast<uint32_t>(c->tuning.slot_cap) < cs.slot_cap)
+      cs.slot_cap = static_cast<uint32_t>(c->tuning.slot_cap);
+    RBM_CUDA(cudaMalloc(&cs.slots, sizeof(uint32_t) * static_cast<size_t>(cs.nbuckets) * cs.slot_cap));
     RBM_CUDA(cudaMalloc(&cs.tmp, sizeof(uint32_t) * n));
+    RBM_CUDA(cudaMalloc(&cs.epoch, sizeof(uint32_t)));
+    RBM_CUDA(cudaMemset(cs.epoch, 0, sizeof(uint32_t)));
     RBM_CUDA(cudaMalloc(&cs.bar, sizeof(unsigned long long)));
     RBM_CUDA(cudaMemset(cs.bar, 0, sizeof(unsigned long long)));
     cs.perm = s.perm;
@@ -853,7 +859,7 @@ rbm_status rbm_get_tuning(const rbm_ctx* ctx, rbm_tuning* tuning) {
   if (!ctx || !tuning) return RBM_ERR_INVALID;
   *tuning = ctx->tuning;
   tuning->bucket_bits = ctx->ps.bucket_bits;
-  tuning->slot_cap = static_cast<int32_t>(ctx->ps.slot_cap);
+  tuning->slot_cap = static_cast<int32_t>(ctx->use_coop ? ctx->cs.slot_cap : ctx->ps.slot_cap);
   tuning->sort_cap = static_cast<int32_t>(ctx->ps.sort_cap);
   tuning->block = ctx->cfg.block;
   tuning->direct_block = ctx->cfg.direct_block;

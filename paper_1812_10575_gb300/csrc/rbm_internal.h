@@ -28,8 +28,11 @@ struct PermScratch {
 
 // Cooperative single-kernel step scratch.
 struct CoopScratch {
-  uint32_t* hist = nullptr;     // [nbuckets] bucket totals, zero between steps
-  uint32_t* tmp = nullptr;      // [n] ids grouped by bucket
+  uint32_t* hist = nullptr;     // [2 nbuckets] bucket totals, two buffers by launch parity (zero initially)
+  uint32_t* slots = nullptr;    // [nbuckets slot_cap] ids grouped by bucket
+  uint32_t slot_cap = 0;        // slots per bucket, at most coop_slot_capacity()
+  uint32_t* tmp = nullptr;      // [n] ids grouped by bucket, compact (bucket overflow only)
+  uint32_t* epoch = nullptr;    // [1] launch counter (zero initially)
   uint32_t* perm = nullptr;     // [n] (shared with PermScratch::perm)
   unsigned long long* bar = nullptr;  // [1] grid barrier arrival counter
   uint32_t grid = 0;            // blocks (one per SM)
@@ -125,6 +128,7 @@ uint32_t max_sort_cap();
 // Cooperative step (coop_step.cu): mode as for launch_rbm_tail.
 cudaError_t prepare_coop_kernels(int* blocks_per_sm);
 uint32_t coop_max_buckets();
+uint32_t coop_slot_capacity();
 size_t coop_smem_bytes(int dtype, int d, uint32_t nbuckets);
 cudaError_t launch_coop_floor(const CoopScratch& cs, size_t smem_bytes, uint64_t wait_ns, int32_t* status,
                               cudaStream_t st);

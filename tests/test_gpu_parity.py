@@ -69,7 +69,8 @@ def test_permutation_bit_exact(n, seed, m, r, path):
                                     dict(path=1, bucket_bits=6, slot_cap=8, sort_cap=4096),  # spill list in smem
                                     dict(path=1, bucket_bits=0, sort_cap=4096),              # one bucket
                                     dict(path=1, bucket_bits=12),                            # separate scan
-                                    dict(path=2)])                                           # cooperative kernel
+                                    dict(path=2),                                            # cooperative kernel
+                                    dict(path=2, slot_cap=8)])                               # ... regrouped compactly
 @pytest.mark.parametrize("p", [2, 5, 40])
 def test_permutation_and_step_under_forced_bucket_paths(tuning, p):
     n, d = 3000, 2
@@ -381,6 +382,30 @@ def test_invalid_parameters_rejected():
         with pytest.raises(rbm.RbmError) as e:
             rbm.System(x if d == 1 else torch.zeros(100, d, device="cuda", dtype=torch.float64), d=d, **kw)
         assert e.value.status == -1
+
+
+def test_cooperative_compact_regrouping_equals_slots():
+    """Buckets that outgrow their slots (slot_cap forced small) take the
+    compact regrouping behind one more grid barrier; six steps, launches
+    alternating the bucket-total buffers, must equal the default run bit for
+    bit, and the permutation must stay the oracle's."""
+    torch = torch_cuda()
+    n, d = 60000, 3
+    X = as_run_precision(workloads.gaussian(n, d, seed=5), "f32")
+    kw = dict(p=2, dt=1e-3, sigma=0.2, v="quadratic", k="reg_attract", k_param=0.01, seed=8)
+    a, xa = _system(X, d, "f32", **kw)
+    b, xb = _system(X, d, "f32", **kw)
+    a.set_tuning(path=2)
+    b.set_tuning(path=2, slot_cap=100)
+    assert a.tuning()["slot_cap"] == 2048 and b.tuning()["slot_cap"] == 100
+    for _ in range(6):
+        a.step()
+        b.step()
+    assert torch.equal(xa, xb)
+    b.m = 4
+    perm = b.permutation().cpu().numpy().view(np.uint32)
+    b.sync()
+    assert np.array_equal(perm, oracle.permutation(_oprm(n, d, "f32", **kw), 4))
 
 
 def test_cooperative_barrier_wait_runs_out_and_is_reported():
