@@ -274,6 +274,9 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_sort_step(PermArgs pa, 
       const uint32_t t = threadIdx.x + k * kSortThreads;
       if (t < nb) {
         idr[k] = (t < nslot) ? pa.slots[static_cast<size_t>(b) * pa.slot_cap + t] : sid[t];
+        // the member's position row is read when its batch is stepped, after
+        // the sort: start bringing it into L2 now
+        if (MODE != kModePerm) prefetch_l2(a.x + static_cast<size_t>(idr[k]) * Ld<D>::value);
         key[k] = perm_key(idr[k], m32, pa.replica, pa.seed);
         const uint32_t sub = sub_of(key[k], pa.bits);
         subr[k] = sub | (atomicAdd(&ssub[sub], 1u) << 16);

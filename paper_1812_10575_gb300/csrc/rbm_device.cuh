@@ -87,6 +87,11 @@ __device__ __forceinline__ void brownian(uint32_t id, uint32_t m32, uint32_t rep
   }
 }
 
+// Hint: bring the line holding *p into L2 (no value is returned, nothing waits).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // ---------------------------------------------------------------------------
 // Positions: row i of the N x ld array, ld = D (D = 1, 2) or 4 (D = 3).
 // ---------------------------------------------------------------------------

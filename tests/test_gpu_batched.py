@@ -91,6 +91,37 @@ def test_batched_fp32_per_step_opinion_workload():
         cur = got
 
 
+def test_batched_full_opinion_workload_sampled():
+    """The full batched workload as the benchmark times it: 4096 replicas of
+    log-uniform size in [256, 65536] (5.1e7 particles, FP32, d = 2), with the
+    launch shape the autotuner picks there (1024 threads, mean buckets of
+    1024).  Permutations of 64 sampled replicas (the largest and the smallest
+    among them) bit-exact, and one step of 24 of them within the FP32 bar."""
+    torch_cuda()
+    sizes = _sizes(4096, 256, 65536, seed=0)
+    kw = dict(p=2, seed=0, **OPINION)
+    rep, x, X = _replicas(sizes, 2, "f32", **kw)
+    rep.set_launch(1024, 1024)
+    perm = rep.permutation().cpu().numpy().view(np.uint32)
+    rep.step()
+    rep.sync()
+    got = from_dev(x, 2)
+    order = np.argsort(sizes)
+    pick = sorted(set(order[::64].tolist()) | {int(order[0]), int(order[-1])})
+    slices = _slices(sizes)
+    for k, r in enumerate(pick):
+        lo, hi = slices[r]
+        prm = oracle.make_params(hi - lo, 2, p=2, dt=OPINION["dt"], sigma=OPINION["sigma"], seed=0,
+                                 k="bounded_conf", k_param=0.25, replica=r, precision="f32")
+        expect = oracle.permutation(prm, 0)
+        assert np.array_equal(perm[lo:hi], expect), f"replica {r} (N={hi - lo})"
+        if k % 3 == 0 or r in (int(order[0]), int(order[-1])):
+            FK = oracle.rbm_interaction(prm, X[lo:hi], expect)
+            ref = oracle.euler_update(prm, X[lo:hi], FK, 0)
+            extra = 32.0 * EPS32 * prm.dt * np.linalg.norm(FK, axis=1)
+            assert_close_per_particle(got[lo:hi], ref, 1e-5, extra=extra, what=f"replica {r}")
+
+
 @pytest.mark.parametrize("p,bucket_target", [(8, 64), (32, 64), (4, 2048)])
 def test_batched_bucket_shapes_fp64(p, bucket_target):
     """Small buckets (a batch straddles almost every bucket boundary, stepped
