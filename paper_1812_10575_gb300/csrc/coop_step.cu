@@ -20,7 +20,7 @@
 //            global position of each bucket in the permutation);
 //   phase 3: block c takes buckets c, c + G, ...: loads the members' ids and
 //            positions into shared memory, sorts them (a counting sort by the
-//            next 11 key bits, then insertion sort of the few ids sharing a
+//            next 10 key bits, then insertion sort of the few ids sharing a
 //            sub-bucket by (key, id)), writes that stretch of the permutation
 //            and steps every batch lying wholly inside the bucket.  The batch
 //            that straddles the bucket's right boundary is stepped by the
