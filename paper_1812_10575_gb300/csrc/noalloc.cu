@@ -129,7 +129,7 @@ extern "C" rbm_status rbm_permutation_noalloc(int64_t n, uint64_t seed, uint32_t
   a.replica = replica;
   a.m_ptr = nullptr;
   a.m_off = m;
-  launch_rbm_tail<float>(ps, 1, /*mode: permutation only*/ 0, &a, cfg, st);
+  launch_rbm_tail<float>(ps, 1, /*mode: permutation only*/ 0, &a, false, cfg, st);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     char msg[160];

@@ -22,6 +22,10 @@
 // block to finish (few buckets) or by k_straddle_fixup (many buckets).  They
 // read only positions no other batch writes, so every update uses the
 // positions of step m as the explicit scheme requires.
+// The random division of a step depends on the step index alone, not on the
+// positions: with a double-buffered scratch (buffer m mod 2 for step m), the
+// sort kernel of step m can also bucket the ids of step m + 1 (lookahead), so
+// that a run of steps needs no k_bucket_scatter launch after its first.
 #include <cstdio>
 
 #include "rbm_batch.cuh"
@@ -48,12 +52,14 @@ __device__ __forceinline__ uint32_t sub_of(uint64_t key, int bits) {
 }
 
 struct PermArgs {
-  uint32_t* cnt;
+  uint32_t* cnt;                // buffer 0; buffer 1 follows each array (double_buffer)
   uint32_t* start;
   uint32_t* slots;
   uint32_t* ovf_cnt;
   uint32_t* ovf;
   uint32_t* done;
+  int double_buffer;
+  int lookahead;                // the sort kernel also buckets the ids of step m + 1
   uint32_t* perm;
   uint32_t n;
   int bits;
@@ -75,11 +81,38 @@ __device__ __forceinline__ uint32_t perm_step_index(const PermArgs& a) {
   return static_cast<uint32_t>(static_cast<uint64_t>(m));
 }
 
+// The scratch of step m: buffer m mod 2 of a double-buffered scratch.
+__device__ __forceinline__ PermArgs for_step(PermArgs a, uint32_t m32) {
+  if (a.double_buffer && (m32 & 1u)) {
+    a.cnt += a.nbuckets;
+    a.start += a.nbuckets;
+    a.slots += static_cast<size_t>(a.nbuckets) * a.slot_cap;
+    a.ovf_cnt += 1;
+    a.ovf += a.n;
+    a.done += 1;
+  }
+  return a;
+}
+
+// Id i of step m32 into its bucket's next slot, or the spill list.
+__device__ __forceinline__ void scatter_one(const PermArgs& a, uint32_t i, uint32_t m32) {
+  const uint64_t key = perm_key(i, m32, a.replica, a.seed);
+  const uint32_t b = bucket_of(key, a.bits);
+  const uint32_t pos = atomicAdd(&a.cnt[b], 1u);
+  if (pos < a.slot_cap) {
+    a.slots[static_cast<size_t>(b) * a.slot_cap + pos] = i;
+  } else {
+    const uint32_t o = atomicAdd(a.ovf_cnt, 1u);  // o < n: the list holds every particle
+    a.ovf[o] = i;
+  }
+}
+
 PermArgs make_perm_args(const PermScratch& ps, uint32_t n, uint2 seed, uint32_t replica, const int64_t* m_ptr,
                         int64_t m_off) {
   PermArgs a;
   a.cnt = ps.cnt; a.start = ps.start; a.slots = ps.slots; a.ovf_cnt = ps.ovf_cnt; a.ovf = ps.ovf;
   a.done = ps.done; a.perm = ps.perm; a.n = n; a.bits = ps.bucket_bits; a.nbuckets = ps.nbuckets;
+  a.double_buffer = ps.double_buffer ? 1 : 0; a.lookahead = 0;
   a.slot_cap = ps.slot_cap; a.sort_cap = ps.sort_cap; a.separate_scan = ps.separate_scan ? 1 : 0;
   a.seed = seed; a.replica = replica; a.m_ptr = m_ptr; a.m_off = m_off; a.skip = ps.skip;
   return a;
@@ -88,26 +121,18 @@ PermArgs make_perm_args(const PermScratch& ps, uint32_t n, uint2 seed, uint32_t 
 // ---------------------------------------------------------------------------
 // Pass 1: bucket every particle by the top bits of its key.
 // ---------------------------------------------------------------------------
-__global__ void k_bucket_scatter(PermArgs a) {
-  if (perm_skipped(a)) return;
-  const uint32_t m32 = perm_step_index(a);
+__global__ void k_bucket_scatter(PermArgs pa_in) {
+  if (perm_skipped(pa_in)) return;
+  const uint32_t m32 = perm_step_index(pa_in);
+  const PermArgs a = for_step(pa_in, m32);
   const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    const uint64_t key = perm_key(i, m32, a.replica, a.seed);
-    const uint32_t b = bucket_of(key, a.bits);
-    const uint32_t pos = atomicAdd(&a.cnt[b], 1u);
-    if (pos < a.slot_cap) {
-      a.slots[static_cast<size_t>(b) * a.slot_cap + pos] = i;
-    } else {
-      const uint32_t o = atomicAdd(a.ovf_cnt, 1u);  // o < n: the list holds every particle
-      a.ovf[o] = i;
-    }
-  }
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) scatter_one(a, i, m32);
 }
 
 // Exclusive scan of the bucket counts by one block (many-bucket case).
-__global__ void k_bucket_scan(PermArgs a) {
-  if (perm_skipped(a)) return;
+__global__ void k_bucket_scan(PermArgs pa_in) {
+  if (perm_skipped(pa_in)) return;
+  const PermArgs a = for_step(pa_in, perm_step_index(pa_in));
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_carry;
   if (threadIdx.x == 0) s_carry = 0;
@@ -228,18 +253,26 @@ __device__ void step_straddling(const StepParams<T>& a, uint32_t m32, const Perm
 // Pass 2: one block per bucket.
 // ---------------------------------------------------------------------------
 template <typename T, int D, int MODE>
-__global__ void __launch_bounds__(kSortThreads) k_bucket_sort_step(PermArgs pa, StepParams<T> a) {
+__global__ void __launch_bounds__(kSortThreads) k_bucket_sort_step(PermArgs pa_in, StepParams<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t* skey = reinterpret_cast<uint64_t*>(smem_raw);       // [sort_cap] keys, sorted
-  uint32_t* sid = reinterpret_cast<uint32_t*>(skey + pa.sort_cap);  // [sort_cap] ids, sorted
-  uint32_t* ssub = sid + pa.sort_cap;                            // [kSub] sub-bucket counts, then starts
+  uint32_t* sid = reinterpret_cast<uint32_t*>(skey + pa_in.sort_cap);  // [sort_cap] ids, sorted
+  uint32_t* ssub = sid + pa_in.sort_cap;                          // [kSub] sub-bucket counts, then starts
   __shared__ uint32_t s_red[32];
   __shared__ uint32_t s_fill;
   __shared__ int s_last;
-  if (perm_skipped(pa)) return;
+  if (perm_skipped(pa_in)) return;
 
   const uint32_t b = blockIdx.x;
-  const uint32_t m32 = perm_step_index(pa);
+  const uint32_t m32 = perm_step_index(pa_in);
+  const PermArgs pa = for_step(pa_in, m32);
+  if (pa_in.lookahead) {
+    // bucket this block's share of the ids for step m + 1 (the other buffer)
+    const PermArgs nx = for_step(pa_in, m32 + 1u);
+    const uint32_t chunk = (pa.n + gridDim.x - 1) / gridDim.x;
+    const uint32_t i0 = min(pa.n, b * chunk), i1 = min(pa.n, i0 + chunk);
+    for (uint32_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) scatter_one(nx, i, m32 + 1u);
+  }
 
   uint32_t start;
   if (pa.separate_scan) {
@@ -368,9 +401,10 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_sort_step(PermArgs pa, 
 
 // Many-bucket case: straddling batches over a grid, then the spill counter reset.
 template <typename T, int D, int MODE>
-__global__ void __launch_bounds__(256) k_straddle_fixup(PermArgs pa, StepParams<T> a) {
-  if (perm_skipped(pa)) return;
-  const uint32_t m32 = perm_step_index(pa);
+__global__ void __launch_bounds__(256) k_straddle_fixup(PermArgs pa_in, StepParams<T> a) {
+  if (perm_skipped(pa_in)) return;
+  const uint32_t m32 = perm_step_index(pa_in);
+  const PermArgs pa = for_step(pa_in, m32);
   const int gpw = 32 / a.p;
   const uint32_t per_block = static_cast<uint32_t>(gpw * (blockDim.x >> 5));
   if (MODE != kModePerm)
@@ -430,8 +464,10 @@ size_t sort_smem_bytes(uint32_t sort_cap) {
 }
 
 template <typename T, int D>
-void launch_tail_d(const PermScratch& ps, int mode, const StepParams<T>& a, const LaunchCfg& cfg, cudaStream_t st) {
-  const PermArgs pa = make_perm_args(ps, a.n, a.seed, a.replica, a.m_ptr, a.m_off);
+void launch_tail_d(const PermScratch& ps, int mode, const StepParams<T>& a, bool lookahead, const LaunchCfg& cfg,
+                   cudaStream_t st) {
+  PermArgs pa = make_perm_args(ps, a.n, a.seed, a.replica, a.m_ptr, a.m_off);
+  pa.lookahead = (lookahead && ps.double_buffer) ? 1 : 0;
   const size_t smem = sort_smem_bytes(ps.sort_cap);
   const bool small_p = a.p <= 32;
   const int block = kSortThreads;
@@ -475,16 +511,18 @@ void launch_bucket_scatter(const PermScratch& ps, uint32_t n, uint2 seed, uint32
 }
 
 template <typename T>
-void launch_rbm_tail(const PermScratch& ps, int d, int mode, const void* params, const LaunchCfg& cfg,
+void launch_rbm_tail(const PermScratch& ps, int d, int mode, const void* params, bool lookahead, const LaunchCfg& cfg,
                      cudaStream_t st) {
   const StepParams<T>& a = *static_cast<const StepParams<T>*>(params);
-  if (d == 1) launch_tail_d<T, 1>(ps, mode, a, cfg, st);
-  else if (d == 2) launch_tail_d<T, 2>(ps, mode, a, cfg, st);
-  else launch_tail_d<T, 3>(ps, mode, a, cfg, st);
+  if (d == 1) launch_tail_d<T, 1>(ps, mode, a, lookahead, cfg, st);
+  else if (d == 2) launch_tail_d<T, 2>(ps, mode, a, lookahead, cfg, st);
+  else launch_tail_d<T, 3>(ps, mode, a, lookahead, cfg, st);
 }
 
-template void launch_rbm_tail<float>(const PermScratch&, int, int, const void*, const LaunchCfg&, cudaStream_t);
-template void launch_rbm_tail<double>(const PermScratch&, int, int, const void*, const LaunchCfg&, cudaStream_t);
+template void launch_rbm_tail<float>(const PermScratch&, int, int, const void*, bool, const LaunchCfg&,
+                                     cudaStream_t);
+template void launch_rbm_tail<double>(const PermScratch&, int, int, const void*, bool, const LaunchCfg&,
+                                      cudaStream_t);
 
 uint32_t max_sort_cap() { return kSortCapMax; }
 

@@ -48,6 +48,7 @@ struct rbm_ctx {
   int64_t sur_graph_len = 0;
   int batched_blocks_per_sm = 0;
   bool use_coop = false;
+  int64_t prepared_m = -1;   // bucket-sort path: the step whose bucket buffer is filled (-1: none)
   bool use_small = false;       // N <= 2048: the whole step in one block (the replica kernel)
   int coop_blocks_per_sm = 0;
   LaunchCfg cfg;
@@ -170,20 +171,24 @@ rbm_status alloc_scratch(rbm_ctx* c) {
   if (sc < 2) sc = 2;
   s.sort_cap = sc;
   s.separate_scan = s.nbuckets > 1024;
-  RBM_CUDA(cudaMalloc(&s.cnt, sizeof(uint32_t) * s.nbuckets));
-  RBM_CUDA(cudaMalloc(&s.start, sizeof(uint32_t) * s.nbuckets));
-  RBM_CUDA(cudaMalloc(&s.slots, sizeof(uint32_t) * static_cast<size_t>(s.nbuckets) * s.slot_cap));
-  RBM_CUDA(cudaMalloc(&s.ovf_cnt, sizeof(uint32_t)));
-  RBM_CUDA(cudaMalloc(&s.ovf, sizeof(uint32_t) * n));
-  RBM_CUDA(cudaMalloc(&s.done, sizeof(uint32_t)));
+  // two buffers: step m uses buffer m mod 2, and a step's sort kernel may
+  // bucket the next step's ids into the other one
+  s.double_buffer = true;
+  RBM_CUDA(cudaMalloc(&s.cnt, sizeof(uint32_t) * 2 * s.nbuckets));
+  RBM_CUDA(cudaMalloc(&s.start, sizeof(uint32_t) * 2 * s.nbuckets));
+  RBM_CUDA(cudaMalloc(&s.slots, sizeof(uint32_t) * 2 * static_cast<size_t>(s.nbuckets) * s.slot_cap));
+  RBM_CUDA(cudaMalloc(&s.ovf_cnt, sizeof(uint32_t) * 2));
+  RBM_CUDA(cudaMalloc(&s.ovf, sizeof(uint32_t) * 2 * static_cast<size_t>(n)));
+  RBM_CUDA(cudaMalloc(&s.done, sizeof(uint32_t) * 2));
   RBM_CUDA(cudaMalloc(&s.perm, sizeof(uint32_t) * n));
   RBM_CUDA(cudaMalloc(&c->xtmp, c->row_bytes * n));
   // Partial sums of the split direct sum: up to 64 chunks of N rows, at most 2^24 rows.
   c->partial_rows = std::min<size_t>(static_cast<size_t>(n) * 64, size_t(1) << 24);
   RBM_CUDA(cudaMalloc(&c->partial, c->row_bytes * c->partial_rows));
-  RBM_CUDA(cudaMemset(s.cnt, 0, sizeof(uint32_t) * s.nbuckets));
-  RBM_CUDA(cudaMemset(s.ovf_cnt, 0, sizeof(uint32_t)));
-  RBM_CUDA(cudaMemset(s.done, 0, sizeof(uint32_t)));
+  RBM_CUDA(cudaMemset(s.cnt, 0, sizeof(uint32_t) * 2 * s.nbuckets));
+  RBM_CUDA(cudaMemset(s.ovf_cnt, 0, sizeof(uint32_t) * 2));
+  RBM_CUDA(cudaMemset(s.done, 0, sizeof(uint32_t) * 2));
+  c->prepared_m = -1;
   c->cfg.block = c->tuning.block > 0 ? c->tuning.block : 256;
   c->cfg.direct_block = c->tuning.direct_block > 0 ? c->tuning.direct_block : 256;
 
@@ -285,6 +290,33 @@ uint2 seed_of(const rbm_ctx* c) {
   return make_uint2(static_cast<uint32_t>(c->prm.seed), static_cast<uint32_t>(c->prm.seed >> 32));
 }
 
+bool uses_bucket_path(const rbm_ctx* c) { return !c->batched && !c->use_small && !c->use_coop; }
+
+// Bucket-sort path: clear the filled buffer (if any), so that both are clean.
+rbm_status forget_prepared(rbm_ctx* c, cudaStream_t st) {
+  if (c->prepared_m < 0 || !uses_bucket_path(c)) {
+    c->prepared_m = -1;
+    return RBM_OK;
+  }
+  const size_t par = static_cast<size_t>(c->prepared_m & 1);
+  RBM_CUDA(cudaMemsetAsync(c->ps.cnt + par * c->ps.nbuckets, 0, sizeof(uint32_t) * c->ps.nbuckets, st));
+  RBM_CUDA(cudaMemsetAsync(c->ps.ovf_cnt + par, 0, sizeof(uint32_t), st));
+  c->prepared_m = -1;
+  return RBM_OK;
+}
+
+// Bucket-sort path, before a captured run of RBM steps from step m: fill
+// step m's buffer unless the previous call did.
+rbm_status prepare_bucket_path(rbm_ctx* c, int64_t m, cudaStream_t st) {
+  if (!uses_bucket_path(c) || c->prepared_m == m) return RBM_OK;
+  rbm_status fs = forget_prepared(c, st);
+  if (fs != RBM_OK) return fs;
+  launch_bucket_scatter(c->ps, static_cast<uint32_t>(c->prm.n), seed_of(c), c->prm.replica, nullptr, m, c->cfg, st);
+  RBM_CUDA(cudaGetLastError());
+  c->prepared_m = m;
+  return RBM_OK;
+}
+
 // Enqueue one RBM step (mode 1), the permutation only (0) or the forces (2).
 rbm_status enqueue_rbm(rbm_ctx* c, int mode, const int64_t* m_ptr, int64_t m_off, void* fout, cudaStream_t st,
                        const int* skip = nullptr) {
@@ -334,21 +366,37 @@ rbm_status enqueue_rbm(rbm_ctx* c, int mode, const int64_t* m_ptr, int64_t m_off
     }
     return RBM_OK;
   }
+  // Bucket-sort path.  A step (not a permutation or force query, not a
+  // step gated by the surrogate's flag) also buckets the ids of the next step
+  // (lookahead).  Eager calls skip the scatter when the previous call filled
+  // this step's buffer; a captured run of steps relies on the host to fill
+  // its first step's buffer before each replay (prepare_bucket_path).
+  const bool lookahead = (mode == 1) && skip == nullptr;
   c->ps.skip = skip;
-  launch_bucket_scatter(c->ps, static_cast<uint32_t>(c->prm.n), seed_of(c), c->prm.replica, m_ptr, m_off, c->cfg,
-                        st);
+  if (m_ptr == nullptr) {
+    if (skip != nullptr || c->prepared_m != m_off) {
+      rbm_status fs = forget_prepared(c, st);
+      if (fs != RBM_OK) return fs;
+      launch_bucket_scatter(c->ps, static_cast<uint32_t>(c->prm.n), seed_of(c), c->prm.replica, nullptr, m_off,
+                            c->cfg, st);
+    }
+  } else if (!lookahead) {
+    launch_bucket_scatter(c->ps, static_cast<uint32_t>(c->prm.n), seed_of(c), c->prm.replica, m_ptr, m_off, c->cfg,
+                          st);
+  }
   if (c->prm.dtype == RBM_F32) {
     StepParams<float> a = step_params<float>(c, m_ptr, m_off);
     a.fout = static_cast<float*>(fout);
     a.skip = skip;
-    launch_rbm_tail<float>(c->ps, c->prm.d, mode, &a, c->cfg, st);
+    launch_rbm_tail<float>(c->ps, c->prm.d, mode, &a, lookahead, c->cfg, st);
   } else {
     StepParams<double> a = step_params<double>(c, m_ptr, m_off);
     a.fout = static_cast<double*>(fout);
     a.skip = skip;
-    launch_rbm_tail<double>(c->ps, c->prm.d, mode, &a, c->cfg, st);
+    launch_rbm_tail<double>(c->ps, c->prm.d, mode, &a, lookahead, c->cfg, st);
   }
   c->ps.skip = nullptr;
+  if (m_ptr == nullptr) c->prepared_m = lookahead ? m_off + 1 : -1;
   RBM_CUDA(cudaGetLastError());
   return RBM_OK;
 }
@@ -746,6 +794,8 @@ rbm_status rbm_run(rbm_ctx* ctx, int64_t steps, int32_t method) {
           if (st != RBM_OK) return st;
         }
         if (ctx->m_dev_value != ctx->m) launch_set_i64(ctx->m_dev, ctx->m, ctx->stream);
+        st = forget_prepared(ctx, ctx->stream);  // its RBM steps scatter their own ids
+        if (st != RBM_OK) return st;
         RBM_CUDA(cudaGraphLaunch(ctx->sur_graph, ctx->stream));
         ctx->m += cycle;
         ctx->m_dev_value = ctx->m;
@@ -769,9 +819,14 @@ rbm_status rbm_run(rbm_ctx* ctx, int64_t steps, int32_t method) {
       if (st != RBM_OK) return st;
     }
     if (ctx->m_dev_value != ctx->m) launch_set_i64(ctx->m_dev, ctx->m, ctx->stream);
+    if (method == RBM_METHOD_RBM) {
+      st = prepare_bucket_path(ctx, ctx->m, ctx->stream);
+      if (st != RBM_OK) return st;
+    }
     RBM_CUDA(cudaGraphLaunch(ctx->graph[method], ctx->stream));
     ctx->m += len;
     ctx->m_dev_value = ctx->m;
+    if (method == RBM_METHOD_RBM && uses_bucket_path(ctx)) ctx->prepared_m = ctx->m;  // the last step's lookahead
     steps -= len;
   }
   for (; steps > 0; --steps) {

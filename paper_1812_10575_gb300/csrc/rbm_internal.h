@@ -11,12 +11,15 @@ namespace rbm {
 
 // Permutation scratch (one particle system or one replica set).
 struct PermScratch {
+  // Each of cnt .. done holds two buffers when double_buffer is set (step m
+  // uses buffer m mod 2; buffer 1 follows buffer 0 in each array).
   uint32_t* cnt = nullptr;      // [nbuckets] members per bucket (zero between steps)
   uint32_t* start = nullptr;    // [nbuckets] first sorted position of each bucket
   uint32_t* slots = nullptr;    // [nbuckets * slot_cap] member ids, bucket-major
   uint32_t* ovf_cnt = nullptr;  // [1] members that did not fit their bucket's slots
   uint32_t* ovf = nullptr;      // [n] those members' ids
   uint32_t* done = nullptr;     // [1] finished-block ticket (last block runs the fix-up)
+  bool double_buffer = false;
   uint32_t* perm = nullptr;     // [n] the random permutation of this step
   int bucket_bits = 0;
   uint32_t nbuckets = 1;
@@ -116,7 +119,8 @@ inline void mark_launch(const LaunchCfg& cfg, cudaStream_t st, const char* name)
 void launch_bucket_scatter(const PermScratch& ps, uint32_t n, uint2 seed, uint32_t replica, const int64_t* m_ptr,
                            int64_t m_off, const LaunchCfg& cfg, cudaStream_t st);
 template <typename T>
-void launch_rbm_tail(const PermScratch& ps, int d, int mode, const void* params, const LaunchCfg& cfg, cudaStream_t st);
+void launch_rbm_tail(const PermScratch& ps, int d, int mode, const void* params, bool lookahead, const LaunchCfg& cfg,
+                     cudaStream_t st);
 void set_last_error_text(const char* text);  // text returned by rbm_last_error()
 cudaError_t prepare_rbm_kernels();  // per-device kernel attributes, called by rbm_init
 void launch_set_i64(int64_t* dst, int64_t value, cudaStream_t st);
