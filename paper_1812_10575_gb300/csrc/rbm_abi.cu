@@ -145,7 +145,9 @@ uint32_t next_pow2(uint32_t v) {
   return p;
 }
 
-// Bucket geometry: about 512 members per bucket by default; slots hold the
+// Bucket geometry: about 1024 members per bucket by default (measured at
+// N = 2^24 with the lookahead scatter: 796 us per step against 907 us with
+// 512 and 1161 us with 256; even at 2^22); slots hold the
 // mean plus eight standard deviations plus 64, the shared-memory sort twice
 // that (power of two, at most max_sort_cap()); members beyond either bound take the
 // spill list and the counting fallback, so any bucket size stays correct.
@@ -155,7 +157,7 @@ rbm_status alloc_scratch(rbm_ctx* c) {
   int bits = c->tuning.bucket_bits;
   if (bits <= 0) {
     bits = 0;
-    while (bits < 22 && (static_cast<uint64_t>(n) >> bits) > 512) ++bits;
+    while (bits < 22 && (static_cast<uint64_t>(n) >> bits) > 1024) ++bits;
   }
   if (bits > 24) bits = 24;
   s.bucket_bits = bits;
