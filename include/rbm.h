@@ -181,7 +181,11 @@ rbm_status rbm_step(rbm_ctx *ctx);
 rbm_status rbm_direct_step(rbm_ctx *ctx);
 
 /* `steps` steps of `method`, launched as CUDA graphs of graph_steps steps
- * (captured on first use, replayed afterwards) plus eager remainder steps. */
+ * (captured on first use, replayed afterwards) plus eager remainder steps.
+ * On the bucket-sort path (1) each RBM step's sort kernel also buckets the
+ * ids of the next step (the random division depends on the step index
+ * only), so a graph needs one bucket-scatter launch, before its first step,
+ * and none when the previous call ended at the same step index. */
 rbm_status rbm_run(rbm_ctx *ctx, int64_t steps, int32_t method);
 
 /* End to end from host memory: copy N x ld positions from x_host (pinned for
