@@ -473,13 +473,13 @@ def run_single(args, w, g):
         "wall_s_timed_region": wall, "kernel_sources": digest,
     }
     if sysm.tuning()["path"] == 2:
-        # the cooperative launch shape with no work: one grid barrier
+        # the cooperative launch shape with no work (a step waits at no grid barrier)
         floor_us = sysm.latency_floor()
         kern_us = 1e3 * avg.get("k_rbm_coop", 0.0)
         line["latency_floor"] = {"floor_us": floor_us, "kernel_us": kern_us,
                                  "frac": floor_us / kern_us if kern_us > 0 else None,
-                                 "what": "same cooperative launch (grid, block, shared memory) and the same "
-                                         "bounded grid barrier with no work; frac = floor / step kernel"}
+                                 "what": "same cooperative launch (grid, block, shared memory) with no work (the "
+                                         "step waits at no grid barrier); frac = floor / step kernel"}
     sysm.close()
     if w.get("quality_steps"):
         line["quality"] = _thomson_quality(g, w, kw)

@@ -160,10 +160,10 @@ typedef struct {
     int32_t wait_limit_us;/* bound of a grid-barrier wait in the cooperative
                              kernel (0 = 1 second); a wait that runs out
                              latches RBM_ERR_TIMEOUT                           */
-    int32_t test_skip_arrival; /* test hook, 0 or 1: block 0 of the next
-                             cooperative step leaves without arriving at the
-                             first barrier, so the other blocks' bounded waits
-                             run out (exercises RBM_ERR_TIMEOUT)              */
+    int32_t test_skip_arrival; /* test hook, 0 or 1: the next cooperative
+                             step first waits at a grid barrier that block 0
+                             leaves without arriving at, so the other blocks'
+                             bounded waits run out (exercises RBM_ERR_TIMEOUT) */
 } rbm_tuning;
 
 /* Create a context for one particle system whose positions live at x_dev
@@ -278,8 +278,8 @@ rbm_status rbm_step_profiled(rbm_ctx *ctx, int32_t method, float *kernel_ms, int
 /* The latency floor of the cooperative RBM-1 step's launch shape: the mean
  * time (microseconds, 20 back-to-back launches after one warm-up, CUDA events
  * on the context's stream) of the same cooperative launch (grid, block,
- * dynamic shared memory) doing only the one bounded grid barrier of a step
- * (common case: no bucket overflow, no general mode).  The
+ * dynamic shared memory) doing nothing: a step in the common case (no
+ * bucket overflow, no general mode) waits at no grid barrier.  The
  * benchmark sets it beside the step kernel's time.  RBM_ERR_STATE when the
  * context does not use the cooperative kernel.  Synchronous. */
 rbm_status rbm_latency_floor(rbm_ctx *ctx, float *us);

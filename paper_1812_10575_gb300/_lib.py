@@ -419,7 +419,7 @@ def rbm_surrogate_load(ctx, state: bytes) -> None:
 
 
 def rbm_latency_floor(ctx) -> float:
-    """Microseconds of the cooperative step's launch shape with no work (one grid barrier)."""
+    """Microseconds of the cooperative step's launch shape with no work (a step in the common case waits at no grid barrier)."""
     us = ctypes.c_float()
     _check(load().rbm_latency_floor(ctx, ctypes.byref(us)), "rbm_latency_floor")
     return us.value

@@ -1,21 +1,23 @@
 // RBM-1 step as one cooperative persistent kernel (systems of up to about
-// eight million particles): one block per SM, all blocks resident, one
-// grid-wide barrier per step in the common case and no atomics outside shared
-// memory except one per (block, bucket).
+// eight million particles): one block per SM, all blocks resident, no
+// grid-wide barrier in the common case and no atomics outside shared memory
+// except one per (block, bucket).
 //
 // The random division is the id list sorted by the 64-bit Philox key with an
 // id tie-break (Algorithm "randomdiv", Sec. 2.1 of arXiv:1812.10575; any
 // uniform shuffle serves and this one is reproducible).  Keys are spread over
 // B = k * gridDim buckets by the monotone map bucket = floor(key * B / 2^64),
 // so concatenating the buckets in order after sorting each one gives the
-// global order.  Per step:
-//   phase 1: every block histograms the buckets of its contiguous id range
-//            (shared-memory counters), reserves its stretch of each bucket
-//            with one global atomicAdd per bucket (the order of blocks inside
-//            a bucket is arbitrary: phase 3 sorts every bucket completely)
-//            and scatters its ids into the buckets' slots (kCap per bucket
-//            by default);
-//   barrier
+// global order.  The random division depends on the step index only, so the
+// bucketing of step m + 1 runs at the end of step m's launch (lookahead) and
+// the launch boundary orders it before its use; a run's first step is
+// bucketed by a launch of its own (prologue).  Per step:
+//   phase 1 (of step m + 1, or the prologue): every block histograms the
+//            buckets of its contiguous id range (shared-memory counters),
+//            reserves its stretch of each bucket with one global atomicAdd
+//            per bucket (the order of blocks inside a bucket is arbitrary:
+//            phase 3 sorts every bucket completely) and scatters its ids into
+//            the buckets' slots (kCap per bucket by default);
 //   phase 2: every block scans the bucket totals into bucket starts (the
 //            global position of each bucket in the permutation);
 //   phase 3: block c takes buckets c, c + G, ...: loads the members' ids and
@@ -32,12 +34,13 @@
 // barrier and a phase 4 step those batches, one warp each, from the
 // permutation in global memory.  A bucket that outgrows its slots (with
 // kCap slots, a deviation of many standard deviations from the mean of about
-// 1024) makes
-// every block regroup its ids compactly at the bucket starts behind one more
-// barrier before phase 3.  The bucket totals are double-buffered by the
-// parity of a launch counter, so each launch clears the buffer the previous
-// launch used and no barrier is spent on clearing.  Every update reads the positions of step m
-// only (explicit scheme); no particle is written by two blocks.  Barrier
+// 1024) makes every block regroup its ids compactly at the bucket starts
+// behind two barriers before phase 3.  The bucket totals come in three
+// buffers (step m uses buffer m mod 3): the launch of step m reads its own,
+// fills step m + 1's and clears step m + 2's, which the launch of step m - 1
+// read, so no barrier is spent on clearing.  Slots come in two buffers
+// (m mod 2).  Every update reads the positions of step m only (explicit
+// scheme); no particle is written by two blocks.  Barrier
 // waits are bounded by wall time; a wait that runs out latches
 // RBM_ERR_TIMEOUT and the kernel returns.
 #include "rbm_batch.cuh"
@@ -55,11 +58,10 @@ constexpr uint32_t kCap = 2048;            // largest bucket sorted in shared me
 constexpr int kMaxAdjacentPick = 7;        // straddling batches handled in phase 3 need <= 7 picks
 
 struct CoopArgs {
-  uint32_t* hist;              // [2 B] bucket totals, two buffers by launch parity
-  uint32_t* slots;             // [B slot_cap] ids grouped by bucket
+  uint32_t* hist;              // [3 B] bucket totals, buffer m mod 3 for step m
+  uint32_t* slots;             // [2 B slot_cap] ids grouped by bucket, buffer m mod 2
   uint32_t slot_cap;           // slots per bucket (<= kCap)
   uint32_t* tmp;               // [N] ids grouped by bucket, compact (bucket overflow only)
-  uint32_t* epoch;             // [1] launch counter: its parity selects the hist buffer
   uint32_t* perm;              // [N] the permutation
   unsigned long long* bar;     // [1] barrier arrival counter (monotonic)
   uint32_t n;
@@ -67,8 +69,11 @@ struct CoopArgs {
   uint2 seed;
   uint32_t replica;
   unsigned long long wait_ns;  // bound of one barrier wait
-  int skip_arrival;            // test hook: block 0 leaves without arriving at the first barrier
-  int64_t* m_bump;             // graph replay: step counter block 0 advances once every block has read it
+  int skip_arrival;            // test hook: the step first waits at a grid barrier block 0 leaves
+  int prologue;                // phase 1 of step m only
+  int lookahead;               // after the step, phase 1 of step m + 1
+  int64_t* m_bump;             // graph replay: the step counter, advanced once every block has read it
+  unsigned long long* arrive;  // [1] blocks that have read the step counter (the last one resets it)
 };
 
 // Grid barrier of this kernel (rbm_grid.cuh), with the test hook that lets
@@ -155,6 +160,32 @@ size_t coop_smem_bytes_t(uint32_t nbuckets) {
   return static_cast<size_t>(kCap) * (8 + 8 + sizeof(Row<T, D>) + 4 * 4) + kSub * 4 + (2 * nbuckets + 1) * 4;
 }
 
+// Phase 1 of step mm for this block's ids [i_lo, i_hi): bucket histogram in
+// shared memory, one reservation per (block, bucket) on the totals h, and the
+// ids scattered into the buckets' slots sl (ids beyond a full bucket's slots
+// are dropped here and regrouped by the step that reads them).
+__device__ void bucket_ids(const CoopArgs& ca, uint32_t mm, uint32_t B, uint32_t i_lo, uint32_t i_hi, uint32_t* h,
+                           uint32_t* sl, uint32_t* s_cnt) {
+  for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) s_cnt[b] = 0;
+  __syncthreads();
+  for (uint32_t i = i_lo + threadIdx.x; i < i_hi; i += blockDim.x) {
+    const uint64_t key = perm_key(i, mm, ca.replica, ca.seed);
+    atomicAdd(&s_cnt[static_cast<uint32_t>(fine_index(key, B) >> kSubBits)], 1u);
+  }
+  __syncthreads();
+  for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) {
+    const uint32_t cnt = s_cnt[b];
+    s_cnt[b] = b * ca.slot_cap + (cnt ? atomicAdd(&h[b], cnt) : 0u);  // this block's first slot in bucket b
+  }
+  __syncthreads();
+  for (uint32_t i = i_lo + threadIdx.x; i < i_hi; i += blockDim.x) {
+    const uint64_t key = perm_key(i, mm, ca.replica, ca.seed);
+    const uint32_t b = static_cast<uint32_t>(fine_index(key, B) >> kSubBits);
+    const uint32_t slot = atomicAdd(&s_cnt[b], 1u);
+    if (slot < (b + 1u) * ca.slot_cap) sl[slot] = i;
+  }
+}
+
 // The e smallest (key, id) among the candidates each thread holds (up to
 // two: (k0, i0), (k1, i1); absent ones have valid flag false), ascending,
 // into sel[0, e).  One block-wide argmin per pick with a single barrier:
@@ -213,6 +244,35 @@ __device__ void select_smallest(uint64_t k0, uint32_t i0, bool v0, uint64_t k1, 
   __syncthreads();
 }
 
+// Phase 4: warp w of block c takes boundaries c + w G, c + (w + W) G, ...
+template <typename T, int D, int MODE>
+__device__ void straddles_from_permutation(const CoopArgs& ca, const StepParams<T>& a, const CoopSmem& sm,
+                                           uint32_t B, uint32_t m32) {
+  const uint32_t G = gridDim.x, c = blockIdx.x, up = static_cast<uint32_t>(a.p);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t nwarps = blockDim.x >> 5;
+  for (uint32_t b = c + static_cast<uint32_t>(warp) * G; b < B; b += nwarps * G) {  // warp-uniform
+    bool valid = b > 0;
+    uint32_t id = 0;
+    int bs = a.p;
+    if (valid) {
+      const uint32_t s = sm.s_start[b];
+      valid = (s % up != 0) && (s < a.n);
+      if (valid) {
+        const uint32_t q = s / up;
+        valid = sm.s_start[b - 1] <= q * up;
+        if (valid) {
+          const uint32_t lo = q * up, hi = min(lo + up, a.n);
+          bs = static_cast<int>(hi - lo);
+          valid = lane < bs;
+          if (valid) id = ca.perm[lo + lane];
+        }
+      }
+    }
+    batch_group<T, D, MODE>(a, m32, id, valid, lane < a.p ? lane : 0, bs);
+  }
+}
+
 template <typename T, int D, int MODE>
 __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepParams<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -227,54 +287,35 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
 
   if (skipped(a)) return;  // uniform: the flag does not change during the launch
   const uint32_t G = gridDim.x, c = blockIdx.x;
-  const uint32_t m32 = step_index(a);
-  // Every block reads the launch counter before it arrives at the barrier;
-  // block 0 advances it after the barrier.
-  const uint32_t parity = *static_cast<volatile uint32_t*>(ca.epoch) & 1u;
-  uint32_t* hist = ca.hist + parity * B;
+  const uint64_t m64 = static_cast<uint64_t>((a.m_ptr ? *a.m_ptr : 0) + a.m_off);
+  const uint32_t m32 = static_cast<uint32_t>(m64);
+  const size_t slot_words = static_cast<size_t>(B) * ca.slot_cap;
+  uint32_t* h_cur = ca.hist + (m64 % 3u) * B;          // step m's totals
+  uint32_t* h_next = ca.hist + ((m64 + 1u) % 3u) * B;  // step m + 1's (filled at the end)
+  uint32_t* h_free = ca.hist + ((m64 + 2u) % 3u) * B;  // step m - 1's, cleared for step m + 2
+  uint32_t* sl_cur = ca.slots + (m64 & 1u) * slot_words;
+  uint32_t* sl_next = ca.slots + ((m64 + 1u) & 1u) * slot_words;
   const uint32_t per = (ca.n + G - 1) / G;
   const uint32_t i_lo = min(ca.n, c * per), i_hi = min(ca.n, i_lo + per);
   const uint32_t up = static_cast<uint32_t>(a.p);
 
-  // phase 1: bucket histogram of ids [i_lo, i_hi) (counts kept in s_start
-  // until the barrier); reserve this block's stretch of every bucket it
-  // touches; scatter the ids into the buckets' slots
-  for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) sm.s_cnt[b] = 0;
-  __syncthreads();
-  for (uint32_t i = i_lo + threadIdx.x; i < i_hi; i += blockDim.x) {
-    const uint64_t key = perm_key(i, m32, ca.replica, ca.seed);
-    atomicAdd(&sm.s_cnt[static_cast<uint32_t>(fine_index(key, B) >> kSubBits)], 1u);
+  if (ca.prologue) {
+    bucket_ids(ca, m32, B, i_lo, i_hi, h_cur, sl_cur, sm.s_cnt);
+    return;
   }
-  __syncthreads();
-  for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) {
-    const uint32_t cnt = sm.s_cnt[b];
-    sm.s_start[b] = cnt;
-    sm.s_cnt[b] = b * ca.slot_cap + (cnt ? atomicAdd(&hist[b], cnt) : 0u);  // this block's first slot in bucket b
+  if (ca.m_bump) {
+    // the last block to have read the step counter advances it (no waiting)
+    __syncthreads();
+    if (threadIdx.x == 0 && ::rbm::atom_add_acq_rel_gpu(ca.arrive, 1ull) == G - 1) {
+      *ca.arrive = 0;
+      *ca.m_bump += 1;
+    }
   }
-  __syncthreads();
-  for (uint32_t i = i_lo + threadIdx.x; i < i_hi; i += blockDim.x) {
-    const uint64_t key = perm_key(i, m32, ca.replica, ca.seed);
-    const uint32_t b = static_cast<uint32_t>(fine_index(key, B) >> kSubBits);
-    const uint32_t slot = atomicAdd(&sm.s_cnt[b], 1u);
-    if (slot < (b + 1u) * ca.slot_cap) ca.slots[slot] = i;  // an overflowing bucket is regrouped below
-  }
-  if (!grid_barrier(ca, a.status, ca.skip_arrival && c == 0)) return;
-  if (c == 0 && threadIdx.x == 0) {
-    if (ca.m_bump) *ca.m_bump += 1;  // every block has read the step index
-    *ca.epoch += 1u;                 // and the launch counter
-  }
-  {
-    // the buffer the previous launch used (it has completed): cleared for the next launch
-    uint32_t* other = ca.hist + (parity ^ 1u) * B;
-    for (uint32_t b = c * blockDim.x + threadIdx.x; b < B; b += G * blockDim.x) other[b] = 0;
-  }
+  if (ca.skip_arrival && !grid_barrier(ca, a.status, c == 0)) return;  // test hook: no block passes
+  for (uint32_t b = c * blockDim.x + threadIdx.x; b < B; b += G * blockDim.x) h_free[b] = 0;
 
-  // phase 2: bucket starts; this block's offset inside each bucket (for the
-  // compact regrouping) is its first slot minus the bucket's slot base
-  for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) {
-    sm.s_cnt[b] -= b * ca.slot_cap + sm.s_start[b];
-    sm.s_start[b] = hist[b];
-  }
+  // phase 2: bucket starts
+  for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) sm.s_start[b] = h_cur[b];
   if (threadIdx.x == 0) {
     sm.s_start[B] = 0;
     s_general = 0;
@@ -283,8 +324,8 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
   __syncthreads();
   block_exclusive_scan(sm.s_start, B + 1, s_warp);  // s_start[B] becomes N
   if (sm.s_start[B] != ca.n) {
-    // totals left over by a launch whose barrier wait ran out: every block
-    // sees the same sum and leaves; nothing has been written but slots
+    // totals not filled for this step (a launch whose barrier wait ran out):
+    // every block sees the same sum and leaves without writing
     if (threadIdx.x == 0) latch_status(a.status, RBM_ERR_STATE);
     return;
   }
@@ -307,15 +348,16 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
   const bool general = s_general != 0;
   const bool compact = s_compact != 0;
   if (compact) {
-    // some bucket outgrew its slots: every block regroups its ids compactly
-    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) sm.s_cnt[b] += sm.s_start[b];
-    __syncthreads();
+    // some bucket outgrew its slots: every block regroups its ids compactly,
+    // counting places on the cleared buffer (cleared again afterwards)
+    if (!grid_barrier(ca, a.status, false)) return;
     for (uint32_t i = i_lo + threadIdx.x; i < i_hi; i += blockDim.x) {
       const uint64_t key = perm_key(i, m32, ca.replica, ca.seed);
       const uint32_t b = static_cast<uint32_t>(fine_index(key, B) >> kSubBits);
-      ca.tmp[atomicAdd(&sm.s_cnt[b], 1u)] = i;
+      ca.tmp[sm.s_start[b] + atomicAdd(&h_free[b], 1u)] = i;
     }
     if (!grid_barrier(ca, a.status, false)) return;
+    for (uint32_t b = c * blockDim.x + threadIdx.x; b < B; b += G * blockDim.x) h_free[b] = 0;
   }
 
   // phase 3: sort each of this block's buckets, write the permutation, step
@@ -331,8 +373,8 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
       for (uint32_t u = threadIdx.x; u < kSub; u += blockDim.x) sm.s_sub[u] = 0;
       // issue every global load of this bucket first: ids, positions, the next bucket's ids
       const uint32_t t0 = threadIdx.x, t1 = threadIdx.x + blockDim.x;  // nb, n1 <= kCap = 2 * blockDim
-      const uint32_t* ids = compact ? ca.tmp + s : ca.slots + static_cast<size_t>(b) * ca.slot_cap;
-      const uint32_t* next_ids = compact ? ca.tmp + end : ca.slots + static_cast<size_t>(b + 1) * ca.slot_cap;
+      const uint32_t* ids = compact ? ca.tmp + s : sl_cur + static_cast<size_t>(b) * ca.slot_cap;
+      const uint32_t* next_ids = compact ? ca.tmp + end : sl_cur + static_cast<size_t>(b + 1) * ca.slot_cap;
       const uint32_t id0 = (t0 < nb) ? ids[t0] : 0u;
       const uint32_t id1 = (t1 < nb) ? ids[t1] : 0u;
       const uint32_t nid0 = (t0 < n1) ? next_ids[t0] : 0u;
@@ -472,42 +514,21 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
     }
     __syncthreads();
   }
-  if (MODE == kModePerm || !general) return;
-  if (!grid_barrier(ca, a.status, false)) return;
-
-  // phase 4 (general mode): batches straddling a bucket boundary; warp w
-  // takes boundaries c + w G, c + (w + W) G, ... (W warps per block); the
-  // first boundary inside a batch takes it
-  const uint32_t nwarps = blockDim.x >> 5;
-  for (uint32_t b = c + static_cast<uint32_t>(warp) * G; b < B; b += nwarps * G) {  // warp-uniform
-    bool valid = b > 0;
-    uint32_t id = 0;
-    int bs = a.p;
-    if (valid) {
-      const uint32_t s = sm.s_start[b];
-      valid = (s % up != 0) && (s < a.n);
-      if (valid) {
-        const uint32_t q = s / up;
-        valid = sm.s_start[b - 1] <= q * up;
-        if (valid) {
-          const uint32_t lo = q * up, hi = min(lo + up, a.n);
-          bs = static_cast<int>(hi - lo);
-          valid = lane < bs;
-          if (valid) id = ca.perm[lo + lane];
-        }
-      }
-    }
-    batch_group<T, D, MODE>(a, m32, id, valid, lane < a.p ? lane : 0, bs);
+  if (MODE != kModePerm && general) {
+    if (!grid_barrier(ca, a.status, false)) return;
+    // phase 4 (general mode): batches straddling a bucket boundary; warp w
+    // takes boundaries c + w G, c + (w + W) G, ... (W warps per block); the
+    // first boundary inside a batch takes it
+    straddles_from_permutation<T, D, MODE>(ca, a, sm, B, m32);
   }
+  // phase 1 of step m + 1 (reads no position; the next launch reads its totals and slots)
+  if (ca.lookahead) bucket_ids(ca, m32 + 1u, B, i_lo, i_hi, h_next, sl_next, sm.s_cnt);
 }
 
 // The latency floor of the step kernel's launch shape: the same cooperative
-// launch (grid, block, dynamic shared memory) and the same bounded grid
-// barrier (one, as a step in the common case) with no work around it.
-__global__ void __launch_bounds__(kCoopThreads, 1) k_coop_floor(unsigned long long* bar, unsigned long long wait_ns,
-                                                                int32_t* status) {
-  ::rbm::grid_barrier(bar, wait_ns, status, false);
-}
+// launch (grid, block, dynamic shared memory) with no work (a step in the
+// common case waits at no grid barrier).
+__global__ void __launch_bounds__(kCoopThreads, 1) k_coop_floor(int32_t* status) { (void)status; }
 
 template <typename T, int D, int MODE>
 cudaError_t launch_coop_k(const CoopScratch& cs, const StepParams<T>& a, const CoopArgs& ca, cudaStream_t st) {
@@ -564,7 +585,8 @@ cudaError_t launch_coop_floor(const CoopScratch& cs, size_t smem_bytes, uint64_t
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_coop_floor, cs.bar, static_cast<unsigned long long>(wait_ns), status);
+  (void)wait_ns;
+  return cudaLaunchKernelEx(&cfg, k_coop_floor, status);
 }
 
 size_t coop_smem_bytes(int dtype, int d, uint32_t nbuckets) {
@@ -589,14 +611,14 @@ cudaError_t prepare_coop_kernels(int* blocks_per_sm) {
 
 template <typename T>
 cudaError_t launch_coop(const CoopScratch& cs, int d, int mode, const void* params, uint64_t wait_ns,
-                        int skip_arrival, bool bump_step, const LaunchCfg& cfg, cudaStream_t st) {
+                        int skip_arrival, bool prologue, bool lookahead, bool bump_step, const LaunchCfg& cfg,
+                        cudaStream_t st) {
   const StepParams<T>& a = *static_cast<const StepParams<T>*>(params);
   CoopArgs ca;
   ca.hist = cs.hist;
   ca.slots = cs.slots;
   ca.slot_cap = cs.slot_cap;
   ca.tmp = cs.tmp;
-  ca.epoch = cs.epoch;
   ca.perm = cs.perm;
   ca.bar = cs.bar;
   ca.n = a.n;
@@ -604,8 +626,11 @@ cudaError_t launch_coop(const CoopScratch& cs, int d, int mode, const void* para
   ca.seed = a.seed;
   ca.replica = a.replica;
   ca.wait_ns = wait_ns;
-  ca.skip_arrival = skip_arrival;
-  ca.m_bump = bump_step ? const_cast<int64_t*>(a.m_ptr) : nullptr;
+  ca.skip_arrival = prologue ? 0 : skip_arrival;
+  ca.prologue = prologue ? 1 : 0;
+  ca.lookahead = lookahead ? 1 : 0;
+  ca.m_bump = (bump_step && !prologue) ? const_cast<int64_t*>(a.m_ptr) : nullptr;
+  ca.arrive = cs.arrive;
   cudaError_t e;
   if (d == 1) {
     e = (mode == kModeStep) ? launch_coop_k<T, 1, kModeStep>(cs, a, ca, st)
@@ -620,13 +645,13 @@ cudaError_t launch_coop(const CoopScratch& cs, int d, int mode, const void* para
       : (mode == kModeForces) ? launch_coop_k<T, 3, kModeForces>(cs, a, ca, st)
                               : launch_coop_k<T, 3, kModePerm>(cs, a, ca, st);
   }
-  mark_launch(cfg, st, "k_rbm_coop");
+  mark_launch(cfg, st, prologue ? "k_rbm_coop_prologue" : "k_rbm_coop");
   return e;
 }
 
-template cudaError_t launch_coop<float>(const CoopScratch&, int, int, const void*, uint64_t, int, bool,
+template cudaError_t launch_coop<float>(const CoopScratch&, int, int, const void*, uint64_t, int, bool, bool, bool,
                                         const LaunchCfg&, cudaStream_t);
-template cudaError_t launch_coop<double>(const CoopScratch&, int, int, const void*, uint64_t, int, bool,
+template cudaError_t launch_coop<double>(const CoopScratch&, int, int, const void*, uint64_t, int, bool, bool, bool,
                                          const LaunchCfg&, cudaStream_t);
 
 }  // namespace rbm

@@ -108,7 +108,7 @@ void free_scratch(rbm_ctx* c) {
   cudaFree(s.cnt); cudaFree(s.start); cudaFree(s.slots); cudaFree(s.ovf_cnt); cudaFree(s.ovf);
   cudaFree(s.done); cudaFree(s.perm);
   s = PermScratch{};
-  cudaFree(c->cs.hist); cudaFree(c->cs.slots); cudaFree(c->cs.tmp); cudaFree(c->cs.epoch); cudaFree(c->cs.bar);
+  cudaFree(c->cs.hist); cudaFree(c->cs.slots); cudaFree(c->cs.tmp); cudaFree(c->cs.bar); cudaFree(c->cs.arrive);
   c->cs = CoopScratch{};
   cudaFree(c->bs.order); cudaFree(c->bs.block_begin); cudaFree(c->bs.offs);
   cudaFree(c->bs.tmp); cudaFree(c->bs.perm);
@@ -243,17 +243,17 @@ rbm_status alloc_scratch(rbm_ctx* c) {
     CoopScratch& cs = c->cs;
     cs.grid = grid;
     cs.nbuckets = k * grid;
-    RBM_CUDA(cudaMalloc(&cs.hist, sizeof(uint32_t) * 2 * cs.nbuckets));
-    RBM_CUDA(cudaMemset(cs.hist, 0, sizeof(uint32_t) * 2 * cs.nbuckets));
+    RBM_CUDA(cudaMalloc(&cs.hist, sizeof(uint32_t) * 3 * cs.nbuckets));
+    RBM_CUDA(cudaMemset(cs.hist, 0, sizeof(uint32_t) * 3 * cs.nbuckets));
     cs.slot_cap = coop_slot_capacity();
     if (c->tuning.slot_cap > 0 && static_cast<uint32_t>(c->tuning.slot_cap) < cs.slot_cap)
       cs.slot_cap = static_cast<uint32_t>(c->tuning.slot_cap);
-    RBM_CUDA(cudaMalloc(&cs.slots, sizeof(uint32_t) * static_cast<size_t>(cs.nbuckets) * cs.slot_cap));
+    RBM_CUDA(cudaMalloc(&cs.slots, sizeof(uint32_t) * 2 * static_cast<size_t>(cs.nbuckets) * cs.slot_cap));
     RBM_CUDA(cudaMalloc(&cs.tmp, sizeof(uint32_t) * n));
-    RBM_CUDA(cudaMalloc(&cs.epoch, sizeof(uint32_t)));
-    RBM_CUDA(cudaMemset(cs.epoch, 0, sizeof(uint32_t)));
     RBM_CUDA(cudaMalloc(&cs.bar, sizeof(unsigned long long)));
     RBM_CUDA(cudaMemset(cs.bar, 0, sizeof(unsigned long long)));
+    RBM_CUDA(cudaMalloc(&cs.arrive, sizeof(unsigned long long)));
+    RBM_CUDA(cudaMemset(cs.arrive, 0, sizeof(unsigned long long)));
     cs.perm = s.perm;
   }
   return RBM_OK;
@@ -293,28 +293,48 @@ uint2 seed_of(const rbm_ctx* c) {
 }
 
 bool uses_bucket_path(const rbm_ctx* c) { return !c->batched && !c->use_small && !c->use_coop; }
+bool uses_lookahead(const rbm_ctx* c) { return !c->batched && !c->use_small; }
 
-// Bucket-sort path: clear the filled buffer (if any), so that both are clean.
+// Lookahead paths: clear the bucketing filled ahead (if any), so that every
+// buffer is clean.  Bucket-sort path: the filled buffer; cooperative path:
+// all three bucket-total buffers (its slots need no clearing).
 rbm_status forget_prepared(rbm_ctx* c, cudaStream_t st) {
-  if (c->prepared_m < 0 || !uses_bucket_path(c)) {
-    c->prepared_m = -1;
-    return RBM_OK;
+  if (c->use_coop && !c->use_small && !c->batched) {
+    RBM_CUDA(cudaMemsetAsync(c->cs.hist, 0, sizeof(uint32_t) * 3 * c->cs.nbuckets, st));
+  } else if (c->prepared_m >= 0 && uses_bucket_path(c)) {
+    const size_t par = static_cast<size_t>(c->prepared_m & 1);
+    RBM_CUDA(cudaMemsetAsync(c->ps.cnt + par * c->ps.nbuckets, 0, sizeof(uint32_t) * c->ps.nbuckets, st));
+    RBM_CUDA(cudaMemsetAsync(c->ps.ovf_cnt + par, 0, sizeof(uint32_t), st));
   }
-  const size_t par = static_cast<size_t>(c->prepared_m & 1);
-  RBM_CUDA(cudaMemsetAsync(c->ps.cnt + par * c->ps.nbuckets, 0, sizeof(uint32_t) * c->ps.nbuckets, st));
-  RBM_CUDA(cudaMemsetAsync(c->ps.ovf_cnt + par, 0, sizeof(uint32_t), st));
   c->prepared_m = -1;
   return RBM_OK;
 }
 
-// Bucket-sort path, before a captured run of RBM steps from step m: fill
-// step m's buffer unless the previous call did.
-rbm_status prepare_bucket_path(rbm_ctx* c, int64_t m, cudaStream_t st) {
-  if (!uses_bucket_path(c) || c->prepared_m == m) return RBM_OK;
+// Before a captured run of RBM steps from step m: bucket step m unless the
+// previous call did.
+rbm_status prepare_lookahead(rbm_ctx* c, int64_t m, cudaStream_t st) {
+  if (!uses_lookahead(c) || c->prepared_m == m) return RBM_OK;
   rbm_status fs = forget_prepared(c, st);
   if (fs != RBM_OK) return fs;
-  launch_bucket_scatter(c->ps, static_cast<uint32_t>(c->prm.n), seed_of(c), c->prm.replica, nullptr, m, c->cfg, st);
-  RBM_CUDA(cudaGetLastError());
+  if (c->use_coop) {
+    const uint64_t wait_ns = 1000ull * 1000000ull;
+    cudaError_t e;
+    if (c->prm.dtype == RBM_F32) {
+      StepParams<float> a = step_params<float>(c, nullptr, m);
+      e = launch_coop<float>(c->cs, c->prm.d, 1, &a, wait_ns, 0, true, false, false, c->cfg, st);
+    } else {
+      StepParams<double> a = step_params<double>(c, nullptr, m);
+      e = launch_coop<double>(c->cs, c->prm.d, 1, &a, wait_ns, 0, true, false, false, c->cfg, st);
+    }
+    if (e != cudaSuccess) {
+      set_error("cudaLaunchKernelEx (cooperative)", e);
+      return RBM_ERR_CUDA;
+    }
+  } else {
+    launch_bucket_scatter(c->ps, static_cast<uint32_t>(c->prm.n), seed_of(c), c->prm.replica, nullptr, m, c->cfg,
+                          st);
+    RBM_CUDA(cudaGetLastError());
+  }
   c->prepared_m = m;
   return RBM_OK;
 }
@@ -345,27 +365,49 @@ rbm_status enqueue_rbm(rbm_ctx* c, int mode, const int64_t* m_ptr, int64_t m_off
     const uint64_t wait_ns = 1000ull * static_cast<uint64_t>(c->tuning.wait_limit_us > 0 ? c->tuning.wait_limit_us
                                                                                           : 1000000);
     const int skip_hook = c->tuning.test_skip_arrival;
-    // Graph replay: the kernel reads the step index from m_ptr and advances
-    // it itself once every block has read it, so each captured step reads
-    // the counter with offset 0.
-    const bool bump = (m_ptr != nullptr) && skip == nullptr;
+    // The bucketing of a step (phase 1) runs at the end of the previous
+    // step's launch (lookahead) or in a prologue launch of its own: eager
+    // calls launch the prologue unless the previous call bucketed this step;
+    // a captured run of steps relies on the host to bucket its first step
+    // before each replay (prepare_lookahead); steps gated by the surrogate's
+    // flag bucket their own ids.
+    const bool lookahead = (mode == 1) && skip == nullptr;
+    // Graph replay of RBM steps: the step launch advances the device step
+    // counter itself once every block has read it, so each captured step
+    // reads the counter with offset 0.
+    const bool bump = (m_ptr != nullptr) && lookahead;
     if (bump) m_off = 0;
-    cudaError_t e;
-    if (c->prm.dtype == RBM_F32) {
-      StepParams<float> a = step_params<float>(c, m_ptr, m_off);
-      a.fout = static_cast<float*>(fout);
-      a.skip = skip;
-      e = launch_coop<float>(c->cs, c->prm.d, mode, &a, wait_ns, skip_hook, bump, c->cfg, st);
+    bool prologue = false;
+    if (m_ptr == nullptr) {
+      if (skip != nullptr || c->prepared_m != m_off) {
+        rbm_status fs = forget_prepared(c, st);
+        if (fs != RBM_OK) return fs;
+        prologue = true;
+      }
     } else {
-      StepParams<double> a = step_params<double>(c, m_ptr, m_off);
-      a.fout = static_cast<double*>(fout);
-      a.skip = skip;
-      e = launch_coop<double>(c->cs, c->prm.d, mode, &a, wait_ns, skip_hook, bump, c->cfg, st);
+      prologue = !lookahead;
+    }
+    cudaError_t e = cudaSuccess;
+    for (int launch = prologue ? 0 : 1; launch < 2 && e == cudaSuccess; ++launch) {
+      if (c->prm.dtype == RBM_F32) {
+        StepParams<float> a = step_params<float>(c, m_ptr, m_off);
+        a.fout = static_cast<float*>(fout);
+        a.skip = skip;
+        e = launch_coop<float>(c->cs, c->prm.d, mode, &a, wait_ns, skip_hook, launch == 0, lookahead, bump, c->cfg,
+                               st);
+      } else {
+        StepParams<double> a = step_params<double>(c, m_ptr, m_off);
+        a.fout = static_cast<double*>(fout);
+        a.skip = skip;
+        e = launch_coop<double>(c->cs, c->prm.d, mode, &a, wait_ns, skip_hook, launch == 0, lookahead, bump, c->cfg,
+                                st);
+      }
     }
     if (e != cudaSuccess) {
       set_error("cudaLaunchKernelEx (cooperative)", e);
       return RBM_ERR_CUDA;
     }
+    if (m_ptr == nullptr) c->prepared_m = lookahead ? m_off + 1 : -1;
     return RBM_OK;
   }
   // Bucket-sort path.  A step (not a permutation or force query, not a
@@ -498,7 +540,7 @@ rbm_status capture_graph(rbm_ctx* c, int32_t method, int64_t len) {
   RBM_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
   rbm_status st = RBM_OK;
   for (int64_t s = 0; s < len && st == RBM_OK; ++s) st = enqueue_step(c, method, c->m_dev, s, c->cap_stream);
-  // The cooperative RBM kernel advances the device step counter itself.
+  // The cooperative RBM step advances the device step counter itself.
   const bool self_bumping = (method == RBM_METHOD_RBM && c->use_coop);
   if (st == RBM_OK && !self_bumping) launch_add_i64(c->m_dev, len, c->cap_stream);
   cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
@@ -822,13 +864,13 @@ rbm_status rbm_run(rbm_ctx* ctx, int64_t steps, int32_t method) {
     }
     if (ctx->m_dev_value != ctx->m) launch_set_i64(ctx->m_dev, ctx->m, ctx->stream);
     if (method == RBM_METHOD_RBM) {
-      st = prepare_bucket_path(ctx, ctx->m, ctx->stream);
+      st = prepare_lookahead(ctx, ctx->m, ctx->stream);
       if (st != RBM_OK) return st;
     }
     RBM_CUDA(cudaGraphLaunch(ctx->graph[method], ctx->stream));
     ctx->m += len;
     ctx->m_dev_value = ctx->m;
-    if (method == RBM_METHOD_RBM && uses_bucket_path(ctx)) ctx->prepared_m = ctx->m;  // the last step's lookahead
+    if (method == RBM_METHOD_RBM && uses_lookahead(ctx)) ctx->prepared_m = ctx->m;  // the last step's lookahead
     steps -= len;
   }
   for (; steps > 0; --steps) {

@@ -31,13 +31,13 @@ struct PermScratch {
 
 // Cooperative single-kernel step scratch.
 struct CoopScratch {
-  uint32_t* hist = nullptr;     // [2 nbuckets] bucket totals, two buffers by launch parity (zero initially)
-  uint32_t* slots = nullptr;    // [nbuckets slot_cap] ids grouped by bucket
+  uint32_t* hist = nullptr;     // [3 nbuckets] bucket totals, buffer m mod 3 for step m (zero initially)
+  uint32_t* slots = nullptr;    // [2 nbuckets slot_cap] ids grouped by bucket, buffer m mod 2
   uint32_t slot_cap = 0;        // slots per bucket, at most coop_slot_capacity()
   uint32_t* tmp = nullptr;      // [n] ids grouped by bucket, compact (bucket overflow only)
-  uint32_t* epoch = nullptr;    // [1] launch counter (zero initially)
   uint32_t* perm = nullptr;     // [n] (shared with PermScratch::perm)
   unsigned long long* bar = nullptr;  // [1] grid barrier arrival counter
+  unsigned long long* arrive = nullptr;  // [1] blocks that have read the step counter (zero between launches)
   uint32_t grid = 0;            // blocks (one per SM)
   uint32_t nbuckets = 0;        // k * grid
 };
@@ -138,8 +138,12 @@ cudaError_t launch_coop_floor(const CoopScratch& cs, size_t smem_bytes, uint64_t
                               cudaStream_t st);
 uint32_t coop_bucket_target();
 template <typename T>
+// prologue: only bucket the ids of the step; lookahead: after the step,
+// bucket the ids of the next one.
+// bump_step: the step launch advances the device step counter a.m_ptr once
+// every block has read it (graph replay).
 cudaError_t launch_coop(const CoopScratch& cs, int d, int mode, const void* params, uint64_t wait_ns, int skip_arrival,
-                        bool bump_step, const LaunchCfg& cfg, cudaStream_t st);
+                        bool prologue, bool lookahead, bool bump_step, const LaunchCfg& cfg, cudaStream_t st);
 
 // Batched replicas (batched.cu): mode as for launch_rbm_tail.
 int batched_max_buckets();
