@@ -151,7 +151,7 @@ typedef struct {
     int32_t direct_block; /* threads per block of the direct kernel          */
     int32_t graph_steps;  /* steps captured per CUDA graph by rbm_run        */
     int32_t path;         /* RBM step: 0 automatic (3 up to 1536 particles in
-                             FP32 / 384 in FP64, 2 up to about 2.3 million,
+                             FP32 / 384 in FP64, 2 up to about 1.7 million,
                              1 beyond), 1 bucket-sort
                              kernels, 2 one cooperative kernel (N up to about 8
                              million, p <= 32), 3 one block for the whole system

@@ -196,15 +196,16 @@ rbm_status alloc_scratch(rbm_ctx* c) {
 
   // Cooperative single-kernel path: one block per SM, B = k * grid buckets of
   // about 1024 members on average, B <= coop_max_buckets() (N up to about
-  // 8M); batches of at most a warp.  Chosen automatically up to 15 buckets
-  // per block (N about 2.3M): beyond that the multi-kernel path is faster
-  // (measured crossover between 2^20 and 2^22); path = 2 forces it.
+  // 8M); batches of at most a warp.  Chosen automatically up to 11 buckets
+  // per block (N about 1.7M): beyond that the multi-kernel path is faster
+  // (measured with both paths bucketing ahead, d = 3, p = 2: 2^20 79 vs
+  // 130 us, 2^21 149 vs 141 us, 2^22 299 vs 205 us); path = 2 forces it.
   const uint32_t grid = static_cast<uint32_t>(c->cfg.num_sms);
   const uint32_t k = static_cast<uint32_t>((static_cast<uint64_t>(n) + static_cast<uint64_t>(grid) *
                                             coop_bucket_target() - 1) / (static_cast<uint64_t>(grid) *
                                                                          coop_bucket_target()));
   const bool coop_fits = c->coop_blocks_per_sm >= 1 && c->prm.p <= 32 && k >= 1 && k * grid <= coop_max_buckets();
-  c->use_coop = (c->tuning.path == 2 || (c->tuning.path == 0 && k <= 15)) && coop_fits;
+  c->use_coop = (c->tuning.path == 2 || (c->tuning.path == 0 && k <= 11)) && coop_fits;
   // Small systems: one block sorts all N keys in shared memory and steps
   // every batch (no grid barrier); the replica kernel with one replica.
   // Chosen automatically up to N = 1536 in FP32 and N = 384 in FP64 (the
