@@ -359,6 +359,49 @@ def test_graph_replay_equals_eager_steps(path):
     assert np.array_equal(xa.cpu().numpy(), xb.cpu().numpy())
 
 
+@pytest.mark.parametrize("path", [1, 2])
+def test_lookahead_bucketing_survives_mixed_calls(path):
+    """The bucket-sort and cooperative paths bucket the next step's ids at the
+    end of each step.  A sequence that mixes graph replays, eager steps, a
+    permutation and a force query at the current step, and a jump back in
+    the step index must equal the same sequence run eagerly step by step, bit
+    for bit, and every permutation must be the oracle's."""
+    torch = torch_cuda()
+    n, d = 20000, 3
+    X = as_run_precision(workloads.gaussian(n, d, seed=12), "f32")
+    kw = dict(p=2, dt=1e-3, sigma=0.2, v="quadratic", k="reg_attract", k_param=0.01, seed=13)
+    prm = _oprm(n, d, "f32", **kw)
+
+    def sequence(s):
+        perms = []
+        s.run(7)                              # graphs of 5 steps + 2 eager ones (or all eager)
+        perms.append((s.m, s.permutation().cpu().numpy().view(np.uint32).copy()))
+        s.step()
+        s.m = 3                               # back in the step index
+        s.step()
+        f = s.forces().cpu().clone()
+        perms.append((s.m, s.permutation().cpu().numpy().view(np.uint32).copy()))
+        s.run(11)
+        s.step()
+        s.sync()
+        return perms, f
+
+    a, xa = _system(X, d, "f32", **kw)
+    b, xb = _system(X, d, "f32", **kw)
+    a.set_tuning(path=path, graph_steps=5)
+    b.set_tuning(path=path, graph_steps=1000)
+    assert a.tuning()["path"] == path and b.tuning()["path"] == path
+    pa, fa = sequence(a)
+    pb, fb = sequence(b)
+    assert torch.equal(xa, xb)
+    assert torch.equal(fa, fb)
+    for (ma, perm_a), (mb, perm_b) in zip(pa, pb):
+        assert ma == mb
+        assert np.array_equal(perm_a, perm_b)
+        assert np.array_equal(perm_a, oracle.permutation(prm, ma))
+    assert a.m == b.m == 4 + 11 + 1
+
+
 def test_pad_lane_preserved_and_step_host_matches():
     torch = torch_cuda()
     n, d = 4096, 3
