@@ -314,8 +314,9 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
   if (ca.skip_arrival && !grid_barrier(ca, a.status, c == 0)) return;  // test hook: no block passes
   for (uint32_t b = c * blockDim.x + threadIdx.x; b < B; b += G * blockDim.x) h_free[b] = 0;
 
-  // phase 2: bucket starts
+  // phase 2: bucket starts (and the sub-bucket counters of phase 3 cleared)
   for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) sm.s_start[b] = h_cur[b];
+  for (uint32_t u = threadIdx.x; u < kSub; u += blockDim.x) sm.s_sub[u] = 0;
   if (threadIdx.x == 0) {
     sm.s_start[B] = 0;
     s_general = 0;
@@ -370,8 +371,8 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
       // smallest keys of the next bucket (non-general mode).
       const bool straddle = (MODE != kModePerm) && !general && end < a.n && end % up != 0;
       const uint32_t n1 = straddle ? sm.s_start[b + 2] - end : 0u;
-      for (uint32_t u = threadIdx.x; u < kSub; u += blockDim.x) sm.s_sub[u] = 0;
       // issue every global load of this bucket first: ids, positions, the next bucket's ids
+      // (s_sub was cleared before the last barrier)
       const uint32_t t0 = threadIdx.x, t1 = threadIdx.x + blockDim.x;  // nb, n1 <= kCap = 2 * blockDim
       const uint32_t* ids = compact ? ca.tmp + s : sl_cur + static_cast<size_t>(b) * ca.slot_cap;
       const uint32_t* next_ids = compact ? ca.tmp + end : sl_cur + static_cast<size_t>(b + 1) * ca.slot_cap;
@@ -384,7 +385,6 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
         if (t0 < nb) x0 = load_row<T, D>(a.x, id0);
         if (t1 < nb) x1 = load_row<T, D>(a.x, id1);
       }
-      __syncthreads();  // s_sub zeroed
       if (t0 < nb) {
         const uint64_t key = perm_key(id0, m32, ca.replica, ca.seed);
         const uint32_t sub = static_cast<uint32_t>(fine_index(key, B)) & (kSub - 1u);
@@ -512,7 +512,9 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
         step_batches<T, D, MODE>(a, m32, ca.perm + s, s, q0, (q_end > q0) ? q_end - q0 : 0u);
       }
     }
-    __syncthreads();
+    // s_sub is read no more in this bucket: clear it for the next one
+    for (uint32_t u = threadIdx.x; u < kSub; u += blockDim.x) sm.s_sub[u] = 0;
+    if (b + G < B) __syncthreads();
   }
   if (MODE != kModePerm && general) {
     if (!grid_barrier(ca, a.status, false)) return;
