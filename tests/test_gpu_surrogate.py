@@ -70,6 +70,37 @@ def test_surrogate_gradient_matches_oracle():
         assert rel < 1e-2, (name, rel)
 
 
+def test_surrogate_network_step_at_full_size_sampled():
+    """The network step at the size the benchmark times (N = 2^22, FP32,
+    d = 2): every particle's force from the tensor-core network, then the
+    Euler-Maruyama update.  The weights stay fixed (a checkpoint with no
+    training iterations and a tolerance that always keeps the network), and
+    4096 sampled particles after one step must match the oracle's network
+    forward (same bfloat16 operand rounding) and update: 1e-5 relative plus
+    dt times the forward's bar (2e-3 of the force scale)."""
+    torch_cuda()
+    n = 1 << 22
+    s, x, X = _system(n, seed=5)
+    s.surrogate_config(train_every=100, fallback_tol=1e30, n_queries=1024, iters_first=0, iters_per_checkpoint=0,
+                       max_rounds=1, lr=1e-3)
+    theta, norm = _params(6)
+    s.surrogate_set_params(theta, norm)
+    s.run(1, "surrogate")
+    s.sync()
+    st = s.surrogate_stats()
+    assert st["surrogate_steps"] == 1 and st["fallback_steps"] == 0 and st["adam_steps"] == 0, st
+    got = from_dev(x, 2)
+    idx = np.sort(np.random.default_rng(7).choice(n, 4096, replace=False))
+    prm = oracle.make_params(n, 2, seed=0, precision="f32", **AGG)
+    FK = np.zeros_like(X)
+    FK[idx] = mlp.predict_force(theta, X[idx].astype(np.float32), norm, emulate_bf16=True)
+    ref = oracle.euler_update(prm, X, FK, 0)
+    scale = np.sqrt(np.mean(FK[idx] ** 2))
+    diff = np.linalg.norm(got[idx] - ref[idx], axis=1)
+    bound = 1e-5 * np.maximum(np.linalg.norm(ref[idx], axis=1), 1.0) + AGG["dt"] * 2e-3 * scale
+    assert np.all(diff <= bound), (diff.max(), bound.min())
+
+
 def _sampled_ids(nq, n, m=0, seed=0, replica=0):
     """Query ids of a checkpoint at step m: floor(w0 n / 2^32) of the Philox
     block at counter (q, m, replica, stream 2)."""
