@@ -284,12 +284,13 @@ def test_cooperative_path_at_millions_of_particles(p):
     assert_close_per_particle(from_dev(x, d), ref, 1e-5, extra=_fp32_bound(prm, X, FK, 0), what=f"p = {p}")
 
 
-def test_multi_kernel_path_at_large_n_full_size():
-    """The large-N sweep's N = 2^24 entry (d = 3, FP32, regularised attraction,
-    p = 2) on the path the library picks there (the multi-kernel bucket sort):
-    the whole permutation bit-exact and one step of every particle within the
-    FP32 bar."""
-    n, d = 1 << 24, 3
+@pytest.mark.parametrize("log2n", [24, 26])
+def test_multi_kernel_path_at_large_n_full_size(log2n):
+    """The large-N sweep's N = 2^24 and N = 2^26 (its largest) entries (d = 3,
+    FP32, regularised attraction, p = 2) on the path the library picks there
+    (the multi-kernel bucket sort): the whole permutation bit-exact and one
+    step of every particle within the FP32 bar."""
+    n, d = 1 << log2n, 3
     kw = dict(p=2, dt=1e-3, sigma=0.2, v="quadratic", k="reg_attract", k_param=0.01)
     X = as_run_precision(workloads.gaussian(n, d, seed=7), "f32")
     s, x = _system(X, d, "f32", seed=3, **kw)
@@ -301,7 +302,7 @@ def test_multi_kernel_path_at_large_n_full_size():
     s.sync()
     FK = oracle.rbm_interaction(prm, X, perm)
     ref = oracle.euler_update(prm, X, FK, 0)
-    assert_close_per_particle(from_dev(x, d), ref, 1e-5, extra=_fp32_bound(prm, X, FK, 0), what="N = 2^24")
+    assert_close_per_particle(from_dev(x, d), ref, 1e-5, extra=_fp32_bound(prm, X, FK, 0), what=f"N = 2^{log2n}")
 
 
 def test_direct_fp32_full_size_sampled():
