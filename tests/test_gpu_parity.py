@@ -403,6 +403,30 @@ def test_lookahead_bucketing_survives_mixed_calls(path):
     assert a.m == b.m == 4 + 11 + 1
 
 
+def test_latency_floor_of_the_cooperative_launch():
+    """rbm_latency_floor times the cooperative step's launch shape with no
+    work: positive, below the step kernel's own time, and leaving positions
+    and step index alone; contexts on another path get RBM_ERR_STATE."""
+    torch = torch_cuda()
+    n, d = 100000, 3
+    X = as_run_precision(workloads.sphere(n, d, seed=2), "f32")
+    s, x = _system(X, d, "f32", p=2, dt=1e-4, k="coulomb", renorm=True)
+    s.set_tuning(path=2)
+    s.step()
+    s.sync()
+    before, m = x.clone(), s.m
+    floor_us = s.latency_floor()
+    assert 0.0 < floor_us < 1000.0
+    assert torch.equal(x, before) and s.m == m
+    step_us = 1e3 * sum(ms for name, ms in s.step_profiled() if name == "k_rbm_coop")
+    assert floor_us < step_us
+    t, _ = _system(X, d, "f32", p=2, dt=1e-4, k="coulomb", renorm=True)
+    t.set_tuning(path=1)
+    with pytest.raises(rbm.RbmError) as e:
+        t.latency_floor()
+    assert e.value.status == -6
+
+
 def test_pad_lane_preserved_and_step_host_matches():
     torch = torch_cuda()
     n, d = 4096, 3
