@@ -371,10 +371,9 @@ def run_single(args, w, g):
     kw = dict(p=w["p"], dt=w["dt"], sigma=w["sigma"], seed=w["seed"], v=w["potential"], v_coef=w["v_coef"],
               k=w["kernel"], k_param=w["k_param"], renorm=w["renorm"], scheme=w["scheme"], replica=g.rank)
     sysm = rbm.System(x, d=d, stream=g.stream, **kw)
-    sysm.set_tuning(graph_steps=1)
     clocks = ClockSampler(g.local).start()
     for _ in range(max(args.warmup, 3)):
-        sysm.run(1)
+        sysm.step()
     sysm.sync()
     soak = rbm.System(x.clone(), d=d, stream=g.stream, **kw)
     t_soak = time.perf_counter()
@@ -383,9 +382,9 @@ def run_single(args, w, g):
         soak.sync()
     soak.close()
 
-    # kernels per replayed one-step graph, plus the counter bump unless the
-    # cooperative kernel advances the step counter itself
-    launches = sysm.launches_per_step("rbm") + (0 if sysm.tuning()["path"] == 2 else 1)
+    # kernels per step (rbm_step; the bucketing of each step was done by the
+    # step before it)
+    launches = sysm.launches_per_step("rbm")
     starts = [g.event() for _ in range(args.steps)]
     ends = [g.event() for _ in range(args.steps)]
     g.barrier()
@@ -393,7 +392,7 @@ def run_single(args, w, g):
     for k in range(args.steps):
         g.flush()
         starts[k].record(g.stream)
-        sysm.run(1)                              # one RBM-1 step (CUDA graph of one step)
+        sysm.step()                              # one RBM-1 step (rbm_step)
         ends[k].record(g.stream)
     g.barrier()
     wall = time.perf_counter() - wall0

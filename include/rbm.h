@@ -406,7 +406,9 @@ rbm_status rbm_autotune(rbm_ctx *ctx, int32_t trial_steps, const char *table_pat
 rbm_status rbm_permutation_noalloc(int64_t n, uint64_t seed, uint32_t replica, int64_t m, uint32_t *perm_dev,
                                    void *cuda_stream);
 
-/* Number of kernel launches one step of `method` enqueues (for accounting). */
+/* Number of kernel launches one step of `method` enqueues inside a run of
+ * steps (for accounting; an RBM-1 run's first step adds the bucketing of its
+ * ids on the bucket-sort and cooperative paths). */
 rbm_status rbm_launches_per_step(const rbm_ctx *ctx, int32_t method, int32_t *launches);
 
 #ifdef __cplusplus

@@ -1612,11 +1612,12 @@ rbm_status rbm_latency_floor(rbm_ctx* ctx, float* us) {
 
 rbm_status rbm_launches_per_step(const rbm_ctx* ctx, int32_t method, int32_t* launches) {
   if (!ctx || !launches) return RBM_ERR_INVALID;
+  // RBM-1 inside a run: the previous step bucketed this one's ids (lookahead)
   if (method == RBM_METHOD_RBM)
-    *launches = (ctx->use_coop || ctx->batched || ctx->use_small) ? 1 : 1 + rbm_tail_launches(ctx->ps, ctx->prm.p);
+    *launches = (ctx->use_coop || ctx->batched || ctx->use_small) ? 1 : rbm_tail_launches(ctx->ps, ctx->prm.p);
   else if (method == RBM_METHOD_DIRECT) *launches = 2;  // upper bound: sum (+ chunk reduction)
-  else if (method == RBM_METHOD_SURROGATE)
-    *launches = 1 + ((ctx->use_coop || ctx->use_small) ? 1 : 1 + rbm_tail_launches(ctx->ps, ctx->prm.p));
+  else if (method == RBM_METHOD_SURROGATE)  // network step + the flag-gated RBM step that buckets its own ids
+    *launches = 1 + (ctx->use_small ? 1 : ctx->use_coop ? 2 : 1 + rbm_tail_launches(ctx->ps, ctx->prm.p));
   else if (method == RBM_METHOD_RBMR) *launches = 1;
   else return RBM_ERR_INVALID;
   return RBM_OK;
