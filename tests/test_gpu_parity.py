@@ -470,6 +470,10 @@ def test_invalid_parameters_rejected():
         with pytest.raises(rbm.RbmError) as e:
             rbm.System(x if d == 1 else torch.zeros(100, d, device="cuda", dtype=torch.float64), d=d, **kw)
         assert e.value.status == -1
+    for rows in (0, 1):                       # no system to divide into batches
+        with pytest.raises(rbm.RbmError) as e:
+            rbm.System(torch.zeros(rows, 1, device="cuda", dtype=torch.float64), d=1, p=2, k="inv1d")
+        assert e.value.status == -1
 
 
 def test_cooperative_compact_regrouping_equals_slots():
