@@ -442,6 +442,11 @@ def test_pad_lane_preserved_and_step_host_matches():
     t.sync()
     assert np.array_equal(host.numpy(), ref.cpu().numpy())
     assert np.all(host.numpy()[:, 3] == 7.25)
+    pageable = host.clone()    # not pinned: the copy-engine path
+    s.step_host(pageable)
+    t.step()
+    t.sync()
+    assert np.array_equal(pageable.numpy(), ref.cpu().numpy())
     del torch
 
 
