@@ -25,6 +25,7 @@ struct rbm_ctx {
   int64_t m = 0;                // host copy of the step counter
   int64_t m_dev_value = -1;     // value last written to m_dev by the host side
   int32_t* status = nullptr;    // device
+  int32_t* status_host = nullptr;  // pinned mirror of the status word (allocated by the first rbm_sync)
   int64_t* m_dev = nullptr;     // device step counter read by graph replays
   void* xtmp = nullptr;         // second position buffer (direct step, generic batches)
   void* xprev = nullptr;        // Verlet: V_0 before the first step, X_{n-1} afterwards
@@ -926,9 +927,12 @@ rbm_status rbm_run(rbm_ctx* ctx, int64_t steps, int32_t method) {
 
 rbm_status rbm_sync(rbm_ctx* ctx) {
   if (!ctx) return RBM_ERR_INVALID;
+  // the status word rides the stream into pinned memory: one wait, not two
+  if (!ctx->status_host)
+    RBM_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&ctx->status_host), sizeof(int32_t), cudaHostAllocDefault));
+  RBM_CUDA(cudaMemcpyAsync(ctx->status_host, ctx->status, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
   RBM_CUDA(cudaStreamSynchronize(ctx->stream));
-  int32_t s = 0;
-  RBM_CUDA(cudaMemcpy(&s, ctx->status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  const int32_t s = *static_cast<volatile int32_t*>(ctx->status_host);
   if (s != 0 && ctx->latched == RBM_OK) ctx->latched = s;
   return static_cast<rbm_status>(ctx->latched);
 }
@@ -1026,6 +1030,7 @@ rbm_status rbm_free(rbm_ctx* ctx) {
   free_scratch(ctx);
   cudaFree(ctx->xprev);
   cudaFree(ctx->status);
+  if (ctx->status_host) cudaFreeHost(ctx->status_host);
   cudaFree(ctx->m_dev);
   delete ctx;
   return RBM_OK;
