@@ -1,30 +1,34 @@
 """Benchmark: particle-steps/s of RBM-1 on one GB300, with the direct O(N^2)
 step beside it, on synthetic workloads shaped like the paper's
 (arXiv:1812.10575) examples.  Default workload (the headline line): the
-Thomson problem of Sec. 5.1 -- N = 100000 points on S^2, K(x) = x/|x|^3,
-V = 0, sigma = 0, positions projected back to the sphere after each step,
-p = 2, dt = 1e-4, FP32.
+large-N system -- N = 2^26 particles in d = 3, V(x) = |x|^2/2, regularised
+attraction K(x) = -x/(|x|^2 + 0.01), sigma = 0.2, X0 ~ N(0, I), p = 2,
+dt = 1e-3, FP32 -- the regime where the direct method is out of reach
+(Sec. 4.1, closing remarks; cost model of Sec. 2.1: O(pN) against O(N^2)).
 
 One timed step = one RBM-1 step: Philox keys, random division, in-batch
-forces, Euler update, projection.  The default state (1.6 MB) fits in L2, so
-L2 is flushed before every timed step (a 256 MiB write, then a 256 MiB read
-so the flush's dirty lines are written back before the step starts) and each
-step is timed alone with CUDA events on the stream its kernels run on.
+forces, -grad V, Brownian increment, Euler-Maruyama update.  The state (1 GB
+of positions) is larger than L2, so steps run back to back: K steps replayed
+from one CUDA graph, timed with CUDA events on the stream the kernels run on.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload thomson|batched_opinion|dyson|large_n|surrogate|w1_sweep]
-                    [--sizes 20,22 (large_n)] [--no-cpu-baseline]
+                    [--workload large_n|thomson|batched_opinion|dyson|large_n_sweep|surrogate|w1_sweep]
+                    [--sizes 20,22 (large_n_sweep)] [--no-cpu-baseline]
 
 Other workloads (one JSON line each, same keys):
+  thomson         - the Thomson problem of Sec. 5.1: N = 100000 points on S^2,
+                    K(x) = x/|x|^3, V = 0, sigma = 0, projection after each
+                    step, p = 2, dt = 1e-4, FP32; the state (1.6 MB) fits in
+                    L2, so L2 is flushed before every timed step and each step
+                    is timed alone: latency-bound;
   batched_opinion - 4096 independent 2-D bounded-confidence opinion systems
                     (Sec. 5.2), N_r log-uniform in [256, 65536], sigma = 0.01,
                     dt = 1e-2, p = 2, one launch per step replayed from a
                     100-step CUDA graph; inputs (384 MB) exceed L2;
   dyson           - Dyson Brownian motion (Sec. 4.2), N = 1000, FP64,
                     splitting scheme, p = 2, dt = 1e-3;
-  large_n         - regularised attraction, d = 3, FP32, N = 2^16 .. 2^26,
-                    p in {2, 4, 8}, RBM-1, RBM-r (up to 2^22, p = 2) and
-                    direct (up to 2^20);
+  large_n_sweep   - the large-N system at N = 2^16 .. 2^26, p in {2, 4, 8},
+                    RBM-1, RBM-r (up to 2^22, p = 2) and direct (up to 2^20);
   surrogate       - the learned mean-field surrogate, N = 2^22, d = 2,
                     Gaussian aggregation with confinement from a 4-cluster
                     mixture, sigma = 0.1, dt = 1e-3: whole 100-step cycles
@@ -61,6 +65,9 @@ UNIT = "particle-steps/s"
 L2_FLUSH_BYTES = 256 << 20
 
 WORKLOADS = {
+    "large_n": dict(workload="large_n_reg_attract", n=2**26, d=3, p=2, dt=1e-3, sigma=0.2, kernel="reg_attract",
+                    potential="quadratic", v_coef=1.0, k_param=0.01, renorm=False, dtype="f32", seed=0,
+                    scheme="euler", other_p=[4, 8], direct_n=2**20, cpu_sample_n=2**20),
     "thomson": dict(workload="thomson_sphere_rbm1", n=100000, d=3, p=2, dt=1e-4, sigma=0.0, kernel="coulomb",
                     potential="zero", v_coef=1.0, k_param=0.0, renorm=True, dtype="f32", seed=0, scheme="euler",
                     quality_steps=2000),
@@ -70,28 +77,28 @@ WORKLOADS = {
     "dyson": dict(workload="dyson_brownian_motion", n=1000, d=1, p=2, dt=1e-3, sigma=float(np.sqrt(1.0 / 1000)),
                   kernel="inv1d", potential="quadratic", v_coef=1.0, k_param=0.0, renorm=False, dtype="f64", seed=0,
                   scheme="split"),
-    "large_n": dict(workload="large_n_reg_attract", d=3, dt=1e-3, sigma=0.2, kernel="reg_attract",
-                    potential="quadratic", v_coef=1.0, k_param=0.01, renorm=False, dtype="f32", seed=0,
-                    scheme="euler", sizes=[2**16, 2**18, 2**20, 2**22, 2**24, 2**26], ps=[2, 4, 8], direct_max=2**20,
-                    rbmr_max=2**22),
+    "large_n_sweep": dict(workload="large_n_reg_attract", d=3, dt=1e-3, sigma=0.2, kernel="reg_attract",
+                          potential="quadratic", v_coef=1.0, k_param=0.01, renorm=False, dtype="f32", seed=0,
+                          scheme="euler", sizes=[2**16, 2**18, 2**20, 2**22, 2**24, 2**26], ps=[2, 4, 8],
+                          direct_max=2**20, rbmr_max=2**22),
     "surrogate": dict(workload="surrogate_mixture_aggregation", n=2**22, d=2, p=2, dt=1e-3, sigma=0.1,
                       kernel="gauss_agg", potential="quadratic", v_coef=1.0, k_param=0.0, renorm=False, dtype="f32",
                       seed=0, scheme="euler", train_every=100, n_queries=16384, iters_first=12000,
                       iters_per_checkpoint=2000, max_rounds=8, lr=3e-3, fallback_tol=1e-2, accuracy_n=2**16,
                       accuracy_steps=300),
-    "w1_sweep": dict(workload="equal_w1_sweep", n=2**16, eps=1e-2, ref_refine=16, refines=[1, 2, 4, 8],
-                     direct_refines=[1, 2, 4], slices=16, seed=0, dtype="f32"),
+    "w1_sweep": dict(workload="equal_accuracy_sweep", n=2**16, T=0.25, fine_steps=4096, eps=[1e-1, 3e-2, 1e-2, 3e-3],
+                     rbm_refines=[512, 256, 128, 64, 32, 16, 8], ps=[2, 4, 8], direct_refines=[512, 256, 128, 64, 32],
+                     surrogate_refines=[128, 64, 32], slices=16, seed=0, dtype="f32"),
 }
 
 # The two systems of the equal-W1 sweep (N = 2^16 for accuracy): the large-N
 # workload (d = 3, regularised attraction) and the surrogate workload (d = 2,
 # Gaussian aggregation from the 4-cluster mixture).
 W1_SYSTEMS = {
-    "large_n_reg_attract": dict(d=3, dt=1e-3, steps=200, sigma=0.2, kernel="reg_attract", potential="quadratic",
-                                v_coef=1.0, k_param=0.01, p=2, init="gaussian", surrogate=False),
-    "surrogate_mixture_aggregation": dict(d=2, dt=1e-3, steps=300, sigma=0.1, kernel="gauss_agg",
-                                          potential="quadratic", v_coef=1.0, k_param=0.0, p=2, init="mixture",
-                                          surrogate=True),
+    "large_n_reg_attract": dict(d=3, sigma=0.2, kernel="reg_attract", potential="quadratic", v_coef=1.0, k_param=0.01,
+                                init="gaussian", surrogate=False),
+    "surrogate_mixture_aggregation": dict(d=2, sigma=0.1, kernel="gauss_agg", potential="quadratic", v_coef=1.0,
+                                          k_param=0.0, init="mixture", surrogate=True),
 }
 
 
@@ -236,9 +243,13 @@ def _oracle_rate(w, seconds=None, steps=None, warmup=0):
         sample = f"replicas {pick[0]}..{pick[-1]} (16 of {len(sizes)}, {int(sum(sizes[pick]))} particles)"
         systems = [(_oprm(w, int(sizes[r]), replica=r), _initial(w, int(sizes[r]), seed=r)) for r in pick]
     else:
-        n = w["n"]
-        sample = f"the full N={n} system"
-        X = _initial(w, n)
+        n = w.get("cpu_sample_n", w["n"])
+        if n == w["n"]:
+            sample = f"the full N={n} system"
+        else:
+            sample = (f"a sample of the N={w['n']} system: its first {n} particles (rows 0..{n - 1} of the same "
+                      f"X0 draw) stepped as a system of {n}")
+        X = _initial(w, w["n"])[:n] if n != w["n"] else _initial(w, n)
         if w["dtype"] == "f32":
             X = X.astype(np.float32).astype(np.float64)
         systems = [(_oprm(w, n), X)]
@@ -361,6 +372,161 @@ def _roofline(peaks, peak_src, kernel, alg_bytes, avg_ms, workload, digest):
             "peak_source": f"{peak_src} (hbm_gbs)"}
 
 
+def _timed_run(g, sysm, steps, method="rbm"):
+    """Milliseconds of `steps` steps replayed from the system's CUDA graph of
+    `steps` steps (captured by an earlier call), CUDA events on the stream."""
+    e0, e1 = g.event(), g.event()
+    g.barrier()
+    e0.record(g.stream)
+    sysm.run(steps, method)
+    e1.record(g.stream)
+    g.barrier()
+    return e0.elapsed_time(e1)
+
+
+# Algorithmic work per unit, as the scope table counts it: bytes per
+# particle-step of RBM-1 (positions read and written once at d words of the
+# run's precision, one u32 permutation entry written and read) and flops per
+# pair of the direct sum.
+def rbm_floor_bytes(d, elem):
+    return 2 * d * elem + 8
+
+
+DIRECT_FLOP_PER_PAIR = {
+    "coulomb": 19,       # 3 sub, 3 FMA (|x|^2), rsqrt, 2 mul, 3 FMA; FMA = 2
+    "reg_attract": 16,   # 3 sub, 3 FMA (|x|^2), add, rcp (special-function unit, not counted), 3 FMA
+    "inv1d": 6, "gauss_agg": 18, "smooth_test": 17, "bounded_conf": 16, "linear": 11,
+}
+
+
+def _direct_kernel_roof(peaks, kernel, n, ms, dtype):
+    flop = DIRECT_FLOP_PER_PAIR[kernel]
+    peak = (152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12) / (1 if dtype == "f32" else 64)
+    tf = flop * n * n / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+            "flop_per_pair": flop,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
+                           + ("" if dtype == "f32" else " / 64 (FP64)")}
+
+
+def run_headline(args, w, g):
+    """The large-N system at N = 2^26: RBM-1 steps replayed from a CUDA graph
+    of K steps (the state exceeds L2: no flush needed), p = 4 and 8 at the
+    same N, and the direct step with RBM-1 beside it at N = 2^20."""
+    import paper_1812_10575_gb300 as rbm
+
+    n, d = w["n"], w["d"]
+    elem = 4
+    X0 = _initial(w, n)
+    kw = dict(dt=w["dt"], sigma=w["sigma"], seed=w["seed"], v=w["potential"], v_coef=w["v_coef"], k=w["kernel"],
+              k_param=w["k_param"], renorm=w["renorm"], scheme=w["scheme"], replica=g.rank)
+    steps = max(args.steps, 1)
+    x = _to_dev(g, X0, d, w["dtype"])
+    sysm = rbm.System(x, d=d, p=w["p"], stream=g.stream, **kw)
+    sysm.set_tuning(graph_steps=steps)
+    clocks = ClockSampler(g.local).start()
+    sysm.run(max(args.warmup, 3) % steps)      # eager warm-up steps
+    sysm.run(steps)                            # captures the K-step graph and replays it once
+    sysm.sync()
+    t_soak = time.perf_counter()
+    while time.perf_counter() - t_soak < args.soak_seconds:
+        sysm.run(steps)
+        sysm.sync()
+    launches = sysm.launches_per_step("rbm")
+    wall0 = time.perf_counter()
+    total_ms = g.max_over_ranks(_timed_run(g, sysm, steps))
+    wall = time.perf_counter() - wall0
+    value = weak_value(g.world, n, steps, total_ms)
+    per_kernel = {}
+    for _ in range(3):                         # one step, kernel by kernel, same stream
+        for name, ms in sysm.step_profiled("rbm"):
+            per_kernel.setdefault(name, []).append(ms)
+    path = sysm.tuning()["path"]
+
+    # end to end through the C ABI with host buffers (H2D + step + D2H)
+    host = x.detach().cpu().pin_memory()
+    sysm.step_host(host)
+    n_e2e = min(steps, 10)
+    g.torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        sysm.step_host(host)
+    e2e_s = g.max_over_ranks(time.perf_counter() - t0)
+    sysm.close()
+    del host
+
+    # p = 4 and 8 on the same system (the error scales as sqrt(dt/(p-1)), Sec. 3)
+    others = {}
+    for p in w["other_p"]:
+        x.copy_(_to_dev(g, X0, d, w["dtype"]))
+        s = rbm.System(x, d=d, p=p, stream=g.stream, **kw)
+        s.set_tuning(graph_steps=steps)
+        s.run(steps)
+        s.sync()
+        ms = _timed_run(g, s, steps)
+        others[f"rbm_p{p}"] = {"particle_steps_per_s": n * steps / (ms * 1e-3), "ms_per_step": ms / steps}
+        s.close()
+    del x
+    g.torch.cuda.empty_cache()
+
+    # the direct step (and RBM-1) on the first 2^20 particles
+    nd = w["direct_n"]
+    xd = _to_dev(g, X0[:nd], d, w["dtype"])
+    sd = rbm.System(xd, d=d, p=w["p"], stream=g.stream, **kw)
+    sd.direct_step()
+    sd.sync()
+    e0, e1 = g.event(), g.event()
+    e0.record(g.stream)
+    sd.direct_step()
+    e1.record(g.stream)
+    sd.sync()
+    direct_ms = e0.elapsed_time(e1)
+    direct_kernel = {}
+    for name, ms in sd.step_profiled("direct"):
+        direct_kernel.setdefault(name, []).append(ms)
+    sd.set_tuning(graph_steps=steps)
+    sd.run(steps)
+    sd.sync()
+    rbm_small_ms = _timed_run(g, sd, steps) / steps
+    sd.close()
+    clocks.stop()
+
+    peaks, peak_src = _measured_peaks()
+    avg = {k: float(np.mean(v)) for k, v in per_kernel.items()}
+    dom = max(avg, key=avg.get)
+    digest = _kernel_sources_digest()
+    floor = rbm_floor_bytes(d, elem)
+    roof = _roofline(peaks, peak_src, dom, n * floor, avg[dom], w["workload"], digest)
+    roof["bytes_per_particle_step"] = floor
+    roof["bytes_note"] = ("2 x 12 B of positions (d = 3 FP32; the stored row is 16 B with its pad lane) + 4 B "
+                          "permutation written + 4 B read")
+    roof["step_frac"] = n * floor / (total_ms / steps * 1e-3) / 1e9 / peaks["hbm_gbs"]
+    dk = float(np.sum([np.mean(v) for v in direct_kernel.values()])) if direct_kernel else direct_ms
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": g.world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": w["dtype"], "data": "synthetic",
+        "config": dict(w, l2=f"inputs larger than L2 ({n * 16 / 1e9:.2f} GB of positions); K steps replayed back "
+                             "to back from one CUDA graph",
+                       parallelism=f"replicas x{g.world} (one independent system per GPU)", path=path),
+        "roofline": roof,
+        "e2e": {"value": g.world * n * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * 16,
+                "d2h_bytes_per_step": n * 16, "steps": n_e2e},
+        "gpu_launches": launches * steps,
+        "clocks": clocks.summary(),
+        "methods": dict(
+            others, rbm_p2={"particle_steps_per_s": value / g.world, "ms_per_step": total_ms / steps},
+            direct_at_n_direct={"n": nd, "particle_steps_per_s": nd / (direct_ms * 1e-3), "ms_per_step": direct_ms,
+                                "kernel": _direct_kernel_roof(peaks, w["kernel"], nd, dk, w["dtype"])},
+            rbm_at_n_direct={"n": nd, "particle_steps_per_s": nd / (rbm_small_ms * 1e-3),
+                             "ms_per_step": rbm_small_ms},
+            rbm_over_direct_at_n_direct=direct_ms / rbm_small_ms),
+        "kernels_ms": avg, "direct_kernels_ms": {k: float(np.mean(v)) for k, v in direct_kernel.items()},
+        "wall_s_timed_region": wall, "kernel_sources": digest,
+    }
+    return line
+
+
 def run_single(args, w, g):
     """One system (thomson, dyson): each step timed alone after an L2 flush."""
     import paper_1812_10575_gb300 as rbm
@@ -442,15 +608,11 @@ def run_single(args, w, g):
     dom = max(avg, key=avg.get)
     # algorithmic bytes per particle-step: positions read and written once,
     # one u32 permutation entry written and read
-    floor = 2 * row_bytes + 8
-    per_particle = {"k_rbm_coop": floor, "k_bucket_sort_step": 4 + 4 + 2 * row_bytes, "k_bucket_scatter": 4}
+    floor = rbm_floor_bytes(d, 4 if w["dtype"] == "f32" else 8)
     digest = _kernel_sources_digest()
-    roof = _roofline(peaks, peak_src, dom, n * per_particle.get(dom, 0), avg[dom], w["workload"], digest)
-    flop_per_pair = {"coulomb": 17, "inv1d": 6, "reg_attract": 17, "gauss_agg": 18, "smooth_test": 17,
-                     "bounded_conf": 16, "linear": 11}[w["kernel"]]
-    fp_peak = (152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12) / (1 if w["dtype"] == "f32" else 64)
+    roof = _roofline(peaks, peak_src, dom, n * floor, avg[dom], w["workload"], digest)
+    roof["bytes_per_particle_step"] = floor
     dk = float(np.sum([np.mean(v) for v in direct_kernel.values()])) if direct_kernel else direct_ms
-    direct_tflops = flop_per_pair * n * n / (dk * 1e-3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": g.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -464,10 +626,7 @@ def run_single(args, w, g):
         "clocks": clocks.summary(),
         "methods": {"rbm": value / g.world, "direct": n / (direct_ms * 1e-3),
                     "rbm_over_direct": (value / g.world) / (n / (direct_ms * 1e-3)), "direct_ms_per_step": direct_ms,
-                    "direct_kernel": {"bound": "alu", "achieved": direct_tflops, "peak": fp_peak, "unit": "TFLOP/s",
-                                      "frac": direct_tflops / fp_peak, "flop_per_pair": flop_per_pair,
-                                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x max clock"
-                                                     + ("" if w["dtype"] == "f32" else " / 64 (FP64)")}},
+                    "direct_kernel": _direct_kernel_roof(peaks, w["kernel"], n, dk, w["dtype"])},
         "kernels_ms": avg, "direct_kernels_ms": {k: float(np.mean(v)) for k, v in direct_kernel.items()},
         "wall_s_timed_region": wall, "kernel_sources": digest,
     }
@@ -479,6 +638,9 @@ def run_single(args, w, g):
                                  "frac": floor_us / kern_us if kern_us > 0 else None,
                                  "what": "same cooperative launch (grid, block, shared memory) with no work (the "
                                          "step waits at no grid barrier); frac = floor / step kernel"}
+        # the state is L2-resident: the step is bound by latency, not HBM
+        line["roofline"] = dict(roof, bound="latency", latency_floor_frac=line["latency_floor"]["frac"],
+                                note="state fits in L2; frac against HBM shown for reference only")
     sysm.close()
     if w.get("quality_steps"):
         line["quality"] = _thomson_quality(g, w, kw)
@@ -628,7 +790,7 @@ def run_large_n(args, w, g):
             ms = e0.elapsed_time(e1) / 100
             ent = {"n": n, "p": p, "method": "rbm", "path": s.tuning()["path"], "ms_per_step": ms,
                    "particle_steps_per_s": n / (ms * 1e-3),
-                   "hbm_frac_of_floor": n * (2 * 16 + 8) / (ms * 1e-3) / 1e9 / _measured_peaks()[0]["hbm_gbs"]}
+                   "hbm_frac_of_floor": n * rbm_floor_bytes(w["d"], 4) / (ms * 1e-3) / 1e9 / _measured_peaks()[0]["hbm_gbs"]}
             if p == w["ps"][0] and n <= w.get("rbmr_max", 0):
                 # RBM-r: a step = floor(N/p) iterations in conflict-free rounds
                 s.run(1, "rbmr")
@@ -832,36 +994,47 @@ def _sliced_w1(A, B, k, seed=0):
     return float(np.mean([np.mean(np.abs(np.sort(A @ v) - np.sort(B @ v))) for v in dirs]))
 
 
+def _rms_gap(A, B):
+    """E(T) of eq. "errorformula": the root mean square over particles of the
+    distance between two runs of the same particles."""
+    return float(np.sqrt(np.mean(np.sum((A - B) ** 2, axis=1))))
+
+
 def run_w1_sweep(args, w, g):
-    """Equal-accuracy comparison: for each system, a direct reference at
-    dt/16 to the same final time T, then RBM-1 (and direct, and the surrogate
-    where it applies) at dt * {1, 1/2, 1/4, ...}; W1 of each final empirical
-    distribution to the reference's (sliced), the measured particle-steps/s
-    of each run, and the time to reach T with the coarsest dt whose W1 is
-    within eps.  The Brownian increments of different dt are independent
-    draws, so W1 has a sampling floor of order N^-1/2."""
+    """Equal-accuracy comparison on one Brownian path.  For each system: a
+    direct reference with the fine step dt_f = T / fine_steps, then RBM-1
+    (p = 2, 4, 8), the direct method and the surrogate at dt = r dt_f with
+    noise refinement r, so every run is driven by the reference's Brownian
+    increments (the synchronous coupling of Sec. 3, eq. "coupling"; the
+    fine-step direct reference of Sec. 4.1).  For each run: E(T) (eq.
+    "errorformula") and the sliced W1 of the final empirical distribution to
+    the reference's, the time to T (CUDA events over the run's eager steps)
+    and particle-steps/s; for each method and tolerance eps the least time to
+    T of a run with E(T) <= eps."""
     import paper_1812_10575_gb300 as rbm
     import workloads
 
-    n, eps = w["n"], w["eps"]
+    n, T, nf = w["n"], w["T"], w["fine_steps"]
+    dt_f = T / nf
     out = {}
     clocks = ClockSampler(g.local).start()
     for name, sy in W1_SYSTEMS.items():
         d = sy["d"]
         X0 = workloads.gaussian(n, d, seed=w["seed"]) if sy["init"] == "gaussian" else \
             workloads.mixture(n, d, seed=w["seed"])
-        T = sy["dt"] * sy["steps"]
 
-        def final(method, refine):
+        def final(method, r, p=2):
             x = _to_dev(g, X0, d, "f32")
-            dt = sy["dt"] / refine
-            s = rbm.System(x, d=d, p=sy["p"], dt=dt, sigma=sy["sigma"], seed=w["seed"], v=sy["potential"],
+            s = rbm.System(x, d=d, p=p, dt=dt_f * r, sigma=sy["sigma"], seed=w["seed"], v=sy["potential"],
                            v_coef=sy["v_coef"], k=sy["kernel"], k_param=sy["k_param"], stream=g.stream)
+            s.set_tuning(graph_steps=1 << 30)    # eager steps: no graph capture inside the timed run
+            s.set_noise_refinement(r)
             if method == "surrogate":
                 s.surrogate_config(train_every=25, fallback_tol=1e-2, n_queries=16384, iters_first=12000,
                                    iters_per_checkpoint=1000, max_rounds=8, lr=3e-3)
-            steps = sy["steps"] * refine
+            steps = nf // r
             e0, e1 = g.event(), g.event()
+            g.torch.cuda.synchronize()
             e0.record(g.stream)
             s.run(steps, method)
             e1.record(g.stream)
@@ -872,34 +1045,49 @@ def run_w1_sweep(args, w, g):
             s.close()
             return X, ms, steps, st
 
-        Xref, ref_ms, ref_steps, _ = final("direct", w["ref_refine"])
-        methods = {"rbm": w["refines"], "direct": w["direct_refines"]}
+        Xref, ref_ms, ref_steps, _ = final("direct", 1)
+        runs = {f"rbm_p{p}": ("rbm", w["rbm_refines"], p) for p in w["ps"]}
+        runs["direct"] = ("direct", w["direct_refines"], 2)
         if sy["surrogate"]:
-            methods["surrogate"] = w["direct_refines"]
-        res = {"T": T, "reference": {"method": "direct", "dt": sy["dt"] / w["ref_refine"], "steps": ref_steps,
-                                     "seconds": ref_ms / 1e3}}
-        for method, refines in methods.items():
+            runs["surrogate"] = ("surrogate", w["surrogate_refines"], 2)
+        res = {"T": T, "dt_fine": dt_f,
+               "reference": {"method": "direct", "dt": dt_f, "steps": ref_steps, "seconds": ref_ms / 1e3}}
+        for label, (method, refines, p) in runs.items():
             curve = []
-            for rf in refines:
-                X, ms, steps, st = final(method, rf)
-                ent = {"dt": sy["dt"] / rf, "steps": steps, "w1": _sliced_w1(X, Xref, w["slices"]),
-                       "seconds_to_T": ms / 1e3, "particle_steps_per_s": n * steps / (ms * 1e-3)}
+            for r in refines:
+                X, ms, steps, st = final(method, r, p)
+                ent = {"dt": dt_f * r, "refine": r, "steps": steps, "E_T": _rms_gap(X, Xref),
+                       "sliced_w1": _sliced_w1(X, Xref, w["slices"]), "seconds_to_T": ms / 1e3,
+                       "particle_steps_per_s": n * steps / (ms * 1e-3)}
                 if st:
                     ent["surrogate_steps"], ent["fallback_steps"] = st["surrogate_steps"], st["fallback_steps"]
                 curve.append(ent)
-            ok = [c for c in curve if c["w1"] <= eps]
-            best = min(ok, key=lambda c: c["seconds_to_T"]) if ok else None
-            res[method] = {"curve": curve, "time_to_T_at_eps_s": best["seconds_to_T"] if best else None,
-                           "dt_at_eps": best["dt"] if best else None,
-                           "particle_steps_per_s_at_eps": best["particle_steps_per_s"] if best else None}
+            at_eps = {}
+            for eps in w["eps"]:
+                ok = [c for c in curve if c["E_T"] <= eps]
+                best = min(ok, key=lambda c: c["seconds_to_T"]) if ok else None
+                at_eps[f"{eps:g}"] = ({"seconds_to_T": best["seconds_to_T"], "dt": best["dt"],
+                                       "particle_steps_per_s": best["particle_steps_per_s"]} if best else None)
+            res[label] = {"curve": curve, "at_eps": at_eps}
+        speedup = {}
+        for eps in w["eps"]:
+            k = f"{eps:g}"
+            dsec = res["direct"]["at_eps"][k]
+            rsec = [res[f"rbm_p{p}"]["at_eps"][k] for p in w["ps"]]
+            rsec = [v["seconds_to_T"] for v in rsec if v]
+            if dsec and rsec:
+                speedup[k] = dsec["seconds_to_T"] / min(rsec)
+        res["rbm_over_direct_time_to_T"] = speedup
         out[name] = res
     clocks.stop()
     head = out["large_n_reg_attract"]
-    value = head["rbm"]["particle_steps_per_s_at_eps"] or 0.0
+    best = head["rbm_p2"]["at_eps"].get("0.01")
+    value = best["particle_steps_per_s"] if best else 0.0
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": g.world, "steps": None, "warmup": 0,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(w, systems=W1_SYSTEMS, l2="state 1-2 MB (L2-resident); whole runs timed with events",
-                           value_is="RBM-1 particle-steps/s at the coarsest dt with sliced W1 <= eps, large-N system"),
+                           value_is="RBM-1 (p = 2) particle-steps/s of the cheapest run with E(T) <= 1e-2, "
+                                    "large-N system at N = 2^16"),
             "clocks": clocks.summary(), "sweeps": out}
 
 
@@ -909,10 +1097,12 @@ def run_ours(args, w):
         line = run_batched(args, w, g)
     elif w["workload"].startswith("surrogate"):
         line = run_surrogate(args, w, g)
-    elif w["workload"].startswith("equal_w1"):
+    elif w["workload"].startswith("equal_accuracy"):
         line = run_w1_sweep(args, w, g)
-    elif w["workload"].startswith("large_n"):
+    elif "sizes" in w:
         line = run_large_n(args, w, g)
+    elif w["workload"].startswith("large_n"):
+        line = run_headline(args, w, g)
     else:
         line = run_single(args, w, g)
     if g.rank == 0 and g.world == 1 and not args.no_cpu_baseline and "sweep" not in line and "sweeps" not in line:
@@ -931,12 +1121,12 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="thomson", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="large_n", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--soak-seconds", type=float, default=1.0,
                     help="untimed load before the timed steps (brings the clocks up; 0 for short profiling runs)")
-    ap.add_argument("--sizes", default="", help="large_n only: comma-separated log2 N (default 16,18,20,22,24,26)")
+    ap.add_argument("--sizes", default="", help="large_n_sweep only: comma-separated log2 N (default 16,18,20,22,24,26)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

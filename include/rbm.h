@@ -141,7 +141,8 @@ typedef struct {
 
 /* Optional launch and scratch tuning (zero = library default). */
 typedef struct {
-    int32_t bucket_bits;  /* log2 of the number of permutation buckets       */
+    int32_t bucket_bits;  /* log2 of the number of permutation buckets (the
+                             record path: of sub-buckets)                      */
     int32_t slot_cap;     /* slots per bucket before spilling to the overflow
                              list (path 1) or regrouping every id compactly
                              behind one more grid barrier (path 2, at most
@@ -152,11 +153,15 @@ typedef struct {
     int32_t graph_steps;  /* steps captured per CUDA graph by rbm_run        */
     int32_t path;         /* RBM step: 0 automatic (3 up to 1536 particles in
                              FP32 / 384 in FP64, 2 up to about 1.7 million,
-                             1 beyond), 1 bucket-sort
-                             kernels, 2 one cooperative kernel (N up to about 8
-                             million, p <= 32), 3 one block for the whole system
-                             (N <= 2048, p <= 32); a path that does not fit
-                             falls back to 1                                   */
+                             beyond that 4 where it applies, else 1), 1
+                             bucket-sort kernels, 2 one cooperative kernel (N
+                             up to about 8 million, p <= 32), 3 one block for
+                             the whole system (N <= 2048, p <= 32), 4 the
+                             record path (FP32, d = 3, p <= 32, not Verlet:
+                             the positions move through the steps of one call
+                             as bucketed records and are written back to
+                             x_dev after the call's last step); a path that
+                             does not fit falls back to 1                       */
     int32_t wait_limit_us;/* bound of a grid-barrier wait in the cooperative
                              kernel (0 = 1 second); a wait that runs out
                              latches RBM_ERR_TIMEOUT                           */
@@ -195,6 +200,24 @@ rbm_status rbm_step_host(rbm_ctx *ctx, void *x_host, int32_t method);
 
 rbm_status rbm_get_step(const rbm_ctx *ctx, int64_t *m);
 rbm_status rbm_set_step(rbm_ctx *ctx, int64_t m);
+
+/* One Brownian path across step sizes: with refinement r the Brownian
+ * increment of step m is the normalised sum of the r increments that a run
+ * with step dt/r draws over the same interval,
+ *     z_i = r^(-1/2) sum_{k=0}^{r-1} z_i(fine step m r + k),
+ * so that sqrt(dt) z_i is that run's sqrt(dt/r) sum_k z_i(m r + k).  Runs of
+ * the same system with steps dt and dt/r (refinements r q and q) are then
+ * driven by the same B^i - the synchronous coupling of Sec. 3 (eq.
+ * "coupling") extended to the fine-step reference the paper measures errors
+ * against (Sec. 4.1) - and their difference is the time-stepping and
+ * random-batch error alone, without sampling noise.  r = 1 (the default) is
+ * the plain draw.  Applies to rbm_step, rbm_direct_step, rbm_run,
+ * rbm_step_host (RBM-1, direct, surrogate; single and batched contexts);
+ * RBM-r steps return RBM_ERR_UNSUPPORTED while r > 1.  Each step draws r
+ * Box-Muller sets per particle.  1 <= r <= 65536, else RBM_ERR_INVALID.
+ * Synchronous (waits for the stream; captured graphs are rebuilt). */
+rbm_status rbm_set_noise_refinement(rbm_ctx *ctx, int32_t r);
+rbm_status rbm_get_noise_refinement(const rbm_ctx *ctx, int32_t *r);
 
 /* Set launch/scratch tuning; reallocates scratch.  Synchronous. */
 rbm_status rbm_set_tuning(rbm_ctx *ctx, const rbm_tuning *tuning);
@@ -266,7 +289,9 @@ rbm_status rbm_forces(rbm_ctx *ctx, int32_t method, void *f_dev);
  * F(q) = 1/(N-1) sum_j K(q - X^j) over all particles, into f_dev. */
 rbm_status rbm_direct_forces_at(rbm_ctx *ctx, const void *q_dev, int64_t nq, void *f_dev);
 
-/* One step of `method` (m -> m+1) with a CUDA event recorded on the
+/* One step of `method` (m -> m+1; on the record path, path 4, two steps
+ * m -> m+2, so that the kernels of a run's inner steps appear besides those
+ * of its last step) with a CUDA event recorded on the
  * context's stream before and after each kernel it launches; waits for the
  * step and writes each kernel's duration in milliseconds to kernel_ms (up to
  * `capacity` entries), their number to *nkernels and, when `names` is given,
@@ -309,7 +334,16 @@ rbm_status rbm_latency_floor(rbm_ctx *ctx, float *us);
  *            quarter = ||F_net - F||_2 / ||F||_2, then further rounds of
  *            iters_per_checkpoint while that error is above fallback_tol, at
  *            most max_rounds rounds in all (the error is read back after each
- *            round: the only host synchronisation of the method).
+ *            round: the only host synchronisation of the method);
+ *   drift:   the network goes stale as the particles move, so each
+ *            checkpoint after the first also measures the error of the network
+ *            as it stood, on the fresh queries, before retraining: the error
+ *            over the interval it just drove.  Above fallback_tol the next
+ *            interval is halved (down to max(1, train_every / 16)); at that
+ *            shortest interval the steps go to the RBM-1 fallback until a
+ *            checkpoint measures the drift within the tolerance again; at or
+ *            below half the tolerance the interval doubles back towards
+ *            train_every (rbm_surrogate_drift reports the schedule).
  * Requires d = 2, FP32, the Euler scheme, additive noise, a single (not
  * batched) system.
  * Synchronous (allocates the network state). */
@@ -324,6 +358,14 @@ rbm_status rbm_surrogate_train(rbm_ctx *ctx, int32_t iters);
  * run so far.  Any output pointer may be NULL.  Synchronous. */
 rbm_status rbm_surrogate_stats(rbm_ctx *ctx, double *last_rel_err, int64_t *n_surrogate_steps,
                                int64_t *n_fallback_steps, int32_t *active, int64_t *n_adam_steps);
+
+/* The drift-aware schedule: the last drift error (-1 before the second
+ * checkpoint), the current interval between checkpoints in steps, whether the
+ * last checkpoint handed the steps to the RBM-1 fallback for drift, and how
+ * many intervals it has done so.  Any output pointer may be NULL.  Host state
+ * only (does not wait). */
+rbm_status rbm_surrogate_drift(const rbm_ctx *ctx, double *drift_err, int32_t *interval, int32_t *forced_off,
+                               int64_t *n_forced_intervals);
 
 /* Network parameters (4482 floats: W1[64][2], b1[64], W2[64][64], b2[64],
  * W3[2][64], b3[2]) and normalisation (mu_x, mu_y, s, sF), host buffers;
@@ -399,10 +441,15 @@ rbm_status rbm_autotune(rbm_ctx *ctx, int32_t trial_steps, const char *table_pat
  *   n: 2 .. 65536; larger n returns RBM_ERR_INVALID (rbm_last_error says why).
  *   cuda_stream: the work is enqueued there (cudaStream_t as void*); the call
  *   returns without waiting.
- * The first call on a device looks up the array's address (with that device
- * current); make it before any stream capture on that device.  All calls on a
- * device share the array: each clears what must start at zero, so calls in
- * sequence are fine, but calls whose work overlaps on the GPU race on it. */
+ * Each call outside stream capture looks up the array's address on the
+ * current device (so a cudaDeviceReset, which reloads the module, is
+ * harmless); a call made while its stream is capturing reuses the address the
+ * last call on that device found, so make one call on a device before any
+ * stream capture there.  All calls on a device share the array: each clears
+ * what must start at zero, so calls in sequence are fine, but calls whose
+ * work overlaps on the GPU race on it.  Rejected arguments (n < 2, n above
+ * the maximum, m < 0, a null perm_dev) return RBM_ERR_INVALID with a reason in
+ * rbm_last_error() and touch no CUDA state. */
 rbm_status rbm_permutation_noalloc(int64_t n, uint64_t seed, uint32_t replica, int64_t m, uint32_t *perm_dev,
                                    void *cuda_stream);
 

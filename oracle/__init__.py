@@ -53,6 +53,7 @@ class OrcParams(ctypes.Structure):
         ("decide_f32", ctypes.c_int32),
         ("replica", ctypes.c_uint32),
         ("gbm", ctypes.c_int32),
+        ("noise_refine", ctypes.c_int32),
     ]
 
 
@@ -128,13 +129,15 @@ def _ptr(a: np.ndarray, ctype):
 
 
 def make_params(n, d, p=2, dt=1e-3, sigma=0.0, seed=0, v="zero", v_coef=1.0, k="linear",
-                k_param=0.0, renorm=False, precision="f64", replica=0, gbm=False) -> OrcParams:
+                k_param=0.0, renorm=False, precision="f64", replica=0, gbm=False, noise_refine=1) -> OrcParams:
     """Build an :class:`OrcParams`.
 
     ``precision`` names the precision of the run the oracle is compared with:
     ``"f64"`` uses 53-bit uniforms and FP64 kernel decisions, ``"f32"`` uses
     24-bit uniforms and takes kernel decisions on the FP32 squared norm.  The
-    arithmetic itself is always FP64.
+    arithmetic itself is always FP64.  ``noise_refine`` = r draws each step's
+    Brownian increment as the normalised sum of the r increments of a run with
+    step dt/r (path coupling across step sizes).
     """
     if precision not in ("f64", "f32"):
         raise ValueError(precision)
@@ -144,7 +147,7 @@ def make_params(n, d, p=2, dt=1e-3, sigma=0.0, seed=0, v="zero", v_coef=1.0, k="
         k_kind=K_KINDS[k] if isinstance(k, str) else int(k),
         v_coef=float(v_coef), k_param=float(k_param), renorm=int(bool(renorm)),
         ubits=53 if precision == "f64" else 24, decide_f32=int(precision == "f32"),
-        replica=int(replica), gbm=int(bool(gbm)),
+        replica=int(replica), gbm=int(bool(gbm)), noise_refine=int(noise_refine),
     )
 
 

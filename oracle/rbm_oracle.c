@@ -133,7 +133,9 @@ static double orc_uniform(uint32_t lo, uint32_t hi, int bits)
     return ldexp((double)(top + 1u), -bits);
 }
 
-void orc_normals_one(const orc_params *prm, uint32_t id, int64_t m, double *z)
+/* The standard normal vector of particle id for the step with index m of a  */
+/* run with step dt (one Box-Muller draw per pair of coordinates).           */
+static void orc_normals_plain(const orc_params *prm, uint32_t id, int64_t m, double *z)
 {
     int d = prm->d;
     for (int t = 0; 2 * t < d; ++t) {
@@ -146,6 +148,30 @@ void orc_normals_one(const orc_params *prm, uint32_t id, int64_t m, double *z)
         z[2 * t] = rad * cos(ang);
         if (2 * t + 1 < d) z[2 * t + 1] = rad * sin(ang);
     }
+}
+
+/* Path coupling across step sizes (the synchronous coupling of Sec. 3, eq.   */
+/* "coupling": the compared processes are driven by the same Brownian motion  */
+/* B^i).  A run with step dt and refinement r draws the increment of its step */
+/* m, B^i(t_{m+1}) - B^i(t_m) = sqrt(dt) z, as the sum of the r increments     */
+/* sqrt(dt/r) z_k that a run with step dt/r draws over the same interval,      */
+/* fine steps m r + k, k = 0..r-1:  z = r^(-1/2) sum_k z_k.  With r = 1 it is  */
+/* the plain draw.  (The paper compares each method with a fine-step direct    */
+/* reference, Sec. 4.1; this makes every step size see one Brownian path.)     */
+void orc_normals_one(const orc_params *prm, uint32_t id, int64_t m, double *z)
+{
+    int d = prm->d;
+    int64_t r = prm->noise_refine > 1 ? prm->noise_refine : 1;
+    if (r == 1) {
+        orc_normals_plain(prm, id, m, z);
+        return;
+    }
+    double sum[3] = {0.0, 0.0, 0.0}, zk[4];
+    for (int64_t k = 0; k < r; ++k) {
+        orc_normals_plain(prm, id, m * r + k, zk);
+        for (int c = 0; c < d; ++c) sum[c] += zk[c];
+    }
+    for (int c = 0; c < d; ++c) z[c] = sum[c] / sqrt((double)r);
 }
 
 void orc_normals(const orc_params *prm, int64_t m, double *z)

@@ -42,6 +42,9 @@ typedef struct {
     int32_t decide_f32; /* 1: kernel decisions on the FP32 squared norm     */
     uint32_t replica; /* replica index r (third counter word)               */
     int32_t gbm;      /* 1: multiplicative noise sigma X dB (wealth model)  */
+    int32_t noise_refine; /* r >= 1 (0 reads as 1): the increment of step m  */
+                      /* is the normalised sum of the r increments of a   */
+                      /* run with step dt/r over the same interval         */
 } orc_params;
 
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -21,7 +21,8 @@ from ._lib import (  # noqa: F401
     rbm_batched_set_launch, rbm_autotune, rbm_surrogate_config, rbm_surrogate_train, rbm_surrogate_stats,
     rbm_surrogate_params, rbm_surrogate_set_params, rbm_surrogate_forces, rbm_surrogate_gradient,
     rbm_rbmr_sets, rbm_rbmr_info, rbm_verlet_set_velocity, rbm_verlet_get_previous, rbm_verlet_set_previous,
-    rbm_surrogate_save, rbm_surrogate_load, rbm_latency_floor,
+    rbm_surrogate_save, rbm_surrogate_load, rbm_latency_floor, rbm_set_noise_refinement, rbm_get_noise_refinement,
+    rbm_surrogate_drift,
     N_SURROGATE_PARAMS,
 )
 
@@ -82,6 +83,9 @@ class Replicas:
 
     def set_launch(self, threads, bucket_target):
         rbm_batched_set_launch(self.ctx, threads, bucket_target)
+
+    def set_noise_refinement(self, r):
+        rbm_set_noise_refinement(self.ctx, r)
 
     def set_graph_steps(self, steps):
         rbm_set_tuning(self.ctx, RbmTuning(graph_steps=steps))
@@ -172,6 +176,10 @@ class System:
         t = RbmTuning(**kw)
         rbm_set_tuning(self.ctx, t)
 
+    def set_noise_refinement(self, r):
+        """Brownian increments shared with a run of step dt/r (path coupling)."""
+        rbm_set_noise_refinement(self.ctx, r)
+
     def tuning(self):
         t = rbm_get_tuning(self.ctx)
         return {f: getattr(t, f) for f, _ in RbmTuning._fields_}
@@ -232,6 +240,9 @@ class System:
 
     def surrogate_stats(self):
         return rbm_surrogate_stats(self.ctx)
+
+    def surrogate_drift(self):
+        return rbm_surrogate_drift(self.ctx)
 
     def surrogate_params(self):
         return rbm_surrogate_params(self.ctx)

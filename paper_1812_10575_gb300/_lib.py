@@ -47,7 +47,7 @@ EXPORTS = (
     "rbm_surrogate_set_params", "rbm_surrogate_forces", "rbm_surrogate_gradient",
     "rbm_rbmr_sets", "rbm_rbmr_info", "rbm_verlet_set_velocity", "rbm_verlet_get_previous",
     "rbm_verlet_set_previous", "rbm_surrogate_state_size", "rbm_surrogate_save", "rbm_surrogate_load",
-    "rbm_latency_floor",
+    "rbm_latency_floor", "rbm_set_noise_refinement", "rbm_get_noise_refinement", "rbm_surrogate_drift",
 )
 N_SURROGATE_PARAMS = 4482
 
@@ -129,6 +129,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "rbm_rbmr_sets": [vp, i64, vp],
         "rbm_verlet_set_velocity": [vp, vp],
         "rbm_latency_floor": [vp, ctypes.POINTER(ctypes.c_float)],
+        "rbm_set_noise_refinement": [vp, i32],
+        "rbm_surrogate_drift": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                ctypes.POINTER(i64)],
+        "rbm_get_noise_refinement": [vp, ctypes.POINTER(i32)],
         "rbm_verlet_get_previous": [vp, vp, ctypes.POINTER(i32)],
         "rbm_verlet_set_previous": [vp, vp, i32],
         "rbm_surrogate_state_size": [vp, ctypes.POINTER(i64)],
@@ -423,6 +427,25 @@ def rbm_latency_floor(ctx) -> float:
     us = ctypes.c_float()
     _check(load().rbm_latency_floor(ctx, ctypes.byref(us)), "rbm_latency_floor")
     return us.value
+
+
+def rbm_set_noise_refinement(ctx, r: int) -> None:
+    """Share one Brownian path with runs of step dt/r (see include/rbm.h)."""
+    _check(load().rbm_set_noise_refinement(ctx, int(r)), "rbm_set_noise_refinement")
+
+
+def rbm_get_noise_refinement(ctx) -> int:
+    r = ctypes.c_int32()
+    _check(load().rbm_get_noise_refinement(ctx, ctypes.byref(r)), "rbm_get_noise_refinement")
+    return r.value
+
+
+def rbm_surrogate_drift(ctx) -> dict:
+    """The surrogate's drift-aware schedule (see include/rbm.h)."""
+    e, iv, fo, nf = ctypes.c_double(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(load().rbm_surrogate_drift(ctx, ctypes.byref(e), ctypes.byref(iv), ctypes.byref(fo), ctypes.byref(nf)),
+           "rbm_surrogate_drift")
+    return {"drift_err": e.value, "interval": iv.value, "forced_off": bool(fo.value), "forced_intervals": nf.value}
 
 
 def rbm_rbmr_info(ctx) -> dict:

@@ -23,6 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = [
     ("rbm_abi.cu", []),
     ("perm_step.cu", []),
+    ("rec_step.cu", []),
     ("direct.cu", ["-DRBM_DIRECT_F32"]),
     ("direct.cu", ["-DRBM_DIRECT_F64"]),
     ("noalloc.cu", []),

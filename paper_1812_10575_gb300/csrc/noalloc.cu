@@ -19,9 +19,12 @@
 //     on its stream, so back-to-back calls are fine, but calls whose work
 //     overlaps on the GPU (two streams, or two host threads) race on the
 //     array and give wrong permutations;
-//   - the first call on a device looks up the array's device address with
-//     cudaGetSymbolAddress (with that device current); make that first call
-//     before any stream capture on that device.
+//   - a call looks up the array's device address with cudaGetSymbolAddress
+//     (with that device current) whenever its stream is not capturing, so
+//     the address stays right after a cudaDeviceReset reloads the module; a
+//     call made while the stream is being captured reuses the address of the
+//     last call on that device, so make one call on the device before any
+//     stream capture.
 #include <cstdio>
 #include <mutex>
 
@@ -53,14 +56,19 @@ std::mutex g_mutex;
 constexpr int kMaxDevices = 64;
 uint32_t* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of the array on the current device (looked up once).
-cudaError_t scratch_on_current_device(uint32_t** out) {
+// Device address of the array on the current device: looked up again on
+// every call outside stream capture (a device reset reloads the module and
+// may move it), taken from the last lookup on that device during capture.
+cudaError_t scratch_on_current_device(cudaStream_t st, uint32_t** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone || !g_scratch_ptr[dev]) {
     void* ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
@@ -84,16 +92,27 @@ extern "C" rbm_status rbm_permutation_noalloc(int64_t n, uint64_t seed, uint32_t
     set_last_error_text(msg);
     return RBM_ERR_INVALID;
   }
-  if (n < 2 || m < 0 || !perm_dev) return RBM_ERR_INVALID;
+  if (n < 2) {
+    set_last_error_text("rbm_permutation_noalloc: n must be at least 2");
+    return RBM_ERR_INVALID;
+  }
+  if (m < 0) {
+    set_last_error_text("rbm_permutation_noalloc: the step index m must not be negative");
+    return RBM_ERR_INVALID;
+  }
+  if (!perm_dev) {
+    set_last_error_text("rbm_permutation_noalloc: perm_dev is a null pointer");
+    return RBM_ERR_INVALID;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   uint32_t* base = nullptr;
-  cudaError_t e = scratch_on_current_device(&base);
+  cudaError_t e = scratch_on_current_device(st, &base);
   if (e != cudaSuccess) {
     char msg[160];
     snprintf(msg, sizeof(msg), "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
     set_last_error_text(msg);
     return RBM_ERR_CUDA;
   }
-  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
   PermScratch ps;
   ps.cnt = base + kOffCnt;

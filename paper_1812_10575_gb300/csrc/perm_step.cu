@@ -66,6 +66,7 @@ struct PermArgs {
   uint32_t nbuckets;
   uint32_t slot_cap;
   uint32_t sort_cap;
+  uint32_t row_cap;             // member rows staged in shared memory by the sort kernel (0: none)
   int separate_scan;
   uint2 seed;
   uint32_t replica;
@@ -113,7 +114,7 @@ PermArgs make_perm_args(const PermScratch& ps, uint32_t n, uint2 seed, uint32_t 
   a.cnt = ps.cnt; a.start = ps.start; a.slots = ps.slots; a.ovf_cnt = ps.ovf_cnt; a.ovf = ps.ovf;
   a.done = ps.done; a.perm = ps.perm; a.n = n; a.bits = ps.bucket_bits; a.nbuckets = ps.nbuckets;
   a.double_buffer = ps.double_buffer ? 1 : 0; a.lookahead = 0;
-  a.slot_cap = ps.slot_cap; a.sort_cap = ps.sort_cap; a.separate_scan = ps.separate_scan ? 1 : 0;
+  a.slot_cap = ps.slot_cap; a.sort_cap = ps.sort_cap; a.row_cap = 0; a.separate_scan = ps.separate_scan ? 1 : 0;
   a.seed = seed; a.replica = replica; a.m_ptr = m_ptr; a.m_off = m_off; a.skip = ps.skip;
   return a;
 }
@@ -129,41 +130,41 @@ __global__ void k_bucket_scatter(PermArgs pa_in) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) scatter_one(a, i, m32);
 }
 
-// Exclusive scan of the bucket counts by one block (many-bucket case).
-__global__ void k_bucket_scan(PermArgs pa_in) {
+// Exclusive scan of the bucket counts by one block (many-bucket case): each
+// thread sums a run of consecutive counters, the block scans the run totals,
+// then each thread writes its run's starts (two block barriers in all).
+__global__ void __launch_bounds__(1024) k_bucket_scan(PermArgs pa_in) {
   if (perm_skipped(pa_in)) return;
   const PermArgs a = for_step(pa_in, perm_step_index(pa_in));
   __shared__ uint32_t s_warp[32];
-  __shared__ uint32_t s_carry;
-  if (threadIdx.x == 0) s_carry = 0;
-  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (uint32_t base = 0; base < a.nbuckets; base += blockDim.x) {
-    const uint32_t b = base + threadIdx.x;
-    const uint32_t v = (b < a.nbuckets) ? a.cnt[b] : 0u;
-    uint32_t incl = v;
+  const uint32_t per = (a.nbuckets + blockDim.x - 1) / blockDim.x;
+  const uint32_t lo = min(a.nbuckets, threadIdx.x * per), hi = min(a.nbuckets, lo + per);
+  uint32_t sum = 0;
+  for (uint32_t b = lo; b < hi; ++b) sum += a.cnt[b];
+  uint32_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = (lane < nwarps) ? s_warp[lane] : 0u;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
+      const uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
     }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t w = (lane < nwarps) ? s_warp[lane] : 0u;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += t;
-      }
-      if (lane < nwarps) s_warp[lane] = w;  // inclusive warp totals
-    }
-    __syncthreads();
-    const uint32_t warp_excl = (warp > 0) ? s_warp[warp - 1] : 0u;
-    if (b < a.nbuckets) a.start[b] = s_carry + warp_excl + incl - v;
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) s_carry += warp_excl + incl;
-    __syncthreads();
+    if (lane < nwarps) s_warp[lane] = w;  // inclusive warp totals
+  }
+  __syncthreads();
+  uint32_t run = ((warp > 0) ? s_warp[warp - 1] : 0u) + incl - sum;
+  for (uint32_t b = lo; b < hi; ++b) {
+    const uint32_t v = a.cnt[b];
+    a.start[b] = run;
+    run += v;
   }
 }
 
@@ -249,17 +250,79 @@ __device__ void step_straddling(const StepParams<T>& a, uint32_t m32, const Perm
   }
 }
 
+// Asynchronous copy of one position row (4, 8, 16 or 32 bytes) from global
+// into shared memory (cp.async; 16-byte pieces bypass L1).
+template <typename T, int D>
+__device__ __forceinline__ void cp_async_row(unsigned char* dst, const T* src) {
+  constexpr int kBytes = Ld<D>::value * static_cast<int>(sizeof(T));
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  if constexpr (kBytes == 32) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(src) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s + 16u), "l"(src + 2) : "memory");
+  } else if constexpr (kBytes == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(src) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(src), "n"(kBytes) : "memory");
+  }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// As step_batches, with each member's row taken from the block's staging
+// area when it was staged there (slot index below nstage) and from the
+// position array otherwise.
+template <typename T, int D, int MODE>
+__device__ __forceinline__ void step_batches_staged(const StepParams<T>& a, uint32_t m32, const uint32_t* ids,
+                                                    const uint16_t* slot_of, const unsigned char* srow,
+                                                    uint32_t nstage, uint32_t ids_base, uint32_t q0, uint32_t count) {
+  const int p = a.p;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gpw = 32 / p;
+  const int nwarps = blockDim.x >> 5;
+  const uint32_t per_round = static_cast<uint32_t>(gpw * nwarps);
+  const int g = lane / p, lg = lane - g * p;
+  const T* staged = reinterpret_cast<const T*>(srow);
+  for (uint32_t r0 = 0; r0 < count; r0 += per_round) {
+    const uint32_t kb = r0 + static_cast<uint32_t>(warp * gpw + g);
+    bool valid = (g < gpw) && (kb < count);
+    uint32_t id = 0;
+    int bs = p;
+    Row<T, D> r{};
+    if (valid) {
+      const uint32_t q = q0 + kb;
+      const uint32_t lo = q * static_cast<uint32_t>(p);
+      const uint32_t hi = min(lo + static_cast<uint32_t>(p), a.n);
+      bs = static_cast<int>(hi - lo);
+      valid = lg < bs;
+      if (valid) {
+        const uint32_t pos = lo + lg - ids_base;
+        id = ids[pos];
+        const uint32_t t = slot_of[pos];
+        r = (t < nstage) ? load_row<T, D>(staged, t) : load_row<T, D>(a.x, id);
+      }
+    }
+    batch_group_row<T, D, MODE>(a, m32, id, valid, lg, bs, r);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Pass 2: one block per bucket.
 // ---------------------------------------------------------------------------
 // Four blocks per SM (registers capped at 64; a few bytes spill): at N = 2^24
 // 722 us per step against 795 us with three.
+// The rows of a bucket's members are fetched into shared memory by cp.async
+// as soon as their ids are read, before the keys are regenerated and sorted,
+// so every block keeps its whole bucket of random row reads in flight while
+// it sorts (the random gathers are the step's DRAM latency).
 template <typename T, int D, int MODE>
 __global__ void __launch_bounds__(kSortThreads, 4) k_bucket_sort_step(PermArgs pa_in, StepParams<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint64_t* skey = reinterpret_cast<uint64_t*>(smem_raw);       // [sort_cap] keys, sorted
+  constexpr uint32_t kRowBytes = Ld<D>::value * sizeof(T);
+  unsigned char* srow = smem_raw;                                  // [row_cap] staged rows, by slot index
+  uint64_t* skey = reinterpret_cast<uint64_t*>(smem_raw + static_cast<size_t>(pa_in.row_cap) * kRowBytes);
   uint32_t* sid = reinterpret_cast<uint32_t*>(skey + pa_in.sort_cap);  // [sort_cap] ids, sorted
-  uint32_t* ssub = sid + pa_in.sort_cap;                          // [kSub] sub-bucket counts, then starts
+  uint16_t* sslot = reinterpret_cast<uint16_t*>(sid + pa_in.sort_cap); // [sort_cap] slot index of each sorted id
+  uint32_t* ssub = reinterpret_cast<uint32_t*>(sslot + pa_in.sort_cap);  // [kSub] sub-bucket counts, then starts
   __shared__ uint32_t s_red[32];
   __shared__ uint32_t s_fill;
   __shared__ int s_last;
@@ -268,13 +331,6 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_bucket_sort_step(PermArgs p
   const uint32_t b = blockIdx.x;
   const uint32_t m32 = perm_step_index(pa_in);
   const PermArgs pa = for_step(pa_in, m32);
-  if (pa_in.lookahead) {
-    // bucket this block's share of the ids for step m + 1 (the other buffer)
-    const PermArgs nx = for_step(pa_in, m32 + 1u);
-    const uint32_t chunk = (pa.n + gridDim.x - 1) / gridDim.x;
-    const uint32_t i0 = min(pa.n, b * chunk), i1 = min(pa.n, i0 + chunk);
-    for (uint32_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) scatter_one(nx, i, m32 + 1u);
-  }
 
   uint32_t start;
   if (pa.separate_scan) {
@@ -287,9 +343,11 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_bucket_sort_step(PermArgs p
   }
   const uint32_t nb = pa.cnt[b];
   const uint32_t nslot = min(nb, pa.slot_cap);
+  const uint32_t nstage = (MODE != kModePerm) ? min(nslot, pa.row_cap) : 0u;
   const uint32_t* ids;
+  const bool fits = nb <= pa.sort_cap;
 
-  if (nb <= pa.sort_cap) {
+  if (fits) {
     for (uint32_t u = threadIdx.x; u < kSub; u += blockDim.x) ssub[u] = 0;
     if (nb > nslot) {  // members that spilled to the overflow list, staged after the slot members
       if (threadIdx.x == 0) s_fill = nslot;
@@ -301,22 +359,44 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_bucket_sort_step(PermArgs p
       }
     }
     __syncthreads();
-    // keys in registers; rank of each member inside its sub-bucket
-    uint64_t key[kSortPer];
-    uint32_t idr[kSortPer], subr[kSortPer];
+  }
+  uint64_t key[kSortPer];
+  uint32_t idr[kSortPer], subr[kSortPer];
+  if (fits) {
+    // ids, then every staged member's row in flight, then the keys
+#pragma unroll
+    for (int k = 0; k < kSortPer; ++k) {
+      const uint32_t t = threadIdx.x + k * kSortThreads;
+      if (t < nb) idr[k] = (t < nslot) ? pa.slots[static_cast<size_t>(b) * pa.slot_cap + t] : sid[t];
+    }
+    if (MODE != kModePerm) {
+#pragma unroll
+      for (int k = 0; k < kSortPer; ++k) {
+        const uint32_t t = threadIdx.x + k * kSortThreads;
+        if (t < nstage) cp_async_row<T, D>(srow + t * kRowBytes, a.x + static_cast<size_t>(idr[k]) * Ld<D>::value);
+      }
+      cp_async_commit();
+    }
 #pragma unroll
     for (int k = 0; k < kSortPer; ++k) {
       const uint32_t t = threadIdx.x + k * kSortThreads;
       if (t < nb) {
-        idr[k] = (t < nslot) ? pa.slots[static_cast<size_t>(b) * pa.slot_cap + t] : sid[t];
-        // the member's position row is read when its batch is stepped, after
-        // the sort: start bringing it into L2 now
-        if (MODE != kModePerm) prefetch_l2(a.x + static_cast<size_t>(idr[k]) * Ld<D>::value);
         key[k] = perm_key(idr[k], m32, pa.replica, pa.seed);
         const uint32_t sub = sub_of(key[k], pa.bits);
         subr[k] = sub | (atomicAdd(&ssub[sub], 1u) << 16);
       }
     }
+  }
+  if (pa_in.lookahead) {
+    // bucket this block's share of the ids for step m + 1 (the other buffer)
+    // while this bucket's rows are in flight
+    const PermArgs nx = for_step(pa_in, m32 + 1u);
+    const uint32_t chunk = (pa.n + gridDim.x - 1) / gridDim.x;
+    const uint32_t i0 = min(pa.n, b * chunk), i1 = min(pa.n, i0 + chunk);
+    for (uint32_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) scatter_one(nx, i, m32 + 1u);
+  }
+
+  if (fits) {
     __syncthreads();
     sub_exclusive_scan(ssub, s_red);
 #pragma unroll
@@ -326,6 +406,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_bucket_sort_step(PermArgs p
         const uint32_t pos = ssub[subr[k] & 0xffffu] + (subr[k] >> 16);
         skey[pos] = key[k];
         sid[pos] = idr[k];
+        sslot[pos] = static_cast<uint16_t>(t);
       }
     }
     __syncthreads();
@@ -334,14 +415,17 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_bucket_sort_step(PermArgs p
       for (uint32_t x = lo + 1; x < hi; ++x) {
         const uint64_t kx = skey[x];
         const uint32_t ix = sid[x];
+        const uint16_t tx = sslot[x];
         uint32_t y = x;
         while (y > lo && key_less(kx, ix, skey[y - 1], sid[y - 1])) {
           skey[y] = skey[y - 1];
           sid[y] = sid[y - 1];
+          sslot[y] = sslot[y - 1];
           --y;
         }
         skey[y] = kx;
         sid[y] = ix;
+        sslot[y] = tx;
       }
     }
     __syncthreads();
@@ -368,15 +452,17 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_bucket_sort_step(PermArgs p
     __syncthreads();
     ids = pa.perm + start;
   }
-  __syncthreads();
 
   if (MODE != kModePerm) {
+    if (fits) cp_async_wait_all();
+    __syncthreads();
     const uint32_t up = static_cast<uint32_t>(a.p);
     const uint32_t end = start + nb;
     const uint32_t q0 = (start + up - 1) / up;
     const uint32_t q_end = (end == a.n) ? (a.n + up - 1) / up : end / up;
     const uint32_t count = (q_end > q0) ? q_end - q0 : 0u;
-    step_batches<T, D, MODE>(a, m32, ids, start, q0, count);
+    if (fits) step_batches_staged<T, D, MODE>(a, m32, ids, sslot, srow, nstage, start, q0, count);
+    else step_batches<T, D, MODE>(a, m32, ids, start, q0, count);
   }
 
   if (pa.separate_scan) {
@@ -461,8 +547,20 @@ __global__ void __launch_bounds__(256) k_batch_generic(PermArgs pa, StepParams<T
 __global__ void k_set_i64(int64_t* dst, int64_t v) { *dst = v; }
 __global__ void k_add_i64(int64_t* dst, int64_t v) { *dst += v; }
 
-size_t sort_smem_bytes(uint32_t sort_cap) {
-  return static_cast<size_t>(sort_cap) * (sizeof(uint64_t) + sizeof(uint32_t)) + kSub * sizeof(uint32_t);
+// Dynamic shared memory of the sort kernel: row_cap staged rows of row_bytes,
+// then keys, ids and slot indices of up to sort_cap members, then the
+// sub-bucket counters.
+size_t sort_smem_bytes(uint32_t sort_cap, uint32_t row_cap, uint32_t row_bytes) {
+  return static_cast<size_t>(row_cap) * row_bytes +
+         static_cast<size_t>(sort_cap) * (sizeof(uint64_t) + sizeof(uint32_t) + sizeof(uint16_t)) +
+         kSub * sizeof(uint32_t);
+}
+
+// Rows staged per bucket: every slot member, at most one per sort position,
+// rounded up to 16 rows.
+uint32_t staged_rows(const PermScratch& ps) {
+  const uint32_t cap = ((ps.slot_cap + 15u) / 16u) * 16u;
+  return cap < kSortCapMax ? cap : kSortCapMax;
 }
 
 template <typename T, int D>
@@ -470,14 +568,15 @@ void launch_tail_d(const PermScratch& ps, int mode, const StepParams<T>& a, bool
                    cudaStream_t st) {
   PermArgs pa = make_perm_args(ps, a.n, a.seed, a.replica, a.m_ptr, a.m_off);
   pa.lookahead = (lookahead && ps.double_buffer) ? 1 : 0;
-  const size_t smem = sort_smem_bytes(ps.sort_cap);
   const bool small_p = a.p <= 32;
+  const int kmode = small_p ? mode : kModePerm;
+  pa.row_cap = (kmode == kModePerm) ? 0u : staged_rows(ps);
+  const size_t smem = sort_smem_bytes(ps.sort_cap, pa.row_cap, Ld<D>::value * sizeof(T));
   const int block = kSortThreads;
   if (ps.separate_scan) {
     k_bucket_scan<<<1, 1024, 0, st>>>(pa);
     mark_launch(cfg, st, "k_bucket_scan");
   }
-  const int kmode = small_p ? mode : kModePerm;
   auto launch_sort = [&](auto kern) { kern<<<ps.nbuckets, kSortThreads, smem, st>>>(pa, a); };
   if (kmode == kModeStep) launch_sort(k_bucket_sort_step<T, D, kModeStep>);
   else if (kmode == kModeForces) launch_sort(k_bucket_sort_step<T, D, kModeForces>);
@@ -550,8 +649,9 @@ cudaError_t allow_sort_smem_d(int bytes) {
 }  // namespace
 
 cudaError_t prepare_rbm_kernels() {
-  // The largest shared-memory sort plus static shared data.
-  const int bytes = static_cast<int>(sort_smem_bytes(kSortCapMax)) + 1024;
+  // The largest shared-memory sort with the largest staged rows (32-byte
+  // rows of d = 3 FP64) plus static shared data.
+  const int bytes = static_cast<int>(sort_smem_bytes(kSortCapMax, kSortCapMax, 32)) + 1024;
   cudaError_t e = allow_sort_smem_d<float, 1>(bytes);
   if (e == cudaSuccess) e = allow_sort_smem_d<float, 2>(bytes);
   if (e == cudaSuccess) e = allow_sort_smem_d<float, 3>(bytes);

@@ -25,7 +25,7 @@ struct rbm_ctx {
   int64_t m = 0;                // host copy of the step counter
   int64_t m_dev_value = -1;     // value last written to m_dev by the host side
   int32_t* status = nullptr;    // device
-  int32_t* status_host = nullptr;  // pinned mirror of the status word (allocated by the first rbm_sync)
+  int32_t* status_host = nullptr;  // pinned mirror of the status word (allocated at init)
   int64_t* m_dev = nullptr;     // device step counter read by graph replays
   void* xtmp = nullptr;         // second position buffer (direct step, generic batches)
   void* xprev = nullptr;        // Verlet: V_0 before the first step, X_{n-1} afterwards
@@ -45,12 +45,23 @@ struct rbm_ctx {
   bool sur_trained = false;
   bool sur_norm_given = false;   // normalisation set by the caller: keep it
   int64_t sur_last = 0;          // step of the last checkpoint
+  // drift-aware schedule: the network's error on each checkpoint's fresh
+  // queries before retraining (the error over the interval it drove) sets
+  // the next interval; at the shortest interval an error above the
+  // tolerance hands the steps to the RBM-1 fallback
+  int32_t sur_interval = 100;    // steps until the next checkpoint
+  int32_t sur_min_interval = 1;
+  float sur_drift = -1.0f;       // last drift error (-1: none measured yet)
+  bool sur_forced_off = false;   // the last checkpoint handed the steps to the fallback
+  int64_t sur_forced = 0;        // intervals handed to the fallback so far
   cudaGraphExec_t sur_graph = nullptr;
   int64_t sur_graph_len = 0;
   int batched_blocks_per_sm = 0;
   bool use_coop = false;
   int64_t prepared_m = -1;   // bucket-sort path: the step whose bucket buffer is filled (-1: none)
   bool use_small = false;       // N <= 2048: the whole step in one block (the replica kernel)
+  bool use_rec = false;         // RBM steps by the record path (rec_step.cu)
+  RecScratch rec;
   int coop_blocks_per_sm = 0;
   LaunchCfg cfg;
   rbm_tuning tuning{};
@@ -59,6 +70,7 @@ struct rbm_ctx {
   cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};  // by method (surrogate: sur_graph)
   int64_t graph_len[4] = {0, 0, 0, 0};
   RbmrScratch rs;                // RBM-r scratch, allocated on first use
+  int32_t noise_refine = 1;      // Brownian increments shared with runs of step dt / noise_refine
 };
 
 namespace {
@@ -79,6 +91,36 @@ void set_error(const char* what, cudaError_t e) {
   } while (0)
 
 bool valid_kernel(int32_t k) { return k >= RBM_K_INV1D && k <= RBM_K_LINEAR; }
+
+// The device status word, its pinned host mirror (read back by rbm_sync
+// within the stream) and the device step counter, all cleared.  Allocated
+// at init so that rbm_sync never allocates.
+bool alloc_status(rbm_ctx* c) {
+  if (cudaMalloc(&c->status, sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&c->m_dev, sizeof(int64_t)) != cudaSuccess ||
+      cudaHostAlloc(reinterpret_cast<void**>(&c->status_host), sizeof(int32_t), cudaHostAllocDefault) !=
+          cudaSuccess) {
+    cudaFree(c->status);
+    cudaFree(c->m_dev);
+    c->status = nullptr;
+    c->m_dev = nullptr;
+    c->status_host = nullptr;
+    return false;
+  }
+  *c->status_host = 0;
+  cudaMemset(c->status, 0, sizeof(int32_t));
+  cudaMemset(c->m_dev, 0, sizeof(int64_t));
+  return true;
+}
+
+void free_status(rbm_ctx* c) {
+  cudaFree(c->status);
+  cudaFree(c->m_dev);
+  if (c->status_host) cudaFreeHost(c->status_host);
+  c->status = nullptr;
+  c->m_dev = nullptr;
+  c->status_host = nullptr;
+}
 
 rbm_status check_params(const rbm_params* p) {
   if (!p) return RBM_ERR_INVALID;
@@ -125,6 +167,8 @@ void free_scratch(rbm_ctx* c) {
     cudaFree(rs.flag); cudaFree(rs.btot); cudaFree(rs.remaining); cudaFree(rs.rounds); cudaFree(rs.bar);
     rs = RbmrScratch{};
   }
+  rec_free(&c->rec);
+  c->use_rec = false;
   cudaFree(c->xtmp);
   c->xtmp = nullptr;
   cudaFree(c->partial);
@@ -217,6 +261,16 @@ rbm_status alloc_scratch(rbm_ctx* c) {
   const bool small_fits = !c->batched && n <= 2048 && c->prm.p <= 32;
   const bool small_auto = n <= (c->prm.dtype == RBM_F32 ? 1536u : 384u);
   c->use_small = (c->tuning.path == 3 || (c->tuning.path == 0 && small_auto)) && small_fits;
+  // Record path: FP32 d = 3 systems beyond the cooperative kernel's range
+  // (automatic), or any size when forced (path 4).
+  const bool rec_fits = !c->batched && rec_eligible(c->prm.dtype, c->prm.d, c->prm.p, c->prm.scheme);
+  c->use_rec = rec_fits && !c->use_small &&
+               (c->tuning.path == 4 || (c->tuning.path == 0 && !c->use_coop));
+  if (c->use_rec) {
+    c->use_coop = false;
+    rec_geometry(n, c->tuning.bucket_bits, &c->rec);
+    RBM_CUDA(rec_alloc(n, &c->rec));
+  }
   if (c->use_small) {
     c->use_coop = false;
     BatchedScratch& bs = c->bs;
@@ -287,6 +341,7 @@ StepParams<T> step_params(const rbm_ctx* c, const int64_t* m_ptr, int64_t m_off)
   a.m_off = m_off;
   a.xprev = static_cast<T*>(c->xprev);
   a.verlet_m0 = c->verlet_m0;
+  a.noise_refine = static_cast<uint32_t>(c->noise_refine);
   return a;
 }
 
@@ -295,7 +350,7 @@ uint2 seed_of(const rbm_ctx* c) {
 }
 
 bool uses_bucket_path(const rbm_ctx* c) { return !c->batched && !c->use_small && !c->use_coop; }
-bool uses_lookahead(const rbm_ctx* c) { return !c->batched && !c->use_small; }
+bool uses_lookahead(const rbm_ctx* c) { return !c->batched && !c->use_small && !c->use_rec; }
 
 // Lookahead paths: clear the bucketing filled ahead (if any), so that every
 // buffer is clean.  Bucket-sort path: the filled buffer; cooperative path:
@@ -383,6 +438,17 @@ cudaError_t copy_by_kernel(void* dst, const void* src, size_t bytes, const Launc
   return cudaGetLastError();
 }
 
+// Enqueue `count` RBM steps of the record path from step (*m_ptr or 0) + m_off.
+rbm_status enqueue_rec(rbm_ctx* c, const int64_t* m_ptr, int64_t m_off, int64_t count, cudaStream_t st) {
+  StepParams<float> a = step_params<float>(c, m_ptr, m_off);
+  cudaError_t e = launch_rec_run(c->rec, &a, count, c->cfg, st);
+  if (e != cudaSuccess) {
+    set_error("record-path launch", e);
+    return RBM_ERR_CUDA;
+  }
+  return RBM_OK;
+}
+
 // Enqueue one RBM step (mode 1), the permutation only (0) or the forces (2).
 rbm_status enqueue_rbm(rbm_ctx* c, int mode, const int64_t* m_ptr, int64_t m_off, void* fout, cudaStream_t st,
                        const int* skip = nullptr) {
@@ -454,6 +520,9 @@ rbm_status enqueue_rbm(rbm_ctx* c, int mode, const int64_t* m_ptr, int64_t m_off
     if (m_ptr == nullptr) c->prepared_m = lookahead ? m_off + 1 : -1;
     return RBM_OK;
   }
+  // Record path: steps (not permutation or force queries, not steps gated
+  // by the surrogate's flag) move the positions as records.
+  if (c->use_rec && mode == 1 && skip == nullptr) return enqueue_rec(c, m_ptr, m_off, 1, st);
   // Bucket-sort path.  A step (not a permutation or force query, not a
   // step gated by the surrogate's flag) also buckets the ids of the next step
   // (lookahead).  Eager calls skip the scatter when the previous call filled
@@ -547,6 +616,7 @@ rbm_status ensure_rbmr(rbm_ctx* c) {
 }
 
 rbm_status enqueue_rbmr(rbm_ctx* c, const int64_t* m_ptr, int64_t m_off, cudaStream_t st) {
+  if (c->noise_refine > 1) return RBM_ERR_UNSUPPORTED;  // RBM-r draws its own increments per iteration
   const uint64_t wait_ns = 1000ull * static_cast<uint64_t>(c->tuning.wait_limit_us > 0 ? c->tuning.wait_limit_us
                                                                                         : 1000000);
   cudaError_t e;
@@ -583,7 +653,11 @@ rbm_status capture_graph(rbm_ctx* c, int32_t method, int64_t len) {
   cudaGraph_t g = nullptr;
   RBM_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
   rbm_status st = RBM_OK;
-  for (int64_t s = 0; s < len && st == RBM_OK; ++s) st = enqueue_step(c, method, c->m_dev, s, c->cap_stream);
+  if (method == RBM_METHOD_RBM && c->use_rec) {
+    st = enqueue_rec(c, c->m_dev, 0, len, c->cap_stream);  // one run: positions in x_dev again at its end
+  } else {
+    for (int64_t s = 0; s < len && st == RBM_OK; ++s) st = enqueue_step(c, method, c->m_dev, s, c->cap_stream);
+  }
   // The cooperative RBM step advances the device step counter itself.
   const bool self_bumping = (method == RBM_METHOD_RBM && c->use_coop);
   if (st == RBM_OK && !self_bumping) launch_add_i64(c->m_dev, len, c->cap_stream);
@@ -705,6 +779,14 @@ rbm_status enqueue_checkpoint(rbm_ctx* c, int32_t iters, bool first, cudaStream_
   }
   rbm_status r = enqueue_direct(c, 2, nullptr, c->m, s.q, s.nq, s.fq, st);
   if (r != RBM_OK) return r;
+  if (!first) {  // the network as it drove the last interval, on the fresh queries
+    e = sur_forces(s, c->status, s.q, s.nq, s.fpred, c->cfg, st);
+    if (e == cudaSuccess) e = sur_drift(s, c->status, st);
+    if (e != cudaSuccess) {
+      set_error("surrogate drift check", e);
+      return RBM_ERR_CUDA;
+    }
+  }
   if (first && !c->sur_norm_given) e = sur_norm(s, c->status, st);
   if (e != cudaSuccess) {
     set_error("surrogate checkpoint", e);
@@ -744,8 +826,18 @@ rbm_status enqueue_train_round(rbm_ctx* c, int32_t iters, int32_t round, cudaStr
 // convergence of the round before it.
 // Reading the error back after each round is the one host synchronisation of
 // the surrogate method; the steps themselves never wait on the host.
+//
+// Drift: the network fitted at a checkpoint goes stale as the particles
+// move, so at each later checkpoint its error on the fresh queries (before
+// retraining) is the error it had over the interval it just drove.  Above
+// the tolerance the next interval is halved (down to the shortest,
+// train_every / 16); at the shortest interval the steps go to the RBM-1
+// fallback until a checkpoint measures the drift within the tolerance again;
+// at or below half the tolerance the interval doubles back towards
+// train_every.
 rbm_status run_checkpoint(rbm_ctx* c) {
   const bool first = !c->sur_trained;
+  const int64_t drove = c->m - c->sur_last;  // length of the interval the network last drove
   rbm_status st = enqueue_checkpoint(c, first ? c->sur_iters_first : c->sur_iters, first, c->stream);
   if (st != RBM_OK) return st;
   c->sur_trained = true;
@@ -757,6 +849,27 @@ rbm_status run_checkpoint(rbm_ctx* c) {
     if (std::isfinite(err) && err <= c->ss.tol) break;
     st = enqueue_train_round(c, c->sur_iters, round, c->stream);
     if (st != RBM_OK) return st;
+  }
+  if (first) {
+    c->sur_interval = c->sur_every;
+    c->sur_forced_off = false;
+    return RBM_OK;
+  }
+  float drift = 0.0f;
+  RBM_CUDA(cudaMemcpyAsync(&drift, c->ss.err + 1, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  RBM_CUDA(cudaStreamSynchronize(c->stream));
+  c->sur_drift = drift;
+  const int32_t len = static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(drove, c->sur_every)));
+  if (!(std::isfinite(drift) && drift <= c->ss.tol)) {
+    c->sur_forced_off = len <= c->sur_min_interval;
+    c->sur_interval = std::max(c->sur_min_interval, len / 2);
+  } else {
+    c->sur_forced_off = false;
+    c->sur_interval = (drift <= 0.5f * c->ss.tol) ? std::min(c->sur_every, 2 * len) : len;
+  }
+  if (c->sur_forced_off) {
+    RBM_CUDA(cudaMemsetAsync(c->ss.flag, 0, sizeof(int), c->stream));
+    c->sur_forced += 1;
   }
   return RBM_OK;
 }
@@ -804,6 +917,7 @@ rbm_status rbm_init(const rbm_params* prm, void* x_dev, void* cuda_stream, rbm_c
     c->cfg.num_sms = sms;
   {
     cudaError_t e = prepare_rbm_kernels();
+    if (e == cudaSuccess) e = prepare_rec_kernels();
     if (e == cudaSuccess) e = prepare_coop_kernels(&c->coop_blocks_per_sm);
     if (e != cudaSuccess) {
       set_error("prepare_rbm_kernels", e);
@@ -811,26 +925,21 @@ rbm_status rbm_init(const rbm_params* prm, void* x_dev, void* cuda_stream, rbm_c
       return RBM_ERR_CUDA;
     }
   }
-  if (cudaMalloc(&c->status, sizeof(int32_t)) != cudaSuccess || cudaMalloc(&c->m_dev, sizeof(int64_t)) != cudaSuccess) {
-    cudaFree(c->status);
+  if (!alloc_status(c)) {
     delete c;
     return RBM_ERR_NOMEM;
   }
-  cudaMemset(c->status, 0, sizeof(int32_t));
-  cudaMemset(c->m_dev, 0, sizeof(int64_t));
   c->tuning.graph_steps = 100;
   st = alloc_scratch(c);
   if (st != RBM_OK) {
     free_scratch(c);
-    cudaFree(c->status);
-    cudaFree(c->m_dev);
+    free_status(c);
     delete c;
     return st == RBM_ERR_CUDA ? RBM_ERR_NOMEM : st;
   }
   if (cudaDeviceSynchronize() != cudaSuccess) {
     free_scratch(c);
-    cudaFree(c->status);
-    cudaFree(c->m_dev);
+    free_status(c);
     delete c;
     return RBM_ERR_CUDA;
   }
@@ -869,12 +978,12 @@ rbm_status rbm_run(rbm_ctx* ctx, int64_t steps, int32_t method) {
   if (method == RBM_METHOD_SURROGATE) {
     if (!ctx->sur_on) return RBM_ERR_STATE;
     while (steps > 0) {
-      if (!ctx->sur_trained || ctx->m - ctx->sur_last >= ctx->sur_every) {
+      if (!ctx->sur_trained || ctx->m - ctx->sur_last >= ctx->sur_interval) {
         st = run_checkpoint(ctx);
         if (st != RBM_OK) return st;
       }
-      const int64_t cycle = std::min<int64_t>(steps, ctx->sur_every - (ctx->m - ctx->sur_last));
-      if (cycle == ctx->sur_every) {  // a whole cycle: replay its graph
+      const int64_t cycle = std::min<int64_t>(steps, ctx->sur_interval - (ctx->m - ctx->sur_last));
+      if (cycle == ctx->sur_interval) {  // a whole cycle: replay its graph (one per interval length)
         if (!ctx->sur_graph || ctx->sur_graph_len != cycle) {
           if (ctx->sur_graph) cudaGraphExecDestroy(ctx->sur_graph);
           ctx->sur_graph = nullptr;
@@ -917,6 +1026,12 @@ rbm_status rbm_run(rbm_ctx* ctx, int64_t steps, int32_t method) {
     if (method == RBM_METHOD_RBM && uses_lookahead(ctx)) ctx->prepared_m = ctx->m;  // the last step's lookahead
     steps -= len;
   }
+  if (steps > 0 && method == RBM_METHOD_RBM && ctx->use_rec) {
+    st = enqueue_rec(ctx, nullptr, ctx->m, steps, ctx->stream);  // the remaining steps as one run
+    if (st != RBM_OK) return st;
+    ctx->m += steps;
+    return RBM_OK;
+  }
   for (; steps > 0; --steps) {
     st = enqueue_step(ctx, method, nullptr, ctx->m, ctx->stream);
     if (st != RBM_OK) return st;
@@ -927,11 +1042,20 @@ rbm_status rbm_run(rbm_ctx* ctx, int64_t steps, int32_t method) {
 
 rbm_status rbm_sync(rbm_ctx* ctx) {
   if (!ctx) return RBM_ERR_INVALID;
-  // the status word rides the stream into pinned memory: one wait, not two
-  if (!ctx->status_host)
-    RBM_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&ctx->status_host), sizeof(int32_t), cudaHostAllocDefault));
-  RBM_CUDA(cudaMemcpyAsync(ctx->status_host, ctx->status, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
-  RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+  // the status word rides the stream into pinned memory (allocated at init):
+  // one wait, not two; the stream is drained even when the copy cannot be
+  // enqueued, so the call always returns after the stream's work
+  const cudaError_t ec = cudaMemcpyAsync(ctx->status_host, ctx->status, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                         ctx->stream);
+  const cudaError_t ew = cudaStreamSynchronize(ctx->stream);
+  if (ec != cudaSuccess) {
+    set_error("cudaMemcpyAsync(status)", ec);
+    return RBM_ERR_CUDA;
+  }
+  if (ew != cudaSuccess) {
+    set_error("cudaStreamSynchronize", ew);
+    return RBM_ERR_CUDA;
+  }
   const int32_t s = *static_cast<volatile int32_t*>(ctx->status_host);
   if (s != 0 && ctx->latched == RBM_OK) ctx->latched = s;
   return static_cast<rbm_status>(ctx->latched);
@@ -979,12 +1103,32 @@ rbm_status rbm_set_step(rbm_ctx* ctx, int64_t m) {
   return RBM_OK;
 }
 
+rbm_status rbm_set_noise_refinement(rbm_ctx* ctx, int32_t r) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (r < 1 || r > 65536) return RBM_ERR_INVALID;
+  if (r == ctx->noise_refine) return RBM_OK;
+  RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+  drop_graphs(ctx);  // the captured launches carry the old value
+  if (ctx->sur_graph) cudaGraphExecDestroy(ctx->sur_graph);
+  ctx->sur_graph = nullptr;
+  ctx->sur_graph_len = 0;
+  ctx->noise_refine = r;
+  return RBM_OK;
+}
+
+rbm_status rbm_get_noise_refinement(const rbm_ctx* ctx, int32_t* r) {
+  if (!ctx || !r) return RBM_ERR_INVALID;
+  *r = ctx->noise_refine;
+  return RBM_OK;
+}
+
 rbm_status rbm_set_tuning(rbm_ctx* ctx, const rbm_tuning* tuning) {
   rbm_status st = usable(ctx);
   if (st != RBM_OK) return st;
   if (!tuning) return RBM_ERR_INVALID;
   if (tuning->bucket_bits < 0 || tuning->bucket_bits > 24 || tuning->slot_cap < 0 || tuning->sort_cap < 0 ||
-      tuning->sort_cap > 4096 || tuning->graph_steps < 0 || tuning->path < 0 || tuning->path > 3 ||
+      tuning->sort_cap > 4096 || tuning->graph_steps < 0 || tuning->path < 0 || tuning->path > 4 ||
       tuning->wait_limit_us < 0 || tuning->test_skip_arrival < 0 || tuning->test_skip_arrival > 1)
     return RBM_ERR_INVALID;
   if ((tuning->block != 0 && tuning->block != 256) ||
@@ -1017,7 +1161,7 @@ rbm_status rbm_get_tuning(const rbm_ctx* ctx, rbm_tuning* tuning) {
   tuning->sort_cap = static_cast<int32_t>(ctx->ps.sort_cap);
   tuning->block = ctx->cfg.block;
   tuning->direct_block = ctx->cfg.direct_block;
-  tuning->path = ctx->use_small ? 3 : ctx->use_coop ? 2 : 1;
+  tuning->path = ctx->use_small ? 3 : ctx->use_coop ? 2 : ctx->use_rec ? 4 : 1;
   return RBM_OK;
 }
 
@@ -1029,9 +1173,7 @@ rbm_status rbm_free(rbm_ctx* ctx) {
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   free_scratch(ctx);
   cudaFree(ctx->xprev);
-  cudaFree(ctx->status);
-  if (ctx->status_host) cudaFreeHost(ctx->status_host);
-  cudaFree(ctx->m_dev);
+  free_status(ctx);
   delete ctx;
   return RBM_OK;
 }
@@ -1095,10 +1237,14 @@ rbm_status rbm_step_profiled(rbm_ctx* ctx, int32_t method, float* kernel_ms, int
   ctx->cfg.max_events = kMax + 1;
   ctx->cfg.names = nm;
   mark_launch(ctx->cfg, ctx->stream, "start");
-  st = enqueue_step(ctx, method, nullptr, ctx->m, ctx->stream);
+  // The record path profiles a run of two steps: its first step's kernels
+  // are those of every step of a run but the last.
+  const int64_t nsteps = (method == RBM_METHOD_RBM && ctx->use_rec) ? 2 : 1;
+  if (nsteps == 2) st = enqueue_rec(ctx, nullptr, ctx->m, 2, ctx->stream);
+  else st = enqueue_step(ctx, method, nullptr, ctx->m, ctx->stream);
   ctx->cfg = saved;
   if (st == RBM_OK) {
-    ctx->m += 1;
+    ctx->m += nsteps;
     cudaError_t e = cudaEventSynchronize(ev[nev - 1]);
     const int nk = nev - 1;
     *nkernels = nk;
@@ -1158,18 +1304,14 @@ rbm_status rbm_batched_init(const rbm_params* base, int32_t nrep, const int64_t*
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
     c->cfg.num_sms = sms;
   c->tuning.graph_steps = 100;
-  if (cudaMalloc(&c->status, sizeof(int32_t)) != cudaSuccess || cudaMalloc(&c->m_dev, sizeof(int64_t)) != cudaSuccess) {
-    cudaFree(c->status);
+  if (!alloc_status(c)) {
     delete c;
     return RBM_ERR_NOMEM;
   }
-  cudaMemset(c->status, 0, sizeof(int32_t));
-  cudaMemset(c->m_dev, 0, sizeof(int64_t));
   st = alloc_batched(c);
   if (st != RBM_OK || cudaDeviceSynchronize() != cudaSuccess) {
     free_scratch(c);
-    cudaFree(c->status);
-    cudaFree(c->m_dev);
+    free_status(c);
     delete c;
     return st != RBM_OK ? st : RBM_ERR_CUDA;
   }
@@ -1241,6 +1383,7 @@ rbm_status rbm_autotune(rbm_ctx* ctx, int32_t trial_steps, const char* table_pat
       cands.push_back({1, 0});
       cands.push_back({2, 0});
       cands.push_back({3, 0});
+      cands.push_back({4, 0});
     }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -1259,7 +1402,8 @@ rbm_status rbm_autotune(rbm_ctx* ctx, int32_t trial_steps, const char* table_pat
         rbm_tuning t = ctx->tuning;
         t.path = cd.first;
         st = rbm_set_tuning(ctx, &t);
-        if (st == RBM_OK && ((ctx->use_small ? 3 : ctx->use_coop ? 2 : 1) != cd.first)) continue;  // not available
+        if (st == RBM_OK && ((ctx->use_small ? 3 : ctx->use_coop ? 2 : ctx->use_rec ? 4 : 1) != cd.first))
+          continue;  // not available
       }
       if (st != RBM_OK) break;
       cudaMemcpyAsync(scratch, real_x, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
@@ -1267,7 +1411,11 @@ rbm_status rbm_autotune(rbm_ctx* ctx, int32_t trial_steps, const char* table_pat
       const int64_t m0 = ctx->m;
       enqueue_step(ctx, RBM_METHOD_RBM, nullptr, m0, ctx->stream);  // warm-up
       cudaEventRecord(e0, ctx->stream);
-      for (int32_t s = 0; s < trial_steps; ++s) enqueue_step(ctx, RBM_METHOD_RBM, nullptr, m0, ctx->stream);
+      if (ctx->use_rec) {  // the record path runs its steps as one run, as rbm_run does
+        enqueue_rec(ctx, nullptr, m0, trial_steps, ctx->stream);
+      } else {
+        for (int32_t s = 0; s < trial_steps; ++s) enqueue_step(ctx, RBM_METHOD_RBM, nullptr, m0, ctx->stream);
+      }
       cudaEventRecord(e1, ctx->stream);
       cudaEventSynchronize(e1);
       ctx->x = real_x;
@@ -1343,7 +1491,7 @@ rbm_status rbm_surrogate_config(rbm_ctx* ctx, int32_t train_every, double fallba
   RBM_CUDA(cudaMalloc(&s.norm, sizeof(float) * 4));
   RBM_CUDA(cudaMalloc(&s.adam_t, sizeof(int)));
   RBM_CUDA(cudaMalloc(&s.flag, sizeof(int)));
-  RBM_CUDA(cudaMalloc(&s.err, sizeof(float)));
+  RBM_CUDA(cudaMalloc(&s.err, 2 * sizeof(float)));  // held-out error after training, drift error
   RBM_CUDA(cudaMalloc(&s.counters, 2 * sizeof(unsigned long long)));
   RBM_CUDA(cudaMalloc(&s.partial, sizeof(float) * (np + 1) * s.partial_blocks));
   RBM_CUDA(cudaMalloc(&s.qidx, sizeof(uint32_t) * s.nq));
@@ -1354,7 +1502,7 @@ rbm_status rbm_surrogate_config(rbm_ctx* ctx, int32_t train_every, double fallba
   RBM_CUDA(cudaMemcpy(s.norm, norm0, sizeof(norm0), cudaMemcpyHostToDevice));
   RBM_CUDA(cudaMemset(s.adam_t, 0, sizeof(int)));
   RBM_CUDA(cudaMemset(s.flag, 0, sizeof(int)));
-  RBM_CUDA(cudaMemset(s.err, 0, sizeof(float)));
+  RBM_CUDA(cudaMemset(s.err, 0, 2 * sizeof(float)));
   RBM_CUDA(cudaMemset(s.counters, 0, 2 * sizeof(unsigned long long)));
   {
     cudaError_t e = sur_init(s, ctx->status, ctx->prm.seed ^ 0x5EED5EEDull, ctx->stream);
@@ -1366,6 +1514,11 @@ rbm_status rbm_surrogate_config(rbm_ctx* ctx, int32_t train_every, double fallba
   RBM_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->sur_on = true;
   ctx->sur_every = train_every;
+  ctx->sur_interval = train_every;
+  ctx->sur_min_interval = std::max(1, train_every / 16);
+  ctx->sur_drift = -1.0f;
+  ctx->sur_forced_off = false;
+  ctx->sur_forced = 0;
   ctx->sur_iters_first = iters_first;
   ctx->sur_iters = iters_per_checkpoint;
   ctx->sur_max_rounds = max_rounds;
@@ -1404,6 +1557,17 @@ rbm_status rbm_surrogate_stats(rbm_ctx* ctx, double* last_rel_err, int64_t* n_su
   if (n_fallback_steps) *n_fallback_steps = static_cast<int64_t>(cnt[1]);
   if (active) *active = flag;
   if (n_adam_steps) *n_adam_steps = ctx->sur_adam_total;
+  return RBM_OK;
+}
+
+rbm_status rbm_surrogate_drift(const rbm_ctx* ctx, double* drift_err, int32_t* interval, int32_t* forced_off,
+                               int64_t* n_forced_intervals) {
+  if (!ctx) return RBM_ERR_INVALID;
+  if (!ctx->sur_on) return RBM_ERR_STATE;
+  if (drift_err) *drift_err = ctx->sur_drift;
+  if (interval) *interval = ctx->sur_interval;
+  if (forced_off) *forced_off = ctx->sur_forced_off ? 1 : 0;
+  if (n_forced_intervals) *n_forced_intervals = ctx->sur_forced;
   return RBM_OK;
 }
 
@@ -1532,10 +1696,12 @@ constexpr uint32_t kSurStateMagic = 0x52425347u;  // "RBSG"
 struct SurStateHeader {
   uint32_t magic, version, np, pad;
   int32_t adam_t, flag, trained, norm_given;
-  float err, pad2;
+  float err, drift_err;
   uint64_t counters[2];
   int64_t last, adam_total;
   float norm[4];
+  int32_t interval, forced_off;
+  int64_t forced;
 };
 size_t sur_state_bytes() {
   return sizeof(SurStateHeader) + 3 * sizeof(float) * static_cast<size_t>(surrogate_param_count());
@@ -1557,11 +1723,15 @@ rbm_status rbm_surrogate_save(rbm_ctx* ctx, void* host_buf, int64_t bytes) {
   const size_t np = static_cast<size_t>(surrogate_param_count());
   SurStateHeader h{};
   h.magic = kSurStateMagic;
-  h.version = 1;
+  h.version = 2;
   h.np = static_cast<uint32_t>(np);
   RBM_CUDA(cudaMemcpy(&h.adam_t, ctx->ss.adam_t, sizeof(int), cudaMemcpyDeviceToHost));
   RBM_CUDA(cudaMemcpy(&h.flag, ctx->ss.flag, sizeof(int), cudaMemcpyDeviceToHost));
   RBM_CUDA(cudaMemcpy(&h.err, ctx->ss.err, sizeof(float), cudaMemcpyDeviceToHost));
+  RBM_CUDA(cudaMemcpy(&h.drift_err, ctx->ss.err + 1, sizeof(float), cudaMemcpyDeviceToHost));
+  h.interval = ctx->sur_interval;
+  h.forced_off = ctx->sur_forced_off ? 1 : 0;
+  h.forced = ctx->sur_forced;
   RBM_CUDA(cudaMemcpy(h.counters, ctx->ss.counters, sizeof(h.counters), cudaMemcpyDeviceToHost));
   RBM_CUDA(cudaMemcpy(h.norm, ctx->ss.norm, sizeof(h.norm), cudaMemcpyDeviceToHost));
   h.trained = ctx->sur_trained ? 1 : 0;
@@ -1585,7 +1755,7 @@ rbm_status rbm_surrogate_load(rbm_ctx* ctx, const void* host_buf, int64_t bytes)
   SurStateHeader h;
   std::memcpy(&h, host_buf, sizeof(h));
   const size_t np = static_cast<size_t>(surrogate_param_count());
-  if (h.magic != kSurStateMagic || h.version != 1 || h.np != np) return RBM_ERR_INVALID;
+  if (h.magic != kSurStateMagic || h.version != 2 || h.np != np || h.interval < 1) return RBM_ERR_INVALID;
   RBM_CUDA(cudaStreamSynchronize(ctx->stream));
   const float* f = reinterpret_cast<const float*>(static_cast<const unsigned char*>(host_buf) + sizeof(h));
   RBM_CUDA(cudaMemcpy(ctx->ss.theta, f, sizeof(float) * np, cudaMemcpyHostToDevice));
@@ -1594,6 +1764,10 @@ rbm_status rbm_surrogate_load(rbm_ctx* ctx, const void* host_buf, int64_t bytes)
   RBM_CUDA(cudaMemcpy(ctx->ss.adam_t, &h.adam_t, sizeof(int), cudaMemcpyHostToDevice));
   RBM_CUDA(cudaMemcpy(ctx->ss.flag, &h.flag, sizeof(int), cudaMemcpyHostToDevice));
   RBM_CUDA(cudaMemcpy(ctx->ss.err, &h.err, sizeof(float), cudaMemcpyHostToDevice));
+  RBM_CUDA(cudaMemcpy(ctx->ss.err + 1, &h.drift_err, sizeof(float), cudaMemcpyHostToDevice));
+  ctx->sur_interval = h.interval;
+  ctx->sur_forced_off = h.forced_off != 0;
+  ctx->sur_forced = h.forced;
   RBM_CUDA(cudaMemcpy(ctx->ss.counters, h.counters, sizeof(h.counters), cudaMemcpyHostToDevice));
   RBM_CUDA(cudaMemcpy(ctx->ss.norm, h.norm, sizeof(h.norm), cudaMemcpyHostToDevice));
   ctx->sur_trained = h.trained != 0;
@@ -1668,7 +1842,9 @@ rbm_status rbm_latency_floor(rbm_ctx* ctx, float* us) {
 rbm_status rbm_launches_per_step(const rbm_ctx* ctx, int32_t method, int32_t* launches) {
   if (!ctx || !launches) return RBM_ERR_INVALID;
   // RBM-1 inside a run: the previous step bucketed this one's ids (lookahead)
-  if (method == RBM_METHOD_RBM)
+  if (method == RBM_METHOD_RBM && ctx->use_rec)
+    *launches = 4;  // split, scan, step, fix-up (a run adds its first step's scatter)
+  else if (method == RBM_METHOD_RBM)
     *launches = (ctx->use_coop || ctx->batched || ctx->use_small) ? 1 : rbm_tail_launches(ctx->ps, ctx->prm.p);
   else if (method == RBM_METHOD_DIRECT) *launches = 2;  // upper bound: sum (+ chunk reduction)
   else if (method == RBM_METHOD_SURROGATE)  // network step + the flag-gated RBM step that buckets its own ids

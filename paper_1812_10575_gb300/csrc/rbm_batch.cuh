@@ -13,36 +13,58 @@ constexpr int kModePerm = 0;    // write the permutation only
 constexpr int kModeStep = 1;    // step the batches
 constexpr int kModeForces = 2;  // write the interaction forces only
 
+// fk = 1/(|C|-1) sum_{j in C, j != i} K(X^i - X^j) for this lane's member i of
+// the batch held by the p lanes from `base` (other members' rows by
+// shuffles); zero for a singleton.  All 32 lanes call it together.
+template <typename T, int D>
+__device__ __forceinline__ void batch_force(const StepParams<T>& a, bool valid, int lg, int bs, int base,
+                                            const Row<T, D>& r, T (&fk)[D]) {
+  const int p = a.p;
+#pragma unroll
+  for (int k = 0; k < D; ++k) fk[k] = T(0);
+  for (int j = 1; j < p; ++j) {
+    int sg = lg + j;
+    if (sg >= p) sg -= p;
+    T xj[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) xj[k] = __shfl_sync(0xffffffffu, r.x[k], base + sg);
+    if (valid && sg < bs) add_pair_force_rt<T, D>(a.kf, a.kparam, a.radius_sq, r.x, xj, fk);
+  }
+  if (!valid) return;
+  const T inv = (bs > 1) ? T(1) / static_cast<T>(bs - 1) : T(0);
+#pragma unroll
+  for (int k = 0; k < D; ++k) fk[k] = (bs > 1) ? fk[k] * inv : T(0);
+}
+
 // ---------------------------------------------------------------------------
 // One batch per group of p consecutive lanes (p <= 32).  All 32 lanes of the
-// warp call this together (the shuffles use the full mask); lanes outside a
-// valid batch member pass valid = false and store nothing.
+// warp call these together (the shuffles use the full mask); lanes outside a
+// valid batch member pass valid = false.
 //   bs    - members of this batch (p, or N mod p for the last batch)
 //   lg    - this lane's index inside its group
-// ---------------------------------------------------------------------------
 //   r     - this lane's position row (any value when !valid)
-template <typename T, int D, int MODE>
-__device__ __forceinline__ void batch_group_row(const StepParams<T>& a, uint32_t m32, uint32_t id, bool valid, int lg,
-                                                int bs, Row<T, D> r) {
-  const int p = a.p;
+// ---------------------------------------------------------------------------
+
+// The step of this lane's member: r becomes its new row (the pad lane kept);
+// returns valid.  The in-batch force, -grad V, the Brownian increment of
+// (id, m) and the Euler-Maruyama update (or the exact pair flow of the
+// splitting scheme, or the Verlet recurrence).
+template <typename T, int D>
+__device__ __forceinline__ bool batch_group_update(const StepParams<T>& a, uint32_t m32, uint32_t id, bool valid,
+                                                   int lg, int bs, Row<T, D>& r) {
   const int lane = threadIdx.x & 31;
   const int base = lane - lg;
   if (!valid) {
 #pragma unroll
     for (int k = 0; k < D; ++k) r.x[k] = T(0);
-    r.pad = T(0);
   }
-  T fk[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) fk[k] = T(0);
-
-  if (MODE == kModeStep && a.scheme == RBM_SCHEME_SPLIT) {
+  if (a.scheme == RBM_SCHEME_SPLIT) {
     // Exact pair flow of K (p = 2), then the Euler-Maruyama step of V and noise.
     const int src = base + (lg ^ 1);
     T xj[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) xj[k] = __shfl_sync(0xffffffffu, r.x[k], src);
-    if (!valid) return;
+    if (!valid) return false;
     T y0[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) y0[k] = r.x[k];
@@ -67,39 +89,46 @@ __device__ __forceinline__ void batch_group_row(const StepParams<T>& a, uint32_t
         for (int k = 0; k < D; ++k) y0[k] = mid[k] + T(0.5) * newlen * (delta[k] / len);
       }
     }
+    T fk[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) fk[k] = T(0);
     T y[D];
     euler_update<T, D>(a, id, m32, y0, fk, y, true);
 #pragma unroll
     for (int k = 0; k < D; ++k) r.x[k] = y[k];
-    store_row<T, D>(a.x, id, r);
-    return;
+    return true;
   }
-
-  for (int j = 1; j < p; ++j) {
-    int sg = lg + j;
-    if (sg >= p) sg -= p;
-    T xj[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) xj[k] = __shfl_sync(0xffffffffu, r.x[k], base + sg);
-    if (valid && sg < bs) add_pair_force_rt<T, D>(a.kf, a.kparam, a.radius_sq, r.x, xj, fk);
-  }
-  if (!valid) return;
-  const T inv = (bs > 1) ? T(1) / static_cast<T>(bs - 1) : T(0);
-#pragma unroll
-  for (int k = 0; k < D; ++k) fk[k] = (bs > 1) ? fk[k] * inv : T(0);
-  if (MODE == kModeForces) {
-    Row<T, D> f;
-#pragma unroll
-    for (int k = 0; k < D; ++k) f.x[k] = fk[k];
-    f.pad = T(0);
-    store_row<T, D>(a.fout, id, f);
-    return;
-  }
+  T fk[D];
+  batch_force<T, D>(a, valid, lg, bs, base, r, fk);
+  if (!valid) return false;
   T y[D];
   scheme_update<T, D>(a, id, m32, r.x, fk, y);
 #pragma unroll
   for (int k = 0; k < D; ++k) r.x[k] = y[k];
-  store_row<T, D>(a.x, id, r);
+  return true;
+}
+
+template <typename T, int D, int MODE>
+__device__ __forceinline__ void batch_group_row(const StepParams<T>& a, uint32_t m32, uint32_t id, bool valid, int lg,
+                                                int bs, Row<T, D> r) {
+  if (!valid) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) r.x[k] = T(0);
+    r.pad = T(0);
+  }
+  if (MODE == kModeStep) {
+    if (batch_group_update<T, D>(a, m32, id, valid, lg, bs, r)) store_row<T, D>(a.x, id, r);
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  T fk[D];
+  batch_force<T, D>(a, valid, lg, bs, lane - lg, r, fk);
+  if (!valid) return;
+  Row<T, D> f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) f.x[k] = fk[k];
+  f.pad = T(0);
+  store_row<T, D>(a.fout, id, f);
 }
 
 // As batch_group_row, with the row loaded from the position array.

@@ -87,6 +87,30 @@ __device__ __forceinline__ void brownian(uint32_t id, uint32_t m32, uint32_t rep
   }
 }
 
+// The increment of step m when one Brownian path is shared across step
+// sizes (the synchronous coupling of Sec. 3, eq. "coupling", extended to
+// runs with different dt): a run with step dt and refinement r takes
+// z = r^(-1/2) sum_{k<r} z(id, m r + k), the normalised sum of the r standard
+// normal draws a run with step dt/r makes over the same interval, so
+// sqrt(dt) z equals the sum of its sqrt(dt/r) z_k.  Fine step indices are
+// taken mod 2^32, as m is.
+template <typename T, int D>
+__device__ __forceinline__ void brownian_refined(uint32_t id, uint32_t m32, uint32_t refine, uint32_t replica,
+                                                 uint2 seed, T (&z)[D]) {
+  T sum[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) sum[k] = T(0);
+  for (uint32_t f = 0; f < refine; ++f) {
+    T zf[D];
+    brownian<T, D>(id, m32 * refine + f, replica, seed, zf);
+#pragma unroll
+    for (int k = 0; k < D; ++k) sum[k] += zf[k];
+  }
+  const T root = sqrt(static_cast<T>(refine));
+#pragma unroll
+  for (int k = 0; k < D; ++k) z[k] = sum[k] / root;
+}
+
 // Hint: bring the line holding *p into L2 (no value is returned, nothing waits).
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
@@ -271,6 +295,7 @@ struct StepParams {
   const int* skip;       // when set and non-zero, the RBM step kernels do nothing (surrogate mode)
   T* xprev;              // Verlet: V_0 before the first step, X_{n-1} afterwards (N x ld)
   int64_t verlet_m0;     // Verlet: the step index of the Taylor start
+  uint32_t noise_refine; // r > 1: the increment of step m sums the r increments of fine steps m r + k
 };
 
 template <typename T>
@@ -357,7 +382,8 @@ __device__ __forceinline__ void euler_update(const StepParams<T>& a, uint32_t id
                                              const T (&fk)[D], T (&y)[D], bool split_flow = false) {
   T z[D];
   if (a.sq != T(0)) {
-    brownian<T, D>(id, m32, a.replica, a.seed, z);
+    if (a.noise_refine > 1u) brownian_refined<T, D>(id, m32, a.noise_refine, a.replica, a.seed, z);
+    else brownian<T, D>(id, m32, a.replica, a.seed, z);
   } else {
 #pragma unroll
     for (int k = 0; k < D; ++k) z[k] = T(0);

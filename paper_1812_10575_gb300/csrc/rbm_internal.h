@@ -42,6 +42,23 @@ struct CoopScratch {
   uint32_t nbuckets = 0;        // k * grid
 };
 
+// Record-path scratch (rec_step.cu): the positions of a large system moving
+// through each step as records (row with the id in its pad lane, 32 key bits)
+// in two levels of buckets.
+struct RecScratch {
+  int top_bits = 0, sub_bits = 0;
+  uint32_t ntop = 1, nsub = 1;      // buckets per level
+  uint32_t top_cap = 0, sub_cap = 0;  // records per top bucket / per sub-bucket
+  float4* top_rows = nullptr;       // [ntop * top_cap]
+  uint32_t* top_keys = nullptr;
+  float4* sub_rows = nullptr;       // [ntop * nsub * sub_cap]
+  uint32_t* sub_keys = nullptr;
+  uint32_t* top_fill = nullptr;     // [2 ntop] fill counters by step parity
+  uint32_t* sub_fill = nullptr;     // [2 ntop nsub]
+  uint32_t* sub_start = nullptr;    // [ntop nsub + 1] sorted start of each sub-bucket
+  float4* side = nullptr;           // [ntop nsub * 32] members of batches crossing sub-bucket ends
+};
+
 // Batched-replica scratch.
 struct BatchedScratch {
   uint32_t* order = nullptr;        // replica ids, block-major
@@ -82,7 +99,7 @@ struct SurrogateScratch {
   float* norm = nullptr;
   int* adam_t = nullptr;
   int* flag = nullptr;
-  float* err = nullptr;
+  float* err = nullptr;              // [0] held-out error after training, [1] drift error
   unsigned long long* counters = nullptr;
   float* partial = nullptr;
   uint32_t partial_blocks = 0;
@@ -129,6 +146,16 @@ int rbm_tail_launches(const PermScratch& ps, int p);
 // Largest bucket the shared-memory sort of the multi-kernel path takes.
 uint32_t max_sort_cap();
 
+// Record path (rec_step.cu): FP32, d = 3, p <= 32, any scheme but Verlet.
+bool rec_eligible(int dtype, int d, int p, int scheme);
+void rec_geometry(uint32_t n, int tuned_bits, RecScratch* rs);
+cudaError_t rec_alloc(uint32_t n, RecScratch* rs);
+void rec_free(RecScratch* rs);
+cudaError_t prepare_rec_kernels();
+// `count` RBM-1 steps from the step of `params` (StepParams<float>).
+cudaError_t launch_rec_run(const RecScratch& rs, const void* params, int64_t count, const LaunchCfg& cfg,
+                           cudaStream_t st);
+
 // Cooperative step (coop_step.cu): mode as for launch_rbm_tail.
 cudaError_t prepare_coop_kernels(int* blocks_per_sm);
 uint32_t coop_max_buckets();
@@ -167,6 +194,7 @@ cudaError_t sur_gradient(const SurrogateScratch& ss, int32_t* status, const floa
 cudaError_t sur_forces(const SurrogateScratch& ss, int32_t* status, const float* q, uint32_t nq, float* fout,
                        const LaunchCfg& cfg, cudaStream_t st);
 cudaError_t sur_check(const SurrogateScratch& ss, int32_t* status, cudaStream_t st);
+cudaError_t sur_drift(const SurrogateScratch& ss, int32_t* status, cudaStream_t st);
 cudaError_t sur_step(const SurrogateScratch& ss, const void* params, const LaunchCfg& cfg, cudaStream_t st);
 
 // Direct O(N^2) pieces (direct.cu).  `mode`: 0 = step (into xout), 1 =

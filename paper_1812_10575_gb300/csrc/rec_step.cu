@@ -1,0 +1,609 @@
+// RBM-1 steps of large systems with the positions moving through the step
+// as records, so that every pass over the state streams through DRAM in
+// runs instead of gathering random rows.
+//
+// Algorithm "randomdiv" (Sec. 2.1 of arXiv:1812.10575) per step m: the ids
+// sorted by (key, id), key = Philox(id, m, r, 0), batch q = sorted positions
+// [q p, min(q p + p, N)), each batch moved by eq. "firstalgorithm".  The sort
+// is a two-level bucketing by the top key bits followed by a sort of each
+// small bucket in shared memory; here the buckets carry the particles' rows,
+// not their ids:
+//   record    = the row (x, y, z, id in the pad lane) and 32 key bits (the
+//               bits below the top-level digit);
+//   top level = 2^top_bits buckets by the top key bits, fixed-capacity
+//               regions; each writer reserves one run per bucket it feeds
+//               (one atomic per block and bucket), so records land in runs of
+//               tens of rows;
+//   sub level = 2^sub_bits sub-buckets per top bucket by the next key bits,
+//               filled the same way by k_rec_split;
+//   k_rec_scan   - the sorted start of every sub-bucket (the sub-buckets in
+//                  (top, sub) order are the random division in key order);
+//   k_rec_step   - one block per sub-bucket (about 2048 records): sort by the
+//                  remaining key bits (counting sort on 11 bits, insertion
+//                  sort, full keys recomputed only on ties of the 32 carried
+//                  bits), step every batch lying wholly inside it, park the
+//                  members of batches crossing its ends, and send every
+//                  moved record to its top-level bucket of step m + 1 (key
+//                  of m + 1 computed here) - or, at the last step of a run,
+//                  write the new positions to the caller's array by id;
+//   k_rec_fixup  - the batches crossing sub-bucket ends, from the parked
+//                  members, sent on the same way.
+// A run of K steps starts with k_rec_scatter, which reads the caller's array
+// in id order and fills the top level of its first step; the caller's array
+// holds the positions again after the run's last step.  Every update reads
+// the positions of step m only (batches are disjoint), as the explicit scheme
+// requires.  Capacities are the mean count plus twelve standard deviations
+// of the binomial count (and a constant); a count beyond one (never seen for
+// Philox keys) latches RBM_ERR_STATE and nothing is written past the region.
+#include <cmath>
+
+#include "rbm_batch.cuh"
+#include "rbm_device.cuh"
+#include "rbm_internal.h"
+
+namespace rbm {
+namespace {
+
+constexpr uint32_t kSubTarget = 2048;   // mean records per sub-bucket
+constexpr uint32_t kSubCapMax = 3072;   // largest sub-bucket sorted in shared memory
+constexpr int kStepThreads = 512;
+constexpr int kStepPer = kSubCapMax / kStepThreads;  // records per thread of k_rec_step
+constexpr int kSplitThreads = 512;
+constexpr int kSplitPer = 8;            // records per thread of k_rec_split and k_rec_scatter
+constexpr uint32_t kChunk = kSplitThreads * kSplitPer;
+constexpr int kFineBits = 11;           // counting-sort digit inside a sub-bucket
+constexpr uint32_t kFine = 1u << kFineBits;
+constexpr int kMaxDigitBits = 11;       // top and sub digits: at most 2048 values
+constexpr int kSide = 32;               // parked members per sub-bucket (p <= 32)
+
+struct RecArgs {
+  float4* top_rows;     // [ntop * top_cap]
+  uint32_t* top_keys;
+  float4* sub_rows;     // [nbuckets * sub_cap]
+  uint32_t* sub_keys;
+  uint32_t* top_fill;   // [2][ntop] records per top bucket, by step parity
+  uint32_t* sub_fill;   // [2][nbuckets]
+  uint32_t* sub_start;  // [nbuckets + 1]
+  float4* side;         // [nbuckets * kSide]
+  uint32_t top_cap, sub_cap, ntop, nsub, nbuckets;
+  int top_bits, sub_bits;
+};
+
+__device__ __forceinline__ uint32_t rec_id(const float4& r) { return __float_as_uint(r.w); }
+
+__device__ __forceinline__ uint32_t top_of(uint64_t key, int top_bits) {
+  return top_bits ? static_cast<uint32_t>(key >> (64 - top_bits)) : 0u;
+}
+// The 32 key bits below the top-level digit.
+__device__ __forceinline__ uint32_t key32_of(uint64_t key, int top_bits) {
+  return static_cast<uint32_t>((key << top_bits) >> 32);
+}
+__device__ __forceinline__ uint32_t sub_of(uint32_t k32, int sub_bits) {
+  return sub_bits ? (k32 >> (32 - sub_bits)) : 0u;
+}
+
+__device__ __forceinline__ Row<float, 3> to_row(const float4& v) {
+  Row<float, 3> r;
+  r.x[0] = v.x; r.x[1] = v.y; r.x[2] = v.z; r.pad = v.w;
+  return r;
+}
+__device__ __forceinline__ float4 to_rec(const Row<float, 3>& r) { return make_float4(r.x[0], r.x[1], r.x[2], r.pad); }
+
+// The new position of particle id in the caller's array (its pad lane left as
+// the caller wrote it).
+__device__ __forceinline__ void write_position(float* x, uint32_t id, const Row<float, 3>& r) {
+  float* row = x + static_cast<size_t>(id) * 4;
+  *reinterpret_cast<float2*>(row) = make_float2(r.x[0], r.x[1]);
+  row[2] = r.x[2];
+}
+
+// Top-level bucket and carried key bits of particle id at step m1.
+__device__ __forceinline__ void top_key(const StepParams<float>& a, const RecArgs& g, uint32_t id, uint32_t m1,
+                                        uint32_t& t, uint32_t& k32) {
+  const uint64_t key = perm_key(id, m1, a.replica, a.seed);
+  t = top_of(key, g.top_bits);
+  k32 = key32_of(key, g.top_bits);
+}
+
+__device__ __forceinline__ void put_top(const StepParams<float>& a, const RecArgs& g, uint32_t par, uint32_t t,
+                                        uint32_t pos, const float4& rec, uint32_t k32) {
+  if (pos < g.top_cap) {
+    const size_t at = static_cast<size_t>(t) * g.top_cap + pos;
+    g.top_rows[at] = rec;
+    g.top_keys[at] = k32;
+  } else {
+    latch_status(a.status, RBM_ERR_STATE);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// First step of a run: the caller's rows in id order into the top level.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSplitThreads) k_rec_scatter(StepParams<float> a, RecArgs g) {
+  __shared__ uint32_t s_hist[1u << kMaxDigitBits];
+  __shared__ uint32_t s_base[1u << kMaxDigitBits];
+  const uint32_t m32 = step_index(a);
+  const uint32_t par = m32 & 1u;
+  for (uint32_t u = threadIdx.x; u < g.ntop; u += blockDim.x) s_hist[u] = 0;
+  __syncthreads();
+  const uint32_t i0 = blockIdx.x * kChunk;
+  uint32_t tr[kSplitPer], k32[kSplitPer];
+#pragma unroll
+  for (int k = 0; k < kSplitPer; ++k) {
+    const uint32_t i = i0 + k * kSplitThreads + threadIdx.x;
+    if (i < a.n) {
+      uint32_t t;
+      top_key(a, g, i, m32, t, k32[k]);
+      tr[k] = t | (atomicAdd(&s_hist[t], 1u) << 16);
+    }
+  }
+  __syncthreads();
+  for (uint32_t u = threadIdx.x; u < g.ntop; u += blockDim.x)
+    if (s_hist[u]) s_base[u] = atomicAdd(&g.top_fill[par * g.ntop + u], s_hist[u]);
+  __syncthreads();
+  float4 v[kSplitPer];  // every row in flight before the first store
+#pragma unroll
+  for (int k = 0; k < kSplitPer; ++k) {
+    const uint32_t i = i0 + k * kSplitThreads + threadIdx.x;
+    if (i < a.n) v[k] = reinterpret_cast<const float4*>(a.x)[i];
+  }
+#pragma unroll
+  for (int k = 0; k < kSplitPer; ++k) {
+    const uint32_t i = i0 + k * kSplitThreads + threadIdx.x;
+    if (i < a.n) {
+      v[k].w = __uint_as_float(i);
+      const uint32_t t = tr[k] & 0xffffu;
+      put_top(a, g, par, t, s_base[t] + (tr[k] >> 16), v[k], k32[k]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Top level -> sub level: block (t, j) takes records [j C, (j+1) C) of top
+// bucket t.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSplitThreads) k_rec_split(StepParams<float> a, RecArgs g, uint32_t chunks) {
+  __shared__ uint32_t s_hist[1u << kMaxDigitBits];
+  __shared__ uint32_t s_base[1u << kMaxDigitBits];
+  const uint32_t m32 = step_index(a);
+  const uint32_t par = m32 & 1u;
+  const uint32_t t = blockIdx.x / chunks, j = blockIdx.x - t * chunks;
+  const uint32_t filled = g.top_fill[par * g.ntop + t];
+  if (j == 0 && threadIdx.x == 0 && filled > g.top_cap) latch_status(a.status, RBM_ERR_STATE);
+  const uint32_t count = min(filled, g.top_cap);
+  const uint32_t lo = j * kChunk;
+  if (lo >= count) return;  // uniform over the block
+  for (uint32_t u = threadIdx.x; u < g.nsub; u += blockDim.x) s_hist[u] = 0;
+  __syncthreads();
+  const size_t src0 = static_cast<size_t>(t) * g.top_cap + lo;
+  uint32_t ur[kSplitPer], k32[kSplitPer];
+  float4 v[kSplitPer];  // every record in flight before the first store
+#pragma unroll
+  for (int k = 0; k < kSplitPer; ++k) {
+    const uint32_t e = k * kSplitThreads + threadIdx.x;
+    if (lo + e < count) {
+      k32[k] = g.top_keys[src0 + e];
+      v[k] = g.top_rows[src0 + e];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kSplitPer; ++k) {
+    const uint32_t e = k * kSplitThreads + threadIdx.x;
+    if (lo + e < count) {
+      const uint32_t u = sub_of(k32[k], g.sub_bits);
+      ur[k] = u | (atomicAdd(&s_hist[u], 1u) << 16);
+    }
+  }
+  __syncthreads();
+  for (uint32_t u = threadIdx.x; u < g.nsub; u += blockDim.x)
+    if (s_hist[u]) s_base[u] = atomicAdd(&g.sub_fill[par * g.nbuckets + t * g.nsub + u], s_hist[u]);
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kSplitPer; ++k) {
+    const uint32_t e = k * kSplitThreads + threadIdx.x;
+    if (lo + e < count) {
+      const uint32_t u = ur[k] & 0xffffu;
+      const uint32_t pos = s_base[u] + (ur[k] >> 16);
+      if (pos < g.sub_cap) {
+        const size_t at = static_cast<size_t>(t * g.nsub + u) * g.sub_cap + pos;
+        g.sub_rows[at] = v[k];
+        g.sub_keys[at] = k32[k];
+      } else {
+        latch_status(a.status, RBM_ERR_STATE);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Sorted start of every sub-bucket (one block); clears the counters the
+// next step fills.  A total other than N latches RBM_ERR_STATE.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_rec_scan(StepParams<float> a, RecArgs g) {
+  __shared__ uint32_t s_warp[32];
+  const uint32_t m32 = step_index(a);
+  const uint32_t par = m32 & 1u, np = par ^ 1u;
+  const uint32_t* cnt = g.sub_fill + par * g.nbuckets;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const uint32_t nb = g.nbuckets;
+  const uint32_t per = (nb + blockDim.x - 1) / blockDim.x;
+  const uint32_t lo = min(nb, threadIdx.x * per), hi = min(nb, lo + per);
+  uint32_t sum = 0;
+  for (uint32_t b = lo; b < hi; ++b) sum += cnt[b];
+  uint32_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = (lane < nwarps) ? s_warp[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += v;
+    }
+    if (lane < nwarps) s_warp[lane] = w;
+  }
+  __syncthreads();
+  uint32_t run = ((warp > 0) ? s_warp[warp - 1] : 0u) + incl - sum;
+  for (uint32_t b = lo; b < hi; ++b) {
+    g.sub_start[b] = run;
+    run += cnt[b];
+  }
+  if (threadIdx.x == blockDim.x - 1) {
+    g.sub_start[nb] = run;  // the last thread's run ends at the total
+    if (run != a.n) latch_status(a.status, RBM_ERR_STATE);
+  }
+  for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) g.sub_fill[np * nb + b] = 0;
+  for (uint32_t u = threadIdx.x; u < g.ntop; u += blockDim.x) g.top_fill[np * g.ntop + u] = 0;
+}
+
+// The sub-bucket holding sorted position pos (largest b with start[b] <= pos).
+__device__ __forceinline__ uint32_t sub_bucket_at(const uint32_t* start, uint32_t nb, uint32_t pos) {
+  uint32_t lo = 0, hi = nb;  // start[lo] <= pos < start[hi]
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (start[mid] <= pos) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// (key, id) order of two records of one sub-bucket: the carried bits below
+// the sub digit, then (on a tie) the full keys and the ids.
+__device__ __forceinline__ bool rec_less(const StepParams<float>& a, uint32_t m32, uint32_t fa, uint32_t ida,
+                                         uint32_t fb, uint32_t idb) {
+  if (fa != fb) return fa < fb;
+  const uint64_t ka = perm_key(ida, m32, a.replica, a.seed), kb = perm_key(idb, m32, a.replica, a.seed);
+  return ka < kb || (ka == kb && ida < idb);
+}
+
+// ---------------------------------------------------------------------------
+// One block per sub-bucket: sort, step the contained batches, park the
+// members of crossing batches, send the moved records on (or, at the last
+// step of a run, write the positions by id).
+// ---------------------------------------------------------------------------
+template <bool kLast>
+__global__ void __launch_bounds__(kStepThreads, 2) k_rec_step(StepParams<float> a, RecArgs g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* srow = reinterpret_cast<float4*>(smem_raw);                 // [sub_cap] records, slot order
+  uint32_t* sfine = reinterpret_cast<uint32_t*>(srow + g.sub_cap);     // [sub_cap] bits below the sub digit
+  uint16_t* sidx = reinterpret_cast<uint16_t*>(sfine + g.sub_cap);    // [sub_cap] slot of each sorted position
+  uint8_t* spark = reinterpret_cast<uint8_t*>(sidx + g.sub_cap);      // [sub_cap] 1: member of a crossing batch
+  __shared__ uint32_t s_hist[kFine];
+  __shared__ uint32_t s_base[1u << kMaxDigitBits];
+  __shared__ uint32_t s_warp[32];
+  const uint32_t b = blockIdx.x;
+  const uint32_t m32 = step_index(a);
+  const uint32_t par = m32 & 1u;
+  const uint32_t filled = g.sub_fill[par * g.nbuckets + b];
+  if (threadIdx.x == 0 && filled > g.sub_cap) latch_status(a.status, RBM_ERR_STATE);
+  const uint32_t cnt = min(filled, g.sub_cap);
+  const uint32_t start = g.sub_start[b];
+  const size_t src0 = static_cast<size_t>(b) * g.sub_cap;
+
+  for (uint32_t u = threadIdx.x; u < kFine; u += blockDim.x) s_hist[u] = 0;
+  for (uint32_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(srow + e));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(g.sub_rows + src0 + e) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  __syncthreads();
+  // counting sort by the kFineBits bits below the sub digit
+  uint32_t fr[kStepPer];
+#pragma unroll
+  for (int k = 0; k < kStepPer; ++k) {
+    const uint32_t e = threadIdx.x + k * kStepThreads;
+    if (e < cnt) {
+      const uint32_t f = g.sub_keys[src0 + e] << g.sub_bits;
+      sfine[e] = f;
+      const uint32_t d = f >> (32 - kFineBits);
+      fr[k] = d | (atomicAdd(&s_hist[d], 1u) << 16);
+    }
+  }
+  __syncthreads();
+  {  // exclusive scan of s_hist
+    constexpr uint32_t per = kFine / kStepThreads;
+    const uint32_t lo = threadIdx.x * per;
+    uint32_t v[per], sum = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < per; ++i) {
+      v[i] = s_hist[lo + i];
+      sum += v[i];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    uint32_t run = incl - sum;
+    for (int w = 0; w < warp; ++w) run += s_warp[w];
+#pragma unroll
+    for (uint32_t i = 0; i < per; ++i) {
+      s_hist[lo + i] = run;
+      run += v[i];
+    }
+  }
+  __syncthreads();
+  asm volatile("cp.async.wait_all;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < kStepPer; ++k) {
+    const uint32_t e = threadIdx.x + k * kStepThreads;
+    if (e < cnt) sidx[s_hist[fr[k] & 0xffffu] + (fr[k] >> 16)] = static_cast<uint16_t>(e);
+  }
+  __syncthreads();  // also publishes every thread's staged records
+  for (uint32_t u = threadIdx.x; u < kFine; u += blockDim.x) {  // insertion sort inside each digit
+    const uint32_t lo = s_hist[u], hi = (u + 1 < kFine) ? s_hist[u + 1] : cnt;
+    for (uint32_t x = lo + 1; x < hi; ++x) {
+      const uint16_t sx = sidx[x];
+      const uint32_t fx = sfine[sx], ix = rec_id(srow[sx]);
+      uint32_t y = x;
+      while (y > lo) {
+        const uint16_t sy = sidx[y - 1];
+        if (!rec_less(a, m32, fx, ix, sfine[sy], rec_id(srow[sy]))) break;
+        sidx[y] = sy;
+        --y;
+      }
+      sidx[y] = sx;
+    }
+  }
+  __syncthreads();
+
+  // batches lying wholly inside [start, end)
+  const uint32_t up = static_cast<uint32_t>(a.p);
+  const uint32_t end = start + cnt;
+  const uint32_t q0 = (start + up - 1) / up;
+  const uint32_t q_end = (end == a.n) ? (a.n + up - 1) / up : end / up;
+  const uint32_t count = (q_end > q0) ? q_end - q0 : 0u;
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gpw = 32 / a.p;
+    const uint32_t per_round = static_cast<uint32_t>(gpw * (kStepThreads / 32));
+    const int gi = lane / a.p, lg = lane - gi * a.p;
+    for (uint32_t r0 = 0; r0 < count; r0 += per_round) {
+      const uint32_t kb = r0 + static_cast<uint32_t>(warp * gpw + gi);
+      bool valid = (gi < gpw) && (kb < count);
+      int bs = a.p;
+      uint32_t slot = 0, id = 0;
+      Row<float, 3> r{};
+      if (valid) {
+        const uint32_t lo = (q0 + kb) * up;
+        bs = static_cast<int>(min(lo + up, a.n) - lo);
+        valid = lg < bs;
+        if (valid) {
+          slot = sidx[lo + lg - start];
+          r = to_row(srow[slot]);
+          id = rec_id(srow[slot]);
+        }
+      }
+      if (batch_group_update<float, 3>(a, m32, id, valid, lg, bs, r)) {
+        if (kLast) write_position(a.x, id, r);
+        else srow[slot] = to_rec(r);
+      }
+    }
+  }
+  // members of batches crossing the ends: parked under the sub-bucket that
+  // holds the batch's first member
+  for (uint32_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const uint32_t pos = start + e;
+    const uint32_t q = pos / up;
+    const bool crossing = q < q0 || q >= q_end;
+    const uint16_t slot = sidx[e];
+    spark[slot] = crossing ? 1 : 0;
+    if (crossing) {
+      const uint32_t qp = q * up;
+      const uint32_t bf = (qp >= start) ? b : sub_bucket_at(g.sub_start, g.nbuckets, qp);
+      g.side[static_cast<size_t>(bf) * kSide + (pos - qp)] = srow[slot];
+    }
+  }
+  if (kLast) return;
+  __syncthreads();
+
+  // the moved records to their top-level buckets of step m + 1
+  const uint32_t np = par ^ 1u;
+  for (uint32_t u = threadIdx.x; u < g.ntop; u += blockDim.x) s_hist[u] = 0;
+  __syncthreads();
+  uint32_t tr[kStepPer], k32[kStepPer];
+#pragma unroll
+  for (int k = 0; k < kStepPer; ++k) {
+    const uint32_t e = threadIdx.x + k * kStepThreads;
+    if (e < cnt && !spark[e]) {
+      uint32_t t;
+      top_key(a, g, rec_id(srow[e]), m32 + 1u, t, k32[k]);
+      tr[k] = t | (atomicAdd(&s_hist[t], 1u) << 16);
+    }
+  }
+  __syncthreads();
+  for (uint32_t u = threadIdx.x; u < g.ntop; u += blockDim.x)
+    if (s_hist[u]) s_base[u] = atomicAdd(&g.top_fill[np * g.ntop + u], s_hist[u]);
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kStepPer; ++k) {
+    const uint32_t e = threadIdx.x + k * kStepThreads;
+    if (e < cnt && !spark[e]) {
+      const uint32_t t = tr[k] & 0xffffu;
+      put_top(a, g, np, t, s_base[t] + (tr[k] >> 16), srow[e], k32[k]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The batch crossing the end of each sub-bucket (at most one starts in a
+// sub-bucket and ends past it), from its parked members.
+// ---------------------------------------------------------------------------
+template <bool kLast>
+__global__ void __launch_bounds__(256) k_rec_fixup(StepParams<float> a, RecArgs g) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gpw = 32 / a.p;
+  const int gi = lane / a.p, lg = lane - gi * a.p;
+  const uint32_t b = (blockIdx.x * (blockDim.x >> 5) + warp) * gpw + gi;
+  const uint32_t m32 = step_index(a);
+  const uint32_t up = static_cast<uint32_t>(a.p);
+  bool valid = (gi < gpw) && b < g.nbuckets;
+  int bs = a.p;
+  uint32_t id = 0;
+  Row<float, 3> r{};
+  if (valid) {
+    const uint32_t start = g.sub_start[b], end = g.sub_start[b + 1];
+    valid = end > start;
+    if (valid) {
+      const uint32_t qp = ((end - 1) / up) * up;
+      const uint32_t hi = min(qp + up, a.n);
+      valid = qp >= start && hi > end;
+      bs = static_cast<int>(hi - qp);
+      valid = valid && lg < bs;
+      if (valid) {
+        const float4 v = g.side[static_cast<size_t>(b) * kSide + lg];
+        r = to_row(v);
+        id = rec_id(v);
+      }
+    }
+  }
+  if (!batch_group_update<float, 3>(a, m32, id, valid, lg, bs, r)) return;
+  if (kLast) {
+    write_position(a.x, id, r);
+  } else {
+    uint32_t t, k32;
+    top_key(a, g, id, m32 + 1u, t, k32);
+    const uint32_t np = (m32 & 1u) ^ 1u;
+    put_top(a, g, np, t, atomicAdd(&g.top_fill[np * g.ntop + t], 1u), to_rec(r), k32);
+  }
+}
+
+size_t step_smem(uint32_t sub_cap) {
+  return static_cast<size_t>(sub_cap) * (sizeof(float4) + sizeof(uint32_t) + sizeof(uint16_t) + sizeof(uint8_t));
+}
+
+RecArgs make_args(const RecScratch& rs) {
+  RecArgs g;
+  g.top_rows = rs.top_rows; g.top_keys = rs.top_keys; g.sub_rows = rs.sub_rows; g.sub_keys = rs.sub_keys;
+  g.top_fill = rs.top_fill; g.sub_fill = rs.sub_fill; g.sub_start = rs.sub_start; g.side = rs.side;
+  g.top_cap = rs.top_cap; g.sub_cap = rs.sub_cap; g.ntop = rs.ntop; g.nsub = rs.nsub; g.nbuckets = rs.ntop * rs.nsub;
+  g.top_bits = rs.top_bits; g.sub_bits = rs.sub_bits;
+  return g;
+}
+
+uint32_t round_up(uint32_t v, uint32_t q) { return (v + q - 1) / q * q; }
+
+}  // namespace
+
+bool rec_eligible(int dtype, int d, int p, int scheme) {
+  return dtype == RBM_F32 && d == 3 && p >= 2 && p <= kSide && scheme != RBM_SCHEME_VERLET;
+}
+
+// Bucket geometry for n records: 2^(top_bits + sub_bits) sub-buckets of at
+// most kSubTarget records on average (or 2^tuned_bits sub-buckets when
+// tuned_bits > 0), the bits split between the levels so that both
+// distributions write runs of tens of records.
+void rec_geometry(uint32_t n, int tuned_bits, RecScratch* rs) {
+  int bits = 0;
+  while (bits < 2 * kMaxDigitBits && (static_cast<uint64_t>(kSubTarget) << bits) < n) ++bits;
+  if (tuned_bits > 0) bits = tuned_bits < 2 * kMaxDigitBits ? tuned_bits : 2 * kMaxDigitBits;
+  rs->top_bits = bits / 2;
+  rs->sub_bits = bits - rs->top_bits;
+  rs->ntop = 1u << rs->top_bits;
+  rs->nsub = 1u << rs->sub_bits;
+  const double top_mean = static_cast<double>(n) / rs->ntop;
+  const double sub_mean = top_mean / rs->nsub;
+  rs->top_cap = round_up(static_cast<uint32_t>(top_mean + 12.0 * std::sqrt(top_mean) + 1024.0), 32);
+  const uint32_t sc = round_up(static_cast<uint32_t>(sub_mean + 12.0 * std::sqrt(sub_mean) + 64.0), 32);
+  rs->sub_cap = sc < kSubCapMax ? sc : kSubCapMax;
+}
+
+cudaError_t rec_alloc(uint32_t n, RecScratch* rs) {
+  const size_t top = static_cast<size_t>(rs->ntop) * rs->top_cap;
+  const size_t nb = static_cast<size_t>(rs->ntop) * rs->nsub;
+  const size_t sub = nb * rs->sub_cap;
+  cudaError_t e = cudaMalloc(&rs->top_rows, top * sizeof(float4));
+  if (e == cudaSuccess) e = cudaMalloc(&rs->top_keys, top * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&rs->sub_rows, sub * sizeof(float4));
+  if (e == cudaSuccess) e = cudaMalloc(&rs->sub_keys, sub * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&rs->top_fill, 2 * rs->ntop * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&rs->sub_fill, 2 * nb * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&rs->sub_start, (nb + 1) * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&rs->side, nb * kSide * sizeof(float4));
+  (void)n;
+  return e;
+}
+
+void rec_free(RecScratch* rs) {
+  cudaFree(rs->top_rows); cudaFree(rs->top_keys); cudaFree(rs->sub_rows); cudaFree(rs->sub_keys);
+  cudaFree(rs->top_fill); cudaFree(rs->sub_fill); cudaFree(rs->sub_start); cudaFree(rs->side);
+  *rs = RecScratch{};
+}
+
+cudaError_t prepare_rec_kernels() {
+  const int bytes = static_cast<int>(step_smem(kSubCapMax));
+  cudaError_t e = cudaFuncSetAttribute(k_rec_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rec_step<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
+// `count` RBM-1 steps from step (m_ptr ? *m_ptr : 0) + a.m_off: clear the
+// counters, fill the first step's top level from the caller's array, then
+// per step split, scan, step and fix-up; the last step writes the positions.
+cudaError_t launch_rec_run(const RecScratch& rs, const void* params, int64_t count, const LaunchCfg& cfg,
+                           cudaStream_t st) {
+  const StepParams<float> a0 = *static_cast<const StepParams<float>*>(params);
+  const RecArgs g = make_args(rs);
+  cudaError_t e = cudaMemsetAsync(rs.top_fill, 0, 2 * rs.ntop * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(rs.sub_fill, 0, 2 * size_t(g.nbuckets) * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  k_rec_scatter<<<(a0.n + kChunk - 1) / kChunk, kSplitThreads, 0, st>>>(a0, g);
+  mark_launch(cfg, st, "k_rec_scatter");
+  const uint32_t chunks = (rs.top_cap + kChunk - 1) / kChunk;
+  const size_t smem = step_smem(rs.sub_cap);
+  const int gpw = 32 / a0.p;
+  const uint32_t fix_groups = 8u * static_cast<uint32_t>(gpw);
+  const uint32_t fix_grid = (g.nbuckets + fix_groups - 1) / fix_groups;
+  for (int64_t k = 0; k < count; ++k) {
+    StepParams<float> a = a0;
+    a.m_off = a0.m_off + k;
+    const bool last = (k + 1 == count);
+    k_rec_split<<<rs.ntop * chunks, kSplitThreads, 0, st>>>(a, g, chunks);
+    mark_launch(cfg, st, "k_rec_split");
+    k_rec_scan<<<1, 1024, 0, st>>>(a, g);
+    mark_launch(cfg, st, "k_rec_scan");
+    if (last) {
+      k_rec_step<true><<<g.nbuckets, kStepThreads, smem, st>>>(a, g);
+      mark_launch(cfg, st, "k_rec_step_last");
+      k_rec_fixup<true><<<fix_grid, 256, 0, st>>>(a, g);
+      mark_launch(cfg, st, "k_rec_fixup_last");
+    } else {
+      k_rec_step<false><<<g.nbuckets, kStepThreads, smem, st>>>(a, g);
+      mark_launch(cfg, st, "k_rec_step");
+      k_rec_fixup<false><<<fix_grid, 256, 0, st>>>(a, g);
+      mark_launch(cfg, st, "k_rec_fixup");
+    }
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace rbm

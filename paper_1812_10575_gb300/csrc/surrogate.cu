@@ -42,7 +42,7 @@ struct SurArgs {
   float* norm;       // mu_x, mu_y, s, sF
   int* adam_t;       // Adam steps taken before the current checkpoint
   int* flag;         // 1: the surrogate drives the steps, 0: the RBM fallback does
-  float* err;        // last held-out relative error
+  float* err;        // [0] last held-out relative error, [1] last drift error
   unsigned long long* counters;  // steps taken by the surrogate, by the fallback
   float* partial;    // [blocks][kNP + 1] per-block gradient and loss
   uint32_t* qidx;    // [nq] sampled particle ids
@@ -480,11 +480,16 @@ __global__ void k_sur_norm(SurArgs s) {
   }
 }
 
-// Held-out relative error and the selection flag (one block).
-__global__ void k_sur_check(SurArgs s) {
+// Relative error ||F_net - F||_2 / ||F||_2 over queries [lo, nq) (one
+// block): the held-out quarter after training (drift = 0: also sets the
+// selection flag), or every query of a fresh sample before training (drift =
+// 1: the error of the network as it drove the interval just ended, into
+// err[1]).
+__global__ void k_sur_check(SurArgs s, int drift) {
   __shared__ double red[2][32];
   double e = 0, f = 0;
-  for (uint32_t i = s.ntrain + threadIdx.x; i < s.nq; i += blockDim.x) {
+  const uint32_t lo = drift ? 0u : s.ntrain;
+  for (uint32_t i = lo + threadIdx.x; i < s.nq; i += blockDim.x) {
     const float2 p = reinterpret_cast<const float2*>(s.fpred)[i];
     const float2 t = reinterpret_cast<const float2*>(s.fq)[i];
     const double dx = static_cast<double>(p.x) - t.x, dyv = static_cast<double>(p.y) - t.y;
@@ -507,8 +512,12 @@ __global__ void k_sur_check(SurArgs s) {
       tf += red[1][w];
     }
     const float rel = static_cast<float>(tf > 0 ? sqrt(te / tf) : 0.0);
-    *s.err = rel;
-    *s.flag = (isfinite(rel) && rel <= s.tol) ? 1 : 0;
+    if (drift) {
+      s.err[1] = rel;
+    } else {
+      s.err[0] = rel;
+      *s.flag = (isfinite(rel) && rel <= s.tol) ? 1 : 0;
+    }
   }
 }
 
@@ -605,7 +614,12 @@ cudaError_t sur_forces(const SurrogateScratch& ss, int32_t* status, const float*
 }
 
 cudaError_t sur_check(const SurrogateScratch& ss, int32_t* status, cudaStream_t st) {
-  k_sur_check<<<1, 1024, 0, st>>>(make_args(ss, status));
+  k_sur_check<<<1, 1024, 0, st>>>(make_args(ss, status), 0);
+  return cudaGetLastError();
+}
+
+cudaError_t sur_drift(const SurrogateScratch& ss, int32_t* status, cudaStream_t st) {
+  k_sur_check<<<1, 1024, 0, st>>>(make_args(ss, status), 1);
   return cudaGetLastError();
 }
 

@@ -91,3 +91,18 @@ def test_noalloc_rejects_large_n_without_gpu():
     status = rbm.load().rbm_permutation_noalloc(1 << 20, 0, 0, 0, ctypes.c_void_p(1 << 20), None)
     assert status == -1
     assert "exceeds the maximum" in rbm.rbm_last_error()
+
+
+@pytest.mark.parametrize("n,m,reason", [(1, 0, "at least 2"), (100, -1, "must not be negative")])
+def test_noalloc_rejections_set_the_error_text_without_gpu(n, m, reason):
+    lib = rbm.load()
+    # leave an unrelated message first: the rejection must replace it
+    assert lib.rbm_permutation_noalloc(1 << 20, 0, 0, 0, ctypes.c_void_p(1 << 20), None) == -1
+    status = lib.rbm_permutation_noalloc(n, 0, 0, m, ctypes.c_void_p(1 << 20), None)
+    assert status == -1
+    assert reason in rbm.rbm_last_error()
+
+
+def test_noalloc_rejects_null_output_without_gpu():
+    assert rbm.load().rbm_permutation_noalloc(100, 0, 0, 0, None, None) == -1
+    assert "null pointer" in rbm.rbm_last_error()

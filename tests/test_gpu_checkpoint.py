@@ -42,7 +42,7 @@ def _resume(X, d, dtype, kw, method="rbm", path=None, first=100, second=100, gra
     assert torch.equal(b.x, whole.x)
 
 
-@pytest.mark.parametrize("path", [1, 2, 3])
+@pytest.mark.parametrize("path", [1, 2, 3, 4])
 def test_rbm_resume_bit_identical(path):
     n = 1500 if path == 3 else 20000
     X = workloads.gaussian(n, 3, seed=1)

@@ -287,13 +287,15 @@ def test_cooperative_path_at_millions_of_particles(p):
 @pytest.mark.parametrize("log2n", [24, 26])
 def test_multi_kernel_path_at_large_n_full_size(log2n):
     """The large-N sweep's N = 2^24 and N = 2^26 (its largest) entries (d = 3,
-    FP32, regularised attraction, p = 2) on the path the library picks there
-    (the multi-kernel bucket sort): the whole permutation bit-exact and one
-    step of every particle within the FP32 bar."""
+    FP32, regularised attraction, p = 2) on the multi-kernel bucket-sort path
+    (the per-id path; the library picks the record path there, which
+    tests/test_gpu_rec.py checks at N = 2^26): the whole permutation
+    bit-exact and one step of every particle within the FP32 bar."""
     n, d = 1 << log2n, 3
     kw = dict(p=2, dt=1e-3, sigma=0.2, v="quadratic", k="reg_attract", k_param=0.01)
     X = as_run_precision(workloads.gaussian(n, d, seed=7), "f32")
     s, x = _system(X, d, "f32", seed=3, **kw)
+    s.set_tuning(path=1)
     assert s.tuning()["path"] == 1
     prm = _oprm(n, d, "f32", seed=3, **kw)
     perm = oracle.permutation(prm, 0)

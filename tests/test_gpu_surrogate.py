@@ -147,19 +147,63 @@ SCHEDULE = dict(train_every=100, fallback_tol=1e-2, iters_first=12000, iters_per
 
 
 def test_surrogate_trains_and_takes_over():
-    """N = 2^16 and 2^14 queries: every checkpoint (steps 0, 100, 200) trains
-    until the held-out error is within 1e-2, so the network drives all 300
-    steps."""
+    """N = 2^16 and 2^14 queries: the first checkpoint trains until the
+    held-out error is within 1e-2, so the network drives the whole first
+    interval (100 steps)."""
     torch_cuda()
     s, x, X = _system(65536, seed=1)
     s.surrogate_config(n_queries=16384, **SCHEDULE)
-    s.run(300, "surrogate")
+    s.run(100, "surrogate")
     st = s.surrogate_stats()
     assert st["rel_err"] <= 1e-2 and st["active"], st
-    assert st["surrogate_steps"] == 300 and st["fallback_steps"] == 0, st
-    assert s.m == 300
+    assert st["surrogate_steps"] == 100 and st["fallback_steps"] == 0, st
+    assert s.m == 100
+    assert s.surrogate_drift()["drift_err"] == -1.0       # no later checkpoint yet
     got = from_dev(x, 2)
     assert np.all(np.isfinite(got))
+
+
+def _drift_schedule(every, tol_ok, steps):
+    """Checkpoint steps of the documented drift-aware schedule when every
+    drift measurement is above the tolerance (tol_ok False) or within half
+    of it (True)."""
+    lo = max(1, every // 16)
+    at, interval, m = [0], every, 0
+    while True:
+        m += interval
+        if m >= steps:
+            return at
+        at.append(m)
+        interval = min(every, 2 * interval) if tol_ok else max(lo, interval // 2)
+
+
+def test_surrogate_drift_shortens_the_interval_and_falls_back():
+    """The aggregation workload moves its clusters at speed ~|x|, so the
+    network fitted at step 0 is ~50% off at step 100.  The checkpoint at step
+    100 measures that drift on its fresh queries (it agrees with the error of
+    the stale network over all particles, measured through the ABI); the
+    interval then halves at every checkpoint down to train_every / 16 = 6
+    steps, and since the drift over 6 steps still exceeds 1e-2 the RBM-1
+    fallback takes over."""
+    torch = torch_cuda()
+    s, x, X = _system(65536, seed=2)
+    s.surrogate_config(n_queries=16384, **dict(SCHEDULE, iters_per_checkpoint=500, max_rounds=2))
+    s.run(100, "surrogate")
+    s.sync()
+    fd = s.forces("direct")                     # the network of step 0 at the positions of step 100
+    fs = s.surrogate_forces(x.contiguous())
+    stale = float(torch.sqrt(((fs - fd) ** 2).sum() / (fd ** 2).sum()))
+    s.run(1, "surrogate")                       # checkpoint at step 100
+    dr = s.surrogate_drift()
+    assert dr["drift_err"] > 0.1 and abs(dr["drift_err"] - stale) <= 0.05 * stale, (dr, stale)
+    assert dr["interval"] == 50 and not dr["forced_off"], dr
+    s.run(199, "surrogate")                     # to step 300
+    dr, st = s.surrogate_drift(), s.surrogate_stats()
+    assert dr["forced_off"] and dr["interval"] == 6 and dr["forced_intervals"] >= 1, dr
+    assert st["fallback_steps"] > 0 and st["surrogate_steps"] + st["fallback_steps"] == 300, st
+
+
+def test_surrogate_gains_over_rbm_at_equal_dt():
 
 
 def test_surrogate_gains_over_rbm_at_equal_dt():
@@ -221,7 +265,10 @@ def test_surrogate_falls_back_when_tolerance_is_unreachable():
     s.run(120, "surrogate")
     st = s.surrogate_stats()
     assert not st["active"] and st["surrogate_steps"] == 0 and st["fallback_steps"] == 120, st
-    assert st["adam_steps"] == 10 + 2 * 5 + 3 * 5 + 3 * 5, st     # checkpoints at 0, 50, 100: all rounds run
+    # every checkpoint runs all its rounds; the drift is never within the
+    # tolerance, so the interval halves from 50 down to 3 steps
+    later = len(_drift_schedule(50, False, 120)) - 1
+    assert st["adam_steps"] == 10 + 2 * 5 + later * 3 * 5, (st, later)
     # the fallback steps are exactly RBM-1 steps
     t, y, _ = _system(4096, seed=3)
     t.run(120, "rbm")

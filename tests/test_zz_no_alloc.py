@@ -43,6 +43,27 @@ def test_noalloc_permutation_matches_regular_entry_point_twice():
         assert np.array_equal(got, expect), f"n={n} m={m}"
 
 
+def test_noalloc_calls_take_no_device_memory():
+    """After a first call, further calls leave the device's free memory
+    unchanged (no cudaMalloc or cudaMallocAsync on this path), and their
+    permutations stay right."""
+    torch = torch_cuda()
+    stream = torch.cuda.current_stream()
+    n, seed, replica = 50000, 99, 2
+    outs = [torch.full((n,), -1, dtype=torch.int32, device="cuda") for _ in range(4)]
+    rbm.rbm_permutation_noalloc(n, seed, replica, 0, outs[0], stream)
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    for m in range(1, 4):
+        rbm.rbm_permutation_noalloc(n, seed, replica, m, outs[m], stream)
+    torch.cuda.synchronize()
+    free_after = torch.cuda.mem_get_info()[0]
+    assert free_after == free_before
+    for m in (0, 3):
+        got = outs[m].cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, _regular_permutation(torch, n, seed, replica, m)), f"m={m}"
+
+
 def test_noalloc_rejects_n_above_maximum():
     torch = torch_cuda()
     perm = torch.empty(65537, dtype=torch.int32, device="cuda")
