@@ -67,13 +67,16 @@ L2_FLUSH_BYTES = 256 << 20
 WORKLOADS = {
     "large_n": dict(workload="large_n_reg_attract", n=2**26, d=3, p=2, dt=1e-3, sigma=0.2, kernel="reg_attract",
                     potential="quadratic", v_coef=1.0, k_param=0.01, renorm=False, dtype="f32", seed=0,
-                    scheme="euler", other_p=[4, 8], direct_n=2**20, cpu_sample_n=2**20),
+                    scheme="euler", other_p=[4, 8], direct_n=2**20, cpu_sample_n=2**20,
+                    surrogate=dict(train_every=100, fallback_tol=1e-2, n_queries=16384, iters_first=4000,
+                                   iters_per_checkpoint=1000, max_rounds=4, lr=3e-3)),
     "thomson": dict(workload="thomson_sphere_rbm1", n=100000, d=3, p=2, dt=1e-4, sigma=0.0, kernel="coulomb",
                     potential="zero", v_coef=1.0, k_param=0.0, renorm=True, dtype="f32", seed=0, scheme="euler",
                     quality_steps=2000),
     "batched_opinion": dict(workload="batched_opinion_replicas", replicas=4096, n_lo=256, n_hi=65536, d=2, p=2,
                             dt=1e-2, sigma=0.01, kernel="bounded_conf", potential="zero", v_coef=1.0, k_param=0.25,
-                            renorm=False, dtype="f32", seed=0, scheme="euler", graph_steps=100),
+                            renorm=False, dtype="f32", seed=0, scheme="euler", graph_steps=100, ps=[2, 4],
+                            eps=1e-2, horizon=1.0),
     "dyson": dict(workload="dyson_brownian_motion", n=1000, d=1, p=2, dt=1e-3, sigma=float(np.sqrt(1.0 / 1000)),
                   kernel="inv1d", potential="quadratic", v_coef=1.0, k_param=0.0, renorm=False, dtype="f64", seed=0,
                   scheme="split"),
@@ -116,6 +119,8 @@ KERNEL_SOURCES = {
     "k_rbm_batched": ["batched.cu", "rbm_batch.cuh", "rbm_device.cuh", "rbm_internal.h"],
     "k_sur_step": ["surrogate.cu", "tc.cuh", "rbm_device.cuh", "rbm_internal.h"],
     "k_bucket_sort_step": ["perm_step.cu", "rbm_batch.cuh", "rbm_device.cuh", "rbm_internal.h"],
+    "k_rec_step": ["rec_step.cu", "rbm_batch.cuh", "rbm_device.cuh", "rbm_internal.h"],
+    "k_direct": ["direct.cu", "rbm_device.cuh", "rbm_internal.h"],
     "k_rbmr_step": ["rbmr.cu", "rbm_grid.cuh", "rbm_device.cuh", "rbm_internal.h"],
 }
 
@@ -466,6 +471,31 @@ def run_headline(args, w, g):
         ms = _timed_run(g, s, steps)
         others[f"rbm_p{p}"] = {"particle_steps_per_s": n * steps / (ms * 1e-3), "ms_per_step": ms / steps}
         s.close()
+
+    # the learned surrogate (3 -> 64 -> 64 -> 3 network) on the same system:
+    # the first checkpoint (queries, direct forces at them, training), then
+    # network steps while it is within its tolerance
+    x.copy_(_to_dev(g, X0, d, w["dtype"]))
+    s = rbm.System(x, d=d, p=w["p"], stream=g.stream, **kw)
+    s.surrogate_config(**w["surrogate"])
+    e0, e1 = g.event(), g.event()
+    e0.record(g.stream)
+    s.run(1, "surrogate")
+    e1.record(g.stream)
+    s.sync()
+    first_ms = e0.elapsed_time(e1)
+    sur_steps = min(steps, w["surrogate"]["train_every"] - 1)
+    e0.record(g.stream)
+    s.run(sur_steps, "surrogate")
+    e1.record(g.stream)
+    s.sync()
+    sur_ms = e0.elapsed_time(e1) / sur_steps
+    others["surrogate"] = {"particle_steps_per_s": n / (sur_ms * 1e-3), "ms_per_step": sur_ms,
+                           "first_checkpoint_ms": first_ms, "steps_timed": sur_steps,
+                           "stats": s.surrogate_stats(),
+                           "note": "network steps between checkpoints (the checkpoint's direct forces at the "
+                                   "queries and its training are reported apart)"}
+    s.close()
     del x
     g.torch.cuda.empty_cache()
 
@@ -493,7 +523,9 @@ def run_headline(args, w, g):
 
     peaks, peak_src = _measured_peaks()
     avg = {k: float(np.mean(v)) for k, v in per_kernel.items()}
-    dom = max(avg, key=avg.get)
+    # the record path's k_rec_step runs every step of a run but the last (which
+    # runs k_rec_step_last): the steady-state kernel is the one to hold to the roofline
+    dom = "k_rec_step" if "k_rec_step" in avg else max(avg, key=avg.get)
     digest = _kernel_sources_digest()
     floor = rbm_floor_bytes(d, elem)
     roof = _roofline(peaks, peak_src, dom, n * floor, avg[dom], w["workload"], digest)
@@ -501,6 +533,7 @@ def run_headline(args, w, g):
     roof["bytes_note"] = ("2 x 12 B of positions (d = 3 FP32; the stored row is 16 B with its pad lane) + 4 B "
                           "permutation written + 4 B read")
     roof["step_frac"] = n * floor / (total_ms / steps * 1e-3) / 1e9 / peaks["hbm_gbs"]
+    roof["kernel_shares"] = {k: v / sum(avg.values()) for k, v in avg.items()}
     dk = float(np.sum([np.mean(v) for v in direct_kernel.values()])) if direct_kernel else direct_ms
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": g.world, "steps": steps,
@@ -710,6 +743,9 @@ def run_batched(args, w, g):
     kw = dict(p=w["p"], dt=w["dt"], sigma=w["sigma"], seed=w["seed"] + 1000 * g.rank, v=w["potential"],
               v_coef=w["v_coef"], k=w["kernel"], k_param=w["k_param"])
     rep = rbm.Replicas(x, sizes, d=d, stream=g.stream, **kw)
+    # p by accuracy: least time to T with E(T) <= eps against the direct
+    # method on one Brownian path (pilot: the replica closest to 16384)
+    acc = rep.autotune_accuracy(w["ps"], w["eps"], w["horizon"], max_halvings=2, pilot_n=16384, trial_steps=2)
     tune = rep.autotune(trial_steps=2, table_path=None)
     steps = max(args.steps, 1)
     rep.set_graph_steps(min(w["graph_steps"], steps))
@@ -756,7 +792,7 @@ def run_batched(args, w, g):
                                    for k in range(8, 17)},
         "config": dict(w, rows=rows, l2=f"inputs ({rows * row_bytes / 1e6:.0f} MB of positions) exceed L2; "
                                         "K steps replayed back to back from CUDA graphs",
-                       parallelism=f"replicas x{g.world}", autotune=tune),
+                       parallelism=f"replicas x{g.world}", autotune=tune, p_by_accuracy=acc),
         "roofline": roof,
         "e2e": {"value": g.world * rows * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": rows * row_bytes,
                 "d2h_bytes_per_step": rows * row_bytes},

@@ -312,7 +312,7 @@ rbm_status rbm_latency_floor(rbm_ctx *ctx, float *us);
 /* ---- learned mean-field surrogate ---------------------------------------- */
 /* The paper has no surrogate.  Its mean-field limit (Sec. 1, eq.
  * "nonlinearfp") drives each particle by the force K * mu; here a
- * 2 -> 64 -> 64 -> 2 tanh network F(x) is trained on the direct-sum force
+ * d -> 64 -> 64 -> d tanh network F(x) (d = 2 or 3) is trained on the direct-sum force
  * F(x) = 1/(N-1) sum_j K(x - X^j) at sampled particles and, while its held-out
  * relative error stays at or below `fallback_tol`, replaces the random-batch
  * force in the Euler-Maruyama step (-grad V and the Brownian increment as in
@@ -344,7 +344,7 @@ rbm_status rbm_latency_floor(rbm_ctx *ctx, float *us);
  *            checkpoint measures the drift within the tolerance again; at or
  *            below half the tolerance the interval doubles back towards
  *            train_every (rbm_surrogate_drift reports the schedule).
- * Requires d = 2, FP32, the Euler scheme, additive noise, a single (not
+ * Requires d = 2 or 3, FP32, the Euler scheme, additive noise, a single (not
  * batched) system.
  * Synchronous (allocates the network state). */
 rbm_status rbm_surrogate_config(rbm_ctx *ctx, int32_t train_every, double fallback_tol, int64_t n_queries,
@@ -367,17 +367,19 @@ rbm_status rbm_surrogate_stats(rbm_ctx *ctx, double *last_rel_err, int64_t *n_su
 rbm_status rbm_surrogate_drift(const rbm_ctx *ctx, double *drift_err, int32_t *interval, int32_t *forced_off,
                                int64_t *n_forced_intervals);
 
-/* Network parameters (4482 floats: W1[64][2], b1[64], W2[64][64], b2[64],
- * W3[2][64], b3[2]) and normalisation (mu_x, mu_y, s, sF), host buffers;
+/* Network parameters (4224 + 129 d floats, 4482 for d = 2 and 4611 for
+ * d = 3: W1[64][d], b1[64], W2[64][64], b2[64], W3[d][64], b3[d]) and
+ * normalisation (d + 2 floats: mu (d values), s, sF), host buffers;
  * set_params also clears the Adam state.  Synchronous. */
 rbm_status rbm_surrogate_params(rbm_ctx *ctx, float *theta_host, float *norm_host);
 rbm_status rbm_surrogate_set_params(rbm_ctx *ctx, const float *theta_host, const float *norm_host);
 
-/* Network force at nq points q_dev (nq x 2 FP32, device) into f_dev. */
+/* Network force at nq points q_dev (nq x ld FP32 rows, device; ld = 2 for
+ * d = 2, 4 for d = 3) into f_dev (same layout). */
 rbm_status rbm_surrogate_forces(rbm_ctx *ctx, const void *q_dev, int64_t nq, void *f_dev);
 
-/* Loss and its gradient (host, 4482 floats) on nb samples: positions x_dev
- * and target forces f_target_dev (nb x 2 FP32, device), nb <= 65536; the
+/* Loss and its gradient (host, 4224 + 129 d floats) on nb samples: positions
+ * x_dev and target forces f_target_dev (nb x ld FP32 rows, device), nb <= 65536; the
  * network's own tensor-core kernels, no update.  Synchronous. */
 rbm_status rbm_surrogate_gradient(rbm_ctx *ctx, const void *x_dev, const void *f_target_dev, int64_t nb,
                                   float *grad_host, double *loss_host);
@@ -427,6 +429,37 @@ rbm_status rbm_batched_set_launch(rbm_ctx *ctx, int32_t threads, int32_t bucket_
  * result is appended to it.  A one-line report is written to `report` (up to
  * report_len bytes, NUL-terminated) when given.  Synchronous. */
 rbm_status rbm_autotune(rbm_ctx *ctx, int32_t trial_steps, const char *table_path, char *report, int32_t report_len);
+
+/* Batch size p of the context from now on (2 <= p <= min(N, 4096); batched
+ * contexts p <= 32; the splitting scheme p = 2): reallocates the scratch and
+ * drops captured graphs; positions and step index unchanged.  Synchronous. */
+rbm_status rbm_set_batch_size(rbm_ctx *ctx, int32_t p);
+
+/* Choose p, and a step, by accuracy.  The error of RBM-1 decays like
+ * sqrt(dt / (p - 1)) (Sec. 3, the convergence theorem) while its cost per step
+ * grows with p, so the batch size is chosen by the least time to reach
+ * T = horizon with E(T) <= eps, E(T) the root mean square distance to the
+ * direct method (eq. "errorformula"), not by step time alone:
+ *   pilot    - the first pilot_n particles of the system (batched contexts:
+ *              the replica whose size is closest to pilot_n, with its own
+ *              replica index), from the current positions;
+ *   error    - for each p in ps[0..nps) and each step dt_k = dt / 2^k,
+ *              k = 0..max_halvings (dt the context's step): RBM-1 to T with
+ *              noise refinement 2^(max_halvings+1-k) against the direct method
+ *              at dt / 2^(max_halvings+1), so all runs share one Brownian path
+ *              (rbm_set_noise_refinement);
+ *   cost     - each p's step time at full size (trial_steps eager steps on a
+ *              scratch copy of the state);
+ *   choice   - among (p, k) with E(T) <= eps the least (T / dt_k) x step time;
+ *              when none meets eps, the smallest error (*met_out = 0).
+ * The chosen p is applied (rbm_set_batch_size); the chosen step is returned
+ * in *dt_out (the context keeps its dt).  With table_path a previous result
+ * for the same workload signature is read instead of searching, and a new
+ * one appended.  Positions and step index are left unchanged.  Not for the
+ * Verlet scheme (RBM_ERR_UNSUPPORTED).  Synchronous. */
+rbm_status rbm_autotune_accuracy(rbm_ctx *ctx, const int32_t *ps, int32_t nps, double eps, double horizon,
+                                 int32_t max_halvings, int64_t pilot_n, int32_t trial_steps, const char *table_path,
+                                 int32_t *p_out, double *dt_out, int32_t *met_out, char *report, int32_t report_len);
 
 /* ---- without allocation ------------------------------------------------ */
 

@@ -1,4 +1,4 @@
-"""FP64 oracle of the mean-field surrogate: a 2 -> 64 -> 64 -> 2 tanh MLP that
+"""FP64 oracle of the mean-field surrogate: a d -> 64 -> 64 -> d tanh MLP (d = 2, 3) that
 approximates the interaction force F(x) = 1/(N-1) sum_j K(x - X^j) (the mean-
 field force K * mu of eq. "nonlinearfp" in arXiv:1812.10575, evaluated on the
 empirical measure), its mean-squared-error gradient and one Adam step.
@@ -9,7 +9,7 @@ surrogate; this module fixes the definitions the CUDA path must match:
   xh = (x - mu) / s                               input normalisation
   z1 = W1 xh + b1,       h1 = tanh(z1)            (64)
   z2 = W2 h1 + b2,       h2 = tanh(z2)            (64)
-  y  = W3 h2 + b3                                 (2)
+  y  = W3 h2 + b3                                 (d)
   F(x) = sF * y                                   output scale
   loss = 1/B sum_s |y_s - t_s|^2,  t_s = F_target,s / sF
 
@@ -17,22 +17,41 @@ Weights enter every product rounded to bfloat16 (the precision the tensor-core
 kernels read them in); the hidden activations that feed the 64 x 64 products
 (h1 forward; h1 and dz2 in the weight gradient; dz2 in dh1) are rounded to
 bfloat16 as well.  Rounding is round-to-nearest-even of the float32 value.
-Everything else is FP64.  Parameter vector layout (float32 masters, 4482):
-W1[64][2], b1[64], W2[64][64], b2[64], W3[2][64], b3[2].
+Everything else is FP64.  Parameter vector layout (float32 masters, 4224 +
+129 d: 4482 for d = 2, 4611 for d = 3): W1[64][d], b1[64], W2[64][64], b2[64],
+W3[d][64], b3[d].  Normalisation vector: mu (d), s, sF.
 """
 from __future__ import annotations
 
 import numpy as np
 
 H = 64
-SIZES = [("W1", (H, 2)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (2, H)), ("b3", (2,))]
-N_PARAMS = sum(int(np.prod(s)) for _, s in SIZES)
+
+
+def sizes(d=2):
+    return [("W1", (H, d)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (d, H)), ("b3", (d,))]
+
+
+def n_params(d=2):
+    return sum(int(np.prod(s)) for _, s in sizes(d))
+
+
+SIZES = sizes(2)
+N_PARAMS = n_params(2)
+
+
+def dim_of(theta):
+    """d of a parameter vector (its length is 4224 + 129 d)."""
+    d = (len(theta) - 4224) // 129
+    if d not in (2, 3) or n_params(d) != len(theta):
+        raise ValueError(f"not a parameter vector of the d -> 64 -> 64 -> d network: {len(theta)}")
+    return d
 
 
 def unpack(theta):
     theta = np.asarray(theta, dtype=np.float64)
     out, o = {}, 0
-    for name, shape in SIZES:
+    for name, shape in sizes(dim_of(theta)):
         k = int(np.prod(shape))
         out[name] = theta[o:o + k].reshape(shape)
         o += k
@@ -40,7 +59,8 @@ def unpack(theta):
 
 
 def pack(p):
-    return np.concatenate([np.asarray(p[name], dtype=np.float64).ravel() for name, _ in SIZES])
+    d = np.asarray(p["b3"]).size
+    return np.concatenate([np.asarray(p[name], dtype=np.float64).ravel() for name, _ in sizes(d)])
 
 
 def bf16(a):
@@ -55,10 +75,11 @@ def bf16(a):
 
 
 def forward(theta, x, norm, emulate_bf16=True):
-    """Returns the output y (B x 2) and the activations needed by backward."""
+    """Returns the output y (B x d) and the activations needed by backward."""
     p = unpack(theta)
+    d = p["b3"].size
     q = bf16 if emulate_bf16 else (lambda a: np.asarray(a, dtype=np.float64))
-    mu, s = np.asarray(norm[:2], dtype=np.float64), float(norm[2])
+    mu, s = np.asarray(norm[:d], dtype=np.float64), float(norm[d])
     xh = (np.asarray(x, dtype=np.float64) - mu) / s
     z1 = xh @ q(p["W1"]).T + p["b1"]
     h1 = np.tanh(z1)
@@ -70,7 +91,7 @@ def forward(theta, x, norm, emulate_bf16=True):
 
 def predict_force(theta, x, norm, emulate_bf16=True):
     y, _ = forward(theta, x, norm, emulate_bf16)
-    return float(norm[3]) * y
+    return float(norm[len(norm) - 1]) * y
 
 
 def loss_and_grad(theta, x, f_target, norm, emulate_bf16=True):
@@ -78,13 +99,13 @@ def loss_and_grad(theta, x, f_target, norm, emulate_bf16=True):
     p = unpack(theta)
     q = bf16 if emulate_bf16 else (lambda a: np.asarray(a, dtype=np.float64))
     y, a = forward(theta, x, norm, emulate_bf16)
-    t = np.asarray(f_target, dtype=np.float64) / float(norm[3])
+    t = np.asarray(f_target, dtype=np.float64) / float(norm[len(norm) - 1])
     B = y.shape[0]
     r = y - t
     loss = float(np.sum(r * r) / B)
-    dy = 2.0 * r / B                                   # B x 2
+    dy = 2.0 * r / B                                   # B x d
     g = {}
-    g["W3"] = dy.T @ a["h2"]                           # 2 x 64
+    g["W3"] = dy.T @ a["h2"]                           # d x 64
     g["b3"] = dy.sum(axis=0)
     dh2 = dy @ q(p["W3"])                              # B x 64
     dz2 = dh2 * (1.0 - a["h2"] * a["h2"])             # tanh' = 1 - tanh^2
@@ -92,7 +113,7 @@ def loss_and_grad(theta, x, f_target, norm, emulate_bf16=True):
     g["b2"] = dz2.sum(axis=0)
     dh1 = q(dz2) @ q(p["W2"])                          # B x 64
     dz1 = dh1 * (1.0 - a["h1"] * a["h1"])
-    g["W1"] = dz1.T @ a["xh"]                          # 64 x 2
+    g["W1"] = dz1.T @ a["xh"]                          # 64 x d
     g["b1"] = dz1.sum(axis=0)
     return loss, pack(g)
 
@@ -114,15 +135,15 @@ def adam_step(theta, m, v, grad, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     return theta, m, v
 
 
-def init_params(seed=0):
+def init_params(seed=0, d=2):
     """Initial parameters: each weight and bias of a layer uniform in
     +-c/sqrt(fan_in), c = 3 for the input layer and 1 otherwise (a seeded
     draw; the CUDA path draws its own start and tests load the same values
     into both sides)."""
     g = np.random.default_rng(np.random.SeedSequence([int(seed), 0x4D4C50]))
     p = {}
-    for name, shape in SIZES:
-        fan_in = 2 if name in ("W1", "b1") else H
+    for name, shape in sizes(d):
+        fan_in = d if name in ("W1", "b1") else H
         c = 3.0 if name in ("W1", "b1") else 1.0
         p[name] = g.uniform(-1, 1, shape) * c / np.sqrt(fan_in)
     return pack(p).astype(np.float32).astype(np.float64)

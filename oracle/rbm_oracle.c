@@ -121,9 +121,9 @@ void orc_permutation(const orc_params *prm, int64_t m, uint32_t *perm)
 
 /* ------------------------------------------------------------------------ */
 /* Brownian increments: Box-Muller on Philox uniforms.                       */
-/* For call t = 0 .. ceil(d/2)-1 the draw (a0,a1,a2,a3) gives the 64-bit      */
-/* words w1 = a1:a0 and w2 = a3:a2; with b uniform bits (53 for FP64 runs,    */
-/* 24 for FP32 runs) u = ((w >> (64-b)) + 1) 2^-b lies in (0, 1], and         */
+/* Pair t = 0 .. ceil(d/2)-1 takes two uniforms u = (top b bits + 1) 2^-b in  */
+/* (0, 1] (b = 53 for FP64 runs, 24 for FP32 runs; see orc_pair_uniforms for  */
+/* which words of which draw), and                                            */
 /* z_{2t} = sqrt(-2 ln u1) cos(2 pi u2), z_{2t+1} = sqrt(-2 ln u1) sin(2 pi u2)*/
 /* ------------------------------------------------------------------------ */
 static double orc_uniform(uint32_t lo, uint32_t hi, int bits)
@@ -135,14 +135,32 @@ static double orc_uniform(uint32_t lo, uint32_t hi, int bits)
 
 /* The standard normal vector of particle id for the step with index m of a  */
 /* run with step dt (one Box-Muller draw per pair of coordinates).           */
+/* Uniform inputs of Box-Muller pair t.  53-bit runs: draw t, the 64-bit    */
+/* words a1:a0 and a3:a2.  24-bit runs: one 32-bit word per uniform, so one   */
+/* draw (call t/2) serves two pairs: even t the words a1, a3 (the same top 24 */
+/* bits the 64-bit reading takes), odd t the words a0, a2.                    */
+static void orc_pair_uniforms(const orc_params *prm, uint32_t id, int64_t m, int t, double *u1, double *u2)
+{
+    uint32_t a[4];
+    if (prm->ubits == 24) {
+        orc_draw(prm->seed, id, m, prm->replica, ORC_STREAM_NOISE, (uint32_t)(t / 2), a);
+        uint32_t w1 = (t % 2 == 0) ? a[1] : a[0];
+        uint32_t w2 = (t % 2 == 0) ? a[3] : a[2];
+        *u1 = orc_uniform(0u, w1, 24);
+        *u2 = orc_uniform(0u, w2, 24);
+        return;
+    }
+    orc_draw(prm->seed, id, m, prm->replica, ORC_STREAM_NOISE, (uint32_t)t, a);
+    *u1 = orc_uniform(a[0], a[1], prm->ubits);
+    *u2 = orc_uniform(a[2], a[3], prm->ubits);
+}
+
 static void orc_normals_plain(const orc_params *prm, uint32_t id, int64_t m, double *z)
 {
     int d = prm->d;
     for (int t = 0; 2 * t < d; ++t) {
-        uint32_t a[4];
-        orc_draw(prm->seed, id, m, prm->replica, ORC_STREAM_NOISE, (uint32_t)t, a);
-        double u1 = orc_uniform(a[0], a[1], prm->ubits);
-        double u2 = orc_uniform(a[2], a[3], prm->ubits);
+        double u1, u2;
+        orc_pair_uniforms(prm, id, m, t, &u1, &u2);
         double rad = sqrt(-2.0 * log(u1));
         double ang = 2.0 * M_PI * u2;
         z[2 * t] = rad * cos(ang);

@@ -22,7 +22,7 @@ from ._lib import (  # noqa: F401
     rbm_surrogate_params, rbm_surrogate_set_params, rbm_surrogate_forces, rbm_surrogate_gradient,
     rbm_rbmr_sets, rbm_rbmr_info, rbm_verlet_set_velocity, rbm_verlet_get_previous, rbm_verlet_set_previous,
     rbm_surrogate_save, rbm_surrogate_load, rbm_latency_floor, rbm_set_noise_refinement, rbm_get_noise_refinement,
-    rbm_surrogate_drift,
+    rbm_surrogate_drift, rbm_set_batch_size, rbm_autotune_accuracy,
     N_SURROGATE_PARAMS,
 )
 
@@ -86,6 +86,12 @@ class Replicas:
 
     def set_noise_refinement(self, r):
         rbm_set_noise_refinement(self.ctx, r)
+
+    def set_batch_size(self, p):
+        rbm_set_batch_size(self.ctx, p)
+
+    def autotune_accuracy(self, ps, eps, horizon, **kw):
+        return rbm_autotune_accuracy(self.ctx, ps, eps, horizon, **kw)
 
     def set_graph_steps(self, steps):
         rbm_set_tuning(self.ctx, RbmTuning(graph_steps=steps))
@@ -180,6 +186,12 @@ class System:
         """Brownian increments shared with a run of step dt/r (path coupling)."""
         rbm_set_noise_refinement(self.ctx, r)
 
+    def set_batch_size(self, p):
+        rbm_set_batch_size(self.ctx, p)
+
+    def autotune_accuracy(self, ps, eps, horizon, **kw):
+        return rbm_autotune_accuracy(self.ctx, ps, eps, horizon, **kw)
+
     def tuning(self):
         t = rbm_get_tuning(self.ctx)
         return {f: getattr(t, f) for f, _ in RbmTuning._fields_}
@@ -231,7 +243,7 @@ class System:
         rbm_rbmr_sets(self.ctx, m, sets)
         return sets
 
-    # learned mean-field surrogate (d = 2, FP32)
+    # learned mean-field surrogate (d = 2 or 3, FP32)
     def surrogate_config(self, **kw):
         rbm_surrogate_config(self.ctx, **kw)
 
@@ -245,10 +257,10 @@ class System:
         return rbm_surrogate_drift(self.ctx)
 
     def surrogate_params(self):
-        return rbm_surrogate_params(self.ctx)
+        return rbm_surrogate_params(self.ctx, self.d)
 
     def surrogate_set_params(self, theta, norm=None):
-        rbm_surrogate_set_params(self.ctx, theta, norm)
+        rbm_surrogate_set_params(self.ctx, theta, norm, self.d)
 
     def surrogate_forces(self, q):
         import torch
@@ -258,7 +270,7 @@ class System:
         return f
 
     def surrogate_gradient(self, x, f_target):
-        return rbm_surrogate_gradient(self.ctx, x, f_target)
+        return rbm_surrogate_gradient(self.ctx, x, f_target, self.d)
 
     def close(self):
         if getattr(self, "ctx", None) is not None:

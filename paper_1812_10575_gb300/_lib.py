@@ -48,8 +48,14 @@ EXPORTS = (
     "rbm_rbmr_sets", "rbm_rbmr_info", "rbm_verlet_set_velocity", "rbm_verlet_get_previous",
     "rbm_verlet_set_previous", "rbm_surrogate_state_size", "rbm_surrogate_save", "rbm_surrogate_load",
     "rbm_latency_floor", "rbm_set_noise_refinement", "rbm_get_noise_refinement", "rbm_surrogate_drift",
+    "rbm_set_batch_size", "rbm_autotune_accuracy",
 )
-N_SURROGATE_PARAMS = 4482
+N_SURROGATE_PARAMS = 4482     # the d = 2 network
+
+
+def surrogate_param_count(d: int = 2) -> int:
+    """Parameters of the d -> 64 -> 64 -> d network: 4224 + 129 d."""
+    return 4224 + 129 * int(d)
 
 
 class RbmParams(ctypes.Structure):
@@ -130,6 +136,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "rbm_verlet_set_velocity": [vp, vp],
         "rbm_latency_floor": [vp, ctypes.POINTER(ctypes.c_float)],
         "rbm_set_noise_refinement": [vp, i32],
+        "rbm_set_batch_size": [vp, i32],
+        "rbm_autotune_accuracy": [vp, ctypes.POINTER(i32), i32, ctypes.c_double, ctypes.c_double, i32, i64, i32,
+                                  ctypes.c_char_p, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(i32), ctypes.c_char_p, i32],
         "rbm_surrogate_drift": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                 ctypes.POINTER(i64)],
         "rbm_get_noise_refinement": [vp, ctypes.POINTER(i32)],
@@ -257,29 +267,30 @@ def rbm_surrogate_stats(ctx) -> dict:
             "adam_steps": na.value}
 
 
-def rbm_surrogate_params(ctx):
+def rbm_surrogate_params(ctx, d=2):
     import numpy as np
 
-    th = np.zeros(N_SURROGATE_PARAMS, dtype=np.float32)
-    nm = np.zeros(4, dtype=np.float32)
+    th = np.zeros(surrogate_param_count(d), dtype=np.float32)
+    nm = np.zeros(d + 2, dtype=np.float32)
     _check(load().rbm_surrogate_params(ctx, th.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                        nm.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), "rbm_surrogate_params")
     return th, nm
 
 
-def rbm_surrogate_set_params(ctx, theta, norm=None) -> None:
-    """Load parameters (4482 floats) and, unless None, the normalisation
-    (mu_x, mu_y, s, sF), which is then kept at the first checkpoint."""
+def rbm_surrogate_set_params(ctx, theta, norm=None, d=2) -> None:
+    """Load parameters (4224 + 129 d floats) and, unless None, the
+    normalisation (mu (d values), s, sF), which is then kept at the first
+    checkpoint."""
     import numpy as np
 
     th = np.ascontiguousarray(np.asarray(theta, dtype=np.float32))
-    if th.size != N_SURROGATE_PARAMS:
-        raise ValueError("expected 4482 parameters")
+    if th.size != surrogate_param_count(d):
+        raise ValueError(f"expected {surrogate_param_count(d)} parameters")
     nm_ptr = None
     if norm is not None:
         nm = np.ascontiguousarray(np.asarray(norm, dtype=np.float32))
-        if nm.size != 4:
-            raise ValueError("expected 4 normalisation values")
+        if nm.size != d + 2:
+            raise ValueError(f"expected {d + 2} normalisation values")
         nm_ptr = nm.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
     _check(load().rbm_surrogate_set_params(ctx, th.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), nm_ptr),
            "rbm_surrogate_set_params")
@@ -290,10 +301,10 @@ def rbm_surrogate_forces(ctx, q, f) -> None:
                                        ctypes.c_void_p(_dev_ptr(f))), "rbm_surrogate_forces")
 
 
-def rbm_surrogate_gradient(ctx, x, f_target):
+def rbm_surrogate_gradient(ctx, x, f_target, d=2):
     import numpy as np
 
-    g = np.zeros(N_SURROGATE_PARAMS, dtype=np.float32)
+    g = np.zeros(surrogate_param_count(d), dtype=np.float32)
     loss = ctypes.c_double()
     _check(load().rbm_surrogate_gradient(ctx, ctypes.c_void_p(_dev_ptr(x)), ctypes.c_void_p(_dev_ptr(f_target)),
                                          int(x.shape[0]), g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
@@ -438,6 +449,24 @@ def rbm_get_noise_refinement(ctx) -> int:
     r = ctypes.c_int32()
     _check(load().rbm_get_noise_refinement(ctx, ctypes.byref(r)), "rbm_get_noise_refinement")
     return r.value
+
+
+def rbm_set_batch_size(ctx, p: int) -> None:
+    _check(load().rbm_set_batch_size(ctx, int(p)), "rbm_set_batch_size")
+
+
+def rbm_autotune_accuracy(ctx, ps, eps, horizon, max_halvings=3, pilot_n=16384, trial_steps=3,
+                          table_path=None) -> dict:
+    """Batch size (and step) by the least time to T at E(T) <= eps (see include/rbm.h)."""
+    arr = (ctypes.c_int32 * len(ps))(*[int(v) for v in ps])
+    p, dt, met = ctypes.c_int32(), ctypes.c_double(), ctypes.c_int32()
+    buf = ctypes.create_string_buffer(4096)
+    _check(load().rbm_autotune_accuracy(ctx, arr, len(ps), float(eps), float(horizon), int(max_halvings),
+                                        int(pilot_n), int(trial_steps),
+                                        table_path.encode() if table_path else None, ctypes.byref(p),
+                                        ctypes.byref(dt), ctypes.byref(met), buf, len(buf)),
+           "rbm_autotune_accuracy")
+    return {"p": p.value, "dt": dt.value, "met": bool(met.value), "report": buf.value.decode()}
 
 
 def rbm_surrogate_drift(ctx) -> dict:

@@ -91,14 +91,14 @@ __device__ void block_scan_any(uint32_t* a, uint32_t len, uint32_t* s_warp) {
 // (or the identity 0 .. nb-1 when ids is null), into b_id[0, nb) by
 // (key, id): counting sort by the kBSubBits key bits below the bucket bits,
 // then insertion sort inside each sub-bucket.  Keys are regenerated.
-__device__ void sort_bucket(const uint32_t* ids, uint32_t nb, uint32_t B, uint32_t m32, uint32_t r, uint2 seed,
+__device__ void sort_bucket(const uint32_t* ids, uint32_t nb, uint32_t B, uint32_t m32, uint32_t r, const PhiloxKeys& ks,
                             uint64_t* a_key, uint64_t* b_key, uint32_t* a_id, uint32_t* b_id, uint32_t* a_sub,
                             uint32_t* s_sub, uint32_t* s_warp) {
   for (uint32_t u = threadIdx.x; u < kBSub; u += blockDim.x) s_sub[u] = 0;
   __syncthreads();
   for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
     const uint32_t id = ids ? ids[j] : j;
-    const uint64_t key = perm_key(id, m32, r, seed);
+    const uint64_t key = perm_key(id, m32, r, ks);
     const uint32_t sub = static_cast<uint32_t>(__umul64hi(key, static_cast<uint64_t>(B) << kBSubBits)) & (kBSub - 1u);
     a_key[j] = key;
     a_id[j] = id;
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(1024, batched_min_blocks<T, D>()) k_rbm_batche
 
     if (B == 1 && n <= kBCap) {
       // the whole replica is one bucket: sort the ids directly, step every batch
-      sort_bucket(nullptr, n, 1u, m32, r, a.seed, a_key, b_key, a_id, b_id, a_sub, s_sub, s_warp);
+      sort_bucket(nullptr, n, 1u, m32, r, a.keys, a_key, b_key, a_id, b_id, a_sub, s_sub, s_warp);
       for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) perm[j] = b_id[j];
       if (MODE != kModePerm) step_batches<T, D, MODE>(ar, m32, b_id, 0u, 0u, (n + up - 1) / up);
       __syncthreads();
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(1024, batched_min_blocks<T, D>()) k_rbm_batche
     for (uint32_t b = threadIdx.x; b <= B; b += blockDim.x) s_hist[b] = 0;
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
-      atomicAdd(&s_hist[static_cast<uint32_t>(__umul64hi(perm_key(i, m32, r, a.seed), B))], 1u);
+      atomicAdd(&s_hist[static_cast<uint32_t>(__umul64hi(perm_key(i, m32, r, a.keys), B))], 1u);
     __syncthreads();
     // 2. bucket starts (s_hist[B] becomes n), scatter of ids; a bucket too
     //    large for shared memory or smaller than a batch selects the general
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(1024, batched_min_blocks<T, D>()) k_rbm_batche
     __syncthreads();
     const bool general = (MODE == kModePerm) || s_general != 0;
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const uint32_t b = static_cast<uint32_t>(__umul64hi(perm_key(i, m32, r, a.seed), B));
+      const uint32_t b = static_cast<uint32_t>(__umul64hi(perm_key(i, m32, r, a.keys), B));
       tmp[atomicAdd(&s_fill[b], 1u)] = i;
     }
     __syncthreads();
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(1024, batched_min_blocks<T, D>()) k_rbm_batche
     for (uint32_t b = 0; b < B; ++b) {
       const uint32_t s = s_hist[b], nb = s_hist[b + 1] - s;
       if (nb <= kBCap) {
-        sort_bucket(tmp + s, nb, B, m32, r, a.seed, a_key, b_key, a_id, b_id, a_sub, s_sub, s_warp);
+        sort_bucket(tmp + s, nb, B, m32, r, a.keys, a_key, b_key, a_id, b_id, a_sub, s_sub, s_warp);
         for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) perm[s + j] = b_id[j];
         if (!general) {
           const uint32_t end = s + nb;
@@ -224,11 +224,11 @@ __global__ void __launch_bounds__(1024, batched_min_blocks<T, D>()) k_rbm_batche
         // a bucket beyond the shared-memory sort (general mode): rank by counting
         for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
           const uint32_t idj = tmp[s + j];
-          const uint64_t kj = perm_key(idj, m32, r, a.seed);
+          const uint64_t kj = perm_key(idj, m32, r, a.keys);
           uint32_t rank = 0;
           for (uint32_t f = 0; f < nb; ++f) {
             const uint32_t idf = tmp[s + f];
-            rank += bkey_less(perm_key(idf, m32, r, a.seed), idf, kj, idj) ? 1u : 0u;
+            rank += bkey_less(perm_key(idf, m32, r, a.keys), idf, kj, idj) ? 1u : 0u;
           }
           perm[s + rank] = idj;
         }

@@ -67,6 +67,7 @@ struct CoopArgs {
   uint32_t n;
   uint32_t nbuckets;           // B = k G
   uint2 seed;
+  PhiloxKeys keys;             // round keys of seed
   uint32_t replica;
   unsigned long long wait_ns;  // bound of one barrier wait
   int skip_arrival;            // test hook: the step first waits at a grid barrier block 0 leaves
@@ -169,7 +170,7 @@ __device__ void bucket_ids(const CoopArgs& ca, uint32_t mm, uint32_t B, uint32_t
   for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) s_cnt[b] = 0;
   __syncthreads();
   for (uint32_t i = i_lo + threadIdx.x; i < i_hi; i += blockDim.x) {
-    const uint64_t key = perm_key(i, mm, ca.replica, ca.seed);
+    const uint64_t key = perm_key(i, mm, ca.replica, ca.keys);
     atomicAdd(&s_cnt[static_cast<uint32_t>(fine_index(key, B) >> kSubBits)], 1u);
   }
   __syncthreads();
@@ -179,7 +180,7 @@ __device__ void bucket_ids(const CoopArgs& ca, uint32_t mm, uint32_t B, uint32_t
   }
   __syncthreads();
   for (uint32_t i = i_lo + threadIdx.x; i < i_hi; i += blockDim.x) {
-    const uint64_t key = perm_key(i, mm, ca.replica, ca.seed);
+    const uint64_t key = perm_key(i, mm, ca.replica, ca.keys);
     const uint32_t b = static_cast<uint32_t>(fine_index(key, B) >> kSubBits);
     const uint32_t slot = atomicAdd(&s_cnt[b], 1u);
     if (slot < (b + 1u) * ca.slot_cap) sl[slot] = i;
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
     // counting places on the cleared buffer (cleared again afterwards)
     if (!grid_barrier(ca, a.status, false)) return;
     for (uint32_t i = i_lo + threadIdx.x; i < i_hi; i += blockDim.x) {
-      const uint64_t key = perm_key(i, m32, ca.replica, ca.seed);
+      const uint64_t key = perm_key(i, m32, ca.replica, ca.keys);
       const uint32_t b = static_cast<uint32_t>(fine_index(key, B) >> kSubBits);
       ca.tmp[sm.s_start[b] + atomicAdd(&h_free[b], 1u)] = i;
     }
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
         if (t1 < nb) x1 = load_row<T, D>(a.x, id1);
       }
       if (t0 < nb) {
-        const uint64_t key = perm_key(id0, m32, ca.replica, ca.seed);
+        const uint64_t key = perm_key(id0, m32, ca.replica, ca.keys);
         const uint32_t sub = static_cast<uint32_t>(fine_index(key, B)) & (kSub - 1u);
         const uint32_t rank = atomicAdd(&sm.s_sub[sub], 1u);
         sm.a_key[t0] = key;
@@ -394,7 +395,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
         sm.a_sub[t0] = sub | (rank << 16);
       }
       if (t1 < nb) {
-        const uint64_t key = perm_key(id1, m32, ca.replica, ca.seed);
+        const uint64_t key = perm_key(id1, m32, ca.replica, ca.keys);
         const uint32_t sub = static_cast<uint32_t>(fine_index(key, B)) & (kSub - 1u);
         const uint32_t rank = atomicAdd(&sm.s_sub[sub], 1u);
         sm.a_key[t1] = key;
@@ -404,8 +405,8 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
       if (straddle) {
         const uint32_t lo = (end / up) * up, hi = min(lo + up, a.n);
         const int pick = static_cast<int>(hi - end);
-        const uint64_t nk0 = (t0 < n1) ? perm_key(nid0, m32, ca.replica, ca.seed) : ~0ull;
-        const uint64_t nk1 = (t1 < n1) ? perm_key(nid1, m32, ca.replica, ca.seed) : ~0ull;
+        const uint64_t nk0 = (t0 < n1) ? perm_key(nid0, m32, ca.replica, ca.keys) : ~0ull;
+        const uint64_t nk1 = (t1 < n1) ? perm_key(nid1, m32, ca.replica, ca.keys) : ~0ull;
         select_smallest(nk0, nid0, t0 < n1, nk1, nid1, t1 < n1, pick, s_sel, s_wkey, s_wid);
         // the lanes of the last warp that step the picked members load their
         // rows now; the registers are read only at the straddling step
@@ -497,11 +498,11 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rbm_coop(CoopArgs ca, StepP
       // rank each member by counting the members before it.
       for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
         const uint32_t idj = ca.tmp[s + j];
-        const uint64_t kj = perm_key(idj, m32, ca.replica, ca.seed);
+        const uint64_t kj = perm_key(idj, m32, ca.replica, ca.keys);
         uint32_t rank = 0;
         for (uint32_t f = 0; f < nb; ++f) {
           const uint32_t idf = ca.tmp[s + f];
-          rank += key_less2(perm_key(idf, m32, ca.replica, ca.seed), idf, kj, idj) ? 1u : 0u;
+          rank += key_less2(perm_key(idf, m32, ca.replica, ca.keys), idf, kj, idj) ? 1u : 0u;
         }
         ca.perm[s + rank] = idj;
       }
@@ -626,6 +627,7 @@ cudaError_t launch_coop(const CoopScratch& cs, int d, int mode, const void* para
   ca.n = a.n;
   ca.nbuckets = cs.nbuckets;
   ca.seed = a.seed;
+  ca.keys = a.keys;
   ca.replica = a.replica;
   ca.wait_ns = wait_ns;
   ca.skip_arrival = prologue ? 0 : skip_arrival;

@@ -11,7 +11,9 @@
 // every warp reads the same source row at once (a broadcast) and applies it
 // to its R targets, so the inner loop is bound by the FP32 (or FP64) pipe:
 // per pair D subtractions, D multiply-adds for |x|^2, the kernel's scale
-// s(|x|^2) and D multiply-adds into the accumulator.  With S > 1 every chunk
+// s(|x|^2) and D multiply-adds into the accumulator.  In FP32 the targets are
+// taken two at a time on packed two-lane instructions (the scale per lane),
+// which halves the issue slots of everything but the scale.  With S > 1 every chunk
 // writes its partial sums and k_direct_finish adds them in chunk order (the
 // result does not depend on scheduling).
 //
@@ -82,6 +84,56 @@ __device__ __forceinline__ void add_pair(const T (&xi)[D], const T (&xj)[D], T k
   if (CHECKED) s = (r2 == T(0)) ? T(0) : s;
 #pragma unroll
   for (int k = 0; k < D; ++k) acc[k] = fma(s, x[k], acc[k]);
+}
+
+// Packed two-lane FP32 arithmetic (sm_100 family): one instruction applies
+// the same round-to-nearest operation to two independent lanes, so a pair of
+// targets against one source costs half the FP32 issue slots of the scalar
+// loop and gives the same bits.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// acc_a += K(xa - xj), acc_b += K(xb - xj) (no coincidence test) with the
+// arithmetic of add_pair<float, D, KF, false> on two packed lanes: the same
+// differences, squared norm (x0 x0, then fused x1 x1 and x2 x2) and fused
+// accumulation, the kernel's scale per lane.
+template <int D, int KF>
+__device__ __forceinline__ void add_pair2(const unsigned long long (&xab)[D], const float (&xj)[D], float kparam,
+                                          float radius_sq, unsigned long long (&acc)[D]) {
+  unsigned long long x[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) x[k] = f2_sub(xab[k], f2_pack(xj[k], xj[k]));
+  unsigned long long r2 = f2_mul(x[0], x[0]);
+#pragma unroll
+  for (int k = 1; k < D; ++k) r2 = f2_fma(x[k], x[k], r2);
+  float r2a, r2b;
+  f2_unpack(r2, r2a, r2b);
+  const unsigned long long sc =
+      f2_pack(kernel_scale<KF>(r2a, kparam, radius_sq), kernel_scale<KF>(r2b, kparam, radius_sq));
+#pragma unroll
+  for (int k = 0; k < D; ++k) acc[k] = f2_fma(sc, x[k], acc[k]);
 }
 
 struct DirectArgs {
@@ -156,6 +208,29 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(StepParams<T> a, Dire
         src_load<T, D>(tile[jj], xj);
 #pragma unroll
         for (int r = 0; r < R; ++r) add_pair<T, D, KF, true>(ri[r].x, xj, a.kparam, a.radius_sq, acc[r]);
+      }
+    } else if constexpr (sizeof(T) == 4 && R % 2 == 0) {
+      // targets (0, 1), (2, 3), ... on packed lanes
+      unsigned long long xab[R / 2][D], acc2[R / 2][D];
+#pragma unroll
+      for (int h = 0; h < R / 2; ++h) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          xab[h][k] = f2_pack(ri[2 * h].x[k], ri[2 * h + 1].x[k]);
+          acc2[h][k] = f2_pack(acc[2 * h][k], acc[2 * h + 1][k]);
+        }
+      }
+#pragma unroll 4
+      for (uint32_t jj = 0; jj < cnt; ++jj) {
+        T xj[D];
+        src_load<T, D>(tile[jj], xj);
+#pragma unroll
+        for (int h = 0; h < R / 2; ++h) add_pair2<D, KF>(xab[h], xj, a.kparam, a.radius_sq, acc2[h]);
+      }
+#pragma unroll
+      for (int h = 0; h < R / 2; ++h) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) f2_unpack(acc2[h][k], acc[2 * h][k], acc[2 * h + 1][k]);
       }
     } else {
 #pragma unroll 4

@@ -315,6 +315,19 @@ rbm_status alloc_scratch(rbm_ctx* c) {
   return RBM_OK;
 }
 
+// Round keys of Philox4x32-10 for a seed: (k0, k1) + r (W0, W1) mod 2^32.
+PhiloxKeys philox_keys(uint64_t seed) {
+  PhiloxKeys ks;
+  uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    ks.k0[r] = k0;
+    ks.k1[r] = k1;
+    k0 += kPhiloxW0;
+    k1 += kPhiloxW1;
+  }
+  return ks;
+}
+
 template <typename T>
 StepParams<T> step_params(const rbm_ctx* c, const int64_t* m_ptr, int64_t m_off) {
   StepParams<T> a{};
@@ -342,6 +355,9 @@ StepParams<T> step_params(const rbm_ctx* c, const int64_t* m_ptr, int64_t m_off)
   a.xprev = static_cast<T*>(c->xprev);
   a.verlet_m0 = c->verlet_m0;
   a.noise_refine = static_cast<uint32_t>(c->noise_refine);
+  // IEEE division in the run's precision, as the kernels would compute it
+  a.inv_pm1 = T(1) / static_cast<T>(p.p - 1);
+  a.keys = philox_keys(p.seed);
   return a;
 }
 
@@ -877,6 +893,67 @@ rbm_status run_checkpoint(rbm_ctx* c) {
 }  // namespace
 
 void rbm::set_last_error_text(const char* text) { snprintf(g_last_error, sizeof(g_last_error), "%s", text); }
+
+namespace {
+
+// sum_i |a_i - b_i|^2 over n rows of ld values (the first d of each row)
+// into *out (FP64, atomically).
+template <typename T>
+__global__ void k_sq_gap(const T* __restrict__ a, const T* __restrict__ b, uint32_t n, int ld, int d, double* out) {
+  double s = 0.0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (int k = 0; k < d; ++k) {
+      const double e = static_cast<double>(a[static_cast<size_t>(i) * ld + k]) - b[static_cast<size_t>(i) * ld + k];
+      s += e * e;
+    }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+// E(T) of eq. "errorformula": root mean square distance of two runs of n particles.
+rbm_status rms_gap(const rbm_ctx* c, const void* a, const void* b, uint32_t n, double* e) {
+  double* dsum = nullptr;
+  RBM_CUDA(cudaMalloc(&dsum, sizeof(double)));
+  RBM_CUDA(cudaMemset(dsum, 0, sizeof(double)));
+  const unsigned blocks = std::min<unsigned>((n + 255) / 256, static_cast<unsigned>(c->cfg.num_sms) * 4);
+  if (c->prm.dtype == RBM_F32)
+    k_sq_gap<float><<<std::max(blocks, 1u), 256>>>(static_cast<const float*>(a), static_cast<const float*>(b), n,
+                                                   c->ld, c->prm.d, dsum);
+  else
+    k_sq_gap<double><<<std::max(blocks, 1u), 256>>>(static_cast<const double*>(a), static_cast<const double*>(b), n,
+                                                    c->ld, c->prm.d, dsum);
+  double h = 0.0;
+  const cudaError_t e1 = cudaMemcpy(&h, dsum, sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(dsum);
+  if (e1 != cudaSuccess) {
+    set_error("rms_gap", e1);
+    return RBM_ERR_CUDA;
+  }
+  *e = std::sqrt(h / static_cast<double>(n));
+  return RBM_OK;
+}
+
+// A pilot run: n particles from x0 (device, copied), parameters prm with
+// batch size p and step dt, noise refinement r, `steps` steps of `method`;
+// the final positions into xout (device, n rows).
+rbm_status pilot_run(const rbm_params& base, int32_t p, double dt, int32_t r, int64_t steps, int32_t method,
+                     const void* x0, void* xout, size_t bytes) {
+  RBM_CUDA(cudaMemcpy(xout, x0, bytes, cudaMemcpyDeviceToDevice));
+  rbm_params prm = base;
+  prm.p = p;
+  prm.dt = dt;
+  rbm_ctx* pc = nullptr;
+  rbm_status st = rbm_init(&prm, xout, nullptr, &pc);
+  if (st != RBM_OK) return st;
+  st = rbm_set_noise_refinement(pc, r);
+  if (st == RBM_OK) st = rbm_run(pc, steps, method);
+  const rbm_status ss = rbm_sync(pc);
+  if (st == RBM_OK) st = ss;
+  rbm_free(pc);
+  return st;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -1456,11 +1533,210 @@ rbm_status rbm_autotune(rbm_ctx* ctx, int32_t trial_steps, const char* table_pat
   return st;
 }
 
+rbm_status rbm_set_batch_size(rbm_ctx* ctx, int32_t p) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  rbm_params chk = ctx->prm;
+  chk.p = p;
+  if (ctx->batched) {
+    chk.n = std::max<int64_t>(chk.n, p);
+    if (p > 32) return RBM_ERR_INVALID;
+  }
+  st = check_params(&chk);
+  if (st != RBM_OK) return st;
+  if (p == ctx->prm.p) return RBM_OK;
+  RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+  drop_graphs(ctx);
+  if (ctx->sur_graph) cudaGraphExecDestroy(ctx->sur_graph);
+  ctx->sur_graph = nullptr;
+  ctx->sur_graph_len = 0;
+  ctx->prm.p = p;
+  free_scratch(ctx);
+  st = ctx->batched ? alloc_batched(ctx) : alloc_scratch(ctx);
+  if (st != RBM_OK) {
+    ctx->latched = st;
+    return st;
+  }
+  RBM_CUDA(cudaDeviceSynchronize());
+  return RBM_OK;
+}
+
+rbm_status rbm_autotune_accuracy(rbm_ctx* ctx, const int32_t* ps, int32_t nps, double eps, double horizon,
+                                 int32_t max_halvings, int64_t pilot_n, int32_t trial_steps, const char* table_path,
+                                 int32_t* p_out, double* dt_out, int32_t* met_out, char* report, int32_t report_len) {
+  rbm_status st = usable(ctx);
+  if (st != RBM_OK) return st;
+  if (!ps || nps < 1 || nps > 16 || !(eps > 0) || !(horizon > 0) || max_halvings < 0 || max_halvings > 8 ||
+      pilot_n < 2 || trial_steps < 1)
+    return RBM_ERR_INVALID;
+  if (ctx->prm.scheme == RBM_SCHEME_VERLET) return RBM_ERR_UNSUPPORTED;  // needs velocities: not a pilot
+  for (int32_t i = 0; i < nps; ++i) {
+    rbm_params chk = ctx->prm;
+    chk.p = ps[i];
+    chk.n = std::max<int64_t>(chk.n, ps[i]);
+    if (check_params(&chk) != RBM_OK || (ctx->batched && ps[i] > 32)) return RBM_ERR_INVALID;
+  }
+  const double dt = ctx->prm.dt;
+  std::ostringstream sig;
+  sig << "accuracy:" << (ctx->batched ? "batched" : "single") << ":" << ctx->prm.dtype << ":" << ctx->prm.d << ":"
+      << ctx->prm.k << ":" << ctx->prm.n << ":" << ctx->rep_n.size() << ":" << dt << ":" << eps << ":" << horizon
+      << ":" << max_halvings;
+  for (int32_t i = 0; i < nps; ++i) sig << ":" << ps[i];
+  const std::string key = sig.str();
+  std::string found;
+  if (table_path) {
+    std::ifstream in(table_path);
+    std::string line;
+    while (std::getline(in, line))
+      if (line.compare(0, key.size() + 1, key + " ") == 0) found = line.substr(key.size() + 1);
+  }
+  int32_t best_p = ctx->prm.p, best_k = 0, met = 0;
+  std::ostringstream rep;
+  if (!found.empty()) {
+    std::istringstream is(found);
+    is >> best_p >> best_k >> met;
+    rep << "table " << key << " " << found;
+  } else {
+    RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+    // pilot: the first pilot_n particles of a single system, or the replica
+    // whose size is closest to pilot_n (with its own replica index)
+    rbm_params base = ctx->prm;
+    size_t row0 = 0;
+    uint32_t npil = static_cast<uint32_t>(std::min<int64_t>(pilot_n, ctx->prm.n));
+    if (ctx->batched) {
+      size_t off = 0, best_off = 0;
+      int64_t best_gap = -1;
+      for (size_t r = 0; r < ctx->rep_n.size(); ++r) {
+        const int64_t gap = std::llabs(ctx->rep_n[r] - pilot_n);
+        if (best_gap < 0 || gap < best_gap) {
+          best_gap = gap;
+          best_off = off;
+          npil = static_cast<uint32_t>(ctx->rep_n[r]);
+          base.replica = static_cast<uint32_t>(r);
+        }
+        off += static_cast<size_t>(ctx->rep_n[r]);
+      }
+      row0 = best_off;
+    }
+    base.n = npil;
+    const size_t bytes = ctx->row_bytes * npil;
+    void *x0 = nullptr, *xref = nullptr, *xrun = nullptr;
+    RBM_CUDA(cudaMalloc(&x0, bytes));
+    RBM_CUDA(cudaMalloc(&xref, bytes));
+    RBM_CUDA(cudaMalloc(&xrun, bytes));
+    RBM_CUDA(cudaMemcpy(x0, static_cast<const char*>(ctx->x) + row0 * ctx->row_bytes, bytes,
+                        cudaMemcpyDeviceToDevice));
+    // the direct reference at dt / 2^(H+1) on the Brownian path every run shares
+    const int32_t rref = 1 << (max_halvings + 1);
+    const int64_t steps_ref = std::llround(horizon / (dt / rref));
+    st = pilot_run(base, std::min<int32_t>(2, static_cast<int32_t>(npil)), dt / rref, 1, steps_ref,
+                   RBM_METHOD_DIRECT, x0, xref, bytes);
+    std::vector<std::vector<double>> err(nps, std::vector<double>(max_halvings + 1, -1.0));
+    for (int32_t i = 0; i < nps && st == RBM_OK; ++i) {
+      if (ps[i] > static_cast<int32_t>(npil)) continue;
+      for (int32_t k = 0; k <= max_halvings && st == RBM_OK; ++k) {
+        const int32_t r = 1 << (max_halvings + 1 - k);
+        st = pilot_run(base, ps[i], dt / (1 << k), r, std::llround(horizon / (dt / (1 << k))), RBM_METHOD_RBM, x0,
+                       xrun, bytes);
+        if (st == RBM_OK) st = rms_gap(ctx, xrun, xref, npil, &err[i][k]);
+      }
+    }
+    cudaFree(x0);
+    cudaFree(xref);
+    cudaFree(xrun);
+    if (st != RBM_OK) return st;
+    // full-size step time of each p on a scratch copy of the state
+    std::vector<double> ms(nps, -1.0);
+    {
+      const size_t full = ctx->row_bytes * static_cast<size_t>(ctx->prm.n);
+      void* scratch = nullptr;
+      RBM_CUDA(cudaMalloc(&scratch, full));
+      void* real_x = ctx->x;
+      const int64_t m0 = ctx->m;
+      const int32_t p0 = ctx->prm.p;
+      const int32_t len0 = ctx->tuning.graph_steps;
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      for (int32_t i = 0; i < nps && st == RBM_OK; ++i) {
+        st = rbm_set_batch_size(ctx, ps[i]);
+        if (st != RBM_OK) break;
+        ctx->tuning.graph_steps = trial_steps + 1;  // eager steps: no capture inside the timing
+        RBM_CUDA(cudaMemcpyAsync(scratch, real_x, full, cudaMemcpyDeviceToDevice, ctx->stream));
+        ctx->x = scratch;
+        st = rbm_run(ctx, 1, RBM_METHOD_RBM);  // warm-up
+        cudaEventRecord(e0, ctx->stream);
+        if (st == RBM_OK) st = rbm_run(ctx, trial_steps, RBM_METHOD_RBM);
+        cudaEventRecord(e1, ctx->stream);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms[i] = t / trial_steps;
+        ctx->x = real_x;
+        ctx->m = m0;
+        ctx->tuning.graph_steps = len0;
+        drop_graphs(ctx);
+        if (st == RBM_OK) st = forget_prepared(ctx, ctx->stream);  // the trial's lookahead bucketing
+        RBM_CUDA(cudaStreamSynchronize(ctx->stream));
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      cudaFree(scratch);
+      ctx->x = real_x;
+      ctx->m = m0;
+      if (st != RBM_OK) return st;
+      st = rbm_set_batch_size(ctx, p0);
+      if (st != RBM_OK) return st;
+    }
+    // least time to T with E(T) <= eps; otherwise the smallest error
+    double best_time = -1.0, best_err = -1.0;
+    for (int32_t i = 0; i < nps; ++i) {
+      rep << "p=" << ps[i] << " (" << ms[i] << " ms/step) E:";
+      for (int32_t k = 0; k <= max_halvings; ++k) rep << " " << err[i][k];
+      rep << "; ";
+      for (int32_t k = 0; k <= max_halvings; ++k) {
+        if (err[i][k] < 0) continue;
+        const double time = std::llround(horizon / (dt / (1 << k))) * ms[i];
+        if (err[i][k] <= eps) {
+          if (!met || time < best_time) {
+            met = 1;
+            best_time = time;
+            best_p = ps[i];
+            best_k = k;
+          }
+          break;  // finer steps only cost more for this p
+        }
+        if (!met && (best_err < 0 || err[i][k] < best_err)) {
+          best_err = err[i][k];
+          best_p = ps[i];
+          best_k = k;
+        }
+      }
+    }
+    rep << "chosen p=" << best_p << " dt=" << dt / (1 << best_k) << (met ? "" : " (eps not met)")
+        << " pilot n=" << npil << " reference dt=" << dt / rref;
+    if (table_path) {
+      std::ofstream outf(table_path, std::ios::app);
+      outf << key << " " << best_p << " " << best_k << " " << met << "\n";
+    }
+  }
+  st = rbm_set_batch_size(ctx, best_p);
+  if (st != RBM_OK) return st;
+  if (p_out) *p_out = best_p;
+  if (dt_out) *dt_out = dt / (1 << best_k);
+  if (met_out) *met_out = met;
+  if (report && report_len > 0) {
+    std::strncpy(report, rep.str().c_str(), static_cast<size_t>(report_len) - 1);
+    report[report_len - 1] = 0;
+  }
+  return RBM_OK;
+}
+
 rbm_status rbm_surrogate_config(rbm_ctx* ctx, int32_t train_every, double fallback_tol, int64_t n_queries,
                                 int32_t iters_first, int32_t iters_per_checkpoint, int32_t max_rounds, double lr) {
   rbm_status st = usable(ctx);
   if (st != RBM_OK) return st;
-  if (ctx->batched || ctx->prm.d != 2 || ctx->prm.dtype != RBM_F32 || ctx->prm.scheme != RBM_SCHEME_EULER ||
+  if (ctx->batched || ctx->prm.d < 2 || ctx->prm.dtype != RBM_F32 || ctx->prm.scheme != RBM_SCHEME_EULER ||
       (ctx->prm.flags & RBM_FLAG_GBM_NOISE))
     return RBM_ERR_UNSUPPORTED;
   if (train_every < 1 || !(fallback_tol > 0) || n_queries < 8 || n_queries > (int64_t(1) << 24) || iters_first < 0 ||
@@ -1476,7 +1752,8 @@ rbm_status rbm_surrogate_config(rbm_ctx* ctx, int32_t train_every, double fallba
     }
   }
   SurrogateScratch& s = ctx->ss;
-  const int np = surrogate_param_count();
+  s.d = ctx->prm.d;
+  const int np = surrogate_param_count(s.d);
   s.nq = static_cast<uint32_t>(n_queries);
   s.ntrain = std::max<uint32_t>(1u, s.nq - s.nq / 4);
   s.lr = static_cast<float>(lr);
@@ -1488,17 +1765,17 @@ rbm_status rbm_surrogate_config(rbm_ctx* ctx, int32_t train_every, double fallba
   RBM_CUDA(cudaMalloc(&s.wq, sizeof(float) * np));
   RBM_CUDA(cudaMalloc(&s.w2f, 64 * 64 * 2));
   RBM_CUDA(cudaMalloc(&s.w2b, 64 * 64 * 2));
-  RBM_CUDA(cudaMalloc(&s.norm, sizeof(float) * 4));
+  RBM_CUDA(cudaMalloc(&s.norm, sizeof(float) * 5));  // mu (d), s, sF
   RBM_CUDA(cudaMalloc(&s.adam_t, sizeof(int)));
   RBM_CUDA(cudaMalloc(&s.flag, sizeof(int)));
   RBM_CUDA(cudaMalloc(&s.err, 2 * sizeof(float)));  // held-out error after training, drift error
   RBM_CUDA(cudaMalloc(&s.counters, 2 * sizeof(unsigned long long)));
   RBM_CUDA(cudaMalloc(&s.partial, sizeof(float) * (np + 1) * s.partial_blocks));
   RBM_CUDA(cudaMalloc(&s.qidx, sizeof(uint32_t) * s.nq));
-  RBM_CUDA(cudaMalloc(&s.q, sizeof(float) * 2 * s.nq));
-  RBM_CUDA(cudaMalloc(&s.fq, sizeof(float) * 2 * s.nq));
-  RBM_CUDA(cudaMalloc(&s.fpred, sizeof(float) * 2 * s.nq));
-  const float norm0[4] = {0.0f, 0.0f, 1.0f, 1.0f};
+  RBM_CUDA(cudaMalloc(&s.q, sizeof(float) * ctx->ld * s.nq));
+  RBM_CUDA(cudaMalloc(&s.fq, sizeof(float) * ctx->ld * s.nq));
+  RBM_CUDA(cudaMalloc(&s.fpred, sizeof(float) * ctx->ld * s.nq));
+  const float norm0[5] = {0.0f, 0.0f, s.d == 3 ? 0.0f : 1.0f, 1.0f, 1.0f};
   RBM_CUDA(cudaMemcpy(s.norm, norm0, sizeof(norm0), cudaMemcpyHostToDevice));
   RBM_CUDA(cudaMemset(s.adam_t, 0, sizeof(int)));
   RBM_CUDA(cudaMemset(s.flag, 0, sizeof(int)));
@@ -1576,8 +1853,10 @@ rbm_status rbm_surrogate_params(rbm_ctx* ctx, float* theta_host, float* norm_hos
   if (!ctx->sur_on) return RBM_ERR_STATE;
   RBM_CUDA(cudaStreamSynchronize(ctx->stream));
   if (theta_host)
-    RBM_CUDA(cudaMemcpy(theta_host, ctx->ss.theta, sizeof(float) * surrogate_param_count(), cudaMemcpyDeviceToHost));
-  if (norm_host) RBM_CUDA(cudaMemcpy(norm_host, ctx->ss.norm, sizeof(float) * 4, cudaMemcpyDeviceToHost));
+    RBM_CUDA(cudaMemcpy(theta_host, ctx->ss.theta, sizeof(float) * surrogate_param_count(ctx->ss.d),
+                        cudaMemcpyDeviceToHost));
+  if (norm_host)
+    RBM_CUDA(cudaMemcpy(norm_host, ctx->ss.norm, sizeof(float) * (ctx->ss.d + 2), cudaMemcpyDeviceToHost));
   return RBM_OK;
 }
 
@@ -1586,7 +1865,7 @@ rbm_status rbm_surrogate_set_params(rbm_ctx* ctx, const float* theta_host, const
   if (st != RBM_OK) return st;
   if (!ctx->sur_on) return RBM_ERR_STATE;
   RBM_CUDA(cudaStreamSynchronize(ctx->stream));
-  const int np = surrogate_param_count();
+  const int np = surrogate_param_count(ctx->ss.d);
   if (theta_host) {
     RBM_CUDA(cudaMemcpy(ctx->ss.theta, theta_host, sizeof(float) * np, cudaMemcpyHostToDevice));
     RBM_CUDA(cudaMemset(ctx->ss.mom1, 0, sizeof(float) * np));
@@ -1594,7 +1873,7 @@ rbm_status rbm_surrogate_set_params(rbm_ctx* ctx, const float* theta_host, const
     RBM_CUDA(cudaMemset(ctx->ss.adam_t, 0, sizeof(int)));
   }
   if (norm_host) {
-    RBM_CUDA(cudaMemcpy(ctx->ss.norm, norm_host, sizeof(float) * 4, cudaMemcpyHostToDevice));
+    RBM_CUDA(cudaMemcpy(ctx->ss.norm, norm_host, sizeof(float) * (ctx->ss.d + 2), cudaMemcpyHostToDevice));
     ctx->sur_norm_given = true;
   }
   cudaError_t e = sur_publish(ctx->ss, ctx->status, ctx->stream);
@@ -1634,7 +1913,7 @@ rbm_status rbm_surrogate_gradient(rbm_ctx* ctx, const void* x_dev, const void* f
     set_error("surrogate gradient", e);
     return RBM_ERR_CUDA;
   }
-  const int np = surrogate_param_count();
+  const int np = surrogate_param_count(ctx->ss.d);
   const uint32_t nblocks = static_cast<uint32_t>((nb + 127) / 128);
   std::vector<float> part(static_cast<size_t>(nblocks) * (np + 1));
   RBM_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -1699,18 +1978,18 @@ struct SurStateHeader {
   float err, drift_err;
   uint64_t counters[2];
   int64_t last, adam_total;
-  float norm[4];
+  float norm[6];
   int32_t interval, forced_off;
   int64_t forced;
 };
-size_t sur_state_bytes() {
-  return sizeof(SurStateHeader) + 3 * sizeof(float) * static_cast<size_t>(surrogate_param_count());
+size_t sur_state_bytes(int d) {
+  return sizeof(SurStateHeader) + 3 * sizeof(float) * static_cast<size_t>(surrogate_param_count(d));
 }
 }  // namespace
 
 rbm_status rbm_surrogate_state_size(const rbm_ctx* ctx, int64_t* bytes) {
   if (!ctx || !bytes) return RBM_ERR_INVALID;
-  *bytes = static_cast<int64_t>(sur_state_bytes());
+  *bytes = static_cast<int64_t>(sur_state_bytes(ctx->sur_on ? ctx->ss.d : ctx->prm.d));
   return RBM_OK;
 }
 
@@ -1718,12 +1997,12 @@ rbm_status rbm_surrogate_save(rbm_ctx* ctx, void* host_buf, int64_t bytes) {
   rbm_status st = usable(ctx);
   if (st != RBM_OK) return st;
   if (!ctx->sur_on) return RBM_ERR_STATE;
-  if (!host_buf || bytes < static_cast<int64_t>(sur_state_bytes())) return RBM_ERR_INVALID;
+  if (!host_buf || bytes < static_cast<int64_t>(sur_state_bytes(ctx->ss.d))) return RBM_ERR_INVALID;
   RBM_CUDA(cudaStreamSynchronize(ctx->stream));
-  const size_t np = static_cast<size_t>(surrogate_param_count());
+  const size_t np = static_cast<size_t>(surrogate_param_count(ctx->ss.d));
   SurStateHeader h{};
   h.magic = kSurStateMagic;
-  h.version = 2;
+  h.version = 3;
   h.np = static_cast<uint32_t>(np);
   RBM_CUDA(cudaMemcpy(&h.adam_t, ctx->ss.adam_t, sizeof(int), cudaMemcpyDeviceToHost));
   RBM_CUDA(cudaMemcpy(&h.flag, ctx->ss.flag, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1733,7 +2012,7 @@ rbm_status rbm_surrogate_save(rbm_ctx* ctx, void* host_buf, int64_t bytes) {
   h.forced_off = ctx->sur_forced_off ? 1 : 0;
   h.forced = ctx->sur_forced;
   RBM_CUDA(cudaMemcpy(h.counters, ctx->ss.counters, sizeof(h.counters), cudaMemcpyDeviceToHost));
-  RBM_CUDA(cudaMemcpy(h.norm, ctx->ss.norm, sizeof(h.norm), cudaMemcpyDeviceToHost));
+  RBM_CUDA(cudaMemcpy(h.norm, ctx->ss.norm, sizeof(float) * 5, cudaMemcpyDeviceToHost));
   h.trained = ctx->sur_trained ? 1 : 0;
   h.norm_given = ctx->sur_norm_given ? 1 : 0;
   h.last = ctx->sur_last;
@@ -1751,11 +2030,11 @@ rbm_status rbm_surrogate_load(rbm_ctx* ctx, const void* host_buf, int64_t bytes)
   rbm_status st = usable(ctx);
   if (st != RBM_OK) return st;
   if (!ctx->sur_on) return RBM_ERR_STATE;
-  if (!host_buf || bytes < static_cast<int64_t>(sur_state_bytes())) return RBM_ERR_INVALID;
+  if (!host_buf || bytes < static_cast<int64_t>(sur_state_bytes(ctx->ss.d))) return RBM_ERR_INVALID;
   SurStateHeader h;
   std::memcpy(&h, host_buf, sizeof(h));
-  const size_t np = static_cast<size_t>(surrogate_param_count());
-  if (h.magic != kSurStateMagic || h.version != 2 || h.np != np || h.interval < 1) return RBM_ERR_INVALID;
+  const size_t np = static_cast<size_t>(surrogate_param_count(ctx->ss.d));
+  if (h.magic != kSurStateMagic || h.version != 3 || h.np != np || h.interval < 1) return RBM_ERR_INVALID;
   RBM_CUDA(cudaStreamSynchronize(ctx->stream));
   const float* f = reinterpret_cast<const float*>(static_cast<const unsigned char*>(host_buf) + sizeof(h));
   RBM_CUDA(cudaMemcpy(ctx->ss.theta, f, sizeof(float) * np, cudaMemcpyHostToDevice));
@@ -1769,7 +2048,7 @@ rbm_status rbm_surrogate_load(rbm_ctx* ctx, const void* host_buf, int64_t bytes)
   ctx->sur_forced_off = h.forced_off != 0;
   ctx->sur_forced = h.forced;
   RBM_CUDA(cudaMemcpy(ctx->ss.counters, h.counters, sizeof(h.counters), cudaMemcpyHostToDevice));
-  RBM_CUDA(cudaMemcpy(ctx->ss.norm, h.norm, sizeof(h.norm), cudaMemcpyHostToDevice));
+  RBM_CUDA(cudaMemcpy(ctx->ss.norm, h.norm, sizeof(float) * 5, cudaMemcpyHostToDevice));
   ctx->sur_trained = h.trained != 0;
   ctx->sur_norm_given = h.norm_given != 0;
   ctx->sur_last = h.last;

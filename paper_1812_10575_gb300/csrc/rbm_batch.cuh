@@ -31,7 +31,7 @@ __device__ __forceinline__ void batch_force(const StepParams<T>& a, bool valid, 
     if (valid && sg < bs) add_pair_force_rt<T, D>(a.kf, a.kparam, a.radius_sq, r.x, xj, fk);
   }
   if (!valid) return;
-  const T inv = (bs > 1) ? T(1) / static_cast<T>(bs - 1) : T(0);
+  const T inv = (bs == p) ? a.inv_pm1 : (bs > 1) ? T(1) / static_cast<T>(bs - 1) : T(0);
 #pragma unroll
   for (int k = 0; k < D; ++k) fk[k] = (bs > 1) ? fk[k] * inv : T(0);
 }

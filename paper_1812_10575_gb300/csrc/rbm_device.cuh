@@ -38,6 +38,23 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
+// The round keys of Philox4x32-10 for one seed (the Weyl sequence k + r W,
+// r = 0..9), computed once on the host and read by the kernels from their
+// launch parameters instead of being advanced in every call.
+struct PhiloxKeys {
+  uint32_t k0[10], k1[10];
+};
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys& ks) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ ks.k0[round], lo1, hi0 ^ c.w ^ ks.k1[round], lo0);
+  }
+  return c;
+}
+
 constexpr uint32_t kStreamPerm = 0;
 constexpr uint32_t kStreamNoise = 1;
 
@@ -46,22 +63,34 @@ __device__ __forceinline__ uint64_t perm_key(uint32_t id, uint32_t m32, uint32_t
   const uint4 w = philox4x32_10(make_uint4(id, m32, replica, kStreamPerm * 256u), seed);
   return (static_cast<uint64_t>(w.y) << 32) | w.x;
 }
+__device__ __forceinline__ uint64_t perm_key(uint32_t id, uint32_t m32, uint32_t replica, const PhiloxKeys& ks) {
+  const uint4 w = philox4x32_10(make_uint4(id, m32, replica, kStreamPerm * 256u), ks);
+  return (static_cast<uint64_t>(w.y) << 32) | w.x;
+}
 
 // ---------------------------------------------------------------------------
-// Box-Muller pair t of particle `id` at step m: u1, u2 from the 64-bit words
-// w1 = a1:a0 and w2 = a3:a2 of draw (id, m, r, 256 + t); u = ((w >> (64-b))
-// + 1) 2^-b in (0, 1] with b = 24 (FP32) or 53 (FP64);
-// z0 = sqrt(-2 ln u1) cos(2 pi u2), z1 = sqrt(-2 ln u1) sin(2 pi u2).
+// Box-Muller pairs of particle `id` at step m.  FP64 runs: pair t from the
+// 64-bit words w1 = a1:a0 and w2 = a3:a2 of draw (id, m, r, 256 + t),
+// u = ((w >> 11) + 1) 2^-53.  FP32 runs: u = ((w >> 8) + 1) 2^-24 of one
+// 32-bit word, and one draw (id, m, r, 256 + q) gives two pairs: pair 2q
+// from words a1, a3 (the top 24 bits of w1, w2, as FP64 runs read them),
+// pair 2q + 1 from words a0, a2.  z0 = sqrt(-2 ln u1) cos(2 pi u2),
+// z1 = sqrt(-2 ln u1) sin(2 pi u2).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void normal_pair(uint4 a, float& z0, float& z1) {
-  const float u1 = static_cast<float>((a.y >> 8) + 1u) * 0x1p-24f;
-  const float u2 = static_cast<float>((a.w >> 8) + 1u) * 0x1p-24f;
+// FP32: the angle is taken as 2 pi u2 - pi in (-pi, pi], where the hardware
+// sine and cosine are accurate to about 4e-7 absolute, and the signs turned
+// back (cos(a - pi) = -cos a, sin(a - pi) = -sin a).
+__device__ __forceinline__ void normal_pair_words(uint32_t w1, uint32_t w2, float& z0, float& z1) {
+  const float u1 = static_cast<float>((w1 >> 8) + 1u) * 0x1p-24f;
+  const float u2 = static_cast<float>((w2 >> 8) + 1u) * 0x1p-24f;
   const float rad = sqrtf(-2.0f * logf(u1));
   float s, c;
-  sincospif(2.0f * u2, &s, &c);
-  z0 = rad * c;
-  z1 = rad * s;
+  __sincosf(fmaf(6.28318530718f, u2, -3.14159265359f), &s, &c);
+  z0 = -rad * c;
+  z1 = -rad * s;
 }
+
+__device__ __forceinline__ void normal_pair(uint4 a, float& z0, float& z1) { normal_pair_words(a.y, a.w, z0, z1); }
 
 __device__ __forceinline__ void normal_pair(uint4 a, double& z0, double& z1) {
   const uint64_t w1 = (static_cast<uint64_t>(a.y) << 32) | a.x;
@@ -76,14 +105,31 @@ __device__ __forceinline__ void normal_pair(uint4 a, double& z0, double& z1) {
 }
 
 template <typename T, int D>
-__device__ __forceinline__ void brownian(uint32_t id, uint32_t m32, uint32_t replica, uint2 seed, T (&z)[D]) {
+__device__ __forceinline__ void brownian(uint32_t id, uint32_t m32, uint32_t replica, const PhiloxKeys& ks,
+                                         T (&z)[D]) {
+  if constexpr (sizeof(T) == 4) {
 #pragma unroll
-  for (int t = 0; 2 * t < D; ++t) {
-    const uint4 a = philox4x32_10(make_uint4(id, m32, replica, kStreamNoise * 256u + t), seed);
-    T z0, z1;
-    normal_pair(a, z0, z1);
-    z[2 * t] = z0;
-    if (2 * t + 1 < D) z[2 * t + 1] = z1;
+    for (int q = 0; 4 * q < D; ++q) {  // two pairs per draw
+      const uint4 a = philox4x32_10(make_uint4(id, m32, replica, kStreamNoise * 256u + q), ks);
+      float z0, z1;
+      normal_pair_words(a.y, a.w, z0, z1);
+      z[4 * q] = z0;
+      if (4 * q + 1 < D) z[4 * q + 1] = z1;
+      if (4 * q + 2 < D) {
+        normal_pair_words(a.x, a.z, z0, z1);
+        z[4 * q + 2] = z0;
+        if (4 * q + 3 < D) z[4 * q + 3] = z1;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; 2 * t < D; ++t) {
+      const uint4 a = philox4x32_10(make_uint4(id, m32, replica, kStreamNoise * 256u + t), ks);
+      T z0, z1;
+      normal_pair(a, z0, z1);
+      z[2 * t] = z0;
+      if (2 * t + 1 < D) z[2 * t + 1] = z1;
+    }
   }
 }
 
@@ -96,13 +142,13 @@ __device__ __forceinline__ void brownian(uint32_t id, uint32_t m32, uint32_t rep
 // taken mod 2^32, as m is.
 template <typename T, int D>
 __device__ __forceinline__ void brownian_refined(uint32_t id, uint32_t m32, uint32_t refine, uint32_t replica,
-                                                 uint2 seed, T (&z)[D]) {
+                                                 const PhiloxKeys& ks, T (&z)[D]) {
   T sum[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) sum[k] = T(0);
   for (uint32_t f = 0; f < refine; ++f) {
     T zf[D];
-    brownian<T, D>(id, m32 * refine + f, replica, seed, zf);
+    brownian<T, D>(id, m32 * refine + f, replica, ks, zf);
 #pragma unroll
     for (int k = 0; k < D; ++k) sum[k] += zf[k];
   }
@@ -296,6 +342,8 @@ struct StepParams {
   T* xprev;              // Verlet: V_0 before the first step, X_{n-1} afterwards (N x ld)
   int64_t verlet_m0;     // Verlet: the step index of the Taylor start
   uint32_t noise_refine; // r > 1: the increment of step m sums the r increments of fine steps m r + k
+  T inv_pm1;             // 1/(p - 1) in the run's precision (IEEE division, on the host)
+  PhiloxKeys keys;       // round keys of `seed`
 };
 
 template <typename T>
@@ -382,8 +430,8 @@ __device__ __forceinline__ void euler_update(const StepParams<T>& a, uint32_t id
                                              const T (&fk)[D], T (&y)[D], bool split_flow = false) {
   T z[D];
   if (a.sq != T(0)) {
-    if (a.noise_refine > 1u) brownian_refined<T, D>(id, m32, a.noise_refine, a.replica, a.seed, z);
-    else brownian<T, D>(id, m32, a.replica, a.seed, z);
+    if (a.noise_refine > 1u) brownian_refined<T, D>(id, m32, a.noise_refine, a.replica, a.keys, z);
+    else brownian<T, D>(id, m32, a.replica, a.keys, z);
   } else {
 #pragma unroll
     for (int k = 0; k < D; ++k) z[k] = T(0);

@@ -109,6 +109,7 @@ struct SurrogateScratch {
   float* fpred = nullptr;
   uint32_t nq = 0, ntrain = 0;
   float lr = 1e-3f, tol = 1e-2f;
+  int d = 2;                        // network dimension (2 or 3); query rows of Ld<d> floats
 };
 
 struct LaunchCfg {
@@ -180,7 +181,7 @@ cudaError_t launch_batched(const BatchedScratch& bs, int d, int mode, const void
                            cudaStream_t st);
 
 // Surrogate network (surrogate.cu).
-int surrogate_param_count();
+int surrogate_param_count(int d);
 cudaError_t prepare_surrogate_kernels();
 cudaError_t sur_init(const SurrogateScratch& ss, int32_t* status, uint64_t seed, cudaStream_t st);
 cudaError_t sur_publish(const SurrogateScratch& ss, int32_t* status, cudaStream_t st);

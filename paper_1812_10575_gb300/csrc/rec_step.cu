@@ -19,9 +19,10 @@
 //   k_rec_scan   - the sorted start of every sub-bucket (the sub-buckets in
 //                  (top, sub) order are the random division in key order);
 //   k_rec_step   - one block per sub-bucket (about 2048 records): sort by the
-//                  remaining key bits (counting sort on 11 bits, insertion
-//                  sort, full keys recomputed only on ties of the 32 carried
-//                  bits), step every batch lying wholly inside it, park the
+//                  remaining key bits (counting sort on 11 bits, then each
+//                  record ranked among the few sharing its digit, full keys
+//                  recomputed only on ties of the 32 carried bits), step
+//                  every batch lying wholly inside it, park the
 //                  members of batches crossing its ends, and send every
 //                  moved record to its top-level bucket of step m + 1 (key
 //                  of m + 1 computed here) - or, at the last step of a run,
@@ -49,8 +50,11 @@ constexpr uint32_t kSubCapMax = 3072;   // largest sub-bucket sorted in shared m
 constexpr int kStepThreads = 512;
 constexpr int kStepPer = kSubCapMax / kStepThreads;  // records per thread of k_rec_step
 constexpr int kSplitThreads = 512;
-constexpr int kSplitPer = 8;            // records per thread of k_rec_split and k_rec_scatter
+constexpr int kSplitPer = 8;            // records per thread of k_rec_scatter
 constexpr uint32_t kChunk = kSplitThreads * kSplitPer;
+constexpr int kSubThreads = 256;        // k_rec_split: 256 threads of 8 records, many blocks per SM
+constexpr int kSubPer = 8;
+constexpr uint32_t kSubChunk = kSubThreads * kSubPer;
 constexpr int kFineBits = 11;           // counting-sort digit inside a sub-bucket
 constexpr uint32_t kFine = 1u << kFineBits;
 constexpr int kMaxDigitBits = 11;       // top and sub digits: at most 2048 values
@@ -100,7 +104,7 @@ __device__ __forceinline__ void write_position(float* x, uint32_t id, const Row<
 // Top-level bucket and carried key bits of particle id at step m1.
 __device__ __forceinline__ void top_key(const StepParams<float>& a, const RecArgs& g, uint32_t id, uint32_t m1,
                                         uint32_t& t, uint32_t& k32) {
-  const uint64_t key = perm_key(id, m1, a.replica, a.seed);
+  const uint64_t key = perm_key(id, m1, a.replica, a.keys);
   t = top_of(key, g.top_bits);
   k32 = key32_of(key, g.top_bits);
 }
@@ -119,14 +123,19 @@ __device__ __forceinline__ void put_top(const StepParams<float>& a, const RecArg
 // ---------------------------------------------------------------------------
 // First step of a run: the caller's rows in id order into the top level.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSplitThreads) k_rec_scatter(StepParams<float> a, RecArgs g) {
+__global__ void __launch_bounds__(kSplitThreads, 2) k_rec_scatter(StepParams<float> a, RecArgs g) {
   __shared__ uint32_t s_hist[1u << kMaxDigitBits];
   __shared__ uint32_t s_base[1u << kMaxDigitBits];
   const uint32_t m32 = step_index(a);
   const uint32_t par = m32 & 1u;
+  const uint32_t i0 = blockIdx.x * kChunk;
+  if (threadIdx.x == 0) {  // the chunk's rows into L2 while the keys are drawn
+    const uint32_t nrow = min(kChunk, a.n - i0);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.x + static_cast<size_t>(i0) * 4),
+                 "r"(nrow * 16u) : "memory");
+  }
   for (uint32_t u = threadIdx.x; u < g.ntop; u += blockDim.x) s_hist[u] = 0;
   __syncthreads();
-  const uint32_t i0 = blockIdx.x * kChunk;
   uint32_t tr[kSplitPer], k32[kSplitPer];
 #pragma unroll
   for (int k = 0; k < kSplitPer; ++k) {
@@ -160,9 +169,9 @@ __global__ void __launch_bounds__(kSplitThreads) k_rec_scatter(StepParams<float>
 
 // ---------------------------------------------------------------------------
 // Top level -> sub level: block (t, j) takes records [j C, (j+1) C) of top
-// bucket t.
+// bucket t (C = kSubChunk).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSplitThreads) k_rec_split(StepParams<float> a, RecArgs g, uint32_t chunks) {
+__global__ void __launch_bounds__(kSubThreads, 6) k_rec_split(StepParams<float> a, RecArgs g, uint32_t chunks) {
   __shared__ uint32_t s_hist[1u << kMaxDigitBits];
   __shared__ uint32_t s_base[1u << kMaxDigitBits];
   const uint32_t m32 = step_index(a);
@@ -171,43 +180,47 @@ __global__ void __launch_bounds__(kSplitThreads) k_rec_split(StepParams<float> a
   const uint32_t filled = g.top_fill[par * g.ntop + t];
   if (j == 0 && threadIdx.x == 0 && filled > g.top_cap) latch_status(a.status, RBM_ERR_STATE);
   const uint32_t count = min(filled, g.top_cap);
-  const uint32_t lo = j * kChunk;
+  const uint32_t lo = j * kSubChunk;
   if (lo >= count) return;  // uniform over the block
   for (uint32_t u = threadIdx.x; u < g.nsub; u += blockDim.x) s_hist[u] = 0;
   __syncthreads();
   const size_t src0 = static_cast<size_t>(t) * g.top_cap + lo;
-  uint32_t ur[kSplitPer], k32[kSplitPer];
-  float4 v[kSplitPer];  // every record in flight before the first store
+  const uint32_t nrec = min(kSubChunk, count - lo);
+  uint32_t ur[kSubPer], k32[kSubPer];
 #pragma unroll
-  for (int k = 0; k < kSplitPer; ++k) {
-    const uint32_t e = k * kSplitThreads + threadIdx.x;
-    if (lo + e < count) {
-      k32[k] = g.top_keys[src0 + e];
-      v[k] = g.top_rows[src0 + e];
-    }
+  for (int k = 0; k < kSubPer; ++k) {
+    const uint32_t e = k * kSubThreads + threadIdx.x;
+    if (e >= nrec) break;
+    k32[k] = g.top_keys[src0 + e];
   }
 #pragma unroll
-  for (int k = 0; k < kSplitPer; ++k) {
-    const uint32_t e = k * kSplitThreads + threadIdx.x;
-    if (lo + e < count) {
-      const uint32_t u = sub_of(k32[k], g.sub_bits);
-      ur[k] = u | (atomicAdd(&s_hist[u], 1u) << 16);
-    }
+  for (int k = 0; k < kSubPer; ++k) {
+    const uint32_t e = k * kSubThreads + threadIdx.x;
+    if (e >= nrec) break;
+    const uint32_t u = sub_of(k32[k], g.sub_bits);
+    ur[k] = u | (atomicAdd(&s_hist[u], 1u) << 16);
   }
   __syncthreads();
   for (uint32_t u = threadIdx.x; u < g.nsub; u += blockDim.x)
     if (s_hist[u]) s_base[u] = atomicAdd(&g.sub_fill[par * g.nbuckets + t * g.nsub + u], s_hist[u]);
   __syncthreads();
+  // rows two at a time: many resident blocks keep the loads in flight
 #pragma unroll
-  for (int k = 0; k < kSplitPer; ++k) {
-    const uint32_t e = k * kSplitThreads + threadIdx.x;
-    if (lo + e < count) {
-      const uint32_t u = ur[k] & 0xffffu;
-      const uint32_t pos = s_base[u] + (ur[k] >> 16);
+  for (int k = 0; k < kSubPer; k += 2) {
+    const uint32_t e0 = k * kSubThreads + threadIdx.x, e1 = e0 + kSubThreads;
+    if (e0 >= nrec) break;
+    const float4 v0 = g.top_rows[src0 + e0];
+    const float4 v1 = (e1 < nrec) ? g.top_rows[src0 + e1] : v0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t e = h ? e1 : e0;
+      if (e >= nrec) break;
+      const uint32_t u = ur[k + h] & 0xffffu;
+      const uint32_t pos = s_base[u] + (ur[k + h] >> 16);
       if (pos < g.sub_cap) {
         const size_t at = static_cast<size_t>(t * g.nsub + u) * g.sub_cap + pos;
-        g.sub_rows[at] = v[k];
-        g.sub_keys[at] = k32[k];
+        g.sub_rows[at] = h ? v1 : v0;
+        g.sub_keys[at] = k32[k + h];
       } else {
         latch_status(a.status, RBM_ERR_STATE);
       }
@@ -277,7 +290,7 @@ __device__ __forceinline__ uint32_t sub_bucket_at(const uint32_t* start, uint32_
 __device__ __forceinline__ bool rec_less(const StepParams<float>& a, uint32_t m32, uint32_t fa, uint32_t ida,
                                          uint32_t fb, uint32_t idb) {
   if (fa != fb) return fa < fb;
-  const uint64_t ka = perm_key(ida, m32, a.replica, a.seed), kb = perm_key(idb, m32, a.replica, a.seed);
+  const uint64_t ka = perm_key(ida, m32, a.replica, a.keys), kb = perm_key(idb, m32, a.replica, a.keys);
   return ka < kb || (ka == kb && ida < idb);
 }
 
@@ -287,14 +300,14 @@ __device__ __forceinline__ bool rec_less(const StepParams<float>& a, uint32_t m3
 // step of a run, write the positions by id).
 // ---------------------------------------------------------------------------
 template <bool kLast>
-__global__ void __launch_bounds__(kStepThreads, 2) k_rec_step(StepParams<float> a, RecArgs g) {
+__global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> a, RecArgs g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* srow = reinterpret_cast<float4*>(smem_raw);                 // [sub_cap] records, slot order
   uint32_t* sfine = reinterpret_cast<uint32_t*>(srow + g.sub_cap);     // [sub_cap] bits below the sub digit
   uint16_t* sidx = reinterpret_cast<uint16_t*>(sfine + g.sub_cap);    // [sub_cap] slot of each sorted position
   uint8_t* spark = reinterpret_cast<uint8_t*>(sidx + g.sub_cap);      // [sub_cap] 1: member of a crossing batch
+  uint32_t* s_base = reinterpret_cast<uint32_t*>(spark + g.sub_cap);   // [ntop] run starts in the top level
   __shared__ uint32_t s_hist[kFine];
-  __shared__ uint32_t s_base[1u << kMaxDigitBits];
   __shared__ uint32_t s_warp[32];
   const uint32_t b = blockIdx.x;
   const uint32_t m32 = step_index(a);
@@ -313,16 +326,17 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_rec_step(StepParams<float> 
   asm volatile("cp.async.commit_group;" ::: "memory");
   __syncthreads();
   // counting sort by the kFineBits bits below the sub digit
+  // the fixed-size loops stop at the first slot past cnt (a sub-bucket holds
+  // about 2048 of the at most 3072 slots)
   uint32_t fr[kStepPer];
 #pragma unroll
   for (int k = 0; k < kStepPer; ++k) {
     const uint32_t e = threadIdx.x + k * kStepThreads;
-    if (e < cnt) {
-      const uint32_t f = g.sub_keys[src0 + e] << g.sub_bits;
-      sfine[e] = f;
-      const uint32_t d = f >> (32 - kFineBits);
-      fr[k] = d | (atomicAdd(&s_hist[d], 1u) << 16);
-    }
+    if (e >= cnt) break;
+    const uint32_t f = g.sub_keys[src0 + e] << g.sub_bits;
+    sfine[e] = f;
+    const uint32_t d = f >> (32 - kFineBits);
+    fr[k] = d | (atomicAdd(&s_hist[d], 1u) << 16);
   }
   __syncthreads();
   {  // exclusive scan of s_hist
@@ -353,26 +367,40 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_rec_step(StepParams<float> 
   }
   __syncthreads();
   asm volatile("cp.async.wait_all;" ::: "memory");
+  // provisional positions: digit order, arbitrary inside a digit
 #pragma unroll
   for (int k = 0; k < kStepPer; ++k) {
     const uint32_t e = threadIdx.x + k * kStepThreads;
-    if (e < cnt) sidx[s_hist[fr[k] & 0xffffu] + (fr[k] >> 16)] = static_cast<uint16_t>(e);
+    if (e >= cnt) break;
+    sidx[s_hist[fr[k] & 0xffffu] + (fr[k] >> 16)] = static_cast<uint16_t>(e);
+    spark[e] = 0;
   }
   __syncthreads();  // also publishes every thread's staged records
-  for (uint32_t u = threadIdx.x; u < kFine; u += blockDim.x) {  // insertion sort inside each digit
-    const uint32_t lo = s_hist[u], hi = (u + 1 < kFine) ? s_hist[u + 1] : cnt;
-    for (uint32_t x = lo + 1; x < hi; ++x) {
-      const uint16_t sx = sidx[x];
-      const uint32_t fx = sfine[sx], ix = rec_id(srow[sx]);
-      uint32_t y = x;
-      while (y > lo) {
-        const uint16_t sy = sidx[y - 1];
-        if (!rec_less(a, m32, fx, ix, sfine[sy], rec_id(srow[sy]))) break;
-        sidx[y] = sy;
-        --y;
+  // final position of each record: its digit's start plus the number of the
+  // digit's records before it in (key, id) order (a digit holds about one)
+  uint16_t fin[kStepPer];
+#pragma unroll
+  for (int k = 0; k < kStepPer; ++k) {
+    const uint32_t e = threadIdx.x + k * kStepThreads;
+    if (e >= cnt) break;
+    const uint32_t d = fr[k] & 0xffffu;
+    const uint32_t lo = s_hist[d], hi = (d + 1 < kFine) ? s_hist[d + 1] : cnt;
+    uint32_t rank = 0;
+    if (hi - lo > 1) {
+      const uint32_t fe = sfine[e], ie = rec_id(srow[e]);
+      for (uint32_t j = lo; j < hi; ++j) {
+        const uint16_t sj = sidx[j];
+        if (sj != e && rec_less(a, m32, sfine[sj], rec_id(srow[sj]), fe, ie)) ++rank;
       }
-      sidx[y] = sx;
     }
+    fin[k] = static_cast<uint16_t>(lo + rank);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kStepPer; ++k) {
+    const uint32_t e = threadIdx.x + k * kStepThreads;
+    if (e >= cnt) break;
+    sidx[fin[k]] = static_cast<uint16_t>(e);
   }
   __syncthreads();
 
@@ -409,16 +437,20 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_rec_step(StepParams<float> 
       }
     }
   }
-  // members of batches crossing the ends: parked under the sub-bucket that
-  // holds the batch's first member
-  for (uint32_t e = threadIdx.x; e < cnt; e += blockDim.x) {
-    const uint32_t pos = start + e;
-    const uint32_t q = pos / up;
-    const bool crossing = q < q0 || q >= q_end;
-    const uint16_t slot = sidx[e];
-    spark[slot] = crossing ? 1 : 0;
-    if (crossing) {
+  // members of batches crossing the ends (sorted positions before q0 p and
+  // from q_end p on): parked under the sub-bucket that holds the batch's
+  // first member
+  {
+    const uint32_t head = (count > 0) ? q0 * up - start : cnt;   // all members when no batch fits inside
+    const uint32_t tail = (count > 0) ? min(cnt, q_end * up - start) : cnt;
+    const uint32_t ncross = head + (cnt - tail);
+    for (uint32_t c = threadIdx.x; c < ncross; c += blockDim.x) {
+      const uint32_t e = (c < head) ? c : tail + (c - head);
+      const uint32_t pos = start + e;
+      const uint32_t q = pos / up;
       const uint32_t qp = q * up;
+      const uint16_t slot = sidx[e];
+      spark[slot] = 1;
       const uint32_t bf = (qp >= start) ? b : sub_bucket_at(g.sub_start, g.nbuckets, qp);
       g.side[static_cast<size_t>(bf) * kSide + (pos - qp)] = srow[slot];
     }
@@ -434,7 +466,8 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_rec_step(StepParams<float> 
 #pragma unroll
   for (int k = 0; k < kStepPer; ++k) {
     const uint32_t e = threadIdx.x + k * kStepThreads;
-    if (e < cnt && !spark[e]) {
+    if (e >= cnt) break;
+    if (!spark[e]) {
       uint32_t t;
       top_key(a, g, rec_id(srow[e]), m32 + 1u, t, k32[k]);
       tr[k] = t | (atomicAdd(&s_hist[t], 1u) << 16);
@@ -447,7 +480,8 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_rec_step(StepParams<float> 
 #pragma unroll
   for (int k = 0; k < kStepPer; ++k) {
     const uint32_t e = threadIdx.x + k * kStepThreads;
-    if (e < cnt && !spark[e]) {
+    if (e >= cnt) break;
+    if (!spark[e]) {
       const uint32_t t = tr[k] & 0xffffu;
       put_top(a, g, np, t, s_base[t] + (tr[k] >> 16), srow[e], k32[k]);
     }
@@ -497,8 +531,12 @@ __global__ void __launch_bounds__(256) k_rec_fixup(StepParams<float> a, RecArgs 
   }
 }
 
-size_t step_smem(uint32_t sub_cap) {
-  return static_cast<size_t>(sub_cap) * (sizeof(float4) + sizeof(uint32_t) + sizeof(uint16_t) + sizeof(uint8_t));
+// Dynamic shared memory of k_rec_step: records, sort bits, sorted slots and
+// crossing flags of sub_cap records (a multiple of 32, so the run starts
+// that follow are aligned), then ntop run starts.
+size_t step_smem(uint32_t sub_cap, uint32_t ntop) {
+  return static_cast<size_t>(sub_cap) * (sizeof(float4) + sizeof(uint32_t) + sizeof(uint16_t) + sizeof(uint8_t)) +
+         static_cast<size_t>(ntop) * sizeof(uint32_t);
 }
 
 RecArgs make_args(const RecScratch& rs) {
@@ -560,9 +598,15 @@ void rec_free(RecScratch* rs) {
 }
 
 cudaError_t prepare_rec_kernels() {
-  const int bytes = static_cast<int>(step_smem(kSubCapMax));
+  const int bytes = static_cast<int>(step_smem(kSubCapMax, 1u << kMaxDigitBits));
   cudaError_t e = cudaFuncSetAttribute(k_rec_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rec_step<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  // the split and scatter kernels hold 16 KB of counters: let several blocks share an SM
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_rec_split, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_rec_scatter, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
   return e;
 }
 
@@ -578,8 +622,8 @@ cudaError_t launch_rec_run(const RecScratch& rs, const void* params, int64_t cou
   if (e != cudaSuccess) return e;
   k_rec_scatter<<<(a0.n + kChunk - 1) / kChunk, kSplitThreads, 0, st>>>(a0, g);
   mark_launch(cfg, st, "k_rec_scatter");
-  const uint32_t chunks = (rs.top_cap + kChunk - 1) / kChunk;
-  const size_t smem = step_smem(rs.sub_cap);
+  const uint32_t chunks = (rs.top_cap + kSubChunk - 1) / kSubChunk;
+  const size_t smem = step_smem(rs.sub_cap, rs.ntop);
   const int gpw = 32 / a0.p;
   const uint32_t fix_groups = 8u * static_cast<uint32_t>(gpw);
   const uint32_t fix_grid = (g.nbuckets + fix_groups - 1) / fix_groups;
@@ -587,7 +631,7 @@ cudaError_t launch_rec_run(const RecScratch& rs, const void* params, int64_t cou
     StepParams<float> a = a0;
     a.m_off = a0.m_off + k;
     const bool last = (k + 1 == count);
-    k_rec_split<<<rs.ntop * chunks, kSplitThreads, 0, st>>>(a, g, chunks);
+    k_rec_split<<<rs.ntop * chunks, kSubThreads, 0, st>>>(a, g, chunks);
     mark_launch(cfg, st, "k_rec_split");
     k_rec_scan<<<1, 1024, 0, st>>>(a, g);
     mark_launch(cfg, st, "k_rec_scan");

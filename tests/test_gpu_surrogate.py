@@ -204,9 +204,6 @@ def test_surrogate_drift_shortens_the_interval_and_falls_back():
 
 
 def test_surrogate_gains_over_rbm_at_equal_dt():
-
-
-def test_surrogate_gains_over_rbm_at_equal_dt():
     """E(T) = sqrt(mean |X_method - X_direct|^2) (eq. "errorformula") after 300
     steps from the same X0 with the same Brownian increments, N = 2^16.  The
     confinement carries the clusters towards the origin at speed ~|x|, so a
@@ -275,3 +272,100 @@ def test_surrogate_falls_back_when_tolerance_is_unreachable():
     s.sync()
     t.sync()
     assert np.array_equal(x.cpu().numpy(), y.cpu().numpy())
+
+
+# ---------------------------------------------------------------------------
+# d = 3: the 3 -> 64 -> 64 -> 3 network on the large-N system (V = |x|^2/2,
+# K(x) = -x/(|x|^2 + 0.01), sigma = 0.2, X0 ~ N(0, I)); rows of 4 floats.
+# ---------------------------------------------------------------------------
+LARGE = dict(p=2, dt=1e-3, sigma=0.2, v="quadratic", k="reg_attract", k_param=0.01)
+
+
+def _system3(n, seed=0):
+    X = workloads.gaussian(n, 3, seed=seed).astype(np.float32).astype(np.float64)
+    x = to_dev(X, "f32")
+    return rbm.System(x, d=3, **LARGE), x, X
+
+
+def _params3(seed):
+    rng = np.random.default_rng(seed)
+    theta = mlp.init_params(seed, d=3) + rng.normal(0, 0.02, mlp.n_params(3))
+    return theta.astype(np.float32), np.array([0.1, -0.2, 0.05, 1.1, 0.4], dtype=np.float32)
+
+
+def _rows(torch, A):
+    t = torch.zeros(A.shape[0], 4, dtype=torch.float32)
+    t[:, :3] = torch.from_numpy(np.asarray(A, dtype=np.float32))
+    return t.cuda()
+
+
+def test_surrogate_3d_forward_matches_oracle():
+    torch = torch_cuda()
+    s, x, X = _system3(1024)
+    s.surrogate_config(n_queries=1024)
+    theta, norm = _params3(1)
+    s.surrogate_set_params(theta, norm)
+    got_theta, got_norm = s.surrogate_params()
+    assert np.array_equal(got_theta, theta) and np.array_equal(got_norm, norm)
+    Q = np.random.default_rng(2).normal(0, 1.5, (1000, 3)).astype(np.float32)
+    f = s.surrogate_forces(_rows(torch, Q)).cpu().numpy()[:, :3].astype(np.float64)
+    s.sync()
+    ref = mlp.predict_force(theta, Q, norm, emulate_bf16=True)
+    scale = np.sqrt(np.mean(ref ** 2))
+    assert np.abs(f - ref).max() / scale < 2e-3
+    assert np.median(np.abs(f - ref)) / scale < 1e-5
+
+
+def test_surrogate_3d_gradient_matches_oracle():
+    torch = torch_cuda()
+    s, x, X = _system3(1024)
+    s.surrogate_config(n_queries=1024)
+    theta, norm = _params3(3)
+    s.surrogate_set_params(theta, norm)
+    rng = np.random.default_rng(4)
+    xs = rng.normal(0, 1.5, (777, 3)).astype(np.float32)          # a ragged last tile
+    ts = rng.normal(0, 0.5, (777, 3)).astype(np.float32)
+    g, loss = s.surrogate_gradient(_rows(torch, xs), _rows(torch, ts))
+    ref_loss, ref_g = mlp.loss_and_grad(theta, xs, ts, norm, emulate_bf16=True)
+    assert abs(loss - ref_loss) <= 1e-5 * abs(ref_loss)
+    p_g, p_r = mlp.unpack(g), mlp.unpack(ref_g)
+    for name, _ in mlp.sizes(3):
+        rel = np.linalg.norm(p_g[name] - p_r[name]) / max(np.linalg.norm(p_r[name]), 1e-30)
+        assert rel < 1e-2, (name, rel)
+
+
+def test_surrogate_3d_network_step_sampled():
+    """One network step at N = 2^20 with fixed weights: sampled particles
+    against the oracle's forward and update; the pad lane is preserved."""
+    torch = torch_cuda()
+    n = 1 << 20
+    s, x, X = _system3(n, seed=5)
+    x[:, 3] = 7.0
+    s.surrogate_config(train_every=100, fallback_tol=1e30, n_queries=1024, iters_first=0, iters_per_checkpoint=0,
+                       max_rounds=1, lr=1e-3)
+    theta, norm = _params3(6)
+    s.surrogate_set_params(theta, norm)
+    s.run(1, "surrogate")
+    s.sync()
+    assert s.surrogate_stats()["surrogate_steps"] == 1
+    assert bool(torch.all(x[:, 3] == 7.0))
+    got = from_dev(x, 3)
+    idx = np.sort(np.random.default_rng(7).choice(n, 4096, replace=False))
+    prm = oracle.make_params(n, 3, seed=0, precision="f32", **LARGE)
+    FK = np.zeros_like(X)
+    FK[idx] = mlp.predict_force(theta, X[idx].astype(np.float32), norm, emulate_bf16=True)
+    ref = oracle.euler_update(prm, X, FK, 0)
+    scale = np.sqrt(np.mean(FK[idx] ** 2))
+    diff = np.linalg.norm(got[idx] - ref[idx], axis=1)
+    bound = 1e-5 * np.maximum(np.linalg.norm(ref[idx], axis=1), 1.0) + LARGE["dt"] * 2e-3 * scale
+    assert np.all(diff <= bound), (diff.max(), bound.min())
+
+
+def test_surrogate_3d_trains_and_drives_the_first_interval():
+    torch_cuda()
+    s, x, X = _system3(65536, seed=1)
+    s.surrogate_config(n_queries=16384, **SCHEDULE)
+    s.run(100, "surrogate")
+    st = s.surrogate_stats()
+    assert st["rel_err"] <= 1e-2 and st["active"] and st["surrogate_steps"] == 100, st
+    assert np.all(np.isfinite(from_dev(x, 3)))

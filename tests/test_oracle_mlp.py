@@ -95,3 +95,45 @@ def test_adam_first_step_moves_each_parameter_by_lr():
     th, m, v = mlp.adam_step(np.zeros(4), np.zeros(4), np.zeros(4), g, 1, lr=0.01)
     np.testing.assert_allclose(th[:3], -0.01 * np.sign(g[:3]), rtol=1e-4)
     assert th[3] == 0.0
+
+
+def test_three_dimensional_gradient_matches_finite_differences():
+    rng = np.random.default_rng(5)
+    d = 3
+    theta = mlp.init_params(4, d=3) * 0.7 + rng.normal(0, 0.05, mlp.n_params(3))
+    assert len(theta) == 4611 and mlp.dim_of(theta) == 3
+    x = rng.normal(0, 1.5, (40, d))
+    t = rng.normal(0, 1, (40, d))
+    norm = np.array([0.1, -0.2, 0.3, 1.3, 0.8])
+    _, g = mlp.loss_and_grad(theta, x, t, norm, emulate_bf16=False)
+    idx = np.concatenate([np.arange(0, 192, 7), rng.choice(len(theta), 60, replace=False),
+                          np.arange(len(theta) - 195, len(theta))])   # W1, random, W3 and b3
+    h = 1e-6
+    for i in idx:
+        e = np.zeros(len(theta))
+        e[i] = h
+        lp, _ = mlp.loss_and_grad(theta + e, x, t, norm, emulate_bf16=False)
+        lm, _ = mlp.loss_and_grad(theta - e, x, t, norm, emulate_bf16=False)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-7 + 1e-6 * abs(fd), (i, fd, g[i])
+
+
+def test_three_dimensional_saturated_network_uses_every_coordinate():
+    """d = 3: hidden units that switch on the third coordinate and on mu_z,
+    and an output row per coordinate (a swapped coordinate or a normalisation
+    read from the d = 2 layout fails).  mu = (0, 0, 1), s = 2, sF = 3."""
+    p = {k: np.zeros(s) for k, s in mlp.sizes(3)}
+    p["W1"][0] = [0, 0, 256]        # h1[0] = sign(z - 1)
+    p["W1"][1] = [256, 0, 0]        # h1[1] = sign(x)
+    p["W2"][2, 0] = 512             # h2[2] = h1[0]
+    p["W2"][3, 1] = 512             # h2[3] = h1[1]
+    p["W3"][0, 2] = 1
+    p["W3"][1, 3] = 2
+    p["W3"][2, 2:4] = [1, 1]
+    p["b3"] = [0.5, 0, -0.25]
+    theta = mlp.pack(p)
+    x = np.array([[1.0, 5.0, 2.0], [-1.0, 0.0, 0.5], [2.0, -3.0, 0.0]])
+    f = mlp.predict_force(theta, x, np.array([0.0, 0.0, 1.0, 2.0, 3.0]))
+    h = np.array([[1, 1], [-1, -1], [-1, 1]])      # (h2[2], h2[3]) per row
+    want = 3 * np.stack([h[:, 0] + 0.5, 2 * h[:, 1], h[:, 0] + h[:, 1] - 0.25], axis=1)
+    np.testing.assert_array_equal(f, want)
