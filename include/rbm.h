@@ -160,7 +160,11 @@ typedef struct {
                              record path (FP32, d = 3, p <= 32, not Verlet:
                              the positions move through the steps of one call
                              as bucketed records and are written back to
-                             x_dev after the call's last step); a path that
+                             x_dev after the call's last step; beyond 2^22
+                             particles a step's splits run on a
+                             second, high-priority stream of the context's
+                             own, forked from and joined back into the
+                             caller's stream within the step); a path that
                              does not fit falls back to 1                       */
     int32_t wait_limit_us;/* bound of a grid-barrier wait in the cooperative
                              kernel (0 = 1 second); a wait that runs out
@@ -296,6 +300,8 @@ rbm_status rbm_direct_forces_at(rbm_ctx *ctx, const void *q_dev, int64_t nq, voi
  * step and writes each kernel's duration in milliseconds to kernel_ms (up to
  * `capacity` entries), their number to *nkernels and, when `names` is given,
  * their ';'-separated names (NUL-terminated, truncated to names_len).
+ * The record path's kernels run one after another on the context's stream
+ * here (not pipelined over two streams as in rbm_run).
  * Synchronous.  Used by the benchmark to time kernels on their own stream. */
 rbm_status rbm_step_profiled(rbm_ctx *ctx, int32_t method, float *kernel_ms, int32_t capacity, int32_t *nkernels,
                              char *names, int32_t names_len);
@@ -486,9 +492,21 @@ rbm_status rbm_autotune_accuracy(rbm_ctx *ctx, const int32_t *ps, int32_t nps, d
 rbm_status rbm_permutation_noalloc(int64_t n, uint64_t seed, uint32_t replica, int64_t m, uint32_t *perm_dev,
                                    void *cuda_stream);
 
+/* Measured FP32 fused multiply-add throughput of the current device in
+ * TFLOP/s (2 flop per FMA): eight independent FMA chains per thread, eight
+ * 256-thread blocks per SM, scalar `fma.rn.f32` (packed = 0) or packed
+ * two-lane `fma.rn.f32x2` (packed = 1); the best of five launches after one
+ * warm-up, CUDA events on `cuda_stream` (a cudaStream_t; NULL = the legacy
+ * default stream).  The ALU roofline of the direct O(N^2) sum.  Allocates
+ * 4 bytes of device memory for the call.  RBM_ERR_INVALID for a null tflops or
+ * packed other than 0 or 1.  Synchronous; needs no context. */
+rbm_status rbm_fp32_fma_peak(int32_t packed, double *tflops, void *cuda_stream);
+
 /* Number of kernel launches one step of `method` enqueues inside a run of
  * steps (for accounting; an RBM-1 run's first step adds the bucketing of its
- * ids on the bucket-sort and cooperative paths). */
+ * ids on the bucket-sort and cooperative paths, and the scatter of the rows
+ * on the record path, whose pipelined steps launch three kernels per group
+ * of top-level buckets and one fix-up). */
 rbm_status rbm_launches_per_step(const rbm_ctx *ctx, int32_t method, int32_t *launches);
 
 #ifdef __cplusplus

@@ -22,7 +22,7 @@ from ._lib import (  # noqa: F401
     rbm_surrogate_params, rbm_surrogate_set_params, rbm_surrogate_forces, rbm_surrogate_gradient,
     rbm_rbmr_sets, rbm_rbmr_info, rbm_verlet_set_velocity, rbm_verlet_get_previous, rbm_verlet_set_previous,
     rbm_surrogate_save, rbm_surrogate_load, rbm_latency_floor, rbm_set_noise_refinement, rbm_get_noise_refinement,
-    rbm_surrogate_drift, rbm_set_batch_size, rbm_autotune_accuracy,
+    rbm_surrogate_drift, rbm_set_batch_size, rbm_autotune_accuracy, rbm_fp32_fma_peak,
     N_SURROGATE_PARAMS,
 )
 

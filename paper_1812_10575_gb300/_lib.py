@@ -47,7 +47,7 @@ EXPORTS = (
     "rbm_surrogate_set_params", "rbm_surrogate_forces", "rbm_surrogate_gradient",
     "rbm_rbmr_sets", "rbm_rbmr_info", "rbm_verlet_set_velocity", "rbm_verlet_get_previous",
     "rbm_verlet_set_previous", "rbm_surrogate_state_size", "rbm_surrogate_save", "rbm_surrogate_load",
-    "rbm_latency_floor", "rbm_set_noise_refinement", "rbm_get_noise_refinement", "rbm_surrogate_drift",
+    "rbm_latency_floor", "rbm_fp32_fma_peak", "rbm_set_noise_refinement", "rbm_get_noise_refinement", "rbm_surrogate_drift",
     "rbm_set_batch_size", "rbm_autotune_accuracy",
 )
 N_SURROGATE_PARAMS = 4482     # the d = 2 network
@@ -135,6 +135,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "rbm_rbmr_sets": [vp, i64, vp],
         "rbm_verlet_set_velocity": [vp, vp],
         "rbm_latency_floor": [vp, ctypes.POINTER(ctypes.c_float)],
+        "rbm_fp32_fma_peak": [i32, ctypes.POINTER(ctypes.c_double), vp],
         "rbm_set_noise_refinement": [vp, i32],
         "rbm_set_batch_size": [vp, i32],
         "rbm_autotune_accuracy": [vp, ctypes.POINTER(i32), i32, ctypes.c_double, ctypes.c_double, i32, i64, i32,
@@ -438,6 +439,15 @@ def rbm_latency_floor(ctx) -> float:
     us = ctypes.c_float()
     _check(load().rbm_latency_floor(ctx, ctypes.byref(us)), "rbm_latency_floor")
     return us.value
+
+
+def rbm_fp32_fma_peak(packed: bool = False, stream=None) -> float:
+    """Measured FP32 FMA throughput (TFLOP/s) of the current device: scalar or
+    packed two-lane FMA chains (see include/rbm.h)."""
+    tf = ctypes.c_double()
+    _check(load().rbm_fp32_fma_peak(1 if packed else 0, ctypes.byref(tf), ctypes.c_void_p(_stream_handle(stream))),
+           "rbm_fp32_fma_peak")
+    return tf.value
 
 
 def rbm_set_noise_refinement(ctx, r: int) -> None:

@@ -31,6 +31,7 @@ UNITS = [
     ("batched.cu", []),
     ("surrogate.cu", []),
     ("rbmr.cu", []),
+    ("peak.cu", []),
 ]
 
 

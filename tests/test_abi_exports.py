@@ -106,3 +106,11 @@ def test_noalloc_rejections_set_the_error_text_without_gpu(n, m, reason):
 def test_noalloc_rejects_null_output_without_gpu():
     assert rbm.load().rbm_permutation_noalloc(100, 0, 0, 0, None, None) == -1
     assert "null pointer" in rbm.rbm_last_error()
+
+
+@pytest.mark.parametrize("packed,null", [(2, False), (-1, False), (0, True)])
+def test_fma_peak_rejects_bad_arguments_without_gpu(packed, null):
+    out = ctypes.c_double()
+    status = rbm.load().rbm_fp32_fma_peak(packed, None if null else ctypes.byref(out), None)
+    assert status == -1
+    assert "rbm_fp32_fma_peak" in rbm.rbm_last_error()

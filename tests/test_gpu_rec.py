@@ -6,7 +6,12 @@ written back by id after the call's last step.
   bucket-sort path bit for bit (both evaluate each batch with the same
   arithmetic on the same rows in the same order), for p from 2 to 32, sizes
   that leave a ragged last batch, bucket geometries down to sub-buckets of a
-  few records (batches crossing many of them), graph replays and eager runs;
+  few records (batches crossing many of them, and crossing the groups of top
+  buckets a pipelined step splits one after another), graph replays and
+  eager runs;
+- the pipelined steps (2, 4 and 8 groups) equal the same steps run one
+  kernel after another (rbm_step_profiled), and the launch count per step
+  is three per group and one;
 - against the oracle: every particle within the FP32 bar after one step, and
   after a 5-step run within a bound that adds the per-step bars;
 - the pad lane of every row is left as the caller wrote it;
@@ -48,7 +53,8 @@ def _run(torch, X, path, steps, p, seed=3, graph_steps=0, bucket_bits=0, **kw):
 
 
 @pytest.mark.parametrize("n,p,bits", [(5000, 2, 0), (5001, 3, 0), (100000, 2, 0), (100003, 7, 0),
-                                      (70001, 32, 0), (5003, 5, 10), (4099, 32, 9), (20000, 2, 12)])
+                                      (70001, 32, 0), (5003, 5, 10), (4099, 32, 9), (20000, 2, 12),
+                                      (300007, 2, 13), (100003, 7, 14), (70001, 32, 16)])
 def test_record_path_run_equals_per_id_path_bitwise(n, p, bits):
     torch = torch_cuda()
     X = as_run_precision(workloads.gaussian(n, 3, seed=2), "f32")
@@ -56,6 +62,28 @@ def test_record_path_run_equals_per_id_path_bitwise(n, p, bits):
     ref = _run(torch, X, 1, 6, p)
     assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)), \
         f"{np.sum(np.any(got != ref, axis=1))} rows differ"
+
+
+@pytest.mark.parametrize("n,bits,groups", [(20000, 12, 2), (300007, 13, 4), (100003, 14, 8)])
+def test_record_path_pipelined_equals_sequential_kernels(n, bits, groups):
+    torch = torch_cuda()
+    X = as_run_precision(workloads.gaussian(n, 3, seed=9), "f32")
+    out = []
+    for profiled in (False, True):
+        x = _x(X, torch, pad_seed=3)
+        s = rbm.System(x, d=3, p=3, seed=2, **KW)
+        s.set_tuning(path=4, bucket_bits=bits)
+        assert s.launches_per_step() == 3 * groups + 1
+        if profiled:
+            names = [k for k, _ in s.step_profiled()]       # two steps, one kernel after another
+            assert names.count("k_rec_split") == 2 and names.count("k_rec_step_last") == 1
+        else:
+            s.run(2)
+        s.sync()
+        assert s.m == 2
+        out.append(x.cpu().numpy())
+        s.close()
+    assert np.array_equal(out[0].view(np.uint32), out[1].view(np.uint32))
 
 
 def test_record_path_graph_replays_equal_eager_run():
