@@ -160,11 +160,7 @@ typedef struct {
                              record path (FP32, d = 3, p <= 32, not Verlet:
                              the positions move through the steps of one call
                              as bucketed records and are written back to
-                             x_dev after the call's last step; beyond 2^22
-                             particles a step's splits run on a
-                             second, high-priority stream of the context's
-                             own, forked from and joined back into the
-                             caller's stream within the step); a path that
+                             x_dev after the call's last step); a path that
                              does not fit falls back to 1                       */
     int32_t wait_limit_us;/* bound of a grid-barrier wait in the cooperative
                              kernel (0 = 1 second); a wait that runs out
@@ -300,8 +296,6 @@ rbm_status rbm_direct_forces_at(rbm_ctx *ctx, const void *q_dev, int64_t nq, voi
  * step and writes each kernel's duration in milliseconds to kernel_ms (up to
  * `capacity` entries), their number to *nkernels and, when `names` is given,
  * their ';'-separated names (NUL-terminated, truncated to names_len).
- * The record path's kernels run one after another on the context's stream
- * here (not pipelined over two streams as in rbm_run).
  * Synchronous.  Used by the benchmark to time kernels on their own stream. */
 rbm_status rbm_step_profiled(rbm_ctx *ctx, int32_t method, float *kernel_ms, int32_t capacity, int32_t *nkernels,
                              char *names, int32_t names_len);
@@ -505,8 +499,7 @@ rbm_status rbm_fp32_fma_peak(int32_t packed, double *tflops, void *cuda_stream);
 /* Number of kernel launches one step of `method` enqueues inside a run of
  * steps (for accounting; an RBM-1 run's first step adds the bucketing of its
  * ids on the bucket-sort and cooperative paths, and the scatter of the rows
- * on the record path, whose pipelined steps launch three kernels per group
- * of top-level buckets and one fix-up). */
+ * on the record path). */
 rbm_status rbm_launches_per_step(const rbm_ctx *ctx, int32_t method, int32_t *launches);
 
 #ifdef __cplusplus

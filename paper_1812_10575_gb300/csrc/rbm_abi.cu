@@ -2122,7 +2122,7 @@ rbm_status rbm_launches_per_step(const rbm_ctx* ctx, int32_t method, int32_t* la
   if (!ctx || !launches) return RBM_ERR_INVALID;
   // RBM-1 inside a run: the previous step bucketed this one's ids (lookahead)
   if (method == RBM_METHOD_RBM && ctx->use_rec)
-    *launches = rec_launches_per_step(ctx->rec);  // per group split, scan, step; the fix-up (a run adds a scatter)
+    *launches = rec_launches_per_step(ctx->rec);  // split, scan, step, fix-up (a run adds its first step's scatter)
   else if (method == RBM_METHOD_RBM)
     *launches = (ctx->use_coop || ctx->batched || ctx->use_small) ? 1 : rbm_tail_launches(ctx->ps, ctx->prm.p);
   else if (method == RBM_METHOD_DIRECT) *launches = 2;  // upper bound: sum (+ chunk reduction)

@@ -49,7 +49,7 @@ struct RecScratch {
   int top_bits = 0, sub_bits = 0;
   uint32_t ntop = 1, nsub = 1;      // buckets per level
   uint32_t top_cap = 0, sub_cap = 0;  // records per top bucket / per sub-bucket
-  float4* top_rows = nullptr;       // [2][ntop * top_cap] by step parity
+  float4* top_rows = nullptr;       // [ntop * top_cap]
   uint32_t* top_keys = nullptr;
   float4* sub_rows = nullptr;       // [ntop * nsub * sub_cap]
   uint32_t* sub_keys = nullptr;
@@ -57,14 +57,6 @@ struct RecScratch {
   uint32_t* sub_fill = nullptr;     // [2 ntop nsub]
   uint32_t* sub_start = nullptr;    // [ntop nsub + 1] sorted start of each sub-bucket
   float4* side = nullptr;           // [ntop nsub * 32] members of batches crossing sub-bucket ends
-  // Pipelining of a step: the top buckets in `groups` groups; the split of
-  // each group runs on `aux` (a non-blocking stream of the greatest
-  // priority) while the caller's stream sorts and steps the groups before.
-  static constexpr int kMaxGroups = 8;
-  int groups = 1;
-  cudaStream_t aux = nullptr;
-  cudaEvent_t ev_start = nullptr;   // caller's stream -> aux at the start of a step
-  cudaEvent_t ev_split[kMaxGroups] = {};  // aux -> caller's stream after each group's split
 };
 
 // Batched-replica scratch.

@@ -59,9 +59,11 @@ constexpr int kFineBits = 11;           // counting-sort digit inside a sub-buck
 constexpr uint32_t kFine = 1u << kFineBits;
 constexpr int kMaxDigitBits = 11;       // top and sub digits: at most 2048 values
 constexpr int kSide = 32;               // parked members per sub-bucket (p <= 32)
+static_assert(kChunk == kSubChunk, "the scatter and split kernels share one staging size");
+constexpr size_t kStageBytes = kChunk * (sizeof(float4) + sizeof(uint32_t));  // records staged by bucket
 
 struct RecArgs {
-  float4* top_rows;     // [2][ntop * top_cap] by step parity
+  float4* top_rows;     // [ntop * top_cap]
   uint32_t* top_keys;
   float4* sub_rows;     // [nbuckets * sub_cap]
   uint32_t* sub_keys;
@@ -69,9 +71,7 @@ struct RecArgs {
   uint32_t* sub_fill;   // [2][nbuckets]
   uint32_t* sub_start;  // [nbuckets + 1]
   float4* side;         // [nbuckets * kSide]
-  size_t top_stride;     // ntop * top_cap: the second parity's offset
   uint32_t top_cap, sub_cap, ntop, nsub, nbuckets;
-  uint32_t t_lo, t_hi;   // the group of top buckets a split, scan or step launch covers
   int top_bits, sub_bits;
 };
 
@@ -111,10 +111,10 @@ __device__ __forceinline__ void top_key(const StepParams<float>& a, const RecArg
   k32 = key32_of(key, g.top_bits);
 }
 
-__device__ __forceinline__ void put_top(const StepParams<float>& a, const RecArgs& g, uint32_t par, uint32_t t,
-                                        uint32_t pos, const float4& rec, uint32_t k32) {
+__device__ __forceinline__ void put_top(const StepParams<float>& a, const RecArgs& g, uint32_t t, uint32_t pos,
+                                        const float4& rec, uint32_t k32) {
   if (pos < g.top_cap) {
-    const size_t at = par * g.top_stride + static_cast<size_t>(t) * g.top_cap + pos;
+    const size_t at = static_cast<size_t>(t) * g.top_cap + pos;
     g.top_rows[at] = rec;
     g.top_keys[at] = k32;
   } else {
@@ -122,51 +122,116 @@ __device__ __forceinline__ void put_top(const StepParams<float>& a, const RecArg
   }
 }
 
+// Exclusive prefix sum of s[0, len) in place (len <= 2048, 512 threads).
+__device__ __forceinline__ void scan_excl_512(uint32_t* s, uint32_t len, uint32_t* s_warp) {
+  constexpr uint32_t per = 4;
+  const uint32_t lo = threadIdx.x * per;
+  uint32_t v[per], sum = 0;
+#pragma unroll
+  for (uint32_t i = 0; i < per; ++i) {
+    v[i] = (lo + i < len) ? s[lo + i] : 0u;
+    sum += v[i];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  uint32_t run = incl - sum;
+  for (int w = 0; w < warp; ++w) run += s_warp[w];
+#pragma unroll
+  for (uint32_t i = 0; i < per; ++i) {
+    if (lo + i < len) s[lo + i] = run;
+    run += v[i];
+  }
+  __syncthreads();
+}
+
+// The run holding local position j: the largest u < len with start[u] <= j
+// (never an empty run: its successor would start at the same place).
+__device__ __forceinline__ uint32_t run_of(const uint32_t* start, uint32_t len, uint32_t j) {
+  uint32_t lo = 0, hi = len;  // start[lo] <= j, and j < start[hi] for hi < len
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (start[mid] <= j) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// The block's records, grouped by bucket in shared memory, out to their runs
+// in the buckets: consecutive threads store consecutive rows of one run, so
+// the stores cover whole lines instead of one line per record.
+//   s_rows/s_keys[j], j < nrec: records in bucket order; s_start[u]: local
+//   start of bucket u; s_base[u]: the run reserved in bucket u.
+template <typename Put>
+__device__ __forceinline__ void store_runs(uint32_t nrec, uint32_t nbkt, const uint32_t* s_start,
+                                           const uint32_t* s_base, Put put) {
+  for (uint32_t j = threadIdx.x; j < nrec; j += blockDim.x) {
+    const uint32_t u = run_of(s_start, nbkt, j);
+    put(u, s_base[u] + (j - s_start[u]), j);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // First step of a run: the caller's rows in id order into the top level.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSplitThreads, 2) k_rec_scatter(StepParams<float> a, RecArgs g) {
-  __shared__ uint32_t s_hist[1u << kMaxDigitBits];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* s_rows = reinterpret_cast<float4*>(smem_raw);              // [kChunk] records by bucket
+  uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_rows + kChunk);   // [kChunk]
+  __shared__ uint32_t s_hist[1u << kMaxDigitBits];  // counts, then local starts
   __shared__ uint32_t s_base[1u << kMaxDigitBits];
+  __shared__ uint32_t s_warp[32];
   const uint32_t m32 = step_index(a);
   const uint32_t par = m32 & 1u;
   const uint32_t i0 = blockIdx.x * kChunk;
+  const uint32_t nrec = min(kChunk, a.n - i0);
   if (threadIdx.x == 0) {  // the chunk's rows into L2 while the keys are drawn
-    const uint32_t nrow = min(kChunk, a.n - i0);
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.x + static_cast<size_t>(i0) * 4),
-                 "r"(nrow * 16u) : "memory");
+                 "r"(nrec * 16u) : "memory");
   }
   for (uint32_t u = threadIdx.x; u < g.ntop; u += blockDim.x) s_hist[u] = 0;
   __syncthreads();
   uint32_t tr[kSplitPer], k32[kSplitPer];
 #pragma unroll
   for (int k = 0; k < kSplitPer; ++k) {
-    const uint32_t i = i0 + k * kSplitThreads + threadIdx.x;
-    if (i < a.n) {
+    const uint32_t e = k * kSplitThreads + threadIdx.x;
+    if (e < nrec) {
       uint32_t t;
-      top_key(a, g, i, m32, t, k32[k]);
+      top_key(a, g, i0 + e, m32, t, k32[k]);
       tr[k] = t | (atomicAdd(&s_hist[t], 1u) << 16);
     }
+  }
+  float4 v[kSplitPer];  // every row in flight before the first store
+#pragma unroll
+  for (int k = 0; k < kSplitPer; ++k) {
+    const uint32_t e = k * kSplitThreads + threadIdx.x;
+    if (e < nrec) v[k] = reinterpret_cast<const float4*>(a.x)[i0 + e];
   }
   __syncthreads();
   for (uint32_t u = threadIdx.x; u < g.ntop; u += blockDim.x)
     if (s_hist[u]) s_base[u] = atomicAdd(&g.top_fill[par * g.ntop + u], s_hist[u]);
   __syncthreads();
-  float4 v[kSplitPer];  // every row in flight before the first store
+  scan_excl_512(s_hist, g.ntop, s_warp);
 #pragma unroll
   for (int k = 0; k < kSplitPer; ++k) {
-    const uint32_t i = i0 + k * kSplitThreads + threadIdx.x;
-    if (i < a.n) v[k] = reinterpret_cast<const float4*>(a.x)[i];
-  }
-#pragma unroll
-  for (int k = 0; k < kSplitPer; ++k) {
-    const uint32_t i = i0 + k * kSplitThreads + threadIdx.x;
-    if (i < a.n) {
-      v[k].w = __uint_as_float(i);
-      const uint32_t t = tr[k] & 0xffffu;
-      put_top(a, g, par, t, s_base[t] + (tr[k] >> 16), v[k], k32[k]);
+    const uint32_t e = k * kSplitThreads + threadIdx.x;
+    if (e < nrec) {
+      const uint32_t at = s_hist[tr[k] & 0xffffu] + (tr[k] >> 16);
+      v[k].w = __uint_as_float(i0 + e);
+      s_rows[at] = v[k];
+      s_keys[at] = k32[k];
     }
   }
+  __syncthreads();
+  store_runs(nrec, g.ntop, s_hist, s_base, [&](uint32_t t, uint32_t pos, uint32_t j) {
+    put_top(a, g, t, pos, s_rows[j], s_keys[j]);
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -174,26 +239,30 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_rec_scatter(StepParams<flo
 // bucket t (C = kSubChunk).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSubThreads, 2) k_rec_split(StepParams<float> a, RecArgs g, uint32_t chunks) {
-  __shared__ uint32_t s_hist[1u << kMaxDigitBits];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* s_rows = reinterpret_cast<float4*>(smem_raw);                // [kSubChunk] records by sub-bucket
+  uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_rows + kSubChunk);  // [kSubChunk]
+  __shared__ uint32_t s_hist[1u << kMaxDigitBits];  // counts, then local starts
   __shared__ uint32_t s_base[1u << kMaxDigitBits];
+  __shared__ uint32_t s_warp[32];
   const uint32_t m32 = step_index(a);
   const uint32_t par = m32 & 1u;
-  const uint32_t tg = blockIdx.x / chunks, j = blockIdx.x - tg * chunks;
-  const uint32_t t = g.t_lo + tg;
+  const uint32_t t = blockIdx.x / chunks, j = blockIdx.x - t * chunks;
   const uint32_t filled = g.top_fill[par * g.ntop + t];
   if (j == 0 && threadIdx.x == 0 && filled > g.top_cap) latch_status(a.status, RBM_ERR_STATE);
   const uint32_t count = min(filled, g.top_cap);
   const uint32_t lo = j * kSubChunk;
   if (lo >= count) return;  // uniform over the block
+  const uint32_t nrec = min(kSubChunk, count - lo);
   for (uint32_t u = threadIdx.x; u < g.nsub; u += blockDim.x) s_hist[u] = 0;
   __syncthreads();
-  const size_t src0 = par * g.top_stride + static_cast<size_t>(t) * g.top_cap + lo;
+  const size_t src0 = static_cast<size_t>(t) * g.top_cap + lo;
   uint32_t ur[kSubPer], k32[kSubPer];
   float4 v[kSubPer];  // every record in flight before the first store
 #pragma unroll
   for (int k = 0; k < kSubPer; ++k) {
     const uint32_t e = k * kSubThreads + threadIdx.x;
-    if (lo + e < count) {
+    if (e < nrec) {
       k32[k] = g.top_keys[src0 + e];
       v[k] = g.top_rows[src0 + e];
     }
@@ -201,7 +270,7 @@ __global__ void __launch_bounds__(kSubThreads, 2) k_rec_split(StepParams<float> 
 #pragma unroll
   for (int k = 0; k < kSubPer; ++k) {
     const uint32_t e = k * kSubThreads + threadIdx.x;
-    if (lo + e < count) {
+    if (e < nrec) {
       const uint32_t u = sub_of(k32[k], g.sub_bits);
       ur[k] = u | (atomicAdd(&s_hist[u], 1u) << 16);
     }
@@ -210,30 +279,31 @@ __global__ void __launch_bounds__(kSubThreads, 2) k_rec_split(StepParams<float> 
   for (uint32_t u = threadIdx.x; u < g.nsub; u += blockDim.x)
     if (s_hist[u]) s_base[u] = atomicAdd(&g.sub_fill[par * g.nbuckets + t * g.nsub + u], s_hist[u]);
   __syncthreads();
+  scan_excl_512(s_hist, g.nsub, s_warp);
 #pragma unroll
   for (int k = 0; k < kSubPer; ++k) {
     const uint32_t e = k * kSubThreads + threadIdx.x;
-    if (lo + e < count) {
-      const uint32_t u = ur[k] & 0xffffu;
-      const uint32_t pos = s_base[u] + (ur[k] >> 16);
-      if (pos < g.sub_cap) {
-        const size_t at = static_cast<size_t>(t * g.nsub + u) * g.sub_cap + pos;
-        g.sub_rows[at] = v[k];
-        g.sub_keys[at] = k32[k];
-      } else {
-        latch_status(a.status, RBM_ERR_STATE);
-      }
+    if (e < nrec) {
+      const uint32_t at = s_hist[ur[k] & 0xffffu] + (ur[k] >> 16);
+      s_rows[at] = v[k];
+      s_keys[at] = k32[k];
     }
   }
+  __syncthreads();
+  store_runs(nrec, g.nsub, s_hist, s_base, [&](uint32_t u, uint32_t pos, uint32_t jj) {
+    if (pos < g.sub_cap) {
+      const size_t at = static_cast<size_t>(t * g.nsub + u) * g.sub_cap + pos;
+      g.sub_rows[at] = s_rows[jj];
+      g.sub_keys[at] = s_keys[jj];
+    } else {
+      latch_status(a.status, RBM_ERR_STATE);
+    }
+  });
 }
 
 // ---------------------------------------------------------------------------
-// Sorted start of the sub-buckets of top buckets [t_lo, t_hi) (one block):
-// the exclusive sum of the counts of every sub-bucket before them (whose
-// splits are done); clears the counters of these sub-buckets for the next
-// step, and the group holding top bucket 0 clears the next step's top-level
-// counters.  The group ending the level checks that the total is N (else
-// RBM_ERR_STATE).
+// Sorted start of every sub-bucket (one block); clears the counters the
+// next step fills.  A total other than N latches RBM_ERR_STATE.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_rec_scan(StepParams<float> a, RecArgs g) {
   __shared__ uint32_t s_warp[32];
@@ -241,8 +311,7 @@ __global__ void __launch_bounds__(1024) k_rec_scan(StepParams<float> a, RecArgs 
   const uint32_t par = m32 & 1u, np = par ^ 1u;
   const uint32_t* cnt = g.sub_fill + par * g.nbuckets;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const uint32_t nb = g.t_hi * g.nsub;       // sums over [0, nb), writes [b_lo, nb)
-  const uint32_t b_lo = g.t_lo * g.nsub;
+  const uint32_t nb = g.nbuckets;
   const uint32_t per = (nb + blockDim.x - 1) / blockDim.x;
   const uint32_t lo = min(nb, threadIdx.x * per), hi = min(nb, lo + per);
   uint32_t sum = 0;
@@ -267,16 +336,15 @@ __global__ void __launch_bounds__(1024) k_rec_scan(StepParams<float> a, RecArgs 
   __syncthreads();
   uint32_t run = ((warp > 0) ? s_warp[warp - 1] : 0u) + incl - sum;
   for (uint32_t b = lo; b < hi; ++b) {
-    if (b >= b_lo) g.sub_start[b] = run;
+    g.sub_start[b] = run;
     run += cnt[b];
   }
-  if (threadIdx.x == blockDim.x - 1 && g.t_hi == g.ntop) {
+  if (threadIdx.x == blockDim.x - 1) {
     g.sub_start[nb] = run;  // the last thread's run ends at the total
     if (run != a.n) latch_status(a.status, RBM_ERR_STATE);
   }
-  for (uint32_t b = b_lo + threadIdx.x; b < nb; b += blockDim.x) g.sub_fill[np * g.nbuckets + b] = 0;
-  if (g.t_lo == 0)
-    for (uint32_t u = threadIdx.x; u < g.ntop; u += blockDim.x) g.top_fill[np * g.ntop + u] = 0;
+  for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) g.sub_fill[np * nb + b] = 0;
+  for (uint32_t u = threadIdx.x; u < g.ntop; u += blockDim.x) g.top_fill[np * g.ntop + u] = 0;
 }
 
 // The sub-bucket holding sorted position pos (largest b with start[b] <=
@@ -315,7 +383,7 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
   uint32_t* s_base = reinterpret_cast<uint32_t*>(spark + g.sub_cap);   // [ntop] run starts in the top level
   __shared__ uint32_t s_hist[kFine];
   __shared__ uint32_t s_warp[32];
-  const uint32_t b = g.t_lo * g.nsub + blockIdx.x;
+  const uint32_t b = blockIdx.x;
   const uint32_t m32 = step_index(a);
   const uint32_t par = m32 & 1u;
   const uint32_t filled = g.sub_fill[par * g.nbuckets + b];
@@ -446,10 +514,10 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
   // members of batches crossing the ends (sorted positions before q0 p and
   // from q_end p on): parked under the sub-bucket that holds the batch's
   // first member
+  const uint32_t head = (count > 0) ? q0 * up - start : cnt;   // all members when no batch fits inside
+  const uint32_t tail = (count > 0) ? min(cnt, q_end * up - start) : cnt;
+  const uint32_t ncross = head + (cnt - tail);
   {
-    const uint32_t head = (count > 0) ? q0 * up - start : cnt;   // all members when no batch fits inside
-    const uint32_t tail = (count > 0) ? min(cnt, q_end * up - start) : cnt;
-    const uint32_t ncross = head + (cnt - tail);
     for (uint32_t c = threadIdx.x; c < ncross; c += blockDim.x) {
       const uint32_t e = (c < head) ? c : tail + (c - head);
       const uint32_t pos = start + e;
@@ -457,7 +525,7 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
       const uint32_t qp = q * up;
       const uint16_t slot = sidx[e];
       spark[slot] = 1;
-      // an earlier sub-bucket (qp < start[b]): its start is already known
+      // an earlier sub-bucket (qp < start[b])
       const uint32_t bf = (qp >= start) ? b : sub_bucket_at(g.sub_start, b, qp);
       g.side[static_cast<size_t>(bf) * kSide + (pos - qp)] = srow[slot];
     }
@@ -484,15 +552,21 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
   for (uint32_t u = threadIdx.x; u < g.ntop; u += blockDim.x)
     if (s_hist[u]) s_base[u] = atomicAdd(&g.top_fill[np * g.ntop + u], s_hist[u]);
   __syncthreads();
+  scan_excl_512(s_hist, g.ntop, s_warp);  // local start of each bucket's run
 #pragma unroll
   for (int k = 0; k < kStepPer; ++k) {
     const uint32_t e = threadIdx.x + k * kStepThreads;
     if (e >= cnt) break;
     if (!spark[e]) {
-      const uint32_t t = tr[k] & 0xffffu;
-      put_top(a, g, np, t, s_base[t] + (tr[k] >> 16), srow[e], k32[k]);
+      sidx[s_hist[tr[k] & 0xffffu] + (tr[k] >> 16)] = static_cast<uint16_t>(e);
+      sfine[e] = k32[k];
     }
   }
+  __syncthreads();
+  store_runs(cnt - ncross, g.ntop, s_hist, s_base, [&](uint32_t t, uint32_t pos, uint32_t j) {
+    const uint32_t e = sidx[j];
+    put_top(a, g, t, pos, srow[e], sfine[e]);
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -534,7 +608,7 @@ __global__ void __launch_bounds__(256) k_rec_fixup(StepParams<float> a, RecArgs 
     uint32_t t, k32;
     top_key(a, g, id, m32 + 1u, t, k32);
     const uint32_t np = (m32 & 1u) ^ 1u;
-    put_top(a, g, np, t, atomicAdd(&g.top_fill[np * g.ntop + t], 1u), to_rec(r), k32);
+    put_top(a, g, t, atomicAdd(&g.top_fill[np * g.ntop + t], 1u), to_rec(r), k32);
   }
 }
 
@@ -550,9 +624,7 @@ RecArgs make_args(const RecScratch& rs) {
   RecArgs g;
   g.top_rows = rs.top_rows; g.top_keys = rs.top_keys; g.sub_rows = rs.sub_rows; g.sub_keys = rs.sub_keys;
   g.top_fill = rs.top_fill; g.sub_fill = rs.sub_fill; g.sub_start = rs.sub_start; g.side = rs.side;
-  g.top_stride = static_cast<size_t>(rs.ntop) * rs.top_cap;
   g.top_cap = rs.top_cap; g.sub_cap = rs.sub_cap; g.ntop = rs.ntop; g.nsub = rs.nsub; g.nbuckets = rs.ntop * rs.nsub;
-  g.t_lo = 0; g.t_hi = rs.ntop;
   g.top_bits = rs.top_bits; g.sub_bits = rs.sub_bits;
   return g;
 }
@@ -582,16 +654,10 @@ void rec_geometry(uint32_t n, int tuned_bits, RecScratch* rs) {
   rs->top_cap = round_up(static_cast<uint32_t>(top_mean + 12.0 * std::sqrt(top_mean) + 1024.0), 32);
   const uint32_t sc = round_up(static_cast<uint32_t>(sub_mean + 12.0 * std::sqrt(sub_mean) + 64.0), 32);
   rs->sub_cap = sc < kSubCapMax ? sc : kSubCapMax;
-  // pipeline groups of at least 2048 sub-buckets (several waves of k_rec_step each)
-  int groups = 1;
-  while (groups < RecScratch::kMaxGroups && static_cast<uint32_t>(2 * groups) <= rs->ntop &&
-         (static_cast<uint64_t>(rs->ntop) * rs->nsub) / (2 * groups) >= 2048)
-    groups *= 2;
-  rs->groups = groups;
 }
 
 cudaError_t rec_alloc(uint32_t n, RecScratch* rs) {
-  const size_t top = 2 * static_cast<size_t>(rs->ntop) * rs->top_cap;  // both step parities
+  const size_t top = static_cast<size_t>(rs->ntop) * rs->top_cap;
   const size_t nb = static_cast<size_t>(rs->ntop) * rs->nsub;
   const size_t sub = nb * rs->sub_cap;
   cudaError_t e = cudaMalloc(&rs->top_rows, top * sizeof(float4));
@@ -602,14 +668,6 @@ cudaError_t rec_alloc(uint32_t n, RecScratch* rs) {
   if (e == cudaSuccess) e = cudaMalloc(&rs->sub_fill, 2 * nb * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&rs->sub_start, (nb + 1) * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&rs->side, nb * kSide * sizeof(float4));
-  if (e == cudaSuccess && rs->groups > 1) {
-    int least = 0, greatest = 0;
-    e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&rs->aux, cudaStreamNonBlocking, greatest);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&rs->ev_start, cudaEventDisableTiming);
-    for (int q = 0; q < rs->groups && e == cudaSuccess; ++q)
-      e = cudaEventCreateWithFlags(&rs->ev_split[q], cudaEventDisableTiming);
-  }
   (void)n;
   return e;
 }
@@ -617,10 +675,6 @@ cudaError_t rec_alloc(uint32_t n, RecScratch* rs) {
 void rec_free(RecScratch* rs) {
   cudaFree(rs->top_rows); cudaFree(rs->top_keys); cudaFree(rs->sub_rows); cudaFree(rs->sub_keys);
   cudaFree(rs->top_fill); cudaFree(rs->sub_fill); cudaFree(rs->sub_start); cudaFree(rs->side);
-  for (int q = 0; q < RecScratch::kMaxGroups; ++q)
-    if (rs->ev_split[q]) cudaEventDestroy(rs->ev_split[q]);
-  if (rs->ev_start) cudaEventDestroy(rs->ev_start);
-  if (rs->aux) cudaStreamDestroy(rs->aux);
   *rs = RecScratch{};
 }
 
@@ -628,7 +682,12 @@ cudaError_t prepare_rec_kernels() {
   const int bytes = static_cast<int>(step_smem(kSubCapMax, 1u << kMaxDigitBits));
   cudaError_t e = cudaFuncSetAttribute(k_rec_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rec_step<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  // the split and scatter kernels hold 16 KB of counters: let several blocks share an SM
+  // the split and scatter kernels stage 4096 records (80 KB) besides 16 KB of counters: two blocks per SM
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_rec_split, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kStageBytes));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_rec_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kStageBytes));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_rec_split, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess)
@@ -637,91 +696,45 @@ cudaError_t prepare_rec_kernels() {
   return e;
 }
 
-// Top buckets of pipeline group q: [q ntop / G, (q + 1) ntop / G).
-static uint32_t group_lo(const RecScratch& rs, int groups, int q) {
-  return static_cast<uint32_t>(static_cast<uint64_t>(rs.ntop) * q / groups);
-}
-
-// Whether a run pipelines its steps: groups to split, a stream to split them
-// on, and no per-kernel timing (which wants the kernels one after another).
-static bool pipelined(const RecScratch& rs, const LaunchCfg& cfg) { return rs.groups > 1 && rs.aux && !cfg.events; }
-
-int rec_launches_per_step(const RecScratch& rs) {
-  return 3 * rs.groups + 1;  // split, scan and step per group, then the fix-up
-}
+int rec_launches_per_step(const RecScratch&) { return 4; }  // split, scan, step, fix-up
 
 // `count` RBM-1 steps from step (m_ptr ? *m_ptr : 0) + a.m_off: clear the
 // counters, fill the first step's top level from the caller's array, then
 // per step split, scan, step and fix-up; the last step writes the positions.
-// Pipelined, step m runs as
-//   stream st:   [record start]      wait(0) scan 0 step 0  wait(1) scan 1 step 1 ...  fix-up
-//   stream aux:  wait(start) split 0 [0] split 1 [1] ...
-// so that each group's split (bound by the latency of its scattered writes)
-// runs under the sorting and stepping of the groups before it.  The groups
-// are disjoint in everything they write except the next step's top-level
-// regions (reserved by atomics) and the parked members of crossing batches
-// (disjoint slots); a group's scan reads only counts of groups already
-// split.
 cudaError_t launch_rec_run(const RecScratch& rs, const void* params, int64_t count, const LaunchCfg& cfg,
                            cudaStream_t st) {
   const StepParams<float> a0 = *static_cast<const StepParams<float>*>(params);
-  const RecArgs g0 = make_args(rs);
+  const RecArgs g = make_args(rs);
   cudaError_t e = cudaMemsetAsync(rs.top_fill, 0, 2 * rs.ntop * sizeof(uint32_t), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(rs.sub_fill, 0, 2 * size_t(g0.nbuckets) * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(rs.sub_fill, 0, 2 * size_t(g.nbuckets) * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
-  k_rec_scatter<<<(a0.n + kChunk - 1) / kChunk, kSplitThreads, 0, st>>>(a0, g0);
+  k_rec_scatter<<<(a0.n + kChunk - 1) / kChunk, kSplitThreads, kStageBytes, st>>>(a0, g);
   mark_launch(cfg, st, "k_rec_scatter");
   const uint32_t chunks = (rs.top_cap + kSubChunk - 1) / kSubChunk;
   const size_t smem = step_smem(rs.sub_cap, rs.ntop);
   const int gpw = 32 / a0.p;
   const uint32_t fix_groups = 8u * static_cast<uint32_t>(gpw);
-  const uint32_t fix_grid = (g0.nbuckets + fix_groups - 1) / fix_groups;
-  const bool pipe = pipelined(rs, cfg);
-  const int groups = pipe ? rs.groups : 1;
-  cudaStream_t split_st = pipe ? rs.aux : st;
-  for (int64_t k = 0; k < count && e == cudaSuccess; ++k) {
+  const uint32_t fix_grid = (g.nbuckets + fix_groups - 1) / fix_groups;
+  for (int64_t k = 0; k < count; ++k) {
     StepParams<float> a = a0;
     a.m_off = a0.m_off + k;
     const bool last = (k + 1 == count);
-    if (pipe) {
-      e = cudaEventRecord(rs.ev_start, st);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(rs.aux, rs.ev_start, 0);
-    }
-    for (int q = 0; q < groups && e == cudaSuccess; ++q) {
-      RecArgs g = g0;
-      g.t_lo = group_lo(rs, groups, q);
-      g.t_hi = group_lo(rs, groups, q + 1);
-      k_rec_split<<<(g.t_hi - g.t_lo) * chunks, kSubThreads, 0, split_st>>>(a, g, chunks);
-      mark_launch(cfg, split_st, "k_rec_split");
-      if (pipe) e = cudaEventRecord(rs.ev_split[q], rs.aux);
-    }
-    for (int q = 0; q < groups && e == cudaSuccess; ++q) {
-      RecArgs g = g0;
-      g.t_lo = group_lo(rs, groups, q);
-      g.t_hi = group_lo(rs, groups, q + 1);
-      if (pipe) e = cudaStreamWaitEvent(st, rs.ev_split[q], 0);
-      if (e != cudaSuccess) break;
-      const uint32_t grid = (g.t_hi - g.t_lo) * g.nsub;
-      k_rec_scan<<<1, 1024, 0, st>>>(a, g);
-      mark_launch(cfg, st, "k_rec_scan");
-      if (last) {
-        k_rec_step<true><<<grid, kStepThreads, smem, st>>>(a, g);
-        mark_launch(cfg, st, "k_rec_step_last");
-      } else {
-        k_rec_step<false><<<grid, kStepThreads, smem, st>>>(a, g);
-        mark_launch(cfg, st, "k_rec_step");
-      }
-    }
-    if (e != cudaSuccess) break;
+    k_rec_split<<<rs.ntop * chunks, kSubThreads, kStageBytes, st>>>(a, g, chunks);
+    mark_launch(cfg, st, "k_rec_split");
+    k_rec_scan<<<1, 1024, 0, st>>>(a, g);
+    mark_launch(cfg, st, "k_rec_scan");
     if (last) {
-      k_rec_fixup<true><<<fix_grid, 256, 0, st>>>(a, g0);
+      k_rec_step<true><<<g.nbuckets, kStepThreads, smem, st>>>(a, g);
+      mark_launch(cfg, st, "k_rec_step_last");
+      k_rec_fixup<true><<<fix_grid, 256, 0, st>>>(a, g);
       mark_launch(cfg, st, "k_rec_fixup_last");
     } else {
-      k_rec_fixup<false><<<fix_grid, 256, 0, st>>>(a, g0);
+      k_rec_step<false><<<g.nbuckets, kStepThreads, smem, st>>>(a, g);
+      mark_launch(cfg, st, "k_rec_step");
+      k_rec_fixup<false><<<fix_grid, 256, 0, st>>>(a, g);
       mark_launch(cfg, st, "k_rec_fixup");
     }
   }
-  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -6,12 +6,9 @@ written back by id after the call's last step.
   bucket-sort path bit for bit (both evaluate each batch with the same
   arithmetic on the same rows in the same order), for p from 2 to 32, sizes
   that leave a ragged last batch, bucket geometries down to sub-buckets of a
-  few records (batches crossing many of them, and crossing the groups of top
-  buckets a pipelined step splits one after another), graph replays and
-  eager runs;
-- the pipelined steps (2, 4 and 8 groups) equal the same steps run one
-  kernel after another (rbm_step_profiled), and the launch count per step
-  is three per group and one;
+  few records (batches crossing many of them), graph replays and eager runs;
+- rbm_step_profiled (two steps, each kernel timed) equals two steps of a
+  run, and a step launches four kernels;
 - against the oracle: every particle within the FP32 bar after one step, and
   after a 5-step run within a bound that adds the per-step bars;
 - the pad lane of every row is left as the caller wrote it;
@@ -64,8 +61,8 @@ def test_record_path_run_equals_per_id_path_bitwise(n, p, bits):
         f"{np.sum(np.any(got != ref, axis=1))} rows differ"
 
 
-@pytest.mark.parametrize("n,bits,groups", [(20000, 12, 2), (300007, 13, 4), (100003, 14, 8)])
-def test_record_path_pipelined_equals_sequential_kernels(n, bits, groups):
+@pytest.mark.parametrize("n,bits", [(20000, 12), (300007, 13), (100003, 14)])
+def test_record_path_profiled_steps_equal_run(n, bits):
     torch = torch_cuda()
     X = as_run_precision(workloads.gaussian(n, 3, seed=9), "f32")
     out = []
@@ -73,7 +70,7 @@ def test_record_path_pipelined_equals_sequential_kernels(n, bits, groups):
         x = _x(X, torch, pad_seed=3)
         s = rbm.System(x, d=3, p=3, seed=2, **KW)
         s.set_tuning(path=4, bucket_bits=bits)
-        assert s.launches_per_step() == 3 * groups + 1
+        assert s.launches_per_step() == 4
         if profiled:
             names = [k for k, _ in s.step_profiled()]       # two steps, one kernel after another
             assert names.count("k_rec_split") == 2 and names.count("k_rec_step_last") == 1
