@@ -288,10 +288,12 @@ def run_reference(args, w):
     return 0
 
 
-def _traffic_for(workload: str, kernel_name: str, digest: str):
+def _traffic_for(workload: str, kernel_name: str, digest: str, n=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current sources of that kernel (`digest`, of all sources, is kept
-    for the line's record)."""
+    for the line's record).  A capture taken at a smaller size `n` (the
+    full-size launch is too large for a multi-pass capture) is scaled to the
+    line's particles: the kernel's traffic grows in proportion to N."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -300,7 +302,10 @@ def _traffic_for(workload: str, kernel_name: str, digest: str):
     ent = data.get(workload, {}).get(kernel_name)
     if not ent or ent.get("sources") != _kernel_sources_digest(kernel_name):
         return None
-    return ent.get("dram_bytes_per_launch")
+    b = ent.get("dram_bytes_per_launch")
+    if b is not None and n is not None and ent.get("n"):
+        b = b * n / ent["n"]
+    return b
 
 
 def max_over_ranks(dist, v, device):
@@ -369,10 +374,10 @@ def _to_dev(g, X, d, dtype):
     return t.to(torch.float32 if dtype == "f32" else torch.float64).to(g.dev).contiguous()
 
 
-def _roofline(peaks, peak_src, kernel, alg_bytes, avg_ms, workload, digest):
+def _roofline(peaks, peak_src, kernel, alg_bytes, avg_ms, workload, digest, n=None):
     achieved = alg_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
     return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": _traffic_for(workload, kernel, digest),
+            "frac": achieved / peaks["hbm_gbs"], "traffic": _traffic_for(workload, kernel, digest, n),
             "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
             "peak_source": f"{peak_src} (hbm_gbs)"}
 
@@ -548,7 +553,7 @@ def run_headline(args, w, g):
     dom = "k_rec_step" if "k_rec_step" in avg else max(avg, key=avg.get)
     digest = _kernel_sources_digest()
     floor = rbm_floor_bytes(d, elem)
-    roof = _roofline(peaks, peak_src, dom, n * floor, avg[dom], w["workload"], digest)
+    roof = _roofline(peaks, peak_src, dom, n * floor, avg[dom], w["workload"], digest, n)
     roof["bytes_per_particle_step"] = floor
     roof["bytes_note"] = ("2 x 12 B of positions (d = 3 FP32; the stored row is 16 B with its pad lane) + 4 B "
                           "permutation written + 4 B read")

@@ -77,13 +77,30 @@ __device__ __forceinline__ uint64_t perm_key(uint32_t id, uint32_t m32, uint32_t
 // pair 2q + 1 from words a0, a2.  z0 = sqrt(-2 ln u1) cos(2 pi u2),
 // z1 = sqrt(-2 ln u1) sin(2 pi u2).
 // ---------------------------------------------------------------------------
-// FP32: the angle is taken as 2 pi u2 - pi in (-pi, pi], where the hardware
+// FP32 radius r^2 = -2 ln u for u = k 2^-24, k = 1 .. 2^24.  With
+// t = 1 - u = (2^24 - k) 2^-24 exact: for t < 2^-7 the series
+// -ln(1 - t) = t + t^2/2 + t^3/3 + t^4/4 + ... to the t^4 term (relative
+// error below t^4/5 < 2^-30), which keeps r^2 accurate where u is close to 1;
+// otherwise the hardware base-2 logarithm, -2 ln 2 log2(u) (absolute error
+// at most 2^-22 in log2 u on [1/2, 1), where here |log2 u| > 2^-7 log2 e,
+// and 2 ulp below 1/2), so that r = sqrt(r^2) is off by less than 2e-6.
+__device__ __forceinline__ float box_muller_r2(uint32_t k) {
+  const uint32_t v = (1u << 24) - k;
+  if (v < (1u << 17)) {
+    const float t = static_cast<float>(v) * 0x1p-24f;
+    return 2.0f * t * fmaf(t, fmaf(t, fmaf(t, 0.25f, 0.333333333f), 0.5f), 1.0f);
+  }
+  return -1.38629436112f * __log2f(static_cast<float>(k) * 0x1p-24f);
+}
+
+// FP32: r from r^2 above by the hardware reciprocal square root (r = 0 at
+// u = 1); the angle is taken as 2 pi u2 - pi in (-pi, pi], where the hardware
 // sine and cosine are accurate to about 4e-7 absolute, and the signs turned
 // back (cos(a - pi) = -cos a, sin(a - pi) = -sin a).
 __device__ __forceinline__ void normal_pair_words(uint32_t w1, uint32_t w2, float& z0, float& z1) {
-  const float u1 = static_cast<float>((w1 >> 8) + 1u) * 0x1p-24f;
   const float u2 = static_cast<float>((w2 >> 8) + 1u) * 0x1p-24f;
-  const float rad = sqrtf(-2.0f * logf(u1));
+  const float r2 = box_muller_r2((w1 >> 8) + 1u);
+  const float rad = (r2 > 0.0f) ? r2 * rsqrtf(r2) : 0.0f;
   float s, c;
   __sincosf(fmaf(6.28318530718f, u2, -3.14159265359f), &s, &c);
   z0 = -rad * c;

@@ -60,7 +60,7 @@ constexpr uint32_t kFine = 1u << kFineBits;
 constexpr int kMaxDigitBits = 11;       // top and sub digits: at most 2048 values
 constexpr int kSide = 32;               // parked members per sub-bucket (p <= 32)
 static_assert(kChunk == kSubChunk, "the scatter and split kernels share one staging size");
-constexpr size_t kStageBytes = kChunk * (sizeof(float4) + sizeof(uint32_t));  // records staged by bucket
+constexpr size_t kStageBytes = kChunk * (sizeof(float4) + sizeof(uint32_t) + sizeof(uint8_t));  // staged records
 
 struct RecArgs {
   float4* top_rows;     // [ntop * top_cap]
@@ -167,12 +167,15 @@ __device__ __forceinline__ uint32_t run_of(const uint32_t* start, uint32_t len, 
 // in the buckets: consecutive threads store consecutive rows of one run, so
 // the stores cover whole lines instead of one line per record.
 //   s_rows/s_keys[j], j < nrec: records in bucket order; s_start[u]: local
-//   start of bucket u; s_base[u]: the run reserved in bucket u.
+//   start of bucket u; s_base[u]: the run reserved in bucket u; s_bkt[j]:
+//   the bucket of position j when there are at most 256 buckets (else null:
+//   found by binary search over s_start).
+constexpr uint32_t kByteBuckets = 256;
 template <typename Put>
 __device__ __forceinline__ void store_runs(uint32_t nrec, uint32_t nbkt, const uint32_t* s_start,
-                                           const uint32_t* s_base, Put put) {
+                                           const uint32_t* s_base, const uint8_t* s_bkt, Put put) {
   for (uint32_t j = threadIdx.x; j < nrec; j += blockDim.x) {
-    const uint32_t u = run_of(s_start, nbkt, j);
+    const uint32_t u = s_bkt ? s_bkt[j] : run_of(s_start, nbkt, j);
     put(u, s_base[u] + (j - s_start[u]), j);
   }
 }
@@ -184,6 +187,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_rec_scatter(StepParams<flo
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* s_rows = reinterpret_cast<float4*>(smem_raw);              // [kChunk] records by bucket
   uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_rows + kChunk);   // [kChunk]
+  uint8_t* s_bkt = reinterpret_cast<uint8_t*>(s_keys + kChunk);       // [kChunk] bucket of each position
   __shared__ uint32_t s_hist[1u << kMaxDigitBits];  // counts, then local starts
   __shared__ uint32_t s_base[1u << kMaxDigitBits];
   __shared__ uint32_t s_warp[32];
@@ -226,10 +230,12 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_rec_scatter(StepParams<flo
       v[k].w = __uint_as_float(i0 + e);
       s_rows[at] = v[k];
       s_keys[at] = k32[k];
+      s_bkt[at] = static_cast<uint8_t>(tr[k]);
     }
   }
   __syncthreads();
-  store_runs(nrec, g.ntop, s_hist, s_base, [&](uint32_t t, uint32_t pos, uint32_t j) {
+  store_runs(nrec, g.ntop, s_hist, s_base, g.ntop <= kByteBuckets ? s_bkt : nullptr,
+             [&](uint32_t t, uint32_t pos, uint32_t j) {
     put_top(a, g, t, pos, s_rows[j], s_keys[j]);
   });
 }
@@ -242,6 +248,7 @@ __global__ void __launch_bounds__(kSubThreads, 2) k_rec_split(StepParams<float> 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* s_rows = reinterpret_cast<float4*>(smem_raw);                // [kSubChunk] records by sub-bucket
   uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_rows + kSubChunk);  // [kSubChunk]
+  uint8_t* s_bkt = reinterpret_cast<uint8_t*>(s_keys + kSubChunk);     // [kSubChunk] sub-bucket of each position
   __shared__ uint32_t s_hist[1u << kMaxDigitBits];  // counts, then local starts
   __shared__ uint32_t s_base[1u << kMaxDigitBits];
   __shared__ uint32_t s_warp[32];
@@ -287,10 +294,12 @@ __global__ void __launch_bounds__(kSubThreads, 2) k_rec_split(StepParams<float> 
       const uint32_t at = s_hist[ur[k] & 0xffffu] + (ur[k] >> 16);
       s_rows[at] = v[k];
       s_keys[at] = k32[k];
+      s_bkt[at] = static_cast<uint8_t>(ur[k]);
     }
   }
   __syncthreads();
-  store_runs(nrec, g.nsub, s_hist, s_base, [&](uint32_t u, uint32_t pos, uint32_t jj) {
+  store_runs(nrec, g.nsub, s_hist, s_base, g.nsub <= kByteBuckets ? s_bkt : nullptr,
+             [&](uint32_t u, uint32_t pos, uint32_t jj) {
     if (pos < g.sub_cap) {
       const size_t at = static_cast<size_t>(t * g.nsub + u) * g.sub_cap + pos;
       g.sub_rows[at] = s_rows[jj];
@@ -359,11 +368,9 @@ __device__ __forceinline__ uint32_t sub_bucket_at(const uint32_t* start, uint32_
   return lo;
 }
 
-// (key, id) order of two records of one sub-bucket: the carried bits below
-// the sub digit, then (on a tie) the full keys and the ids.
-__device__ __forceinline__ bool rec_less(const StepParams<float>& a, uint32_t m32, uint32_t fa, uint32_t ida,
-                                         uint32_t fb, uint32_t idb) {
-  if (fa != fb) return fa < fb;
+// (key, id) order of two records of one sub-bucket whose carried bits below
+// the sub digit are equal: the full keys, then the ids.
+__device__ __forceinline__ bool rec_key_less(const StepParams<float>& a, uint32_t m32, uint32_t ida, uint32_t idb) {
   const uint64_t ka = perm_key(ida, m32, a.replica, a.keys), kb = perm_key(idb, m32, a.replica, a.keys);
   return ka < kb || (ka == kb && ida < idb);
 }
@@ -377,7 +384,9 @@ template <bool kLast>
 __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> a, RecArgs g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* srow = reinterpret_cast<float4*>(smem_raw);                 // [sub_cap] records, slot order
-  uint32_t* sfine = reinterpret_cast<uint32_t*>(srow + g.sub_cap);     // [sub_cap] bits below the sub digit
+  // sfine: the bits below the sub digit by provisional position, later the
+  // next step's carried key bits by slot
+  uint32_t* sfine = reinterpret_cast<uint32_t*>(srow + g.sub_cap);     // [sub_cap]
   uint16_t* sidx = reinterpret_cast<uint16_t*>(sfine + g.sub_cap);    // [sub_cap] slot of each sorted position
   uint8_t* spark = reinterpret_cast<uint8_t*>(sidx + g.sub_cap);      // [sub_cap] 1: member of a crossing batch
   uint32_t* s_base = reinterpret_cast<uint32_t*>(spark + g.sub_cap);   // [ntop] run starts in the top level
@@ -402,13 +411,12 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
   // counting sort by the kFineBits bits below the sub digit
   // the fixed-size loops stop at the first slot past cnt (a sub-bucket holds
   // about 2048 of the at most 3072 slots)
-  uint32_t fr[kStepPer];
+  uint32_t fr[kStepPer];  // digit | provisional rank << 16
 #pragma unroll
   for (int k = 0; k < kStepPer; ++k) {
     const uint32_t e = threadIdx.x + k * kStepThreads;
     if (e >= cnt) break;
     const uint32_t f = g.sub_keys[src0 + e] << g.sub_bits;
-    sfine[e] = f;
     const uint32_t d = f >> (32 - kFineBits);
     fr[k] = d | (atomicAdd(&s_hist[d], 1u) << 16);
   }
@@ -441,40 +449,50 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
   }
   __syncthreads();
   asm volatile("cp.async.wait_all;" ::: "memory");
-  // provisional positions: digit order, arbitrary inside a digit
-#pragma unroll
-  for (int k = 0; k < kStepPer; ++k) {
-    const uint32_t e = threadIdx.x + k * kStepThreads;
-    if (e >= cnt) break;
-    sidx[s_hist[fr[k] & 0xffffu] + (fr[k] >> 16)] = static_cast<uint16_t>(e);
-    spark[e] = 0;
-  }
-  __syncthreads();  // also publishes every thread's staged records
-  // final position of each record: its digit's start plus the number of the
-  // digit's records before it in (key, id) order (a digit holds about one)
-  uint16_t fin[kStepPer];
+  // provisional positions: digit order, arbitrary inside a digit; the slot
+  // and the bits below the sub digit stored by provisional position
 #pragma unroll
   for (int k = 0; k < kStepPer; ++k) {
     const uint32_t e = threadIdx.x + k * kStepThreads;
     if (e >= cnt) break;
     const uint32_t d = fr[k] & 0xffffu;
+    const uint32_t pp = s_hist[d] + (fr[k] >> 16);
+    sidx[pp] = static_cast<uint16_t>(e);
+    sfine[pp] = g.sub_keys[src0 + e] << g.sub_bits;  // read again (cached) rather than held across the scan
+    spark[e] = 0;
+    fr[k] = pp | (d << 16);
+  }
+  __syncthreads();  // also publishes every thread's staged records
+  // final position of each record: its digit's start plus the number of the
+  // digit's records before it in (key, id) order (a digit holds about one);
+  // the digit's bits are read in a run, the slots only on equal bits
+#pragma unroll
+  for (int k = 0; k < kStepPer; ++k) {
+    const uint32_t e = threadIdx.x + k * kStepThreads;
+    if (e >= cnt) break;
+    const uint32_t d = fr[k] >> 16;
     const uint32_t lo = s_hist[d], hi = (d + 1 < kFine) ? s_hist[d + 1] : cnt;
     uint32_t rank = 0;
     if (hi - lo > 1) {
-      const uint32_t fe = sfine[e], ie = rec_id(srow[e]);
+      const uint32_t fe = sfine[fr[k] & 0xffffu];
       for (uint32_t j = lo; j < hi; ++j) {
-        const uint16_t sj = sidx[j];
-        if (sj != e && rec_less(a, m32, sfine[sj], rec_id(srow[sj]), fe, ie)) ++rank;
+        const uint32_t fj = sfine[j];
+        if (fj < fe) {
+          ++rank;
+        } else if (fj == fe) {
+          const uint16_t sj = sidx[j];
+          if (sj != e && rec_key_less(a, m32, rec_id(srow[sj]), rec_id(srow[e]))) ++rank;
+        }
       }
     }
-    fin[k] = static_cast<uint16_t>(lo + rank);
+    fr[k] = lo + rank;
   }
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < kStepPer; ++k) {
     const uint32_t e = threadIdx.x + k * kStepThreads;
     if (e >= cnt) break;
-    sidx[fin[k]] = static_cast<uint16_t>(e);
+    sidx[fr[k]] = static_cast<uint16_t>(e);
   }
   __syncthreads();
 
@@ -537,11 +555,13 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
   const uint32_t np = par ^ 1u;
   for (uint32_t u = threadIdx.x; u < g.ntop; u += blockDim.x) s_hist[u] = 0;
   __syncthreads();
+  constexpr uint32_t kParked = 0xffffffffu;
   uint32_t tr[kStepPer], k32[kStepPer];
 #pragma unroll
   for (int k = 0; k < kStepPer; ++k) {
     const uint32_t e = threadIdx.x + k * kStepThreads;
     if (e >= cnt) break;
+    tr[k] = kParked;
     if (!spark[e]) {
       uint32_t t;
       top_key(a, g, rec_id(srow[e]), m32 + 1u, t, k32[k]);
@@ -553,17 +573,22 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
     if (s_hist[u]) s_base[u] = atomicAdd(&g.top_fill[np * g.ntop + u], s_hist[u]);
   __syncthreads();
   scan_excl_512(s_hist, g.ntop, s_warp);  // local start of each bucket's run
+  // the records in bucket order: sidx[j] the slot at position j, spark[j]
+  // (read for the last time in the loop above) its bucket
 #pragma unroll
   for (int k = 0; k < kStepPer; ++k) {
     const uint32_t e = threadIdx.x + k * kStepThreads;
     if (e >= cnt) break;
-    if (!spark[e]) {
-      sidx[s_hist[tr[k] & 0xffffu] + (tr[k] >> 16)] = static_cast<uint16_t>(e);
+    if (tr[k] != kParked) {
+      const uint32_t at = s_hist[tr[k] & 0xffffu] + (tr[k] >> 16);
+      sidx[at] = static_cast<uint16_t>(e);
+      spark[at] = static_cast<uint8_t>(tr[k]);
       sfine[e] = k32[k];
     }
   }
   __syncthreads();
-  store_runs(cnt - ncross, g.ntop, s_hist, s_base, [&](uint32_t t, uint32_t pos, uint32_t j) {
+  store_runs(cnt - ncross, g.ntop, s_hist, s_base, g.ntop <= kByteBuckets ? spark : nullptr,
+             [&](uint32_t t, uint32_t pos, uint32_t j) {
     const uint32_t e = sidx[j];
     put_top(a, g, t, pos, srow[e], sfine[e]);
   });
