@@ -167,17 +167,24 @@ __device__ __forceinline__ uint32_t run_of(const uint32_t* start, uint32_t len, 
 // in the buckets: consecutive threads store consecutive rows of one run, so
 // the stores cover whole lines instead of one line per record.
 //   s_rows/s_keys[j], j < nrec: records in bucket order; s_start[u]: local
-//   start of bucket u; s_base[u]: the run reserved in bucket u; s_bkt[j]:
-//   the bucket of position j when there are at most 256 buckets (else null:
-//   found by binary search over s_start).
+//   start of bucket u; s_shift[u]: the start of the run reserved in bucket u
+//   minus s_start[u] (so that local position j lands at s_shift[u] + j);
+//   s_bkt[j]: the bucket of position j when there are at most 256 buckets
+//   (else null: found by binary search over s_start).
 constexpr uint32_t kByteBuckets = 256;
 template <typename Put>
 __device__ __forceinline__ void store_runs(uint32_t nrec, uint32_t nbkt, const uint32_t* s_start,
-                                           const uint32_t* s_base, const uint8_t* s_bkt, Put put) {
+                                           const uint32_t* s_shift, const uint8_t* s_bkt, Put put) {
   for (uint32_t j = threadIdx.x; j < nrec; j += blockDim.x) {
     const uint32_t u = s_bkt ? s_bkt[j] : run_of(s_start, nbkt, j);
-    put(u, s_base[u] + (j - s_start[u]), j);
+    put(u, s_shift[u] + j, j);
   }
+}
+
+// s_base[u] -= s_start[u] for the buckets that received records (run by the
+// block between the local scan and the barrier before store_runs).
+__device__ __forceinline__ void shift_bases(uint32_t* s_base, const uint32_t* s_start, uint32_t nbkt) {
+  for (uint32_t u = threadIdx.x; u < nbkt; u += blockDim.x) s_base[u] -= s_start[u];
 }
 
 // ---------------------------------------------------------------------------
@@ -222,6 +229,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_rec_scatter(StepParams<flo
     if (s_hist[u]) s_base[u] = atomicAdd(&g.top_fill[par * g.ntop + u], s_hist[u]);
   __syncthreads();
   scan_excl_512(s_hist, g.ntop, s_warp);
+  shift_bases(s_base, s_hist, g.ntop);
 #pragma unroll
   for (int k = 0; k < kSplitPer; ++k) {
     const uint32_t e = k * kSplitThreads + threadIdx.x;
@@ -247,8 +255,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_rec_scatter(StepParams<flo
 __global__ void __launch_bounds__(kSubThreads, 2) k_rec_split(StepParams<float> a, RecArgs g, uint32_t chunks) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* s_rows = reinterpret_cast<float4*>(smem_raw);                // [kSubChunk] records by sub-bucket
-  uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_rows + kSubChunk);  // [kSubChunk]
-  uint8_t* s_bkt = reinterpret_cast<uint8_t*>(s_keys + kSubChunk);     // [kSubChunk] sub-bucket of each position
+  uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_rows + kSubChunk);  // [kSubChunk] (their sub digit: the bucket)
   __shared__ uint32_t s_hist[1u << kMaxDigitBits];  // counts, then local starts
   __shared__ uint32_t s_base[1u << kMaxDigitBits];
   __shared__ uint32_t s_warp[32];
@@ -287,6 +294,7 @@ __global__ void __launch_bounds__(kSubThreads, 2) k_rec_split(StepParams<float> 
     if (s_hist[u]) s_base[u] = atomicAdd(&g.sub_fill[par * g.nbuckets + t * g.nsub + u], s_hist[u]);
   __syncthreads();
   scan_excl_512(s_hist, g.nsub, s_warp);
+  shift_bases(s_base, s_hist, g.nsub);
 #pragma unroll
   for (int k = 0; k < kSubPer; ++k) {
     const uint32_t e = k * kSubThreads + threadIdx.x;
@@ -294,20 +302,22 @@ __global__ void __launch_bounds__(kSubThreads, 2) k_rec_split(StepParams<float> 
       const uint32_t at = s_hist[ur[k] & 0xffffu] + (ur[k] >> 16);
       s_rows[at] = v[k];
       s_keys[at] = k32[k];
-      s_bkt[at] = static_cast<uint8_t>(ur[k]);
     }
   }
   __syncthreads();
-  store_runs(nrec, g.nsub, s_hist, s_base, g.nsub <= kByteBuckets ? s_bkt : nullptr,
-             [&](uint32_t u, uint32_t pos, uint32_t jj) {
+  // runs out, the sub-bucket of each position read off its key
+  for (uint32_t jj = threadIdx.x; jj < nrec; jj += blockDim.x) {
+    const uint32_t kk = s_keys[jj];
+    const uint32_t u = sub_of(kk, g.sub_bits);
+    const uint32_t pos = s_base[u] + jj;
     if (pos < g.sub_cap) {
       const size_t at = static_cast<size_t>(t * g.nsub + u) * g.sub_cap + pos;
       g.sub_rows[at] = s_rows[jj];
-      g.sub_keys[at] = s_keys[jj];
+      g.sub_keys[at] = kk;
     } else {
       latch_status(a.status, RBM_ERR_STATE);
     }
-  });
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -573,6 +583,7 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
     if (s_hist[u]) s_base[u] = atomicAdd(&g.top_fill[np * g.ntop + u], s_hist[u]);
   __syncthreads();
   scan_excl_512(s_hist, g.ntop, s_warp);  // local start of each bucket's run
+  shift_bases(s_base, s_hist, g.ntop);
   // the records in bucket order: sidx[j] the slot at position j, spark[j]
   // (read for the last time in the loop above) its bucket
 #pragma unroll
