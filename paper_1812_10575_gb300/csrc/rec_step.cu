@@ -325,42 +325,57 @@ __global__ void __launch_bounds__(kSubThreads, 2) k_rec_split(StepParams<float> 
 // next step fills.  A total other than N latches RBM_ERR_STATE.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_rec_scan(StepParams<float> a, RecArgs g) {
+  constexpr uint32_t kPer = 4, kSpan = 1024 * kPer;  // counts per thread and per pass
+  __shared__ uint32_t s_cnt[kSpan];
   __shared__ uint32_t s_warp[32];
   const uint32_t m32 = step_index(a);
   const uint32_t par = m32 & 1u, np = par ^ 1u;
   const uint32_t* cnt = g.sub_fill + par * g.nbuckets;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const uint32_t nb = g.nbuckets;
-  const uint32_t per = (nb + blockDim.x - 1) / blockDim.x;
-  const uint32_t lo = min(nb, threadIdx.x * per), hi = min(nb, lo + per);
-  uint32_t sum = 0;
-  for (uint32_t b = lo; b < hi; ++b) sum += cnt[b];
-  uint32_t incl = sum;
+  uint32_t carry = 0;  // total of the passes before
+  for (uint32_t base = 0; base < nb; base += kSpan) {
+    // coalesced in, kPer consecutive counts per thread, coalesced out
+    for (uint32_t i = threadIdx.x; i < kSpan; i += blockDim.x) s_cnt[i] = (base + i < nb) ? cnt[base + i] : 0u;
+    __syncthreads();
+    uint32_t v[kPer], sum = 0;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += v;
-  }
-  if (lane == 31) s_warp[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t w = (lane < nwarps) ? s_warp[lane] : 0u;
+    for (uint32_t k = 0; k < kPer; ++k) {
+      v[k] = s_cnt[threadIdx.x * kPer + k];
+      sum += v[k];
+    }
+    uint32_t incl = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t v = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += v;
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
     }
-    if (lane < nwarps) s_warp[lane] = w;
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = (lane < nwarps) ? s_warp[lane] : 0u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += t;
+      }
+      if (lane < nwarps) s_warp[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = carry + ((warp > 0) ? s_warp[warp - 1] : 0u) + incl - sum;
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+      s_cnt[threadIdx.x * kPer + k] = run;
+      run += v[k];
+    }
+    carry += s_warp[nwarps - 1];
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < kSpan && base + i < nb; i += blockDim.x) g.sub_start[base + i] = s_cnt[i];
+    __syncthreads();  // s_cnt and s_warp free for the next pass
   }
-  __syncthreads();
-  uint32_t run = ((warp > 0) ? s_warp[warp - 1] : 0u) + incl - sum;
-  for (uint32_t b = lo; b < hi; ++b) {
-    g.sub_start[b] = run;
-    run += cnt[b];
-  }
-  if (threadIdx.x == blockDim.x - 1) {
-    g.sub_start[nb] = run;  // the last thread's run ends at the total
-    if (run != a.n) latch_status(a.status, RBM_ERR_STATE);
+  if (threadIdx.x == 0) {
+    g.sub_start[nb] = carry;
+    if (carry != a.n) latch_status(a.status, RBM_ERR_STATE);
   }
   for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) g.sub_fill[np * nb + b] = 0;
   for (uint32_t u = threadIdx.x; u < g.ntop; u += blockDim.x) g.top_fill[np * g.ntop + u] = 0;
