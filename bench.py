@@ -515,11 +515,22 @@ def run_headline(args, w, g):
     e1.record(g.stream)
     s.sync()
     sur_ms = e0.elapsed_time(e1) / sur_steps
+    # a whole cycle: the next train_every steps, which hold one later checkpoint
+    # (queries, direct forces at them, the drift check, retraining)
+    every = w["surrogate"]["train_every"]
+    e0.record(g.stream)
+    s.run(every, "surrogate")
+    e1.record(g.stream)
+    s.sync()
+    cycle_ms = e0.elapsed_time(e1)
     others["surrogate"] = {"particle_steps_per_s": n / (sur_ms * 1e-3), "ms_per_step": sur_ms,
                            "first_checkpoint_ms": first_ms, "steps_timed": sur_steps,
-                           "stats": s.surrogate_stats(),
-                           "note": "network steps between checkpoints (the checkpoint's direct forces at the "
-                                   "queries and its training are reported apart)"}
+                           "cycle": {"steps": every, "ms": cycle_ms,
+                                     "particle_steps_per_s": n * every / (cycle_ms * 1e-3)},
+                           "stats": s.surrogate_stats(), "drift": s.surrogate_drift(),
+                           "note": "network steps between checkpoints; `cycle` times train_every steps "
+                                   "holding one later checkpoint (direct forces at the queries, drift check, "
+                                   "retraining)"}
     s.close()
     del x
     g.torch.cuda.empty_cache()

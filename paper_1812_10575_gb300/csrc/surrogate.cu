@@ -497,8 +497,18 @@ __global__ void k_sur_adam(SurArgs s, uint32_t nblocks, int it, int iters) {
   const float c1 = 1.0f - powf(b1, static_cast<float>(t)), c2 = 1.0f - powf(b2, static_cast<float>(t));
   const float lr = s.lr * powf(0.01f, static_cast<float>(it) / static_cast<float>(iters > 1 ? iters - 1 : 1));
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kNP; i += gridDim.x * blockDim.x) {
+    // the block partials summed in block order; up to a minibatch of 4096
+    // samples (32 blocks) every load is issued before the first add
+    constexpr uint32_t kUnroll = 32;
+    float pb[kUnroll];
+#pragma unroll
+    for (uint32_t b = 0; b < kUnroll; ++b)
+      pb[b] = (b < nblocks) ? s.partial[static_cast<size_t>(b) * (kNP + 1) + i] : 0.0f;
     float g = 0.0f;
-    for (uint32_t b = 0; b < nblocks; ++b) g += s.partial[static_cast<size_t>(b) * (kNP + 1) + i];
+#pragma unroll
+    for (uint32_t b = 0; b < kUnroll; ++b)
+      if (b < nblocks) g += pb[b];
+    for (uint32_t b = kUnroll; b < nblocks; ++b) g += s.partial[static_cast<size_t>(b) * (kNP + 1) + i];
     const float m = b1 * s.mom1[i] + (1.0f - b1) * g;
     const float v = b2 * s.mom2[i] + (1.0f - b2) * g * g;
     s.mom1[i] = m;
