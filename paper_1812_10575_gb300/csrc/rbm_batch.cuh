@@ -16,7 +16,7 @@ constexpr int kModeForces = 2;  // write the interaction forces only
 // fk = 1/(|C|-1) sum_{j in C, j != i} K(X^i - X^j) for this lane's member i of
 // the batch held by the p lanes from `base` (other members' rows by
 // shuffles); zero for a singleton.  All 32 lanes call it together.
-template <typename T, int D>
+template <typename T, int D, int KF = -1>
 __device__ __forceinline__ void batch_force(const StepParams<T>& a, bool valid, int lg, int bs, int base,
                                             const Row<T, D>& r, T (&fk)[D]) {
   const int p = a.p;
@@ -28,7 +28,7 @@ __device__ __forceinline__ void batch_force(const StepParams<T>& a, bool valid, 
     T xj[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) xj[k] = __shfl_sync(0xffffffffu, r.x[k], base + sg);
-    if (valid && sg < bs) add_pair_force_rt<T, D>(a.kf, a.kparam, a.radius_sq, r.x, xj, fk);
+    if (valid && sg < bs) add_pair_force_rt<T, D, KF>(a.kf, a.kparam, a.radius_sq, r.x, xj, fk);
   }
   if (!valid) return;
   const T inv = (bs == p) ? a.inv_pm1 : (bs > 1) ? T(1) / static_cast<T>(bs - 1) : T(0);
@@ -48,8 +48,11 @@ __device__ __forceinline__ void batch_force(const StepParams<T>& a, bool valid, 
 // The step of this lane's member: r becomes its new row (the pad lane kept);
 // returns valid.  The in-batch force, -grad V, the Brownian increment of
 // (id, m) and the Euler-Maruyama update (or the exact pair flow of the
-// splitting scheme, or the Verlet recurrence).
-template <typename T, int D>
+// splitting scheme, or the Verlet recurrence).  KF >= 0 fixes the kernel
+// family at compile time; kPlain (the caller has checked: Euler-Maruyama,
+// additive noise, no projection, no noise refinement) drops the other
+// schemes' branches.  The arithmetic is the same in every form.
+template <typename T, int D, int KF = -1, bool kPlain = false>
 __device__ __forceinline__ bool batch_group_update(const StepParams<T>& a, uint32_t m32, uint32_t id, bool valid,
                                                    int lg, int bs, Row<T, D>& r) {
   const int lane = threadIdx.x & 31;
@@ -57,6 +60,16 @@ __device__ __forceinline__ bool batch_group_update(const StepParams<T>& a, uint3
   if (!valid) {
 #pragma unroll
     for (int k = 0; k < D; ++k) r.x[k] = T(0);
+  }
+  if constexpr (kPlain) {
+    T fk[D];
+    batch_force<T, D, KF>(a, valid, lg, bs, base, r, fk);
+    if (!valid) return false;
+    T y[D];
+    euler_update_plain<T, D>(a, id, m32, r.x, fk, y);
+#pragma unroll
+    for (int k = 0; k < D; ++k) r.x[k] = y[k];
+    return true;
   }
   if (a.scheme == RBM_SCHEME_SPLIT) {
     // Exact pair flow of K (p = 2), then the Euler-Maruyama step of V and noise.
@@ -99,7 +112,7 @@ __device__ __forceinline__ bool batch_group_update(const StepParams<T>& a, uint3
     return true;
   }
   T fk[D];
-  batch_force<T, D>(a, valid, lg, bs, base, r, fk);
+  batch_force<T, D, KF>(a, valid, lg, bs, base, r, fk);
   if (!valid) return false;
   T y[D];
   scheme_update<T, D>(a, id, m32, r.x, fk, y);

@@ -320,15 +320,18 @@ __device__ __forceinline__ T kernel_scale_rt(int kf, T r2, T kparam, T radius_sq
   }
 }
 
-// acc += K(xi - xj), runtime kernel family.
-template <typename T, int D>
+// acc += K(xi - xj): the kernel family KF fixed at compile time, or (KF < 0)
+// chosen at run time from kf; the same arithmetic either way.
+template <typename T, int D, int KF = -1>
 __device__ __forceinline__ void add_pair_force_rt(int kf, T kparam, T radius_sq, const T (&xi)[D], const T (&xj)[D],
                                                   T (&acc)[D]) {
   T x[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) x[k] = fsub_rn(xi[k], xj[k]);
   const T r2 = sqnorm_rn<T, D>(x);
-  const T s = (r2 == T(0)) ? T(0) : kernel_scale_rt<T>(kf, r2, kparam, radius_sq);
+  T s;
+  if constexpr (KF < 0) s = (r2 == T(0)) ? T(0) : kernel_scale_rt<T>(kf, r2, kparam, radius_sq);
+  else s = (r2 == T(0)) ? T(0) : kernel_scale<KF>(r2, kparam, radius_sq);
 #pragma unroll
   for (int k = 0; k < D; ++k) acc[k] += s * x[k];
 }
@@ -454,6 +457,28 @@ __device__ __forceinline__ void euler_update(const StepParams<T>& a, uint32_t id
     for (int k = 0; k < D; ++k) z[k] = T(0);
   }
   euler_apply<T, D>(a, x, fk, z, y, split_flow);
+}
+
+// euler_update for the plain configuration (Euler-Maruyama, additive noise,
+// no projection, no noise refinement), with its arithmetic.
+template <typename T, int D>
+__device__ __forceinline__ void euler_update_plain(const StepParams<T>& a, uint32_t id, uint32_t m32, const T (&x)[D],
+                                                   const T (&fk)[D], T (&y)[D]) {
+  T z[D];
+  if (a.sq != T(0)) {
+    brownian<T, D>(id, m32, a.replica, a.keys, z);
+  } else {
+#pragma unroll
+    for (int k = 0; k < D; ++k) z[k] = T(0);
+  }
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const T fv = (a.vkind == RBM_V_QUADRATIC) ? -a.vcoef * x[k] : T(0);
+    y[k] = x[k] + a.dt * (fk[k] + fv) + a.sq * z[k];
+    ok = ok && finite_val(y[k]);
+  }
+  if (!ok) latch_status(a.status, RBM_ERR_NONFINITE);
 }
 
 // The update of the configured scheme after the interaction force fk.

@@ -405,7 +405,7 @@ __device__ __forceinline__ bool rec_key_less(const StepParams<float>& a, uint32_
 // members of crossing batches, send the moved records on (or, at the last
 // step of a run, write the positions by id).
 // ---------------------------------------------------------------------------
-template <bool kLast>
+template <bool kLast, int KF, bool kPlain>
 __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> a, RecArgs g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* srow = reinterpret_cast<float4*>(smem_raw);                 // [sub_cap] records, slot order
@@ -548,7 +548,7 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
           id = rec_id(srow[slot]);
         }
       }
-      if (batch_group_update<float, 3>(a, m32, id, valid, lg, bs, r)) {
+      if (batch_group_update<float, 3, KF, kPlain>(a, m32, id, valid, lg, bs, r)) {
         if (kLast) write_position(a.x, id, r);
         else srow[slot] = to_rec(r);
       }
@@ -624,7 +624,7 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
 // The batch crossing the end of each sub-bucket (at most one starts in a
 // sub-bucket and ends past it), from its parked members.
 // ---------------------------------------------------------------------------
-template <bool kLast>
+template <bool kLast, int KF, bool kPlain>
 __global__ void __launch_bounds__(256) k_rec_fixup(StepParams<float> a, RecArgs g) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gpw = 32 / a.p;
@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(256) k_rec_fixup(StepParams<float> a, RecArgs 
       }
     }
   }
-  if (!batch_group_update<float, 3>(a, m32, id, valid, lg, bs, r)) return;
+  if (!batch_group_update<float, 3, KF, kPlain>(a, m32, id, valid, lg, bs, r)) return;
   if (kLast) {
     write_position(a.x, id, r);
   } else {
@@ -729,10 +729,66 @@ void rec_free(RecScratch* rs) {
   *rs = RecScratch{};
 }
 
+namespace {
+
+// The sort-and-step kernel and the fix-up of one step, with the kernel
+// family fixed at compile time on the plain configuration (Euler-Maruyama,
+// additive noise, no projection, no noise refinement), or any configuration
+// with the family chosen at run time (KF < 0).  The same arithmetic in every
+// instance.
+template <int KF, bool kPlain>
+void launch_step_pair(bool last, const StepParams<float>& a, const RecArgs& g, size_t smem, uint32_t fix_grid,
+                      const LaunchCfg& cfg, cudaStream_t st) {
+  if (last) {
+    k_rec_step<true, KF, kPlain><<<g.nbuckets, kStepThreads, smem, st>>>(a, g);
+    mark_launch(cfg, st, "k_rec_step_last");
+    k_rec_fixup<true, KF, kPlain><<<fix_grid, 256, 0, st>>>(a, g);
+    mark_launch(cfg, st, "k_rec_fixup_last");
+  } else {
+    k_rec_step<false, KF, kPlain><<<g.nbuckets, kStepThreads, smem, st>>>(a, g);
+    mark_launch(cfg, st, "k_rec_step");
+    k_rec_fixup<false, KF, kPlain><<<fix_grid, 256, 0, st>>>(a, g);
+    mark_launch(cfg, st, "k_rec_fixup");
+  }
+}
+
+template <int KF, bool kPlain>
+cudaError_t allow_step_smem(int bytes) {
+  cudaError_t e = cudaFuncSetAttribute(k_rec_step<false, KF, kPlain>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_rec_step<true, KF, kPlain>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
+using StepPairLaunch = void (*)(bool, const StepParams<float>&, const RecArgs&, size_t, uint32_t, const LaunchCfg&,
+                                cudaStream_t);
+
+StepPairLaunch step_pair_for(const StepParams<float>& a) {
+  const bool plain = a.scheme == RBM_SCHEME_EULER && !a.gbm && !a.renorm && a.noise_refine <= 1u;
+  if (!plain) return launch_step_pair<-1, false>;
+  switch (a.kf) {
+    case RBM_K_COULOMB: return launch_step_pair<RBM_K_COULOMB, true>;
+    case RBM_K_BOUNDED_CONF: return launch_step_pair<RBM_K_BOUNDED_CONF, true>;
+    case RBM_K_GAUSS_AGG: return launch_step_pair<RBM_K_GAUSS_AGG, true>;
+    case RBM_K_REG_ATTRACT: return launch_step_pair<RBM_K_REG_ATTRACT, true>;
+    case RBM_K_SMOOTH_TEST: return launch_step_pair<RBM_K_SMOOTH_TEST, true>;
+    case RBM_K_LINEAR: return launch_step_pair<RBM_K_LINEAR, true>;
+    default: return launch_step_pair<-1, true>;
+  }
+}
+
+}  // namespace
+
 cudaError_t prepare_rec_kernels() {
   const int bytes = static_cast<int>(step_smem(kSubCapMax, 1u << kMaxDigitBits));
-  cudaError_t e = cudaFuncSetAttribute(k_rec_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rec_step<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e = allow_step_smem<-1, false>(bytes);
+  if (e == cudaSuccess) e = allow_step_smem<-1, true>(bytes);
+  if (e == cudaSuccess) e = allow_step_smem<RBM_K_COULOMB, true>(bytes);
+  if (e == cudaSuccess) e = allow_step_smem<RBM_K_BOUNDED_CONF, true>(bytes);
+  if (e == cudaSuccess) e = allow_step_smem<RBM_K_GAUSS_AGG, true>(bytes);
+  if (e == cudaSuccess) e = allow_step_smem<RBM_K_REG_ATTRACT, true>(bytes);
+  if (e == cudaSuccess) e = allow_step_smem<RBM_K_SMOOTH_TEST, true>(bytes);
+  if (e == cudaSuccess) e = allow_step_smem<RBM_K_LINEAR, true>(bytes);
   // the split and scatter kernels stage 4096 records (80 KB) besides 16 KB of counters: two blocks per SM
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_rec_split, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kStageBytes));
@@ -766,6 +822,7 @@ cudaError_t launch_rec_run(const RecScratch& rs, const void* params, int64_t cou
   const int gpw = 32 / a0.p;
   const uint32_t fix_groups = 8u * static_cast<uint32_t>(gpw);
   const uint32_t fix_grid = (g.nbuckets + fix_groups - 1) / fix_groups;
+  const StepPairLaunch step_pair = step_pair_for(a0);
   for (int64_t k = 0; k < count; ++k) {
     StepParams<float> a = a0;
     a.m_off = a0.m_off + k;
@@ -774,17 +831,7 @@ cudaError_t launch_rec_run(const RecScratch& rs, const void* params, int64_t cou
     mark_launch(cfg, st, "k_rec_split");
     k_rec_scan<<<1, 1024, 0, st>>>(a, g);
     mark_launch(cfg, st, "k_rec_scan");
-    if (last) {
-      k_rec_step<true><<<g.nbuckets, kStepThreads, smem, st>>>(a, g);
-      mark_launch(cfg, st, "k_rec_step_last");
-      k_rec_fixup<true><<<fix_grid, 256, 0, st>>>(a, g);
-      mark_launch(cfg, st, "k_rec_fixup_last");
-    } else {
-      k_rec_step<false><<<g.nbuckets, kStepThreads, smem, st>>>(a, g);
-      mark_launch(cfg, st, "k_rec_step");
-      k_rec_fixup<false><<<fix_grid, 256, 0, st>>>(a, g);
-      mark_launch(cfg, st, "k_rec_fixup");
-    }
+    step_pair(last, a, g, smem, fix_grid, cfg, st);
   }
   return cudaGetLastError();
 }
