@@ -174,7 +174,7 @@ __device__ __forceinline__ void layer1_to_smem(const float* sW1, const float* sB
 // selects the surrogate; MODE 1 writes the surrogate force at query points.
 // ---------------------------------------------------------------------------
 template <int MODE, int D>
-__global__ void __launch_bounds__(128, 8) k_sur_infer(SurArgs s, StepParams<float> a, const float* qpts, uint32_t nq,
+__global__ void __launch_bounds__(128) k_sur_infer(SurArgs s, StepParams<float> a, const float* qpts, uint32_t nq,
                                                    float* fout) {
   using L = Lay<D>;
   __shared__ __align__(1024) unsigned char sA[128 * kH * 2];
@@ -245,22 +245,16 @@ __global__ void __launch_bounds__(128, 8) k_sur_infer(SurArgs s, StepParams<floa
       if (tid == 0) latch_status(s.status, RBM_ERR_TIMEOUT);
       break;
     }
+    float z[kH];
+    tc::tmem_ld64(tmem + ((static_cast<uint32_t>(warp) * 32u) << 16), z);
     float yo[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) yo[c] = sB3[c];
-    // layer 2 in four loads of 16 columns (fewer live registers, more
-    // resident blocks), the sum over o in the same order
 #pragma unroll
-    for (int q = 0; q < kH / 16; ++q) {
-      float z[16];
-      tc::tmem_ld16(tmem + ((static_cast<uint32_t>(warp) * 32u) << 16) + static_cast<uint32_t>(q * 16), z);
+    for (int o = 0; o < kH; ++o) {
+      const float h2 = act_tanh(z[o] + sB2[o]);
 #pragma unroll
-      for (int oo = 0; oo < 16; ++oo) {
-        const int o = q * 16 + oo;
-        const float h2 = act_tanh(z[oo] + sB2[o]);
-#pragma unroll
-        for (int c = 0; c < D; ++c) yo[c] = fmaf(sW3[c * kH + o], h2, yo[c]);
-      }
+      for (int c = 0; c < D; ++c) yo[c] = fmaf(sW3[c * kH + o], h2, yo[c]);
     }
     float fk[D];
 #pragma unroll
@@ -666,24 +660,11 @@ SurArgs make_args(const SurrogateScratch& ss, int32_t* status) {
 
 int surrogate_param_count(int d) { return d == 3 ? Lay<3>::NP : Lay<2>::NP; }
 
-// Resident blocks per SM of the inference kernel [MODE][D - 2] (registers
-// and shared memory decide; each block holds 64 tensor-memory columns, so at
-// most 8 fit the SM's 512), measured once by prepare_surrogate_kernels.
-static int g_infer_blocks_per_sm[2][2] = {{4, 4}, {4, 4}};
-
-template <int MODE, int D>
-cudaError_t measure_infer_residency() {
-  int b = 0;
-  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sur_infer<MODE, D>, 128, 0);
-  if (e == cudaSuccess) g_infer_blocks_per_sm[MODE][D - 2] = std::max(1, std::min(b, 8));
-  return e;
-}
-
-// A grid of resident blocks that loop over the 128-row tiles.
-template <int MODE, int D>
+// A grid of four 128-thread blocks per SM looping over the 128-row tiles
+// (measured: eight blocks per SM with the accumulators read in 16-column
+// pieces to fit 64 registers ran the step 2x slower).
 uint32_t infer_grid(uint32_t tiles, int num_sms) {
-  const uint32_t cap = static_cast<uint32_t>(num_sms) * static_cast<uint32_t>(g_infer_blocks_per_sm[MODE][D - 2]);
-  return std::max(1u, std::min(tiles, cap));
+  return std::max(1u, std::min(tiles, static_cast<uint32_t>(num_sms) * 4u));
 }
 
 cudaError_t prepare_surrogate_kernels() {
@@ -691,10 +672,6 @@ cudaError_t prepare_surrogate_kernels() {
       cudaFuncSetAttribute(k_sur_grad<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kGradSmem));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_sur_grad<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kGradSmem));
-  if (e == cudaSuccess) e = measure_infer_residency<0, 2>();
-  if (e == cudaSuccess) e = measure_infer_residency<0, 3>();
-  if (e == cudaSuccess) e = measure_infer_residency<1, 2>();
-  if (e == cudaSuccess) e = measure_infer_residency<1, 3>();
   return e;
 }
 
@@ -762,7 +739,7 @@ cudaError_t sur_forces(const SurrogateScratch& ss, int32_t* status, const float*
   StepParams<float> a{};
   a.status = status;
   const uint32_t tiles = (nq + 127) / 128;
-  SUR_BY_D((k_sur_infer<1, D><<<infer_grid<1, D>(tiles, cfg.num_sms), 128, 0, st>>>(make_args(ss, status), a, q, nq,
+  SUR_BY_D((k_sur_infer<1, D><<<infer_grid(tiles, cfg.num_sms), 128, 0, st>>>(make_args(ss, status), a, q, nq,
                                                                                      fout)));
   mark_launch(cfg, st, "k_sur_forces");
   return cudaGetLastError();
@@ -781,7 +758,7 @@ cudaError_t sur_drift(const SurrogateScratch& ss, int32_t* status, cudaStream_t 
 cudaError_t sur_step(const SurrogateScratch& ss, const void* params, const LaunchCfg& cfg, cudaStream_t st) {
   const StepParams<float>& a = *static_cast<const StepParams<float>*>(params);
   const uint32_t tiles = (a.n + 127) / 128;
-  SUR_BY_D((k_sur_infer<0, D><<<infer_grid<0, D>(tiles, cfg.num_sms), 128, 0, st>>>(make_args(ss, a.status), a,
+  SUR_BY_D((k_sur_infer<0, D><<<infer_grid(tiles, cfg.num_sms), 128, 0, st>>>(make_args(ss, a.status), a,
                                                                                      nullptr, 0u, nullptr)));
   mark_launch(cfg, st, "k_sur_step");
   return cudaGetLastError();
