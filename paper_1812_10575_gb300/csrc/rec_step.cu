@@ -52,15 +52,22 @@ constexpr int kStepPer = kSubCapMax / kStepThreads;  // records per thread of k_
 constexpr int kSplitThreads = 512;
 constexpr int kSplitPer = 8;            // records per thread of k_rec_scatter
 constexpr uint32_t kChunk = kSplitThreads * kSplitPer;
-constexpr int kSubThreads = 512;        // k_rec_split: 512 threads of 8 records (measured: 256 threads at
-constexpr int kSubPer = 8;              // six blocks per SM, rows loaded late, ran 30 % slower)
+constexpr int kSubThreads = 512;        // k_rec_split: 512 threads of 6 records, three blocks per SM
+constexpr int kSubPer = 6;
 constexpr uint32_t kSubChunk = kSubThreads * kSubPer;
 constexpr int kFineBits = 11;           // counting-sort digit inside a sub-bucket
 constexpr uint32_t kFine = 1u << kFineBits;
 constexpr int kMaxDigitBits = 11;       // top and sub digits: at most 2048 values
 constexpr int kSide = 32;               // parked members per sub-bucket (p <= 32)
-static_assert(kChunk == kSubChunk, "the scatter and split kernels share one staging size");
-constexpr size_t kStageBytes = kChunk * (sizeof(float4) + sizeof(uint32_t) + sizeof(uint8_t));  // staged records
+constexpr size_t kStageBytes = kChunk * (sizeof(float4) + sizeof(uint32_t) + sizeof(uint8_t));  // scatter staging
+
+// Dynamic shared memory of k_rec_split: the chunk's records in arrival order
+// (rows, keys), the arrival index of each grouped position, and the
+// sub-bucket counters and run starts.
+size_t split_smem(uint32_t nsub) {
+  return static_cast<size_t>(kSubChunk) * (sizeof(float4) + sizeof(uint32_t) + sizeof(uint16_t)) +
+         2 * static_cast<size_t>(nsub) * sizeof(uint32_t);
+}
 
 struct RecArgs {
   float4* top_rows;     // [ntop * top_cap]
@@ -250,14 +257,18 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_rec_scatter(StepParams<flo
 
 // ---------------------------------------------------------------------------
 // Top level -> sub level: block (t, j) takes records [j C, (j+1) C) of top
-// bucket t (C = kSubChunk).
+// bucket t (C = kSubChunk).  The rows go straight into shared memory in
+// arrival order (cp.async) while the keys are counted; each grouped position
+// then names the arrival index it holds, and the runs are stored by
+// consecutive threads.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSubThreads, 2) k_rec_split(StepParams<float> a, RecArgs g, uint32_t chunks) {
+__global__ void __launch_bounds__(kSubThreads, 3) k_rec_split(StepParams<float> a, RecArgs g, uint32_t chunks) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4* s_rows = reinterpret_cast<float4*>(smem_raw);                // [kSubChunk] records by sub-bucket
-  uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_rows + kSubChunk);  // [kSubChunk] (their sub digit: the bucket)
-  __shared__ uint32_t s_hist[1u << kMaxDigitBits];  // counts, then local starts
-  __shared__ uint32_t s_base[1u << kMaxDigitBits];
+  float4* s_rows = reinterpret_cast<float4*>(smem_raw);                 // [kSubChunk] arrival order
+  uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_rows + kSubChunk);   // [kSubChunk] arrival order
+  uint16_t* s_inv = reinterpret_cast<uint16_t*>(s_keys + kSubChunk);    // [kSubChunk] arrival index by position
+  uint32_t* s_hist = reinterpret_cast<uint32_t*>(s_inv + kSubChunk);    // [nsub] counts, then local starts
+  uint32_t* s_base = s_hist + g.nsub;                                    // [nsub] run starts (shifted)
   __shared__ uint32_t s_warp[32];
   const uint32_t m32 = step_index(a);
   const uint32_t par = m32 & 1u;
@@ -268,24 +279,22 @@ __global__ void __launch_bounds__(kSubThreads, 2) k_rec_split(StepParams<float> 
   const uint32_t lo = j * kSubChunk;
   if (lo >= count) return;  // uniform over the block
   const uint32_t nrec = min(kSubChunk, count - lo);
+  const size_t src0 = static_cast<size_t>(t) * g.top_cap + lo;
+  for (uint32_t e = threadIdx.x; e < nrec; e += blockDim.x) {
+    const uint32_t sa = static_cast<uint32_t>(__cvta_generic_to_shared(s_rows + e));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(g.top_rows + src0 + e) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
   for (uint32_t u = threadIdx.x; u < g.nsub; u += blockDim.x) s_hist[u] = 0;
   __syncthreads();
-  const size_t src0 = static_cast<size_t>(t) * g.top_cap + lo;
-  uint32_t ur[kSubPer], k32[kSubPer];
-  float4 v[kSubPer];  // every record in flight before the first store
+  uint32_t ur[kSubPer];
 #pragma unroll
   for (int k = 0; k < kSubPer; ++k) {
     const uint32_t e = k * kSubThreads + threadIdx.x;
     if (e < nrec) {
-      k32[k] = g.top_keys[src0 + e];
-      v[k] = g.top_rows[src0 + e];
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < kSubPer; ++k) {
-    const uint32_t e = k * kSubThreads + threadIdx.x;
-    if (e < nrec) {
-      const uint32_t u = sub_of(k32[k], g.sub_bits);
+      const uint32_t kk = g.top_keys[src0 + e];
+      s_keys[e] = kk;
+      const uint32_t u = sub_of(kk, g.sub_bits);
       ur[k] = u | (atomicAdd(&s_hist[u], 1u) << 16);
     }
   }
@@ -298,21 +307,19 @@ __global__ void __launch_bounds__(kSubThreads, 2) k_rec_split(StepParams<float> 
 #pragma unroll
   for (int k = 0; k < kSubPer; ++k) {
     const uint32_t e = k * kSubThreads + threadIdx.x;
-    if (e < nrec) {
-      const uint32_t at = s_hist[ur[k] & 0xffffu] + (ur[k] >> 16);
-      s_rows[at] = v[k];
-      s_keys[at] = k32[k];
-    }
+    if (e < nrec) s_inv[s_hist[ur[k] & 0xffffu] + (ur[k] >> 16)] = static_cast<uint16_t>(e);
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
   // runs out, the sub-bucket of each position read off its key
   for (uint32_t jj = threadIdx.x; jj < nrec; jj += blockDim.x) {
-    const uint32_t kk = s_keys[jj];
+    const uint32_t e = s_inv[jj];
+    const uint32_t kk = s_keys[e];
     const uint32_t u = sub_of(kk, g.sub_bits);
     const uint32_t pos = s_base[u] + jj;
     if (pos < g.sub_cap) {
       const size_t at = static_cast<size_t>(t * g.nsub + u) * g.sub_cap + pos;
-      g.sub_rows[at] = s_rows[jj];
+      g.sub_rows[at] = s_rows[e];
       g.sub_keys[at] = kk;
     } else {
       latch_status(a.status, RBM_ERR_STATE);
@@ -789,9 +796,11 @@ cudaError_t prepare_rec_kernels() {
   if (e == cudaSuccess) e = allow_step_smem<RBM_K_REG_ATTRACT, true>(bytes);
   if (e == cudaSuccess) e = allow_step_smem<RBM_K_SMOOTH_TEST, true>(bytes);
   if (e == cudaSuccess) e = allow_step_smem<RBM_K_LINEAR, true>(bytes);
-  // the split and scatter kernels stage 4096 records (80 KB) besides 16 KB of counters: two blocks per SM
+  // the scatter stages 4096 records (84 KB) besides 16 KB of counters (two blocks per SM), the split 3072
+  // records (66 KB) besides its counters (three blocks per SM)
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_rec_split, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kStageBytes));
+    e = cudaFuncSetAttribute(k_rec_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(split_smem(1u << kMaxDigitBits)));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_rec_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kStageBytes));
@@ -827,7 +836,7 @@ cudaError_t launch_rec_run(const RecScratch& rs, const void* params, int64_t cou
     StepParams<float> a = a0;
     a.m_off = a0.m_off + k;
     const bool last = (k + 1 == count);
-    k_rec_split<<<rs.ntop * chunks, kSubThreads, kStageBytes, st>>>(a, g, chunks);
+    k_rec_split<<<rs.ntop * chunks, kSubThreads, split_smem(rs.nsub), st>>>(a, g, chunks);
     mark_launch(cfg, st, "k_rec_split");
     k_rec_scan<<<1, 1024, 0, st>>>(a, g);
     mark_launch(cfg, st, "k_rec_scan");
