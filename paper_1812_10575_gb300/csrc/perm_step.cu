@@ -206,7 +206,7 @@ __device__ void sub_exclusive_scan(uint32_t* a, uint32_t* s_warp) {
   if (lane == 31) s_warp[warp] = incl;
   __syncthreads();
   uint32_t run = incl - sum;
-  for (int w = 0; w < warp; ++w) run += s_warp[w];
+  run += warps_before(s_warp, warp, lane);
 #pragma unroll
   for (uint32_t i = 0; i < per; ++i) {
     a[lo + i] = run;

@@ -377,6 +377,15 @@ __device__ __forceinline__ uint32_t step_index(const StepParams<T>& a) {
   return static_cast<uint32_t>(static_cast<uint64_t>(m));
 }
 
+// Sum of s_warp[0 .. warp): the totals of the warps before the calling one
+// in a block scan, added by the warp's lanes at once.
+__device__ __forceinline__ uint32_t warps_before(const uint32_t* s_warp, int warp, int lane) {
+  uint32_t v = (lane < warp) ? s_warp[lane] : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __device__ __forceinline__ void latch_status(int32_t* status, int32_t code) {
   if (status) atomicCAS(status, 0, code);
 }

@@ -149,7 +149,7 @@ __device__ __forceinline__ void scan_excl_512(uint32_t* s, uint32_t len, uint32_
   if (lane == 31) s_warp[warp] = incl;
   __syncthreads();
   uint32_t run = incl - sum;
-  for (int w = 0; w < warp; ++w) run += s_warp[w];
+  run += warps_before(s_warp, warp, lane);
 #pragma unroll
   for (uint32_t i = 0; i < per; ++i) {
     if (lo + i < len) s[lo + i] = run;
@@ -400,11 +400,24 @@ __device__ __forceinline__ uint32_t sub_bucket_at(const uint32_t* start, uint32_
   return lo;
 }
 
-// (key, id) order of two records of one sub-bucket whose carried bits below
-// the sub digit are equal: the full keys, then the ids.
-__device__ __forceinline__ bool rec_key_less(const StepParams<float>& a, uint32_t m32, uint32_t ida, uint32_t idb) {
-  const uint64_t ka = perm_key(ida, m32, a.replica, a.keys), kb = perm_key(idb, m32, a.replica, a.keys);
-  return ka < kb || (ka == kb && ida < idb);
+// Records of positions [lo, hi) other than pp whose carried bits equal fe
+// and that come before record e in (key, id) order: the full keys are drawn
+// again.  Two records of a sub-bucket share all their carried bits about once
+// in eight sub-buckets, so the caller counts equal bits in its loop and calls
+// this only then.
+__device__ __forceinline__ uint32_t rec_rank_ties(const StepParams<float>& a, uint32_t m32, const float4* srow,
+                                               const uint32_t* sfine, const uint16_t* sidx, uint32_t lo, uint32_t hi,
+                                               uint32_t pp, uint32_t fe, uint32_t e) {
+  const uint32_t ide = rec_id(srow[e]);
+  const uint64_t ke = perm_key(ide, m32, a.replica, a.keys);
+  uint32_t before = 0;
+  for (uint32_t j = lo; j < hi; ++j) {
+    if (j == pp || sfine[j] != fe) continue;
+    const uint32_t idj = rec_id(srow[sidx[j]]);
+    const uint64_t kj = perm_key(idj, m32, a.replica, a.keys);
+    if (kj < ke || (kj == ke && idj < ide)) ++before;
+  }
+  return before;
 }
 
 // ---------------------------------------------------------------------------
@@ -472,7 +485,7 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
     if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
     uint32_t run = incl - sum;
-    for (int w = 0; w < warp; ++w) run += s_warp[w];
+    run += warps_before(s_warp, warp, lane);
 #pragma unroll
     for (uint32_t i = 0; i < per; ++i) {
       s_hist[lo + i] = run;
@@ -506,16 +519,15 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
     const uint32_t lo = s_hist[d], hi = (d + 1 < kFine) ? s_hist[d + 1] : cnt;
     uint32_t rank = 0;
     if (hi - lo > 1) {
-      const uint32_t fe = sfine[fr[k] & 0xffffu];
+      const uint32_t pp = fr[k] & 0xffffu;
+      const uint32_t fe = sfine[pp];
+      uint32_t equal = 0;  // records with the same carried bits, itself included
       for (uint32_t j = lo; j < hi; ++j) {
         const uint32_t fj = sfine[j];
-        if (fj < fe) {
-          ++rank;
-        } else if (fj == fe) {
-          const uint16_t sj = sidx[j];
-          if (sj != e && rec_key_less(a, m32, rec_id(srow[sj]), rec_id(srow[e]))) ++rank;
-        }
+        rank += (fj < fe) ? 1u : 0u;
+        equal += (fj == fe) ? 1u : 0u;
       }
+      if (equal > 1) rank += rec_rank_ties(a, m32, srow, sfine, sidx, lo, hi, pp, fe, e);
     }
     fr[k] = lo + rank;
   }

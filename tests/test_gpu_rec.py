@@ -7,6 +7,9 @@ written back by id after the call's last step.
   arithmetic on the same rows in the same order), for p from 2 to 32, sizes
   that leave a ragged last batch, bucket geometries down to sub-buckets of a
   few records (batches crossing many of them), graph replays and eager runs;
+  at N = 2^20 + 3 keys that agree in all the bits a sub-bucket sorts on (the
+  top 37 of 64) occur about four times per step, so the full-key order of
+  such ties is exercised as well;
 - rbm_step_profiled (two steps, each kernel timed) equals two steps of a
   run, and a step launches four kernels;
 - against the oracle: every particle within the FP32 bar after one step, and
@@ -51,7 +54,8 @@ def _run(torch, X, path, steps, p, seed=3, graph_steps=0, bucket_bits=0, **kw):
 
 @pytest.mark.parametrize("n,p,bits", [(5000, 2, 0), (5001, 3, 0), (100000, 2, 0), (100003, 7, 0),
                                       (70001, 32, 0), (5003, 5, 10), (4099, 32, 9), (20000, 2, 12),
-                                      (300007, 2, 13), (100003, 7, 14), (70001, 32, 16)])
+                                      (300007, 2, 13), (100003, 7, 14), (70001, 32, 16),
+                                      (1048579, 3, 0)])
 def test_record_path_run_equals_per_id_path_bitwise(n, p, bits):
     torch = torch_cuda()
     X = as_run_precision(workloads.gaussian(n, 3, seed=2), "f32")
