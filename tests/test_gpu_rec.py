@@ -14,6 +14,8 @@ written back by id after the call's last step.
   run, and a step launches four kernels;
 - against the oracle: every particle within the FP32 bar after one step, and
   after a 5-step run within a bound that adds the per-step bars;
+- every kernel family's step instance (the family fixed at compile time on
+  the plain Euler-Maruyama configuration) equals the per-id path bit for bit;
 - the pad lane of every row is left as the caller wrote it;
 - the full-size large-N system (N = 2^26, the benchmarked launch
   configuration): one step of every particle within the FP32 bar of the
@@ -107,6 +109,19 @@ def test_record_path_schemes_equal_per_id_path(kw):
     X = as_run_precision(X0, "f32")
     assert np.array_equal(_run(torch, X, 4, 5, 2, **kw).view(np.uint32),
                           _run(torch, X, 1, 5, 2, **kw).view(np.uint32))
+
+
+@pytest.mark.parametrize("k,k_param", [("coulomb", 0.0), ("bounded_conf", 0.5), ("gauss_agg", 0.0),
+                                       ("smooth_test", 0.0), ("linear", 0.7), ("reg_attract", 0.01)])
+def test_record_path_every_kernel_family_equals_per_id_path(k, k_param):
+    """The step kernels instantiated per kernel family (plain Euler-Maruyama
+    configuration) give the per-id path's bits for every family."""
+    torch = torch_cuda()
+    n = 30011
+    X = as_run_precision(workloads.gaussian(n, 3, seed=3), "f32")
+    kw = dict(k=k, k_param=k_param, sigma=0.3)
+    assert np.array_equal(_run(torch, X, 4, 4, 3, **kw).view(np.uint32),
+                          _run(torch, X, 1, 4, 3, **kw).view(np.uint32))
 
 
 def _fp32_bound(prm, X, FK, m):
