@@ -129,14 +129,28 @@ __device__ __forceinline__ void put_top(const StepParams<float>& a, const RecArg
   }
 }
 
-// Exclusive prefix sum of s[0, len) in place (len <= 2048, 512 threads).
-__device__ __forceinline__ void scan_excl_512(uint32_t* s, uint32_t len, uint32_t* s_warp) {
-  constexpr uint32_t per = 4;
+// The buckets [0, len) counted in s_hist (len <= 2048, 512 threads): reserves
+// the run of every non-empty bucket u in the global counter fill[u] (one
+// atomic per bucket; consecutive threads on consecutive counters, so that a
+// warp's atomics fall in one line, and issued before the scan so that their
+// latency overlaps it), turns s_hist into the local starts (exclusive prefix
+// sum) and sets s_base[u] = run start - local start, so that local position
+// j of bucket u lands at s_base[u] + j.  Ends with a barrier.
+__device__ __forceinline__ void reserve_runs_512(uint32_t* s_hist, uint32_t len, uint32_t* s_warp, uint32_t* s_base,
+                                                 uint32_t* fill) {
+  constexpr uint32_t per = 4;  // len <= per * 512
+  uint32_t r[per];
+#pragma unroll
+  for (uint32_t i = 0; i < per; ++i) {
+    const uint32_t u = threadIdx.x + i * 512u;
+    const uint32_t c = (u < len) ? s_hist[u] : 0u;
+    r[i] = c ? atomicAdd(&fill[u], c) : 0u;
+  }
   const uint32_t lo = threadIdx.x * per;
   uint32_t v[per], sum = 0;
 #pragma unroll
   for (uint32_t i = 0; i < per; ++i) {
-    v[i] = (lo + i < len) ? s[lo + i] : 0u;
+    v[i] = (lo + i < len) ? s_hist[lo + i] : 0u;
     sum += v[i];
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -147,12 +161,20 @@ __device__ __forceinline__ void scan_excl_512(uint32_t* s, uint32_t len, uint32_
     if (lane >= o) incl += t;
   }
   if (lane == 31) s_warp[warp] = incl;
+#pragma unroll
+  for (uint32_t i = 0; i < per; ++i) {
+    const uint32_t u = threadIdx.x + i * 512u;
+    if (u < len) s_base[u] = r[i];
+  }
   __syncthreads();
   uint32_t run = incl - sum;
   run += warps_before(s_warp, warp, lane);
 #pragma unroll
   for (uint32_t i = 0; i < per; ++i) {
-    if (lo + i < len) s[lo + i] = run;
+    if (lo + i < len) {
+      s_hist[lo + i] = run;
+      s_base[lo + i] -= run;
+    }
     run += v[i];
   }
   __syncthreads();
@@ -188,11 +210,6 @@ __device__ __forceinline__ void store_runs(uint32_t nrec, uint32_t nbkt, const u
   }
 }
 
-// s_base[u] -= s_start[u] for the buckets that received records (run by the
-// block between the local scan and the barrier before store_runs).
-__device__ __forceinline__ void shift_bases(uint32_t* s_base, const uint32_t* s_start, uint32_t nbkt) {
-  for (uint32_t u = threadIdx.x; u < nbkt; u += blockDim.x) s_base[u] -= s_start[u];
-}
 
 // ---------------------------------------------------------------------------
 // First step of a run: the caller's rows in id order into the top level.
@@ -232,11 +249,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_rec_scatter(StepParams<flo
     if (e < nrec) v[k] = reinterpret_cast<const float4*>(a.x)[i0 + e];
   }
   __syncthreads();
-  for (uint32_t u = threadIdx.x; u < g.ntop; u += blockDim.x)
-    if (s_hist[u]) s_base[u] = atomicAdd(&g.top_fill[par * g.ntop + u], s_hist[u]);
-  __syncthreads();
-  scan_excl_512(s_hist, g.ntop, s_warp);
-  shift_bases(s_base, s_hist, g.ntop);
+  reserve_runs_512(s_hist, g.ntop, s_warp, s_base, g.top_fill + par * g.ntop);
 #pragma unroll
   for (int k = 0; k < kSplitPer; ++k) {
     const uint32_t e = k * kSplitThreads + threadIdx.x;
@@ -299,11 +312,7 @@ __global__ void __launch_bounds__(kSubThreads, 3) k_rec_split(StepParams<float> 
     }
   }
   __syncthreads();
-  for (uint32_t u = threadIdx.x; u < g.nsub; u += blockDim.x)
-    if (s_hist[u]) s_base[u] = atomicAdd(&g.sub_fill[par * g.nbuckets + t * g.nsub + u], s_hist[u]);
-  __syncthreads();
-  scan_excl_512(s_hist, g.nsub, s_warp);
-  shift_bases(s_base, s_hist, g.nsub);
+  reserve_runs_512(s_hist, g.nsub, s_warp, s_base, g.sub_fill + par * g.nbuckets + t * g.nsub);
 #pragma unroll
   for (int k = 0; k < kSubPer; ++k) {
     const uint32_t e = k * kSubThreads + threadIdx.x;
@@ -538,6 +547,10 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
     if (e >= cnt) break;
     sidx[fr[k]] = static_cast<uint16_t>(e);
   }
+  // the digit starts are no longer read: clear the counters of the next
+  // step's top-level buckets here, not behind a barrier of their own
+  if (!kLast)
+    for (uint32_t u = threadIdx.x; u < g.ntop; u += blockDim.x) s_hist[u] = 0;
   __syncthreads();
 
   // batches lying wholly inside [start, end)
@@ -595,10 +608,9 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
   if (kLast) return;
   __syncthreads();
 
-  // the moved records to their top-level buckets of step m + 1
+  // the moved records to their top-level buckets of step m + 1 (s_hist was
+  // cleared before the batches were stepped)
   const uint32_t np = par ^ 1u;
-  for (uint32_t u = threadIdx.x; u < g.ntop; u += blockDim.x) s_hist[u] = 0;
-  __syncthreads();
   constexpr uint32_t kParked = 0xffffffffu;
   uint32_t tr[kStepPer], k32[kStepPer];
 #pragma unroll
@@ -613,11 +625,7 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
     }
   }
   __syncthreads();
-  for (uint32_t u = threadIdx.x; u < g.ntop; u += blockDim.x)
-    if (s_hist[u]) s_base[u] = atomicAdd(&g.top_fill[np * g.ntop + u], s_hist[u]);
-  __syncthreads();
-  scan_excl_512(s_hist, g.ntop, s_warp);  // local start of each bucket's run
-  shift_bases(s_base, s_hist, g.ntop);
+  reserve_runs_512(s_hist, g.ntop, s_warp, s_base, g.top_fill + np * g.ntop);  // local start of each bucket's run
   // the records in bucket order: sidx[j] the slot at position j, spark[j]
   // (read for the last time in the loop above) its bucket
 #pragma unroll
