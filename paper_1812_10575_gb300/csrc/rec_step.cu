@@ -59,6 +59,7 @@ constexpr int kFineBits = 11;           // counting-sort digit inside a sub-buck
 constexpr uint32_t kFine = 1u << kFineBits;
 constexpr int kMaxDigitBits = 11;       // top and sub digits: at most 2048 values
 constexpr int kSide = 32;               // parked members per sub-bucket (p <= 32)
+constexpr uint32_t kPrefetchAhead = 456; // k_rec_step blocks resident at once (152 SMs x 3)
 constexpr size_t kStageBytes = kChunk * (sizeof(float4) + sizeof(uint32_t) + sizeof(uint8_t));  // scatter staging
 
 // Dynamic shared memory of k_rec_split: the chunk's records in arrival order
@@ -454,6 +455,18 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
   const uint32_t cnt = min(filled, g.sub_cap);
   const uint32_t start = g.sub_start[b];
   const size_t src0 = static_cast<size_t>(b) * g.sub_cap;
+  if (threadIdx.x == 0) {  // the sub-bucket a block starting about one wave later takes, into L2
+    const uint32_t bn = b + kPrefetchAhead;
+    if (bn < g.nbuckets) {
+      const uint32_t cn = min(g.sub_fill[par * g.nbuckets + bn], g.sub_cap);
+      if (cn > 0) {
+        const size_t at = static_cast<size_t>(bn) * g.sub_cap;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g.sub_rows + at), "r"(cn * 16u) : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g.sub_keys + at),
+                     "r"(((cn + 3u) & ~3u) * 4u) : "memory");
+      }
+    }
+  }
 
   for (uint32_t u = threadIdx.x; u < kFine; u += blockDim.x) s_hist[u] = 0;
   for (uint32_t e = threadIdx.x; e < cnt; e += blockDim.x) {
