@@ -137,7 +137,10 @@ constexpr int batched_min_blocks() {
   return (sizeof(T) == 4 && D <= 2) ? 2 : 1;
 }
 
-template <typename T, int D, int MODE>
+// KF >= 0: the kernel family fixed at compile time for the plain
+// configuration (kPlain: Euler-Maruyama, additive noise, no projection, no
+// noise refinement); the same arithmetic as the run-time form.
+template <typename T, int D, int MODE, int KF = -1, bool kPlain = false>
 __global__ void __launch_bounds__(1024, batched_min_blocks<T, D>()) k_rbm_batched(BatchedArgs ba, StepParams<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t* a_key = reinterpret_cast<uint64_t*>(smem_raw);  // [kBCap]
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(1024, batched_min_blocks<T, D>()) k_rbm_batche
       // the whole replica is one bucket: sort the ids directly, step every batch
       sort_bucket(nullptr, n, 1u, m32, r, a.keys, a_key, b_key, a_id, b_id, a_sub, s_sub, s_warp);
       for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) perm[j] = b_id[j];
-      if (MODE != kModePerm) step_batches<T, D, MODE>(ar, m32, b_id, 0u, 0u, (n + up - 1) / up);
+      if (MODE != kModePerm) step_batches<T, D, MODE, KF, kPlain>(ar, m32, b_id, 0u, 0u, (n + up - 1) / up);
       __syncthreads();
       continue;
     }
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(1024, batched_min_blocks<T, D>()) k_rbm_batche
           const uint32_t end = s + nb;
           const uint32_t q0 = (s + up - 1) / up;
           const uint32_t q_end = (end == n) ? (n + up - 1) / up : end / up;
-          step_batches<T, D, MODE>(ar, m32, b_id, s, q0, (q_end > q0) ? q_end - q0 : 0u);
+          step_batches<T, D, MODE, KF, kPlain>(ar, m32, b_id, s, q0, (q_end > q0) ? q_end - q0 : 0u);
         }
       } else {
         // a bucket beyond the shared-memory sort (general mode): rank by counting
@@ -240,7 +243,7 @@ __global__ void __launch_bounds__(1024, batched_min_blocks<T, D>()) k_rbm_batche
     //    the general mode; members read from the permutation just written
     if (MODE != kModePerm) {
       if (general) {
-        step_batches<T, D, MODE>(ar, m32, perm, 0u, 0u, (n + up - 1) / up);
+        step_batches<T, D, MODE, KF, kPlain>(ar, m32, perm, 0u, 0u, (n + up - 1) / up);
       } else {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         const int gpw = 32 / a.p, nwarps = blockDim.x >> 5;
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(1024, batched_min_blocks<T, D>()) k_rbm_batche
               if (valid) id = perm[lo + lg];
             }
           }
-          batch_group<T, D, MODE>(ar, m32, id, valid, lg, bs);
+          batch_group<T, D, MODE, KF, kPlain>(ar, m32, id, valid, lg, bs);
         }
       }
     }
@@ -284,8 +287,54 @@ cudaError_t launch_batched_k(const BatchedScratch& bs, const StepParams<T>& a, c
   ba.perm = bs.perm;
   ba.bucket_target = static_cast<uint32_t>(bs.bucket_target);
   ba.rep_base = bs.rep_base;
-  k_rbm_batched<T, D, MODE><<<bs.grid, bs.threads, batched_smem<T, D>(), st>>>(ba, a);
+  const size_t smem = batched_smem<T, D>();
+  if constexpr (sizeof(T) == 4 && MODE == kModeStep) {
+    // FP32 steps of the plain configuration take the kernel family's own instance
+    if (a.scheme == RBM_SCHEME_EULER && !a.gbm && !a.renorm && a.noise_refine <= 1u) {
+      switch (a.kf) {
+#define RBM_BATCHED_KF(kf) \
+  case kf:                 \
+    k_rbm_batched<T, D, kModeStep, kf, true><<<bs.grid, bs.threads, smem, st>>>(ba, a); \
+    return cudaGetLastError();
+        RBM_BATCHED_KF(RBM_K_INV1D)
+        RBM_BATCHED_KF(RBM_K_COULOMB)
+        RBM_BATCHED_KF(RBM_K_BOUNDED_CONF)
+        RBM_BATCHED_KF(RBM_K_GAUSS_AGG)
+        RBM_BATCHED_KF(RBM_K_REG_ATTRACT)
+        RBM_BATCHED_KF(RBM_K_SMOOTH_TEST)
+        RBM_BATCHED_KF(RBM_K_LINEAR)
+#undef RBM_BATCHED_KF
+        default: break;
+      }
+    }
+  }
+  k_rbm_batched<T, D, MODE><<<bs.grid, bs.threads, smem, st>>>(ba, a);
   return cudaGetLastError();
+}
+
+// The dynamic shared-memory allowance of the FP32 step instances of the
+// plain configuration.
+template <typename T, int D, int KF>
+cudaError_t allow_plain_kf(int smem) {
+  return cudaFuncSetAttribute(k_rbm_batched<T, D, kModeStep, KF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem);
+}
+
+template <typename T, int D>
+cudaError_t allow_plain_smem(int smem) {
+  if constexpr (sizeof(T) != 4) {
+    (void)smem;
+    return cudaSuccess;
+  } else {
+    cudaError_t e = allow_plain_kf<T, D, RBM_K_INV1D>(smem);
+    if (e == cudaSuccess) e = allow_plain_kf<T, D, RBM_K_COULOMB>(smem);
+    if (e == cudaSuccess) e = allow_plain_kf<T, D, RBM_K_BOUNDED_CONF>(smem);
+    if (e == cudaSuccess) e = allow_plain_kf<T, D, RBM_K_GAUSS_AGG>(smem);
+    if (e == cudaSuccess) e = allow_plain_kf<T, D, RBM_K_REG_ATTRACT>(smem);
+    if (e == cudaSuccess) e = allow_plain_kf<T, D, RBM_K_SMOOTH_TEST>(smem);
+    if (e == cudaSuccess) e = allow_plain_kf<T, D, RBM_K_LINEAR>(smem);
+    return e;
+  }
 }
 
 template <typename T, int D>
@@ -296,6 +345,7 @@ cudaError_t prepare_batched_d(int threads, int* blocks_per_sm) {
     e = cudaFuncSetAttribute(k_rbm_batched<T, D, kModeStep>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_rbm_batched<T, D, kModeForces>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = allow_plain_smem<T, D>(smem);
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_rbm_batched<T, D, kModeStep>, threads, smem);
   return e;

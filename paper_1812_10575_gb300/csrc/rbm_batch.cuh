@@ -121,7 +121,7 @@ __device__ __forceinline__ bool batch_group_update(const StepParams<T>& a, uint3
   return true;
 }
 
-template <typename T, int D, int MODE>
+template <typename T, int D, int MODE, int KF = -1, bool kPlain = false>
 __device__ __forceinline__ void batch_group_row(const StepParams<T>& a, uint32_t m32, uint32_t id, bool valid, int lg,
                                                 int bs, Row<T, D> r) {
   if (!valid) {
@@ -130,12 +130,12 @@ __device__ __forceinline__ void batch_group_row(const StepParams<T>& a, uint32_t
     r.pad = T(0);
   }
   if (MODE == kModeStep) {
-    if (batch_group_update<T, D>(a, m32, id, valid, lg, bs, r)) store_row<T, D>(a.x, id, r);
+    if (batch_group_update<T, D, KF, kPlain>(a, m32, id, valid, lg, bs, r)) store_row<T, D>(a.x, id, r);
     return;
   }
   const int lane = threadIdx.x & 31;
   T fk[D];
-  batch_force<T, D>(a, valid, lg, bs, lane - lg, r, fk);
+  batch_force<T, D, KF>(a, valid, lg, bs, lane - lg, r, fk);
   if (!valid) return;
   Row<T, D> f;
 #pragma unroll
@@ -145,17 +145,17 @@ __device__ __forceinline__ void batch_group_row(const StepParams<T>& a, uint32_t
 }
 
 // As batch_group_row, with the row loaded from the position array.
-template <typename T, int D, int MODE>
+template <typename T, int D, int MODE, int KF = -1, bool kPlain = false>
 __device__ __forceinline__ void batch_group(const StepParams<T>& a, uint32_t m32, uint32_t id, bool valid, int lg,
                                             int bs) {
   Row<T, D> r{};
   if (valid) r = load_row<T, D>(a.x, id);
-  batch_group_row<T, D, MODE>(a, m32, id, valid, lg, bs, r);
+  batch_group_row<T, D, MODE, KF, kPlain>(a, m32, id, valid, lg, bs, r);
 }
 
 // Steps the batches whose first sorted position is q0 + k (k < count), ids
 // read from `ids` at offset (batch start - ids_base).  Warp-uniform loop.
-template <typename T, int D, int MODE>
+template <typename T, int D, int MODE, int KF = -1, bool kPlain = false>
 __device__ __forceinline__ void step_batches(const StepParams<T>& a, uint32_t m32, const uint32_t* ids, uint32_t ids_base,
                              uint32_t q0, uint32_t count) {
   const int p = a.p;
@@ -177,7 +177,7 @@ __device__ __forceinline__ void step_batches(const StepParams<T>& a, uint32_t m3
       valid = lg < bs;
       if (valid) id = ids[lo + lg - ids_base];
     }
-    batch_group<T, D, MODE>(a, m32, id, valid, lg, bs);
+    batch_group<T, D, MODE, KF, kPlain>(a, m32, id, valid, lg, bs);
   }
 }
 
