@@ -13,7 +13,8 @@
 // synchronisation only:
 //   1. a shared-memory histogram of B_r = ceil(N_r / target) buckets
 //      (monotone in the key; keys are regenerated from Philox wherever they
-//      are needed, never stored);
+//      are needed, never stored; each particle's bucket is kept as 16 bits
+//      in id order for the scatter);
 //   2. scan, scatter of ids to bucket order;
 //   3. per bucket: counting sort in shared memory by the next 11 key bits and
 //      insertion sort of equal sub-buckets by (key, id); the sorted ids form
@@ -37,6 +38,7 @@ constexpr uint32_t kBSubBits = 11;
 constexpr uint32_t kBSub = 1u << kBSubBits;
 constexpr uint32_t kBCap = 2048;       // largest bucket sorted in shared memory
 constexpr uint32_t kBMaxBuckets = 512;  // per replica
+static_assert(kBMaxBuckets <= 65536, "bucket indices are kept as 16 bits");
 
 struct BatchedArgs {
   const uint32_t* order;        // replica ids, block-major
@@ -44,6 +46,7 @@ struct BatchedArgs {
   const uint64_t* offs;         // [R + 1] first row of each replica
   uint32_t* tmp;                // [rows] ids grouped by bucket
   uint32_t* perm;               // [rows] permutation (replica-local ids)
+  uint16_t* bkt;                // [rows] bucket of each particle (histogram pass -> scatter pass)
   uint32_t bucket_target;       // mean members per bucket
   uint32_t rep_base;            // replica index in the counters = list index + rep_base
 };
@@ -186,11 +189,16 @@ __global__ void __launch_bounds__(1024, batched_min_blocks<T, D>()) k_rbm_batche
       continue;
     }
 
-    // 1. bucket histogram (keys regenerated, never stored)
+    // 1. bucket histogram (keys regenerated, never stored; each particle's
+    //    bucket kept in global scratch, in id order, for the scatter)
+    uint16_t* bkt = ba.bkt + off;
     for (uint32_t b = threadIdx.x; b <= B; b += blockDim.x) s_hist[b] = 0;
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
-      atomicAdd(&s_hist[static_cast<uint32_t>(__umul64hi(perm_key(i, m32, r, a.keys), B))], 1u);
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint32_t b = static_cast<uint32_t>(__umul64hi(perm_key(i, m32, r, a.keys), B));
+      bkt[i] = static_cast<uint16_t>(b);
+      atomicAdd(&s_hist[b], 1u);
+    }
     __syncthreads();
     // 2. bucket starts (s_hist[B] becomes n), scatter of ids; a bucket too
     //    large for shared memory or smaller than a batch selects the general
@@ -205,10 +213,7 @@ __global__ void __launch_bounds__(1024, batched_min_blocks<T, D>()) k_rbm_batche
     }
     __syncthreads();
     const bool general = (MODE == kModePerm) || s_general != 0;
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const uint32_t b = static_cast<uint32_t>(__umul64hi(perm_key(i, m32, r, a.keys), B));
-      tmp[atomicAdd(&s_fill[b], 1u)] = i;
-    }
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) tmp[atomicAdd(&s_fill[bkt[i]], 1u)] = i;
     __syncthreads();
     // 3. sort every bucket; outside the general mode step the batches lying
     //    wholly inside it straight from the sorted ids in shared memory
@@ -285,6 +290,7 @@ cudaError_t launch_batched_k(const BatchedScratch& bs, const StepParams<T>& a, c
   ba.offs = bs.offs;
   ba.tmp = bs.tmp;
   ba.perm = bs.perm;
+  ba.bkt = bs.bkt;
   ba.bucket_target = static_cast<uint32_t>(bs.bucket_target);
   ba.rep_base = bs.rep_base;
   const size_t smem = batched_smem<T, D>();

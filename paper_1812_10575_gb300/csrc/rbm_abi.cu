@@ -154,7 +154,7 @@ void free_scratch(rbm_ctx* c) {
   cudaFree(c->cs.hist); cudaFree(c->cs.slots); cudaFree(c->cs.tmp); cudaFree(c->cs.bar); cudaFree(c->cs.arrive);
   c->cs = CoopScratch{};
   cudaFree(c->bs.order); cudaFree(c->bs.block_begin); cudaFree(c->bs.offs);
-  cudaFree(c->bs.tmp); cudaFree(c->bs.perm);
+  cudaFree(c->bs.tmp); cudaFree(c->bs.perm); cudaFree(c->bs.bkt);
   {
     const int threads = c->bs.threads, target = c->bs.bucket_target;
     c->bs = BatchedScratch{};
@@ -294,6 +294,7 @@ rbm_status alloc_scratch(rbm_ctx* c) {
     RBM_CUDA(cudaMemcpy(bs.offs, offs01, 2 * sizeof(uint64_t), cudaMemcpyHostToDevice));
     RBM_CUDA(cudaMalloc(&bs.tmp, sizeof(uint32_t) * n));
     RBM_CUDA(cudaMalloc(&bs.perm, sizeof(uint32_t) * n));
+    RBM_CUDA(cudaMalloc(&bs.bkt, sizeof(uint16_t) * n));
   }
   if (c->use_coop) {
     CoopScratch& cs = c->cs;
@@ -755,6 +756,7 @@ rbm_status alloc_batched(rbm_ctx* c) {
   RBM_CUDA(cudaMemcpy(bs.offs, offs.data(), sizeof(uint64_t) * offs.size(), cudaMemcpyHostToDevice));
   RBM_CUDA(cudaMalloc(&bs.tmp, sizeof(uint32_t) * rows));
   RBM_CUDA(cudaMalloc(&bs.perm, sizeof(uint32_t) * rows));
+  RBM_CUDA(cudaMalloc(&bs.bkt, sizeof(uint16_t) * rows));
   RBM_CUDA(cudaMalloc(&c->xtmp, c->row_bytes * rows));
   return build_batched_schedule(c);
 }

@@ -66,6 +66,7 @@ struct BatchedScratch {
   uint64_t* offs = nullptr;         // [nrep + 1] first row of each replica
   uint32_t* tmp = nullptr;          // [rows]
   uint32_t* perm = nullptr;         // [rows]
+  uint16_t* bkt = nullptr;          // [rows] bucket of each particle, from the histogram pass
   uint32_t grid = 0;
   int threads = 512;
   int bucket_target = 1024;
