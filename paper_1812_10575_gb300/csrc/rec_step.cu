@@ -11,17 +11,21 @@
 //   record    = the row (x, y, z, id in the pad lane) and 32 key bits (the
 //               bits below the top-level digit);
 //   top level = 2^top_bits buckets by the top key bits, fixed-capacity
-//               regions; each writer reserves one run per bucket it feeds
-//               (one atomic per block and bucket), so records land in runs of
-//               tens of rows;
+//               regions; each writer groups its records by bucket in shared
+//               memory, reserves one run per bucket it feeds (one atomic per
+//               block and bucket) and stores each run with consecutive
+//               threads on consecutive rows, so records land in runs of tens
+//               of rows;
 //   sub level = 2^sub_bits sub-buckets per top bucket by the next key bits,
 //               filled the same way by k_rec_split;
 //   k_rec_scan   - the sorted start of every sub-bucket (the sub-buckets in
 //                  (top, sub) order are the random division in key order);
-//   k_rec_step   - one block per sub-bucket (about 2048 records): sort by the
-//                  remaining key bits (counting sort on 11 bits, then each
-//                  record ranked among the few sharing its digit, full keys
-//                  recomputed only on ties of the 32 carried bits), step
+//   k_rec_step   - one block per sub-bucket (about 2048 records, the rows
+//                  of the sub-bucket a block one wave later takes prefetched
+//                  into L2): sort by the remaining key bits (counting sort on
+//                  11 bits, then each record ranked among the few sharing its
+//                  digit, full keys recomputed only on ties of the carried
+//                  bits), step
 //                  every batch lying wholly inside it, park the
 //                  members of batches crossing its ends, and send every
 //                  moved record to its top-level bucket of step m + 1 (key
