@@ -374,6 +374,22 @@ def _to_dev(g, X, d, dtype):
     return t.to(torch.float32 if dtype == "f32" else torch.float64).to(g.dev).contiguous()
 
 
+def _run_shares(avg, steps):
+    """Each kernel's share of a K-step run, from its per-launch time in the
+    profiled step: the record path's scatter and last step run once per run,
+    its inner step and fix-up K - 1 times, every other kernel once per step."""
+    reps = {}
+    for k in avg:
+        if k == "k_rec_scatter" or k.endswith("_last"):
+            reps[k] = 1
+        elif k in ("k_rec_step", "k_rec_fixup"):
+            reps[k] = max(steps - 1, 0)
+        else:
+            reps[k] = steps
+    tot = sum(avg[k] * reps[k] for k in avg)
+    return {k: avg[k] * reps[k] / tot for k in avg} if tot > 0 else {}
+
+
 def _roofline(peaks, peak_src, kernel, alg_bytes, avg_ms, workload, digest, n=None):
     achieved = alg_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
     return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -569,7 +585,7 @@ def run_headline(args, w, g):
     roof["bytes_note"] = ("2 x 12 B of positions (d = 3 FP32; the stored row is 16 B with its pad lane) + 4 B "
                           "permutation written + 4 B read")
     roof["step_frac"] = n * floor / (total_ms / steps * 1e-3) / 1e9 / peaks["hbm_gbs"]
-    roof["kernel_shares"] = {k: v / sum(avg.values()) for k, v in avg.items()}
+    roof["kernel_shares"] = _run_shares(avg, steps)
     dk = float(np.sum([np.mean(v) for v in direct_kernel.values()])) if direct_kernel else direct_ms
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": g.world, "steps": steps,

@@ -454,41 +454,49 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
   const uint32_t b = blockIdx.x;
   const uint32_t m32 = step_index(a);
   const uint32_t par = m32 & 1u;
+  // the sub-bucket a block starting about one wave later takes is
+  // prefetched into L2; its count is loaded together with this block's
+  const uint32_t bn = b + kPrefetchAhead;
+  const bool pf = threadIdx.x == 0 && bn < g.nbuckets;
+  const uint32_t filled_next = pf ? g.sub_fill[par * g.nbuckets + bn] : 0u;
   const uint32_t filled = g.sub_fill[par * g.nbuckets + b];
   if (threadIdx.x == 0 && filled > g.sub_cap) latch_status(a.status, RBM_ERR_STATE);
   const uint32_t cnt = min(filled, g.sub_cap);
   const uint32_t start = g.sub_start[b];
   const size_t src0 = static_cast<size_t>(b) * g.sub_cap;
-  if (threadIdx.x == 0) {  // the sub-bucket a block starting about one wave later takes, into L2
-    const uint32_t bn = b + kPrefetchAhead;
-    if (bn < g.nbuckets) {
-      const uint32_t cn = min(g.sub_fill[par * g.nbuckets + bn], g.sub_cap);
-      if (cn > 0) {
-        const size_t at = static_cast<size_t>(bn) * g.sub_cap;
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g.sub_rows + at), "r"(cn * 16u) : "memory");
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g.sub_keys + at),
-                     "r"(((cn + 3u) & ~3u) * 4u) : "memory");
-      }
-    }
-  }
-
-  for (uint32_t u = threadIdx.x; u < kFine; u += blockDim.x) s_hist[u] = 0;
   for (uint32_t e = threadIdx.x; e < cnt; e += blockDim.x) {
     const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(srow + e));
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(g.sub_rows + src0 + e) : "memory");
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
+  if (pf) {
+    const uint32_t cn = min(filled_next, g.sub_cap);
+    if (cn > 0) {
+      const size_t at = static_cast<size_t>(bn) * g.sub_cap;
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g.sub_rows + at), "r"(cn * 16u) : "memory");
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g.sub_keys + at),
+                   "r"(((cn + 3u) & ~3u) * 4u) : "memory");
+    }
+  }
+  // the carried key bits of this thread's records, in flight across the
+  // clearing barrier (the slots past cnt, about a third of the kStepPer,
+  // are predicated off)
+  uint32_t fr[kStepPer];  // key bits, then digit | provisional rank << 16
+#pragma unroll
+  for (int k = 0; k < kStepPer; ++k) {
+    const uint32_t e = threadIdx.x + k * kStepThreads;
+    if (e < cnt) fr[k] = g.sub_keys[src0 + e];
+  }
+  for (uint32_t u = threadIdx.x; u < kFine; u += blockDim.x) s_hist[u] = 0;
   __syncthreads();
   // counting sort by the kFineBits bits below the sub digit
   // the fixed-size loops stop at the first slot past cnt (a sub-bucket holds
   // about 2048 of the at most 3072 slots)
-  uint32_t fr[kStepPer];  // digit | provisional rank << 16
 #pragma unroll
   for (int k = 0; k < kStepPer; ++k) {
     const uint32_t e = threadIdx.x + k * kStepThreads;
     if (e >= cnt) break;
-    const uint32_t f = g.sub_keys[src0 + e] << g.sub_bits;
-    const uint32_t d = f >> (32 - kFineBits);
+    const uint32_t d = (fr[k] << g.sub_bits) >> (32 - kFineBits);
     fr[k] = d | (atomicAdd(&s_hist[d], 1u) << 16);
   }
   __syncthreads();
@@ -548,7 +556,17 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
       const uint32_t pp = fr[k] & 0xffffu;
       const uint32_t fe = sfine[pp];
       uint32_t equal = 0;  // records with the same carried bits, itself included
-      for (uint32_t j = lo; j < hi; ++j) {
+      // the digit's first four members read together (predicated), the rest
+      // (a digit of more than four: about one in fifty) one by one
+#pragma unroll
+      for (uint32_t q = 0; q < 4; ++q) {
+        if (lo + q < hi) {
+          const uint32_t fj = sfine[lo + q];
+          rank += (fj < fe) ? 1u : 0u;
+          equal += (fj == fe) ? 1u : 0u;
+        }
+      }
+      for (uint32_t j = lo + 4; j < hi; ++j) {
         const uint32_t fj = sfine[j];
         rank += (fj < fe) ? 1u : 0u;
         equal += (fj == fe) ? 1u : 0u;
