@@ -56,7 +56,7 @@ constexpr int kStepPer = kSubCapMax / kStepThreads;  // records per thread of k_
 constexpr int kSplitThreads = 512;
 constexpr int kSplitPer = 8;            // records per thread of k_rec_scatter
 constexpr uint32_t kChunk = kSplitThreads * kSplitPer;
-constexpr int kSubThreads = 512;        // k_rec_split: 512 threads of 6 records, three blocks per SM
+constexpr int kSubThreads = 384;        // k_rec_split: 384 threads of 6 records, four blocks per SM
 constexpr int kSubPer = 6;
 constexpr uint32_t kSubChunk = kSubThreads * kSubPer;
 constexpr int kFineBits = 11;           // counting-sort digit inside a sub-bucket
@@ -134,20 +134,21 @@ __device__ __forceinline__ void put_top(const StepParams<float>& a, const RecArg
   }
 }
 
-// The buckets [0, len) counted in s_hist (len <= 2048, 512 threads): reserves
-// the run of every non-empty bucket u in the global counter fill[u] (one
-// atomic per bucket; consecutive threads on consecutive counters, so that a
-// warp's atomics fall in one line, and issued before the scan so that their
-// latency overlaps it), turns s_hist into the local starts (exclusive prefix
-// sum) and sets s_base[u] = run start - local start, so that local position
-// j of bucket u lands at s_base[u] + j.  Ends with a barrier.
-__device__ __forceinline__ void reserve_runs_512(uint32_t* s_hist, uint32_t len, uint32_t* s_warp, uint32_t* s_base,
-                                                 uint32_t* fill) {
-  constexpr uint32_t per = 4;  // len <= per * 512
+// The buckets [0, len) counted in s_hist (len <= 2048, kThreads threads):
+// reserves the run of every non-empty bucket u in the global counter fill[u]
+// (one atomic per bucket; consecutive threads on consecutive counters, so
+// that a warp's atomics fall in one line, and issued before the scan so that
+// their latency overlaps it), turns s_hist into the local starts (exclusive
+// prefix sum) and sets s_base[u] = run start - local start, so that local
+// position j of bucket u lands at s_base[u] + j.  Ends with a barrier.
+template <int kThreads>
+__device__ __forceinline__ void reserve_runs(uint32_t* s_hist, uint32_t len, uint32_t* s_warp, uint32_t* s_base,
+                                             uint32_t* fill) {
+  constexpr uint32_t per = (2048u + kThreads - 1) / kThreads;  // len <= per * kThreads
   uint32_t r[per];
 #pragma unroll
   for (uint32_t i = 0; i < per; ++i) {
-    const uint32_t u = threadIdx.x + i * 512u;
+    const uint32_t u = threadIdx.x + i * static_cast<uint32_t>(kThreads);
     const uint32_t c = (u < len) ? s_hist[u] : 0u;
     r[i] = c ? atomicAdd(&fill[u], c) : 0u;
   }
@@ -168,7 +169,7 @@ __device__ __forceinline__ void reserve_runs_512(uint32_t* s_hist, uint32_t len,
   if (lane == 31) s_warp[warp] = incl;
 #pragma unroll
   for (uint32_t i = 0; i < per; ++i) {
-    const uint32_t u = threadIdx.x + i * 512u;
+    const uint32_t u = threadIdx.x + i * static_cast<uint32_t>(kThreads);
     if (u < len) s_base[u] = r[i];
   }
   __syncthreads();
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_rec_scatter(StepParams<flo
     if (e < nrec) v[k] = reinterpret_cast<const float4*>(a.x)[i0 + e];
   }
   __syncthreads();
-  reserve_runs_512(s_hist, g.ntop, s_warp, s_base, g.top_fill + par * g.ntop);
+  reserve_runs<kSplitThreads>(s_hist, g.ntop, s_warp, s_base, g.top_fill + par * g.ntop);
 #pragma unroll
   for (int k = 0; k < kSplitPer; ++k) {
     const uint32_t e = k * kSplitThreads + threadIdx.x;
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_rec_scatter(StepParams<flo
 // then names the arrival index it holds, and the runs are stored by
 // consecutive threads.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSubThreads, 3) k_rec_split(StepParams<float> a, RecArgs g, uint32_t chunks) {
+__global__ void __launch_bounds__(kSubThreads, 4) k_rec_split(StepParams<float> a, RecArgs g, uint32_t chunks) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* s_rows = reinterpret_cast<float4*>(smem_raw);                 // [kSubChunk] arrival order
   uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_rows + kSubChunk);   // [kSubChunk] arrival order
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(kSubThreads, 3) k_rec_split(StepParams<float> 
     }
   }
   __syncthreads();
-  reserve_runs_512(s_hist, g.nsub, s_warp, s_base, g.sub_fill + par * g.nbuckets + t * g.nsub);
+  reserve_runs<kSubThreads>(s_hist, g.nsub, s_warp, s_base, g.sub_fill + par * g.nbuckets + t * g.nsub);
 #pragma unroll
   for (int k = 0; k < kSubPer; ++k) {
     const uint32_t e = k * kSubThreads + threadIdx.x;
@@ -660,7 +661,7 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
     }
   }
   __syncthreads();
-  reserve_runs_512(s_hist, g.ntop, s_warp, s_base, g.top_fill + np * g.ntop);  // local start of each bucket's run
+  reserve_runs<kStepThreads>(s_hist, g.ntop, s_warp, s_base, g.top_fill + np * g.ntop);  // local start of each bucket's run
   // the records in bucket order: sidx[j] the slot at position j, spark[j]
   // (read for the last time in the loop above) its bucket
 #pragma unroll
@@ -851,8 +852,8 @@ cudaError_t prepare_rec_kernels() {
   if (e == cudaSuccess) e = allow_step_smem<RBM_K_REG_ATTRACT, true>(bytes);
   if (e == cudaSuccess) e = allow_step_smem<RBM_K_SMOOTH_TEST, true>(bytes);
   if (e == cudaSuccess) e = allow_step_smem<RBM_K_LINEAR, true>(bytes);
-  // the scatter stages 4096 records (84 KB) besides 16 KB of counters (two blocks per SM), the split 3072
-  // records (66 KB) besides its counters (three blocks per SM)
+  // the scatter stages 4096 records (84 KB) besides 16 KB of counters (two blocks per SM), the split 2304
+  // records (50 KB) besides its counters (four blocks per SM)
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_rec_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(split_smem(1u << kMaxDigitBits)));
