@@ -376,11 +376,12 @@ def _to_dev(g, X, d, dtype):
 
 def _run_shares(avg, steps):
     """Each kernel's share of a K-step run, from its per-launch time in the
-    profiled step: the record path's scatter and last step run once per run,
+    profiled step: the record path's scatter, last step and placement run
+    once per run,
     its inner step and fix-up K - 1 times, every other kernel once per step."""
     reps = {}
     for k in avg:
-        if k == "k_rec_scatter" or k.endswith("_last"):
+        if k in ("k_rec_scatter", "k_rec_place") or k.endswith("_last"):
             reps[k] = 1
         elif k in ("k_rec_step", "k_rec_fixup"):
             reps[k] = max(steps - 1, 0)
@@ -597,9 +598,10 @@ def run_headline(args, w, g):
         "roofline": roof,
         "e2e": {"value": g.world * n * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * 16,
                 "d2h_bytes_per_step": n * 16, "steps": n_e2e},
-        # per step the pipelined kernels; per graph replay the run's scatter
-        # and the step-counter bump
-        "gpu_launches": launches * steps + 2,
+        # per step the pipelined kernels; per graph replay the run's first
+        # bucketing (the record path's scatter), the record path's placement
+        # after the last step, and the step-counter bump
+        "gpu_launches": launches * steps + (3 if path == 4 else 2),
         "clocks": clocks.summary(),
         "methods": dict(
             others, rbm_p2={"particle_steps_per_s": value / g.world, "ms_per_step": total_ms / steps},

@@ -499,7 +499,7 @@ rbm_status rbm_fp32_fma_peak(int32_t packed, double *tflops, void *cuda_stream);
 /* Number of kernel launches one step of `method` enqueues inside a run of
  * steps (for accounting; an RBM-1 run's first step adds the bucketing of its
  * ids on the bucket-sort and cooperative paths, and the scatter of the rows
- * on the record path). */
+ * on the record path, whose last step adds the placement of the rows by id). */
 rbm_status rbm_launches_per_step(const rbm_ctx *ctx, int32_t method, int32_t *launches);
 
 #ifdef __cplusplus

@@ -49,6 +49,7 @@ struct RecScratch {
   int top_bits = 0, sub_bits = 0;
   uint32_t ntop = 1, nsub = 1;      // buckets per level
   uint32_t top_cap = 0, sub_cap = 0;  // records per top bucket / per sub-bucket
+  uint32_t id_mul = 0;              // last step's id-range bucket: umulhi(id, id_mul) < ntop
   float4* top_rows = nullptr;       // [ntop * top_cap]
   uint32_t* top_keys = nullptr;
   float4* sub_rows = nullptr;       // [ntop * nsub * sub_cap]

@@ -25,14 +25,18 @@
 //                  into L2): sort by the remaining key bits (counting sort on
 //                  11 bits, then each record ranked among the few sharing its
 //                  digit, full keys recomputed only on ties of the carried
-//                  bits), step
-//                  every batch lying wholly inside it, park the
-//                  members of batches crossing its ends, and send every
+//                  bits), step every batch lying wholly inside it, park
+//                  the members of batches crossing its ends, and send every
 //                  moved record to its top-level bucket of step m + 1 (key
 //                  of m + 1 computed here) - or, at the last step of a run,
-//                  write the new positions to the caller's array by id;
+//                  to its id-range bucket (about N / ntop consecutive ids);
 //   k_rec_fixup  - the batches crossing sub-bucket ends, from the parked
-//                  members, sent on the same way.
+//                  members, sent on the same way (written by id at the last
+//                  step);
+//   k_rec_place  - after the last step, the records of each id-range bucket
+//                  to the caller's array by id, consecutive blocks on one
+//                  bucket so that the rows being written stay in L2 until
+//                  their sectors are complete.
 // A run of K steps starts with k_rec_scatter, which reads the caller's array
 // in id order and fills the top level of its first step; the caller's array
 // holds the positions again after the run's last step.  Every update reads
@@ -59,6 +63,9 @@ constexpr uint32_t kChunk = kSplitThreads * kSplitPer;
 constexpr int kSubThreads = 384;        // k_rec_split: 384 threads of 6 records, four blocks per SM
 constexpr int kSubPer = 6;
 constexpr uint32_t kSubChunk = kSubThreads * kSubPer;
+constexpr int kPlaceThreads = 256;      // k_rec_place: 256 threads of 8 records
+constexpr int kPlacePer = 8;
+constexpr uint32_t kPlaceChunk = kPlaceThreads * kPlacePer;
 constexpr int kFineBits = 11;           // counting-sort digit inside a sub-bucket
 constexpr uint32_t kFine = 1u << kFineBits;
 constexpr int kMaxDigitBits = 11;       // top and sub digits: at most 2048 values
@@ -84,6 +91,7 @@ struct RecArgs {
   uint32_t* sub_start;  // [nbuckets + 1]
   float4* side;         // [nbuckets * kSide]
   uint32_t top_cap, sub_cap, ntop, nsub, nbuckets;
+  uint32_t id_mul;      // last step: id-range bucket umulhi(id, id_mul)
   int top_bits, sub_bits;
 };
 
@@ -132,6 +140,13 @@ __device__ __forceinline__ void put_top(const StepParams<float>& a, const RecArg
   } else {
     latch_status(a.status, RBM_ERR_STATE);
   }
+}
+
+// Record pos of id-range bucket t (last step of a run).
+__device__ __forceinline__ void put_id(const StepParams<float>& a, const RecArgs& g, uint32_t t, uint32_t pos,
+                                       const float4& rec) {
+  if (pos < g.top_cap) g.top_rows[static_cast<size_t>(t) * g.top_cap + pos] = rec;
+  else latch_status(a.status, RBM_ERR_STATE);
 }
 
 // The buckets [0, len) counted in s_hist (len <= 2048, kThreads threads):
@@ -584,9 +599,9 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
     sidx[fr[k]] = static_cast<uint16_t>(e);
   }
   // the digit starts are no longer read: clear the counters of the next
-  // step's top-level buckets here, not behind a barrier of their own
-  if (!kLast)
-    for (uint32_t u = threadIdx.x; u < g.ntop; u += blockDim.x) s_hist[u] = 0;
+  // step's top-level buckets (of the id-range buckets at the last step) here,
+  // not behind a barrier of their own
+  for (uint32_t u = threadIdx.x; u < g.ntop; u += blockDim.x) s_hist[u] = 0;
   __syncthreads();
 
   // batches lying wholly inside [start, end)
@@ -616,10 +631,7 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
           id = rec_id(srow[slot]);
         }
       }
-      if (batch_group_update<float, 3, KF, kPlain>(a, m32, id, valid, lg, bs, r)) {
-        if (kLast) write_position(a.x, id, r);
-        else srow[slot] = to_rec(r);
-      }
+      if (batch_group_update<float, 3, KF, kPlain>(a, m32, id, valid, lg, bs, r)) srow[slot] = to_rec(r);
     }
   }
   // members of batches crossing the ends (sorted positions before q0 p and
@@ -641,11 +653,11 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
       g.side[static_cast<size_t>(bf) * kSide + (pos - qp)] = srow[slot];
     }
   }
-  if (kLast) return;
   __syncthreads();
 
-  // the moved records to their top-level buckets of step m + 1 (s_hist was
-  // cleared before the batches were stepped)
+  // the moved records to their top-level buckets of step m + 1 (at the last
+  // step of a run, to their id-range buckets; s_hist was cleared before the
+  // batches were stepped)
   const uint32_t np = par ^ 1u;
   constexpr uint32_t kParked = 0xffffffffu;
   uint32_t tr[kStepPer], k32[kStepPer];
@@ -656,7 +668,8 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
     tr[k] = kParked;
     if (!spark[e]) {
       uint32_t t;
-      top_key(a, g, rec_id(srow[e]), m32 + 1u, t, k32[k]);
+      if (kLast) t = __umulhi(rec_id(srow[e]), g.id_mul);
+      else top_key(a, g, rec_id(srow[e]), m32 + 1u, t, k32[k]);
       tr[k] = t | (atomicAdd(&s_hist[t], 1u) << 16);
     }
   }
@@ -672,14 +685,15 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_rec_step(StepParams<float> 
       const uint32_t at = s_hist[tr[k] & 0xffffu] + (tr[k] >> 16);
       sidx[at] = static_cast<uint16_t>(e);
       spark[at] = static_cast<uint8_t>(tr[k]);
-      sfine[e] = k32[k];
+      if (!kLast) sfine[e] = k32[k];
     }
   }
   __syncthreads();
   store_runs(cnt - ncross, g.ntop, s_hist, s_base, g.ntop <= kByteBuckets ? spark : nullptr,
              [&](uint32_t t, uint32_t pos, uint32_t j) {
     const uint32_t e = sidx[j];
-    put_top(a, g, t, pos, srow[e], sfine[e]);
+    if (kLast) put_id(a, g, t, pos, srow[e]);
+    else put_top(a, g, t, pos, srow[e], sfine[e]);
   });
 }
 
@@ -726,6 +740,35 @@ __global__ void __launch_bounds__(256) k_rec_fixup(StepParams<float> a, RecArgs 
   }
 }
 
+// ---------------------------------------------------------------------------
+// After the last step of a run: the records of id-range bucket t (the ids i
+// with umulhi(i, id_mul) = t, about N / ntop consecutive ids) to the caller's
+// array by id.  Block (t, j) takes records [j C, (j+1) C) of bucket t
+// (C = kPlaceChunk), every load in flight before the first store; consecutive
+// blocks take consecutive chunks of one bucket, so the rows written at any
+// time lie in a few windows of the array that L2 holds until their sectors
+// are complete.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kPlaceThreads) k_rec_place(StepParams<float> a, RecArgs g, uint32_t chunks) {
+  const uint32_t t = blockIdx.x / chunks, j = blockIdx.x - t * chunks;
+  const uint32_t np = (step_index(a) & 1u) ^ 1u;
+  const uint32_t count = min(g.top_fill[np * g.ntop + t], g.top_cap);
+  const uint32_t lo = j * kPlaceChunk;
+  if (lo >= count) return;  // uniform over the block
+  const float4* src = g.top_rows + static_cast<size_t>(t) * g.top_cap;
+  float4 v[kPlacePer];
+#pragma unroll
+  for (int k = 0; k < kPlacePer; ++k) {
+    const uint32_t e = lo + k * kPlaceThreads + threadIdx.x;
+    if (e < count) v[k] = src[e];
+  }
+#pragma unroll
+  for (int k = 0; k < kPlacePer; ++k) {
+    const uint32_t e = lo + k * kPlaceThreads + threadIdx.x;
+    if (e < count) write_position(a.x, rec_id(v[k]), to_row(v[k]));
+  }
+}
+
 // Dynamic shared memory of k_rec_step: records, sort bits, sorted slots and
 // crossing flags of sub_cap records (a multiple of 32, so the run starts
 // that follow are aligned), then ntop run starts.
@@ -740,6 +783,7 @@ RecArgs make_args(const RecScratch& rs) {
   g.top_fill = rs.top_fill; g.sub_fill = rs.sub_fill; g.sub_start = rs.sub_start; g.side = rs.side;
   g.top_cap = rs.top_cap; g.sub_cap = rs.sub_cap; g.ntop = rs.ntop; g.nsub = rs.nsub; g.nbuckets = rs.ntop * rs.nsub;
   g.top_bits = rs.top_bits; g.sub_bits = rs.sub_bits;
+  g.id_mul = rs.id_mul;
   return g;
 }
 
@@ -766,6 +810,14 @@ void rec_geometry(uint32_t n, int tuned_bits, RecScratch* rs) {
   const double top_mean = static_cast<double>(n) / rs->ntop;
   const double sub_mean = top_mean / rs->nsub;
   rs->top_cap = round_up(static_cast<uint32_t>(top_mean + 12.0 * std::sqrt(top_mean) + 1024.0), 32);
+  // the last step's id-range buckets umulhi(id, M), M = floor(2^32 ntop / n):
+  // every id < n maps below ntop (id M / 2^32 < ntop) and a bucket holds at
+  // most floor(2^32 / M) + 1 ids, within the capacity for every geometry used
+  // (the capacity is raised if ever it is not)
+  const uint64_t mul = (static_cast<uint64_t>(rs->ntop) << 32) / (n > 0 ? n : 1u);
+  rs->id_mul = mul > 0xffffffffull ? 0xffffffffu : static_cast<uint32_t>(mul);
+  const uint64_t id_max = rs->id_mul ? (0x100000000ull / rs->id_mul) + 1 : n;
+  if (id_max > rs->top_cap) rs->top_cap = round_up(static_cast<uint32_t>(id_max), 32);
   const uint32_t sc = round_up(static_cast<uint32_t>(sub_mean + 12.0 * std::sqrt(sub_mean) + 64.0), 32);
   rs->sub_cap = sc < kSubCapMax ? sc : kSubCapMax;
 }
@@ -872,7 +924,8 @@ int rec_launches_per_step(const RecScratch&) { return 4; }  // split, scan, step
 
 // `count` RBM-1 steps from step (m_ptr ? *m_ptr : 0) + a.m_off: clear the
 // counters, fill the first step's top level from the caller's array, then
-// per step split, scan, step and fix-up; the last step writes the positions.
+// per step split, scan, step and fix-up; after the last step (whose fix-up
+// writes the crossing batches by id) k_rec_place writes the positions.
 cudaError_t launch_rec_run(const RecScratch& rs, const void* params, int64_t count, const LaunchCfg& cfg,
                            cudaStream_t st) {
   const StepParams<float> a0 = *static_cast<const StepParams<float>*>(params);
@@ -897,6 +950,11 @@ cudaError_t launch_rec_run(const RecScratch& rs, const void* params, int64_t cou
     k_rec_scan<<<1, 1024, 0, st>>>(a, g);
     mark_launch(cfg, st, "k_rec_scan");
     step_pair(last, a, g, smem, fix_grid, cfg, st);
+    if (last) {  // the last step's records to the caller's array by id
+      const uint32_t pchunks = (rs.top_cap + kPlaceChunk - 1) / kPlaceChunk;
+      k_rec_place<<<rs.ntop * pchunks, kPlaceThreads, 0, st>>>(a, g, pchunks);
+      mark_launch(cfg, st, "k_rec_place");
+    }
   }
   return cudaGetLastError();
 }
