@@ -62,6 +62,8 @@ struct rbm_ctx {
   bool use_small = false;       // N <= 2048: the whole step in one block (the replica kernel)
   bool use_rec = false;         // RBM steps by the record path (rec_step.cu)
   RecScratch rec;
+  cudaStream_t copy_stream = nullptr;  // record path, host buffers: the chunked copies
+  cudaEvent_t host_ev[2 * kHostChunks + 2] = {};
   int coop_blocks_per_sm = 0;
   LaunchCfg cfg;
   rbm_tuning tuning{};
@@ -1158,6 +1160,22 @@ rbm_status rbm_step_host(rbm_ctx* ctx, void* x_host, int32_t method) {
   // 1.57e9 against 1.50e9 particle-steps/s); larger or pageable buffers take
   // cudaMemcpyAsync (at 400 MB the copy engine was 2 % faster).
   void* mapped = (bytes <= (size_t(16) << 20)) ? mapped_device_pointer(x_host) : nullptr;
+  if (!mapped && method == RBM_METHOD_RBM && ctx->use_rec) {
+    // the record path copies in and scatters, and places and copies out, in
+    // chunks on two streams (the kernels of one chunk under the next one's copy)
+    if (!ctx->copy_stream) RBM_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t& ev : ctx->host_ev)
+      if (!ev) RBM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    StepParams<float> a = step_params<float>(ctx, nullptr, ctx->m);
+    const cudaError_t e = launch_rec_host_step(ctx->rec, &a, x_host, ctx->cfg, ctx->stream, ctx->copy_stream,
+                                               ctx->host_ev);
+    if (e != cudaSuccess) {
+      set_error("record-path host step", e);
+      return RBM_ERR_CUDA;
+    }
+    ctx->m += 1;
+    return rbm_sync(ctx);
+  }
   if (mapped) RBM_CUDA(copy_by_kernel(ctx->x, mapped, bytes, ctx->cfg, ctx->stream));
   else RBM_CUDA(cudaMemcpyAsync(ctx->x, x_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
   st = enqueue_step(ctx, method, nullptr, ctx->m, ctx->stream);
@@ -1250,6 +1268,9 @@ rbm_status rbm_free(rbm_ctx* ctx) {
   drop_graphs(ctx);
   free_surrogate(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  for (cudaEvent_t ev : ctx->host_ev)
+    if (ev) cudaEventDestroy(ev);
   free_scratch(ctx);
   cudaFree(ctx->xprev);
   free_status(ctx);

@@ -160,6 +160,14 @@ cudaError_t launch_rec_run(const RecScratch& rs, const void* params, int64_t cou
                            cudaStream_t st);
 // Kernel launches of one step of a run (after its first step's scatter).
 int rec_launches_per_step(const RecScratch& rs);
+// One record-path step of positions held in host memory (x_host, N rows of
+// 16 bytes; a.x the device copy): the rows are copied in and scattered, and
+// placed and copied out, in kHostChunks chunks, the copies on copy_st and
+// the kernels on st, each chunk's kernels overlapping the next chunk's copy.
+// ev: 2 kHostChunks + 2 events.  On return st is ordered after the copies out.
+constexpr int kHostChunks = 8;
+cudaError_t launch_rec_host_step(const RecScratch& rs, const void* params, void* x_host, const LaunchCfg& cfg,
+                                 cudaStream_t st, cudaStream_t copy_st, cudaEvent_t* ev);
 
 // Cooperative step (coop_step.cu): mode as for launch_rbm_tail.
 cudaError_t prepare_coop_kernels(int* blocks_per_sm);

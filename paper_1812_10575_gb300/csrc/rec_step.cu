@@ -44,6 +44,7 @@
 // requires.  Capacities are the mean count plus twelve standard deviations
 // of the binomial count (and a constant); a count beyond one (never seen for
 // Philox keys) latches RBM_ERR_STATE and nothing is written past the region.
+#include <algorithm>
 #include <cmath>
 
 #include "rbm_batch.cuh"
@@ -233,9 +234,10 @@ __device__ __forceinline__ void store_runs(uint32_t nrec, uint32_t nbkt, const u
 
 
 // ---------------------------------------------------------------------------
-// First step of a run: the caller's rows in id order into the top level.
+// First step of a run: the caller's rows in id order into the top level
+// (block b takes rows [(block0 + b) C, ...), C = kChunk).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSplitThreads, 2) k_rec_scatter(StepParams<float> a, RecArgs g) {
+__global__ void __launch_bounds__(kSplitThreads, 2) k_rec_scatter(StepParams<float> a, RecArgs g, uint32_t block0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* s_rows = reinterpret_cast<float4*>(smem_raw);              // [kChunk] records by bucket
   uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_rows + kChunk);   // [kChunk]
@@ -245,7 +247,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_rec_scatter(StepParams<flo
   __shared__ uint32_t s_warp[32];
   const uint32_t m32 = step_index(a);
   const uint32_t par = m32 & 1u;
-  const uint32_t i0 = blockIdx.x * kChunk;
+  const uint32_t i0 = (block0 + blockIdx.x) * kChunk;
   const uint32_t nrec = min(kChunk, a.n - i0);
   if (threadIdx.x == 0) {  // the chunk's rows into L2 while the keys are drawn
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.x + static_cast<size_t>(i0) * 4),
@@ -743,14 +745,17 @@ __global__ void __launch_bounds__(256) k_rec_fixup(StepParams<float> a, RecArgs 
 // ---------------------------------------------------------------------------
 // After the last step of a run: the records of id-range bucket t (the ids i
 // with umulhi(i, id_mul) = t, about N / ntop consecutive ids) to the caller's
-// array by id.  Block (t, j) takes records [j C, (j+1) C) of bucket t
+// array by id, for the buckets t0, t0 + 1, ...  Block (t - t0, j) takes
+// records [j C, (j+1) C) of bucket t
 // (C = kPlaceChunk), every load in flight before the first store; consecutive
 // blocks take consecutive chunks of one bucket, so the rows written at any
 // time lie in a few windows of the array that L2 holds until their sectors
 // are complete.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kPlaceThreads) k_rec_place(StepParams<float> a, RecArgs g, uint32_t chunks) {
-  const uint32_t t = blockIdx.x / chunks, j = blockIdx.x - t * chunks;
+__global__ void __launch_bounds__(kPlaceThreads) k_rec_place(StepParams<float> a, RecArgs g, uint32_t chunks,
+                                                              uint32_t t0) {
+  const uint32_t tb = blockIdx.x / chunks, j = blockIdx.x - tb * chunks;
+  const uint32_t t = t0 + tb;
   const uint32_t np = (step_index(a) & 1u) ^ 1u;
   const uint32_t count = min(g.top_fill[np * g.ntop + t], g.top_cap);
   const uint32_t lo = j * kPlaceChunk;
@@ -926,15 +931,26 @@ int rec_launches_per_step(const RecScratch&) { return 4; }  // split, scan, step
 // counters, fill the first step's top level from the caller's array, then
 // per step split, scan, step and fix-up; after the last step (whose fix-up
 // writes the crossing batches by id) k_rec_place writes the positions.
-cudaError_t launch_rec_run(const RecScratch& rs, const void* params, int64_t count, const LaunchCfg& cfg,
-                           cudaStream_t st) {
-  const StepParams<float> a0 = *static_cast<const StepParams<float>*>(params);
-  const RecArgs g = make_args(rs);
-  cudaError_t e = cudaMemsetAsync(rs.top_fill, 0, 2 * rs.ntop * sizeof(uint32_t), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(rs.sub_fill, 0, 2 * size_t(g.nbuckets) * sizeof(uint32_t), st);
-  if (e != cudaSuccess) return e;
-  k_rec_scatter<<<(a0.n + kChunk - 1) / kChunk, kSplitThreads, kStageBytes, st>>>(a0, g);
-  mark_launch(cfg, st, "k_rec_scatter");
+namespace {
+
+// The first id of id-range bucket t (the smallest i with umulhi(i, mul) >= t),
+// at most n.
+uint32_t first_id_of(uint32_t t, uint32_t mul, uint32_t n) {
+  const uint64_t v = ((static_cast<uint64_t>(t) << 32) + mul - 1) / mul;
+  return v < n ? static_cast<uint32_t>(v) : n;
+}
+
+void launch_place(const RecScratch& rs, const RecArgs& g, const StepParams<float>& a, uint32_t t0, uint32_t t1,
+                  const LaunchCfg& cfg, cudaStream_t st) {
+  const uint32_t pchunks = (rs.top_cap + kPlaceChunk - 1) / kPlaceChunk;
+  k_rec_place<<<(t1 - t0) * pchunks, kPlaceThreads, 0, st>>>(a, g, pchunks, t0);
+  mark_launch(cfg, st, "k_rec_place");
+}
+
+// Steps m_off .. m_off + count - 1 of a run whose first top level is filled
+// (the last one sends its records to the id-range buckets).
+cudaError_t launch_rec_steps(const RecScratch& rs, const RecArgs& g, const StepParams<float>& a0, int64_t count,
+                             const LaunchCfg& cfg, cudaStream_t st) {
   const uint32_t chunks = (rs.top_cap + kSubChunk - 1) / kSubChunk;
   const size_t smem = step_smem(rs.sub_cap, rs.ntop);
   const int gpw = 32 / a0.p;
@@ -950,13 +966,80 @@ cudaError_t launch_rec_run(const RecScratch& rs, const void* params, int64_t cou
     k_rec_scan<<<1, 1024, 0, st>>>(a, g);
     mark_launch(cfg, st, "k_rec_scan");
     step_pair(last, a, g, smem, fix_grid, cfg, st);
-    if (last) {  // the last step's records to the caller's array by id
-      const uint32_t pchunks = (rs.top_cap + kPlaceChunk - 1) / kPlaceChunk;
-      k_rec_place<<<rs.ntop * pchunks, kPlaceThreads, 0, st>>>(a, g, pchunks);
-      mark_launch(cfg, st, "k_rec_place");
-    }
   }
   return cudaGetLastError();
+}
+
+cudaError_t clear_fill(const RecScratch& rs, const RecArgs& g, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(rs.top_fill, 0, 2 * rs.ntop * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(rs.sub_fill, 0, 2 * size_t(g.nbuckets) * sizeof(uint32_t), st);
+  return e;
+}
+
+}  // namespace
+
+cudaError_t launch_rec_run(const RecScratch& rs, const void* params, int64_t count, const LaunchCfg& cfg,
+                           cudaStream_t st) {
+  const StepParams<float> a0 = *static_cast<const StepParams<float>*>(params);
+  const RecArgs g = make_args(rs);
+  cudaError_t e = clear_fill(rs, g, st);
+  if (e != cudaSuccess) return e;
+  k_rec_scatter<<<(a0.n + kChunk - 1) / kChunk, kSplitThreads, kStageBytes, st>>>(a0, g, 0u);
+  mark_launch(cfg, st, "k_rec_scatter");
+  e = launch_rec_steps(rs, g, a0, count, cfg, st);
+  if (e == cudaSuccess && count > 0) {  // the last step's records to the caller's array by id
+    StepParams<float> a = a0;
+    a.m_off = a0.m_off + count - 1;
+    launch_place(rs, g, a, 0u, rs.ntop, cfg, st);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+cudaError_t launch_rec_host_step(const RecScratch& rs, const void* params, void* x_host, const LaunchCfg& cfg,
+                                 cudaStream_t st, cudaStream_t copy_st, cudaEvent_t* ev) {
+  const StepParams<float> a = *static_cast<const StepParams<float>*>(params);
+  const RecArgs g = make_args(rs);
+  constexpr size_t kRow = 4 * sizeof(float);
+  char* host = static_cast<char*>(x_host);
+  char* dev = reinterpret_cast<char*>(a.x);
+  cudaError_t e = cudaEventRecord(ev[0], st);  // the copies wait for the work before the call
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(copy_st, ev[0], 0);
+  if (e == cudaSuccess) e = clear_fill(rs, g, st);
+  // in: chunk j of the rows copied on copy_st, then scattered on st
+  const uint32_t nblk = (a.n + kChunk - 1) / kChunk;
+  for (int j = 0; j < kHostChunks && e == cudaSuccess; ++j) {
+    const uint32_t b0 = static_cast<uint32_t>(uint64_t(nblk) * j / kHostChunks);
+    const uint32_t b1 = static_cast<uint32_t>(uint64_t(nblk) * (j + 1) / kHostChunks);
+    if (b1 == b0) continue;
+    const size_t r0 = size_t(b0) * kChunk, r1 = std::min(size_t(b1) * kChunk, size_t(a.n));
+    e = cudaMemcpyAsync(dev + r0 * kRow, host + r0 * kRow, (r1 - r0) * kRow, cudaMemcpyHostToDevice, copy_st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1 + j], copy_st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[1 + j], 0);
+    if (e == cudaSuccess) {
+      k_rec_scatter<<<b1 - b0, kSplitThreads, kStageBytes, st>>>(a, g, b0);
+      mark_launch(cfg, st, "k_rec_scatter");
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) e = launch_rec_steps(rs, g, a, 1, cfg, st);
+  // out: the rows of id-range buckets [t0, t1) placed on st, then copied on copy_st
+  for (int j = 0; j < kHostChunks && e == cudaSuccess; ++j) {
+    const uint32_t t0 = static_cast<uint32_t>(uint64_t(rs.ntop) * j / kHostChunks);
+    const uint32_t t1 = static_cast<uint32_t>(uint64_t(rs.ntop) * (j + 1) / kHostChunks);
+    if (t1 == t0) continue;
+    launch_place(rs, g, a, t0, t1, cfg, st);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1 + kHostChunks + j], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(copy_st, ev[1 + kHostChunks + j], 0);
+    const size_t i0 = first_id_of(t0, rs.id_mul, a.n);
+    const size_t i1 = (t1 == rs.ntop) ? a.n : first_id_of(t1, rs.id_mul, a.n);
+    if (e == cudaSuccess && i1 > i0)
+      e = cudaMemcpyAsync(host + i0 * kRow, dev + i0 * kRow, (i1 - i0) * kRow, cudaMemcpyDeviceToHost, copy_st);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1 + 2 * kHostChunks], copy_st);  // st waits for the copies out
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[1 + 2 * kHostChunks], 0);
+  return e;
 }
 
 }  // namespace rbm

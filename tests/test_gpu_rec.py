@@ -17,6 +17,10 @@ written back by id after the call's last step.
 - every kernel family's step instance (the family fixed at compile time on
   the plain Euler-Maruyama configuration) equals the per-id path bit for bit;
 - the pad lane of every row is left as the caller wrote it;
+- a step of positions in host memory (rbm_step_host) beyond 16 MB, where the
+  rows are copied in and scattered, and placed and copied out, in chunks on
+  two streams, equals the same step on device-resident positions bit for bit
+  (pinned and pageable host buffers, pad lanes kept), over several calls;
 - the full-size large-N system (N = 2^26, the benchmarked launch
   configuration): one step of every particle within the FP32 bar of the
   oracle.
@@ -154,6 +158,34 @@ def test_record_path_against_oracle_one_step_and_run():
     s.sync()
     assert_close_per_particle(from_dev(x, 3), cur, 0.0, extra=2.0 * bound, what="5-step run")
     assert torch.equal(x[:, 3], pad)
+
+
+@pytest.mark.parametrize("n,bits", [(1048579, 0), (1100007, 13)])
+def test_record_path_host_step_equals_device_step(n, bits):
+    torch = torch_cuda()
+    X = as_run_precision(workloads.gaussian(n, 3, seed=6), "f32")
+    x = _x(X, torch, pad_seed=5)
+    ref = x.clone()
+    s = rbm.System(x, d=3, p=3, seed=4, **KW)
+    t = rbm.System(ref, d=3, p=3, seed=4, **KW)
+    for sysm in (s, t):
+        sysm.set_tuning(path=4, bucket_bits=bits)
+        assert sysm.tuning()["path"] == 4
+    host = x.cpu().pin_memory()
+    assert host.numel() * 4 > (16 << 20)     # beyond the mapped-copy size: the chunked copies
+    for _ in range(2):
+        s.step_host(host)
+        t.step()
+        t.sync()
+        assert np.array_equal(host.numpy().view(np.uint32), ref.cpu().numpy().view(np.uint32))
+    pageable = host.clone()
+    s.step_host(pageable)
+    t.step()
+    t.sync()
+    assert np.array_equal(pageable.numpy().view(np.uint32), ref.cpu().numpy().view(np.uint32))
+    assert s.m == 3 and t.m == 3
+    s.close()
+    t.close()
 
 
 def test_record_path_full_size_large_n():
