@@ -308,6 +308,28 @@ def _traffic_for(workload: str, kernel_name: str, digest: str, n=None):
     return b
 
 
+def _issue_rate(workload: str, kernel_name: str, avg_ms: float, n, sm_mhz: float, num_sms: int = 152):
+    """The kernel's instruction issue against the SMs' issue rate (four warp
+    schedulers per SM, one warp instruction per scheduler and clock), from the
+    warp instructions of the committed ncu capture (scaled by N like the
+    traffic) and the launch's measured time; None without a capture taken on
+    the current sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path) or avg_ms <= 0:
+        return None
+    with open(path) as f:
+        ent = json.load(f).get(workload, {}).get(kernel_name)
+    if not ent or ent.get("sources") != _kernel_sources_digest(kernel_name) or not ent.get("warp_inst_per_launch"):
+        return None
+    inst = ent["warp_inst_per_launch"] * (n / ent["n"] if n is not None and ent.get("n") else 1.0)
+    achieved = inst / (avg_ms * 1e-3)
+    peak = 4.0 * num_sms * sm_mhz * 1e6
+    return {"warp_instructions_per_launch": inst, "achieved": achieved, "peak": peak,
+            "unit": "warp instructions/s", "frac": achieved / peak,
+            "peak_source": f"{num_sms} SMs x 4 schedulers x 1 warp instruction per clock x {sm_mhz:.0f} MHz "
+                           "(median SM clock under load)"}
+
+
 def max_over_ranks(dist, v, device):
     """The largest of every rank's v (the job's time is its slowest rank's)."""
     import torch
@@ -587,6 +609,11 @@ def run_headline(args, w, g):
                           "permutation written + 4 B read")
     roof["step_frac"] = n * floor / (total_ms / steps * 1e-3) / 1e9 / peaks["hbm_gbs"]
     roof["kernel_shares"] = _run_shares(avg, steps)
+    clk = clocks.summary()
+    sms = g.torch.cuda.get_device_properties(g.torch.cuda.current_device()).multi_processor_count
+    issue = _issue_rate(w["workload"], dom, avg[dom], n, clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0, sms)
+    if issue is not None:
+        roof["issue"] = issue
     dk = float(np.sum([np.mean(v) for v in direct_kernel.values()])) if direct_kernel else direct_ms
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": g.world, "steps": steps,
