@@ -16,7 +16,7 @@
 //      are needed, never stored; each particle's bucket is kept as 16 bits
 //      in id order for the scatter);
 //   2. scan, scatter of ids to bucket order;
-//   3. per bucket: counting sort in shared memory by the next 11 key bits and
+//   3. per bucket: counting sort in shared memory by the next 10 key bits and
 //      insertion sort of equal sub-buckets by (key, id); the sorted ids form
 //      the replica's stretch of the permutation, and the batches lying wholly
 //      inside the bucket are stepped at once from the sorted ids (groups of p
@@ -34,7 +34,9 @@
 namespace rbm {
 namespace {
 
-constexpr uint32_t kBSubBits = 11;
+constexpr uint32_t kBSubBits = 10;    // sub-buckets of about one member for buckets of about 1024
+                                       // (the clearing, scan and visit of every sub-bucket cost more than
+                                       // the insertion sort saves with 2^11)
 constexpr uint32_t kBSub = 1u << kBSubBits;
 constexpr uint32_t kBCap = 2048;       // largest bucket sorted in shared memory
 constexpr uint32_t kBMaxBuckets = 512;  // per replica
