@@ -195,7 +195,13 @@ rbm_status rbm_run(rbm_ctx *ctx, int64_t steps, int32_t method);
 
 /* End to end from host memory: copy N x ld positions from x_host (pinned for
  * speed, pageable accepted) to the context's device positions, take one step
- * of `method`, copy them back to x_host and wait.  Returns latched errors. */
+ * of `method`, copy them back to x_host and wait.  Returns latched errors.
+ * Up to 16 MB of pinned positions are moved by a copy kernel through the
+ * mapped host address.  On the record path (path 4) larger buffers are moved
+ * in eight chunks on a second stream the context creates on first use: each
+ * chunk of rows is scattered as soon as it lands, and after the step each
+ * contiguous range of ids is copied back as soon as its rows are placed.
+ * The device positions hold the new step too on return. */
 rbm_status rbm_step_host(rbm_ctx *ctx, void *x_host, int32_t method);
 
 rbm_status rbm_get_step(const rbm_ctx *ctx, int64_t *m);
